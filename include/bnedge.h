@@ -1,0 +1,193 @@
+/*
+ * bnedge.h -- C ABI of the GB300 library for exact Bayesian-network edge
+ * posteriors (Chen, Tian, Nikolova, Aluru, arXiv 1408.1664; built on
+ * Koivisto's forward-backward dynamic program).
+ *
+ * Given m samples of n discrete variables, an in-degree bound d and the
+ * order-modular prior of Eq. 4 (q_i = 1, rho_i(G) = exp(log_rho[|G|])), the
+ * library returns P(u->v | D) for all n(n-1) ordered pairs (Eq. 11 divided by
+ * P(D) = F(V), Algorithm 1) together with log P(D).  Every step runs in CUDA
+ * kernels for sm_103a:
+ *   1. BDeu local scores log B_i(G), |G| <= d, from bit-exact contingency
+ *      counts (Eq. 6; Algorithm 1, step 1);
+ *   2. A_i(S), the truncated upward zeta transform of B_i (Eq. 7,
+ *      Definition 1, Algorithm 2);
+ *   3. the forward sum F(S) (Eq. 9) and the backward sum R(S) (Eq. 10) over
+ *      the subset lattice, level by level in popcount (Section 3.1.1);
+ *   4. Gamma_v(G), the truncated downward zeta transform of
+ *      F(S) R(V-{v}-S) (Eq. 12, Definition 2, Algorithm 3);
+ *   5. the edge reduction of Eq. 11 and the division by P(D).
+ *
+ * Conventions used by every entry point:
+ *   - variable i (0-based) is bit i of a subset mask (the paper's variable
+ *     i+1 is bit i, Section 3.1.1);
+ *   - data is m x n row-major uint8 with data[s*n + i] < arity[i];
+ *   - the families of node i are the parent sets G of V-{i} with |G| <= d,
+ *     ordered by |G| and then by increasing mask value; K(n,d) =
+ *     sum_{k<=d} C(n-1,k) families per node; per-family arrays are laid out
+ *     [i*K + f];
+ *   - the parent configuration of a family is a mixed-radix number with the
+ *     lowest-numbered parent least significant; cell = config*r_i + x_i;
+ *   - post is n x n row-major, post[u*n + v] = P(u->v | D), diagonal 0;
+ *   - an in-degree bound d > n-1 is treated as d = n-1;
+ *   - limits: 1 <= n <= 31, d >= 0, m >= 0 (m = 0 is valid input),
+ *     1 <= arity[i] <= 255, at most 65536 cells (q*r_i) per family.
+ *
+ * Errors: every function returns BN_OK (0) or a negative BN_E* code and never
+ * throws or aborts.  bn_strerror() names a code.  On error the output
+ * buffers are left unspecified.
+ *
+ * Ownership: the caller owns every buffer it passes.  The context owns all
+ * device memory it allocates (workspace grown on demand and kept for reuse).
+ * A context is used by one host thread at a time.
+ */
+#ifndef BNEDGE_H
+#define BNEDGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BN_OK = 0,
+    BN_EINVAL = -1,          /* invalid argument or input data               */
+    BN_ENOMEM = -2,          /* device or host memory budget exceeded        */
+    BN_EAGAIN = -3,          /* job not finished yet (bn_poll)               */
+    BN_ETIMEOUT = -4,        /* bn_wait timed out                            */
+    BN_EDEVICE_TIMEOUT = -5, /* a bounded device-side wait gave up           */
+    BN_ECUDA = -6,           /* a CUDA runtime call failed                   */
+    BN_ECANCELED = -7,       /* job canceled                                 */
+    BN_ENOTFOUND = -8        /* unknown job id                               */
+};
+
+enum {
+    BN_FP64 = 0,         /* every DP array in FP64, natural-log domain        */
+    BN_FP32_SHIFTED = 1  /* DP arrays in FP32 log2 domain, each node's scores
+                            shifted by their FP64 maximum; scores, P(D) and the
+                            final division stay FP64                          */
+};
+
+typedef struct bn_ctx bn_ctx;
+
+typedef struct bn_ctx_opts {
+    int32_t device;          /* CUDA device ordinal                           */
+    int32_t slots;           /* concurrent jobs for bn_submit (>= 1)          */
+    uint64_t mem_budget;     /* device bytes the context may hold; 0 = 90% of
+                                the free memory at creation                   */
+    int32_t fail_alloc_after;/* test hook: allocations after this many fail
+                                with BN_ENOMEM; < 0 disables                  */
+    int32_t reserved;
+} bn_ctx_opts;
+
+typedef struct bn_job_desc {
+    int32_t n;               /* number of variables                           */
+    int32_t d;               /* in-degree bound                               */
+    int32_t m;               /* number of samples                             */
+    int32_t precision;       /* BN_FP64 or BN_FP32_SHIFTED                    */
+    const uint8_t* data;     /* m*n bytes, host or device (data_on_device)    */
+    const uint8_t* arity;    /* n bytes, host                                 */
+    double ess;              /* BDeu equivalent sample size (> 0)             */
+    const double* log_rho;   /* d+1 host doubles: log prior per parent-set
+                                size; NULL = all zero                         */
+    int32_t data_on_device;  /* nonzero: data is a device pointer             */
+    int32_t reserved;
+} bn_job_desc;
+
+typedef struct bn_stats {
+    double ms_scores;        /* device time of each stage, CUDA events on the
+                                launching stream                              */
+    double ms_upzeta;        /* the single up-zeta launch                     */
+    double ms_forward;       /* all F level launches                          */
+    double ms_backward;      /* all R' level launches                         */
+    double ms_gamma_p1;      /* sum over v of the Gamma phase-1 launches      */
+    double ms_gamma_p2;      /* sum over v of the Gamma phase-2 launches      */
+    double ms_edges;         /* edge reduction and division                   */
+    double ms_total;         /* first kernel to last kernel                   */
+    double cells;            /* n * 2^n                                       */
+    double alg_bytes;        /* algorithmic HBM bytes of the DP arrays        */
+    int32_t kernels;         /* kernel launches of the job                    */
+    int32_t precision;
+} bn_stats;
+
+/* Context.  bn_ctx_create returns BN_EINVAL for a NULL pointer or bad
+ * options, BN_ECUDA when the device cannot be used. */
+int bn_ctx_create(bn_ctx** ctx, const bn_ctx_opts* opts /* NULL = defaults */);
+int bn_ctx_destroy(bn_ctx* ctx);
+
+/* Number of families per node, K(n, d) = sum_{k<=min(d,n-1)} C(n-1, k);
+ * 0 for invalid n or d. */
+int64_t bn_num_families(int32_t n, int32_t d);
+
+/* Step 1 only (Eq. 6, Algorithm 1 step 1): parent_mask[i*K+f] and
+ * log_B[i*K+f] (FP64, natural log, including log_rho) on the host.  Blocks
+ * until done. */
+int bn_scores(bn_ctx* ctx, const bn_job_desc* job, uint32_t* parent_mask,
+              double* log_B);
+
+/* Steps 1-5 (Algorithm 1).  post: n*n host doubles; log_PD: host double or
+ * NULL.  Blocks until the result is in the host buffers. */
+int bn_edge_posteriors(bn_ctx* ctx, const bn_job_desc* job, double* post,
+                       double* log_PD);
+
+/* Steps 1-5 enqueued on `stream` (a cudaStream_t, NULL = the context's own
+ * stream) without host synchronisation.  post_dev: n*n device doubles;
+ * log_PD_dev: one device double or NULL.  job->data may be host or device;
+ * a host copy is taken before return.  The context's workspace is reused by
+ * the next call on the same context: calls on one context are ordered by
+ * the caller (same stream, or synchronise in between). */
+int bn_edge_posteriors_async(bn_ctx* ctx, const bn_job_desc* job,
+                             double* post_dev, double* log_PD_dev,
+                             void* stream);
+
+/* Serving.  bn_submit copies the inputs, admits the job when a slot and
+ * enough device memory (by its n*2^n footprint) are free -- queuing it
+ * otherwise -- and returns at once.  Jobs in different slots run
+ * concurrently on separate streams.  BN_ENOMEM if the job can never fit the
+ * budget. */
+int bn_submit(bn_ctx* ctx, const bn_job_desc* job, uint64_t* job_id);
+/* BN_OK with the result copied out and the job retired, BN_EAGAIN while it
+ * runs or waits, or the job's error code. */
+int bn_poll(bn_ctx* ctx, uint64_t job_id, double* post, double* log_PD);
+/* Like bn_poll but blocks up to timeout_s seconds (BN_ETIMEOUT). */
+int bn_wait(bn_ctx* ctx, uint64_t job_id, double timeout_s, double* post,
+            double* log_PD);
+/* Cancels a queued job (BN_OK) or reports that it already runs. */
+int bn_cancel(bn_ctx* ctx, uint64_t job_id);
+/* Stage timings of a job run by bn_edge_posteriors (job_id 0 = the last
+ * such call) or of a retired served job. */
+int bn_job_stats(bn_ctx* ctx, uint64_t job_id, bn_stats* stats);
+/* Stage timings of the most recent bn_edge_posteriors / _async calls on this
+ * context (up to 32 are kept), oldest first: writes min(max, kept) entries
+ * and their number to *count.  Waits for those calls to finish. */
+int bn_stats_history(bn_ctx* ctx, bn_stats* out, int32_t max, int32_t* count);
+
+const char* bn_strerror(int code);
+
+/* ---- test hooks: stage dumps of the last bn_edge_posteriors call ------- */
+enum {
+    BN_STAGE_LOGB = 1,   /* n*K doubles, natural log, unshifted               */
+    BN_STAGE_MASKS = 2,  /* n*K uint32 parent masks                           */
+    BN_STAGE_SHIFT = 3,  /* n doubles: c_i = max_f log_B[i*K+f]               */
+    BN_STAGE_A = 4,      /* n*2^(n-1) values: A_i(S) - c_i at index
+                            i*2^(n-1) + (S with bit i removed)                */
+    BN_STAGE_F = 5,      /* 2^n values: F(S) - sum_{j in S} c_j               */
+    BN_STAGE_RC = 6,     /* 2^n values: R(V-T) - sum_{j not in T} c_j at T    */
+    BN_STAGE_GAMMA = 7   /* n*K values: Gamma_v(G) - sum_{j != v} c_j         */
+};
+/* Copies a stage array of the last job into host memory.  DP arrays are
+ * doubles (natural log) for BN_FP64 and floats (log2) for BN_FP32_SHIFTED;
+ * `bytes` must equal the stage size.  BN_EINVAL otherwise. */
+int bn_debug_stage(bn_ctx* ctx, int32_t stage, void* host_out, size_t bytes);
+/* Contingency counts of one family computed by the device counting routine:
+ * counts[config*r_i + x_i], q*r_i int64 values on the host. */
+int bn_debug_counts(bn_ctx* ctx, const bn_job_desc* job, int32_t i,
+                    uint32_t parent_mask, int64_t* counts, int64_t cells);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BNEDGE_H */

@@ -1,0 +1,290 @@
+"""Thin ctypes binding of the C ABI in ``include/bnedge.h``.
+
+Only argument marshalling happens here: every step of the computation runs
+in the CUDA kernels of ``_build/libbnedge.so``.  Loading fails loudly when the
+library has not been built (there is no CPU fallback).  Functions carry the C
+names (``bn_ctx_create``, ``bn_edge_posteriors``, ...); ``Context`` wraps them
+for numpy / torch callers.  Device pointers and CUDA streams may be given as
+integers or as torch tensors / streams (``data_ptr()`` / ``cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BN_OK, BN_EINVAL, BN_ENOMEM, BN_EAGAIN, BN_ETIMEOUT = 0, -1, -2, -3, -4
+BN_EDEVICE_TIMEOUT, BN_ECUDA, BN_ECANCELED, BN_ENOTFOUND = -5, -6, -7, -8
+BN_FP64, BN_FP32_SHIFTED = 0, 1
+PRECISIONS = {"fp64": BN_FP64, "fp32": BN_FP32_SHIFTED}
+(BN_STAGE_LOGB, BN_STAGE_MASKS, BN_STAGE_SHIFT, BN_STAGE_A, BN_STAGE_F, BN_STAGE_RC,
+ BN_STAGE_GAMMA) = range(1, 8)
+
+
+class BnError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {bn_strerror(code)} ({code})")
+
+
+class bn_ctx_opts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("mem_budget", C.c_uint64),
+                ("fail_alloc_after", C.c_int32), ("reserved", C.c_int32)]
+
+
+class bn_job_desc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("d", C.c_int32), ("m", C.c_int32), ("precision", C.c_int32),
+                ("data", C.c_void_p), ("arity", C.c_void_p), ("ess", C.c_double),
+                ("log_rho", C.c_void_p), ("data_on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class bn_stats(C.Structure):
+    _fields_ = [("ms_scores", C.c_double), ("ms_upzeta", C.c_double),
+                ("ms_forward", C.c_double), ("ms_backward", C.c_double),
+                ("ms_gamma_p1", C.c_double), ("ms_gamma_p2", C.c_double),
+                ("ms_edges", C.c_double), ("ms_total", C.c_double), ("cells", C.c_double),
+                ("alg_bytes", C.c_double), ("kernels", C.c_int32), ("precision", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
+           "bn_edge_posteriors", "bn_edge_posteriors_async", "bn_submit", "bn_poll", "bn_wait",
+           "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror", "bn_debug_stage",
+           "bn_debug_counts"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> C.CDLL:
+    """Load the CUDA library (building it first only when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build()); there is no CPU fallback")
+    L = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "bn_ctx_create": (C.c_int, [C.POINTER(P), C.POINTER(bn_ctx_opts)]),
+        "bn_ctx_destroy": (C.c_int, [P]),
+        "bn_num_families": (C.c_int64, [C.c_int32, C.c_int32]),
+        "bn_scores": (C.c_int, [P, C.POINTER(bn_job_desc), P, P]),
+        "bn_edge_posteriors": (C.c_int, [P, C.POINTER(bn_job_desc), P, P]),
+        "bn_edge_posteriors_async": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
+        "bn_submit": (C.c_int, [P, C.POINTER(bn_job_desc), C.POINTER(C.c_uint64)]),
+        "bn_poll": (C.c_int, [P, C.c_uint64, P, P]),
+        "bn_wait": (C.c_int, [P, C.c_uint64, C.c_double, P, P]),
+        "bn_cancel": (C.c_int, [P, C.c_uint64]),
+        "bn_job_stats": (C.c_int, [P, C.c_uint64, C.POINTER(bn_stats)]),
+        "bn_stats_history": (C.c_int, [P, C.POINTER(bn_stats), C.c_int32,
+                                       C.POINTER(C.c_int32)]),
+        "bn_strerror": (C.c_char_p, [C.c_int]),
+        "bn_debug_stage": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
+        "bn_debug_counts": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_uint32, P,
+                                      C.c_int64]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(x) -> int | None:
+    """Address of a numpy array, a torch tensor or an integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "cuda_stream"):
+        return int(x.cuda_stream)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+# ---- C-named entry points ------------------------------------------------
+
+def bn_strerror(code: int) -> str:
+    if _lib is None:
+        return {0: "ok", -1: "invalid argument", -2: "out of memory"}.get(code, f"error {code}")
+    return _lib.bn_strerror(code).decode()
+
+
+def bn_num_families(n: int, d: int) -> int:
+    return int(load().bn_num_families(n, d))
+
+
+def bn_ctx_create(device: int = 0, slots: int = 4, mem_budget: int = 0,
+                  fail_alloc_after: int = -1) -> int:
+    h = C.c_void_p()
+    opts = bn_ctx_opts(device, slots, mem_budget, fail_alloc_after, 0)
+    rc = load().bn_ctx_create(C.byref(h), C.byref(opts))
+    if rc:
+        raise BnError(rc, "bn_ctx_create")
+    return h.value
+
+
+def bn_ctx_destroy(ctx: int) -> int:
+    return load().bn_ctx_destroy(ctx)
+
+
+class Job:
+    """A bn_job_desc plus the arrays it points to (kept alive with it)."""
+
+    def __init__(self, data, arity, d: int, ess: float = 1.0, log_rho=None,
+                 precision: str | int = "fp64", m: int | None = None):
+        self.arity = np.ascontiguousarray(arity, dtype=np.uint8)
+        n = int(self.arity.shape[0])
+        on_dev = not isinstance(data, np.ndarray)
+        if on_dev:
+            self.data = data
+            if m is None:
+                m = int(data.numel()) // n if hasattr(data, "numel") else None
+            if m is None:
+                raise ValueError("m is required for a device pointer")
+        else:
+            self.data = np.ascontiguousarray(data, dtype=np.uint8).reshape(-1, n)
+            m = int(self.data.shape[0])
+        self.log_rho = None if log_rho is None else np.ascontiguousarray(log_rho, np.float64)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.n, self.d, self.m = n, int(d), int(m)
+        self.desc = bn_job_desc(n, int(d), int(m), prec,
+                                _ptr(self.data) if m > 0 else None, _ptr(self.arity),
+                                float(ess), _ptr(self.log_rho), 1 if on_dev else 0, 0)
+
+
+def bn_edge_posteriors(ctx: int, job: Job, post: np.ndarray | None = None):
+    n = job.n
+    post = np.zeros((n, n)) if post is None else post
+    lpd = np.zeros(1)
+    rc = load().bn_edge_posteriors(ctx, C.byref(job.desc), _ptr(post), _ptr(lpd))
+    if rc:
+        raise BnError(rc, "bn_edge_posteriors")
+    return post, float(lpd[0])
+
+
+def bn_edge_posteriors_async(ctx: int, job: Job, post_dev, log_PD_dev=None, stream=None) -> None:
+    rc = load().bn_edge_posteriors_async(ctx, C.byref(job.desc), _ptr(post_dev),
+                                         _ptr(log_PD_dev), _ptr(stream))
+    if rc:
+        raise BnError(rc, "bn_edge_posteriors_async")
+
+
+def bn_scores(ctx: int, job: Job):
+    K = bn_num_families(job.n, job.d)
+    masks = np.zeros((job.n, K), dtype=np.uint32)
+    logB = np.zeros((job.n, K))
+    rc = load().bn_scores(ctx, C.byref(job.desc), _ptr(masks), _ptr(logB))
+    if rc:
+        raise BnError(rc, "bn_scores")
+    return masks, logB
+
+
+def bn_submit(ctx: int, job: Job) -> int:
+    jid = C.c_uint64()
+    rc = load().bn_submit(ctx, C.byref(job.desc), C.byref(jid))
+    if rc:
+        raise BnError(rc, "bn_submit")
+    return int(jid.value)
+
+
+def bn_poll(ctx: int, job_id: int, n: int):
+    """(rc, post, log_PD); rc is BN_OK, BN_EAGAIN or an error code."""
+    post = np.zeros((n, n))
+    lpd = np.zeros(1)
+    rc = load().bn_poll(ctx, job_id, _ptr(post), _ptr(lpd))
+    return rc, post, float(lpd[0])
+
+
+def bn_wait(ctx: int, job_id: int, n: int, timeout_s: float = 60.0):
+    post = np.zeros((n, n))
+    lpd = np.zeros(1)
+    rc = load().bn_wait(ctx, job_id, float(timeout_s), _ptr(post), _ptr(lpd))
+    return rc, post, float(lpd[0])
+
+
+def bn_cancel(ctx: int, job_id: int) -> int:
+    return int(load().bn_cancel(ctx, job_id))
+
+
+def bn_job_stats(ctx: int, job_id: int = 0) -> dict:
+    st = bn_stats()
+    rc = load().bn_job_stats(ctx, job_id, C.byref(st))
+    if rc:
+        raise BnError(rc, "bn_job_stats")
+    return st.as_dict()
+
+
+def bn_stats_history(ctx: int, max_entries: int = 32) -> list:
+    arr = (bn_stats * max_entries)()
+    cnt = C.c_int32()
+    rc = load().bn_stats_history(ctx, arr, max_entries, C.byref(cnt))
+    if rc:
+        raise BnError(rc, "bn_stats_history")
+    return [arr[k].as_dict() for k in range(cnt.value)]
+
+
+def bn_debug_stage(ctx: int, stage: int, shape, dtype) -> np.ndarray:
+    out = np.zeros(shape, dtype=dtype)
+    rc = load().bn_debug_stage(ctx, stage, _ptr(out), out.nbytes)
+    if rc:
+        raise BnError(rc, "bn_debug_stage")
+    return out
+
+
+def bn_debug_counts(ctx: int, job: Job, i: int, mask: int, cells: int) -> np.ndarray:
+    out = np.zeros(cells, dtype=np.int64)
+    rc = load().bn_debug_counts(ctx, C.byref(job.desc), i, mask, _ptr(out), cells)
+    if rc:
+        raise BnError(rc, "bn_debug_counts")
+    return out
+
+
+class Context:
+    """Owns one bn_ctx."""
+
+    def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0,
+                 fail_alloc_after: int = -1):
+        self.h = bn_ctx_create(device, slots, mem_budget, fail_alloc_after)
+
+    def close(self):
+        if self.h:
+            bn_ctx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def edge_posteriors(self, data, arity, d, ess=1.0, log_rho=None, precision="fp64"):
+        return bn_edge_posteriors(self.h, Job(data, arity, d, ess, log_rho, precision))
+
+    def scores(self, data, arity, d, ess=1.0, log_rho=None):
+        return bn_scores(self.h, Job(data, arity, d, ess, log_rho))
+
+    def stats(self, job_id: int = 0) -> dict:
+        return bn_job_stats(self.h, job_id)

@@ -1,0 +1,761 @@
+// bn_kernels.cu -- sm_103a kernels of the five steps of Algorithm 1.
+//
+// Step 1  k_pack_planes, k_lgamma_table, k_scores, k_node_max, k_shift_scores
+// Step 2  k_upzeta         truncated upward zeta (Eq. 7, Definition 1)
+// Step 3  k_forward_level, k_backward_level   F (Eq. 9) and R (Eq. 10)
+// Step 4  k_gamma_p1, k_gamma_p2              truncated downward zeta (Eq. 12)
+// Step 5  k_edges          Eq. 11 and the division by P(D)
+//
+// Values are logs: natural logs in FP64, base-2 logs in FP32 (see
+// bn_device.cuh).  Every node's scores are shifted by their maximum c_i
+// before step 2: replacing B_i by B_i / exp(c_i) scales every order's weight
+// by the same factor prod_i exp(-c_i), which cancels in P(u->v | D), and
+// keeps the log magnitudes of A, F, R and Gamma small.
+#include "bn_device.cuh"
+#include "bn_kernels.cuh"
+
+#include <cmath>
+
+namespace bn {
+
+static constexpr unsigned FULL = 0xffffffffu;
+
+// ===========================================================================
+// Step 1: local scores.
+// ===========================================================================
+
+// planes[(v*rmax + x)*W + w] bit b  <=>  data[(64w + b)*n + v] == x.
+__global__ void k_pack_planes(const uint8_t* __restrict__ data, int n, int m, int rmax, int W,
+                              uint64_t* __restrict__ planes)
+{
+    const int64_t total = (int64_t)n * rmax * W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(t % W);
+        const int64_t vx = t / W;
+        const int x = (int)(vx % rmax);
+        const int v = (int)(vx / rmax);
+        uint64_t word = 0;
+        const int s0 = w * 64;
+        const int cnt = min(64, m - s0);
+        for (int b = 0; b < cnt; ++b)
+            word |= (uint64_t)(data[(size_t)(s0 + b) * n + v] == x) << b;
+        planes[t] = word;
+    }
+}
+
+// err |= 1 when some data value is not below its variable's arity.
+__global__ void k_check_data(const uint8_t* __restrict__ data, const uint8_t* __restrict__ arity,
+                             int n, int m, int* err)
+{
+    const int64_t total = (int64_t)n * m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (data[t] >= arity[t % n]) atomicOr(err, 1);
+    }
+}
+
+// T[row*(m+1) + N] = lgamma(alpha_row + N) - lgamma(alpha_row), N = 0..m.
+__global__ void k_lgamma_table(const double* __restrict__ alpha, int rows, int m,
+                               double* __restrict__ T)
+{
+    const int64_t total = (int64_t)rows * (m + 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(t / (m + 1));
+        const int N = (int)(t % (m + 1));
+        const double a = alpha[row];
+        T[t] = N == 0 ? 0.0 : lgamma(a + (double)N) - lgamma(a);
+    }
+}
+
+__device__ __forceinline__ int find_row(const double* Dvals, int rows, double D)
+{
+    int lo = 0, hi = rows - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Dvals[mid] < D) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long to_fixed(double x) { return __double2ull_rn(x); }
+__device__ __forceinline__ unsigned long long to_fixed(float x) { return __float2ull_rn(x); }
+template <typename T> __device__ __forceinline__ T from_fixed(unsigned long long u);
+template <> __device__ __forceinline__ double from_fixed<double>(unsigned long long u)
+{
+    return __ull2double_rn(u);
+}
+template <> __device__ __forceinline__ float from_fixed<float>(unsigned long long u)
+{
+    return __ull2float_rn(u);
+}
+
+// One warp per family x = i*K + f.  Counts N_jk = popc(AND of bit planes),
+// lanes split the words of a plane and the cells of the table lookups.
+//   log B_i(G) = log rho(|G|) + sum_j [ -T_q(N_j) + sum_k T_qr(N_jk) ]
+// with T_a(N) = lgamma(a+N) - lgamma(a), a = ess/q and ess/(q r_i).
+__global__ void __launch_bounds__(256)
+k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__ arity,
+         const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
+         const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
+         int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
+         double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t xi = warp0; xi < x_count; xi += nwarps) {
+        const int64_t x = x_begin + xi;
+        const int i = (int)(x / K);
+        uint32_t f = (uint32_t)(x % K);
+        int k = 0;
+        while (f >= binom(n - 1, k)) { f -= binom(n - 1, k); ++k; }
+        const uint32_t cm = colex_unrank(f, k, n - 1);
+        const uint32_t G = expand(cm, i);
+        int par[32];
+        int rad[32];
+        int np = 0;
+        double q = 1.0;
+        for (uint32_t g = G; g; g &= g - 1) {
+            const int p = __ffs(g) - 1;
+            par[np] = p;
+            rad[np] = arity[p];
+            q *= (double)arity[p];
+            ++np;
+        }
+        const int ri = arity[i];
+        const int row_q = find_row(Dvals, rows, q);
+        const int row_qr = find_row(Dvals, rows, q * ri);
+        const double* Tq = T + (size_t)row_q * (m + 1);
+        const double* Tqr = T + (size_t)row_qr * (m + 1);
+        const int64_t qi = (int64_t)q;
+        int dig[32];
+        for (int t = 0; t < np; ++t) dig[t] = 0;
+        double acc = 0.0;
+        for (int64_t cfg = 0; cfg < qi; ++cfg) {
+            uint32_t Nj = 0;
+            for (int xv = 0; xv < ri; ++xv) {
+                uint32_t part = 0;
+                for (int w = lane; w < W; w += 32) {
+                    uint64_t M = planes[((size_t)i * rmax + xv) * W + w];
+                    for (int t = 0; t < np; ++t)
+                        M &= planes[((size_t)par[t] * rmax + dig[t]) * W + w];
+                    part += (uint32_t)__popcll(M);
+                }
+                const uint32_t N = __reduce_add_sync(FULL, part);
+                Nj += N;
+                const int64_t cell = cfg * ri + xv;
+                if (lane == (int)(cell & 31)) {
+                    acc += Tqr[N];
+                    if (debug_counts) debug_counts[cell] = N;
+                }
+            }
+            if (lane == (int)(cfg & 31)) acc -= Tq[Nj];
+            for (int t = 0; t < np; ++t) {          // mixed-radix increment
+                if (++dig[t] < rad[t]) break;
+                dig[t] = 0;
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+            masks[x] = G;
+            cmasks[x] = cm;
+        }
+    }
+    (void)d;
+}
+
+// cmax[i] = max_f logB[i*K + f]; one block per node.
+__global__ void k_node_max(int64_t K, const double* __restrict__ logB, double* __restrict__ cmax)
+{
+    __shared__ double red[32];
+    const int i = blockIdx.x;
+    double mx = -INFINITY;
+    for (int64_t f = threadIdx.x; f < K; f += blockDim.x) mx = fmax(mx, logB[(size_t)i * K + f]);
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -INFINITY;
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+        if (threadIdx.x == 0) cmax[i] = mx;
+    }
+}
+
+template <typename T>
+__global__ void k_shift_scores(int64_t total, int64_t K, const double* __restrict__ logB,
+                               const double* __restrict__ cmax, T* __restrict__ lbs)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x)
+        lbs[x] = (T)LogOps<T>::from_ln(logB[x] - cmax[x / K]);
+}
+
+// ===========================================================================
+// Step 2: A_i(S) = sum_{G subset S, |G| <= d} B_i(G)  (Eq. 7, q_i = 1).
+//
+// Index space of node i: the n-1 bits of S with bit i removed.  One block per
+// tile (i, H): H = the high n-1-b bits, the 2^b low-bit patterns L in shared
+// memory.  The high dimensions of the transform are done by scattering every
+// family G = (g_L, G_H) with G_H subset H into slot g_L (log-sum-exp via two
+// shared-memory atomic passes: max, then sum of exp); the b low dimensions
+// are then summed in shared memory one dimension at a time (the butterfly of
+// Algorithm 2).  Every family has |G| <= d, so the truncation is exact; A is
+// written to HBM exactly once, coalesced.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_upzeta(int n, int b, int64_t K, int qbits, const uint32_t* __restrict__ cmasks,
+         const T* __restrict__ lbs, T* __restrict__ A)
+{
+    using O = typename OrdInt<T>::type;
+    using U = unsigned long long;
+    using L = LogOps<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t tileN = 1u << b;
+    U* sm = reinterpret_cast<U*>(smem_raw);
+    T* vals = reinterpret_cast<T*>(sm + tileN);
+    O* mx = reinterpret_cast<O*>(vals + tileN);
+    const int h = n - 1 - b;
+    const int i = (int)(blockIdx.x >> h);
+    const uint32_t H = blockIdx.x & ((1u << h) - 1u);
+    const uint32_t lowm = tileN - 1u;
+    const O enc_ninf = ord_enc(L::ninf());
+    const T qscale = (T)ldexp(1.0, qbits);
+
+    for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) {
+        mx[t] = enc_ninf;
+        sm[t] = 0ull;
+    }
+    __syncthreads();
+    const uint32_t* cm_i = cmasks + (size_t)i * K;
+    const T* lb_i = lbs + (size_t)i * K;
+    for (int64_t f = threadIdx.x; f < K; f += blockDim.x) {
+        const uint32_t c = cm_i[f];
+        if (((c >> b) & ~H) == 0u) atomicMax(&mx[c & lowm], ord_enc(lb_i[f]));
+    }
+    __syncthreads();
+    // Sum of exp(value - slot max) in fixed point: every term is in (0, 1] and
+    // a slot holds at most K terms, so 2^qbits * K < 2^64; integer atomics
+    // make the sum independent of the order of arrival.
+    for (int64_t f = threadIdx.x; f < K; f += blockDim.x) {
+        const uint32_t c = cm_i[f];
+        if (((c >> b) & ~H) == 0u) {
+            const uint32_t slot = c & lowm;
+            const T e = L::ex(lb_i[f] - ord_dec(mx[slot]));
+            atomicAdd(&sm[slot], to_fixed(e * qscale));
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) {
+        const O e = mx[t];
+        vals[t] = (e == enc_ninf) ? L::ninf()
+                                  : ord_dec(e) + L::lg(from_fixed<T>(sm[t]) / qscale);
+    }
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        const uint32_t jm = (1u << j) - 1u;
+        for (uint32_t p = threadIdx.x; p < (tileN >> 1); p += blockDim.x) {
+            const uint32_t lo = ((p & ~jm) << 1) | (p & jm);
+            const uint32_t hi = lo | (1u << j);
+            vals[hi] = L::lse(vals[hi], vals[lo]);
+        }
+        __syncthreads();
+    }
+    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << b);
+    for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) out[t] = vals[t];
+}
+
+// ===========================================================================
+// Step 3: F and R' = R(V - .) over the lattice, level by level.
+//
+// A warp owns a tile of 2^wb consecutive subsets (the low wb bits vary, one
+// subset per lane).  Tiles are keyed by their high bits Ht and launched one
+// popcount level of Ht at a time (the sub-cube order of Section 3.2.2).
+// Terms across tiles read the previous level's tiles; the wb in-tile levels
+// are resolved with warp shuffles.
+//   F(S)  = sum_{i in S}     A_i(S - {i}) F(S - {i}),  F(empty) = 1  (Eq. 9)
+//   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),       R'(V) = 1
+// where R'(T) = R(V - T) turns Eq. 10 into a recursion over T.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_forward_level(int n, int wb, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ F)
+{
+    using L = LogOps<T>;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= ntiles) return;
+    const uint32_t Ht = colex_unrank(warp, hl, n - wb);
+    const uint32_t lb = (uint32_t)lane & ((1u << wb) - 1u);
+    const bool active = lane < (1 << wb);
+    const uint32_t S = (Ht << wb) | lb;
+    const size_t half = (size_t)1 << (n - 1);
+    LseAcc<T> X;
+    T a[5];
+    if (active) {
+        for (int i = wb; i < n; ++i) {
+            if (S >> i & 1u) {
+                const uint32_t Si = S & ~(1u << i);
+                X.add(A[(size_t)i * half + squeeze(Si, i)] + F[Si]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        a[i] = L::ninf();
+        if (i < wb && active && (S >> i & 1u))
+            a[i] = A[(size_t)i * half + squeeze(S & ~(1u << i), i)];
+    }
+    T Fv = (S == 0u) ? T(0) : X.value();
+    for (int l = 1; l <= wb; ++l) {
+        T nb[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Fv, 1 << i);
+        if (active && __popc(lb) == l) {
+            LseAcc<T> acc = X;
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                if (i < wb && (lb >> i & 1u)) acc.add(a[i] + nb[i]);
+            Fv = acc.value();
+        }
+    }
+    if (active) F[S] = Fv;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_backward_level(int n, int wb, int hl, uint32_t ntiles, const T* __restrict__ A,
+                 T* __restrict__ Rc)
+{
+    using L = LogOps<T>;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= ntiles) return;
+    const uint32_t Ht = colex_unrank(warp, hl, n - wb);
+    const uint32_t wmask = (1u << wb) - 1u;
+    const uint32_t lb = (uint32_t)lane & wmask;
+    const bool active = lane < (1 << wb);
+    const uint32_t Tm = (Ht << wb) | lb;
+    const uint32_t full = (n == 32) ? 0xffffffffu : ((1u << n) - 1u);
+    const size_t half = (size_t)1 << (n - 1);
+    LseAcc<T> X;
+    T a[5];
+    if (active) {
+        for (int i = wb; i < n; ++i) {
+            if (!(Tm >> i & 1u))
+                X.add(A[(size_t)i * half + squeeze(Tm, i)] + Rc[Tm | (1u << i)]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        a[i] = L::ninf();
+        if (i < wb && active && !(Tm >> i & 1u)) a[i] = A[(size_t)i * half + squeeze(Tm, i)];
+    }
+    T Rv = (Tm == full) ? T(0) : X.value();
+    for (int l = wb - 1; l >= 0; --l) {
+        T nb[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Rv, 1 << i);
+        if (active && __popc(lb) == l) {
+            LseAcc<T> acc = X;
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                if (i < wb && !(lb >> i & 1u)) acc.add(a[i] + nb[i]);
+            Rv = acc.value();
+        }
+    }
+    if (active) Rc[Tm] = Rv;
+}
+
+// ===========================================================================
+// Step 4: Gamma_v(G) = sum_{G subset S subset V-{v}} F(S) R'(S + {v}), |G|<=d
+// (Eq. 12; F(S) R(V-{v}-S) = F(S) R'(S + {v}), the pairing of Section 3.1.2).
+//
+// Phase 1: one block per tile of the n-1 bits of S (bit v removed), 2^b low
+// bits in shared memory: load s_v = F + R', run the downward butterflies over
+// the b low dimensions with the guard of Algorithm 3 (only patterns with at
+// most d elements among the dimensions done so far), and keep the outputs
+// with at most d low elements: row H of W, nlow entries in canonical order.
+// Phase 2: one block per column g of W (a low pattern, d' = d - |g|): the
+// downward transform over the h high dimensions, truncated at d', chunk by
+// chunk of 2^hc rows; each output is stored at its family index.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gamma_p1(int n, int d, int v, int b, uint32_t nlow, const T* __restrict__ F,
+           const T* __restrict__ Rc, T* __restrict__ W)
+{
+    using L = LogOps<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* vals = reinterpret_cast<T*>(smem_raw);
+    const uint32_t tileN = 1u << b;
+    const uint32_t H = blockIdx.x;
+    const uint32_t bv = 1u << v;
+    for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) {
+        const uint32_t S = expand((H << b) | t, v);
+        vals[t] = F[S] + Rc[S | bv];
+    }
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        const uint32_t jm = (1u << j) - 1u;
+        for (uint32_t p = threadIdx.x; p < (tileN >> 1); p += blockDim.x) {
+            const uint32_t lo = ((p & ~jm) << 1) | (p & jm);
+            if (__popc(lo & jm) <= d) vals[lo] = L::lse(vals[lo], vals[lo | (1u << j)]);
+        }
+        __syncthreads();
+    }
+    T* row = W + (size_t)H * nlow;
+    for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x)
+        if (__popc(t) <= d) row[small_subset_rank(t, b)] = vals[t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, const T* __restrict__ W,
+           T* __restrict__ Gam)
+{
+    using L = LogOps<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int h = n - 1 - b;
+    const int hh = h - hc;
+    const uint32_t col = blockIdx.x;
+    // low pattern g of this column
+    int kg = 0;
+    uint32_t r = col;
+    while (r >= binom(b, kg)) { r -= binom(b, kg); ++kg; }
+    const uint32_t g = colex_unrank(r, kg, b);
+    const int dp = d - kg;
+    const uint32_t nout = num_small_subsets(h, dp);
+    const uint32_t chunkN = 1u << hc;
+    T* vals = reinterpret_cast<T*>(smem_raw);
+    T* acc = vals + chunkN;
+    uint32_t* gh = reinterpret_cast<uint32_t*>(acc + nout);
+    for (uint32_t o = threadIdx.x; o < nout; o += blockDim.x) {
+        uint32_t ro = o;
+        int k = 0;
+        while (ro >= binom(h, k)) { ro -= binom(h, k); ++k; }
+        gh[o] = colex_unrank(ro, k, h);
+        acc[o] = L::ninf();
+    }
+    const uint32_t lowc = chunkN - 1u;
+    for (uint32_t Hhi = 0; Hhi < (1u << hh); ++Hhi) {
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < chunkN; t += blockDim.x)
+            vals[t] = W[(size_t)((Hhi << hc) | t) * nlow + col];
+        __syncthreads();
+        for (int j = 0; j < hc; ++j) {
+            const uint32_t jm = (1u << j) - 1u;
+            for (uint32_t p = threadIdx.x; p < (chunkN >> 1); p += blockDim.x) {
+                const uint32_t lo = ((p & ~jm) << 1) | (p & jm);
+                if (__popc(lo & jm) <= dp) vals[lo] = L::lse(vals[lo], vals[lo | (1u << j)]);
+            }
+            __syncthreads();
+        }
+        for (uint32_t o = threadIdx.x; o < nout; o += blockDim.x) {
+            const uint32_t G = gh[o];
+            if (((G >> hc) & ~Hhi) == 0u) acc[o] = L::lse(acc[o], vals[G & lowc]);
+        }
+    }
+    __syncthreads();
+    for (uint32_t o = threadIdx.x; o < nout; o += blockDim.x) {
+        const uint32_t cm = g | (gh[o] << b);      // mask over the n-1 bits of V-{v}
+        const int k = __popc(cm);
+        uint32_t f = 0;
+        for (int s = 0; s < k; ++s) f += binom(n - 1, s);
+        int t = 1;
+        for (uint32_t x = cm; x; x &= x - 1, ++t) f += binom(__ffs(x) - 1, t);
+        Gam[f] = acc[o];
+    }
+}
+
+// ===========================================================================
+// Step 5: log P(u->v, D) = log sum_{G: u in G} B_v(G) Gamma_v(G)  (Eq. 11)
+// and P(u->v | D) = P(u->v, D) / P(D).  One block per endpoint v, FP64.
+// P(D) is F(V) on the FP64 path (Algorithm 1) and sum_G B_v(G) Gamma_v(G) on
+// the FP32 path (the same quantity, Eq. 11 summed over all G, computed from
+// the same Gamma_v so that rounding common to numerator and denominator
+// cancels).  Block 0 also writes log P(D) = F~(V) + sum_i c_i.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_edges(int n, int64_t K, int use_z, int qbits, const double* __restrict__ logB,
+        const double* __restrict__ cmax, const uint32_t* __restrict__ masks,
+        const T* __restrict__ Gam, const T* __restrict__ F, const int* __restrict__ err,
+        double* __restrict__ post, double* __restrict__ log_PD)
+{
+    using L = LogOps<T>;
+    __shared__ unsigned long long Nu[32];
+    __shared__ double red[32];
+    const double qscale = ldexp(1.0, qbits);
+    const int v = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int nw = blockDim.x >> 5;
+    if (tid < 32) Nu[tid] = 0ull;
+    const uint32_t full = (1u << n) - 1u;
+    const double lnFV = L::to_ln((double)F[full]);
+    double mx = -INFINITY;
+    for (int64_t f = tid; f < K; f += blockDim.x) {
+        const size_t x = (size_t)v * K + f;
+        mx = fmax(mx, logB[x] - cmax[v] + L::to_ln((double)Gam[x]));
+    }
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = -INFINITY;
+    for (int w = 0; w < nw; ++w) mx = fmax(mx, red[w]);
+    __syncthreads();
+    double z = 0.0;
+    for (int64_t f = tid; f < K; f += blockDim.x) {
+        const size_t x = (size_t)v * K + f;
+        const double e = exp(logB[x] - cmax[v] + L::to_ln((double)Gam[x]) - mx);
+        z += e;
+        // e <= 1; fixed point keeps the per-u sums independent of arrival order
+        const unsigned long long q = __double2ull_rn(e * qscale);
+        for (uint32_t g = masks[x]; g; g &= g - 1) atomicAdd(&Nu[__ffs(g) - 1], q);
+    }
+    z = warp_sum(z);
+    if ((tid & 31) == 0) red[tid >> 5] = z;
+    __syncthreads();
+    z = 0.0;
+    for (int w = 0; w < nw; ++w) z += red[w];
+    const double lognorm = use_z ? mx + log(z) : lnFV;
+    const bool bad = err && *err;
+    for (int u = tid; u < n; u += blockDim.x) {
+        double p = 0.0;
+        if (u != v && Nu[u] > 0ull)
+            p = exp(mx + log(__ull2double_rn(Nu[u]) / qscale) - lognorm);
+        post[(size_t)u * n + v] = bad ? NAN : p;
+    }
+    if (v == 0 && tid == 0 && log_PD) {
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c += cmax[i];
+        *log_PD = bad ? NAN : lnFV + c;
+    }
+}
+
+// ===========================================================================
+// Launchers.
+// ===========================================================================
+static int grid_for(int64_t work, int threads, int cap = 152 * 32)
+{
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int W,
+                               uint64_t* planes, cudaStream_t s)
+{
+    const int64_t total = (int64_t)n * rmax * W;
+    k_pack_planes<<<grid_for(total, 256), 256, 0, s>>>(data, n, m, rmax, W, planes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_data(const uint8_t* data, const uint8_t* arity, int n, int m,
+                              int* err, cudaStream_t s)
+{
+    if ((int64_t)n * m == 0) return cudaSuccess;
+    k_check_data<<<grid_for((int64_t)n * m, 256), 256, 0, s>>>(data, arity, n, m, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T, cudaStream_t s)
+{
+    const int64_t total = (int64_t)rows * (m + 1);
+    k_lgamma_table<<<grid_for(total, 256), 256, 0, s>>>(alpha, rows, m, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* planes,
+                          const double* Dvals, const double* T, const double* log_rho,
+                          int64_t x_begin, int64_t x_count, uint32_t* masks, uint32_t* cmasks,
+                          double* logB, int64_t* debug_counts, cudaStream_t s)
+{
+    const int threads = 256;
+    const int64_t warps_wanted = x_count;
+    int grid = grid_for(warps_wanted * 32, threads, 152 * 64);
+    k_scores<<<grid, threads, 0, s>>>(P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+                                      P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
+                                      logB, debug_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s)
+{
+    k_node_max<<<P.n, 256, 0, s>>>(P.K, logB, cmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double* cmax, void* lbs,
+                                cudaStream_t s)
+{
+    const int64_t total = (int64_t)P.n * P.K;
+    if (P.prec == 0)
+        k_shift_scores<double><<<grid_for(total, 256), 256, 0, s>>>(total, P.K, logB, cmax,
+                                                                    (double*)lbs);
+    else
+        k_shift_scores<float><<<grid_for(total, 256), 256, 0, s>>>(total, P.K, logB, cmax,
+                                                                   (float*)lbs);
+    return cudaGetLastError();
+}
+
+size_t upzeta_smem_bytes(const Plan& P)
+{
+    const size_t es = P.prec == 0 ? 8 : 4;
+    return ((size_t)1 << P.b_up) * (8 + 2 * es);
+}
+
+// Fractional bits of a fixed-point sum of at most `terms` values in (0, 1].
+static int fixed_bits(int64_t terms)
+{
+    int b = 0;
+    while (((int64_t)1 << b) <= terms) ++b;
+    return 63 - b;
+}
+
+cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* A,
+                          cudaStream_t s)
+{
+    const int h = P.n - 1 - P.b_up;
+    const unsigned grid = (unsigned)P.n << h;
+    const size_t sm = upzeta_smem_bytes(P);
+    if (P.prec == 0)
+        k_upzeta<double><<<grid, 256, sm, s>>>(P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
+                                               (const double*)lbs, (double*)A);
+    else
+        k_upzeta<float><<<grid, 256, sm, s>>>(P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
+                                              (const float*)lbs, (float*)A);
+    return cudaGetLastError();
+}
+
+static uint32_t host_binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int t = 1; t <= k; ++t) r = r * (uint64_t)(n - k + t) / (uint64_t)t;
+    return (uint32_t)r;
+}
+
+cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches)
+{
+    const int nh = P.n - P.wb;
+    for (int hl = 0; hl <= nh; ++hl) {
+        const uint32_t nt = host_binom(nh, hl);
+        const unsigned grid = (unsigned)(((uint64_t)nt * 32 + 255) / 256);
+        if (P.prec == 0)
+            k_forward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const double*)A,
+                                                         (double*)F);
+        else
+            k_forward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const float*)A,
+                                                        (float*)F);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (launches) ++*launches;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s, int* launches)
+{
+    const int nh = P.n - P.wb;
+    for (int hl = nh; hl >= 0; --hl) {
+        const uint32_t nt = host_binom(nh, hl);
+        const unsigned grid = (unsigned)(((uint64_t)nt * 32 + 255) / 256);
+        if (P.prec == 0)
+            k_backward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const double*)A,
+                                                          (double*)Rc);
+        else
+            k_backward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const float*)A,
+                                                         (float*)Rc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (launches) ++*launches;
+    }
+    return cudaSuccess;
+}
+
+size_t gamma_p1_smem_bytes(const Plan& P)
+{
+    return ((size_t)1 << P.b_g) * (P.prec == 0 ? 8 : 4);
+}
+
+size_t gamma_p2_smem_bytes(const Plan& P)
+{
+    const int h = P.n - 1 - P.b_g;
+    uint64_t nout = 0;
+    for (int k = 0; k <= P.d && k <= h; ++k) nout += host_binom(h, k);
+    const size_t es = P.prec == 0 ? 8 : 4;
+    return ((size_t)1 << P.hc_g) * es + nout * es + nout * 4 + 16;
+}
+
+cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc, void* W,
+                            cudaStream_t s)
+{
+    const int h = P.n - 1 - P.b_g;
+    const size_t sm1 = gamma_p1_smem_bytes(P);
+    if (P.prec == 0)
+        k_gamma_p1<double><<<1u << h, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
+                                                     (const double*)F, (const double*)Rc,
+                                                     (double*)W);
+    else
+        k_gamma_p1<float><<<1u << h, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
+                                                    (const float*)F, (const float*)Rc,
+                                                    (float*)W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam_v, cudaStream_t s)
+{
+    const size_t sm2 = gamma_p2_smem_bytes(P);
+    if (P.prec == 0)
+        k_gamma_p2<double><<<P.nlow_g, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
+                                                      (const double*)W, (double*)Gam_v);
+    else
+        k_gamma_p2<float><<<P.nlow_g, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
+                                                     (const float*)W, (float*)Gam_v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
+                         const uint32_t* masks, const void* Gam, const void* F, const int* err,
+                         double* post, double* log_PD, cudaStream_t s)
+{
+    if (P.prec == 0)
+        k_edges<double><<<P.n, 256, 0, s>>>(P.n, P.K, 0, fixed_bits(P.K), logB, cmax, masks,
+                                            (const double*)Gam,
+                                            (const double*)F, err, post, log_PD);
+    else
+        k_edges<float><<<P.n, 256, 0, s>>>(P.n, P.K, 1, fixed_bits(P.K), logB, cmax, masks,
+                                           (const float*)Gam,
+                                           (const float*)F, err, post, log_PD);
+    return cudaGetLastError();
+}
+
+cudaError_t set_kernel_attributes()
+{
+    cudaError_t e;
+    const int big = 227 * 1024;
+#define SETA(k)                                                                      \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+    if (e != cudaSuccess) return e;
+    SETA(k_upzeta<double>)
+    SETA(k_upzeta<float>)
+    SETA(k_gamma_p1<double>)
+    SETA(k_gamma_p1<float>)
+    SETA(k_gamma_p2<double>)
+    SETA(k_gamma_p2<float>)
+#undef SETA
+    return cudaSuccess;
+}
+
+}  // namespace bn

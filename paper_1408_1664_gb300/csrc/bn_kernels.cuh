@@ -1,0 +1,55 @@
+// bn_kernels.cuh -- host-side launch interface of the device kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bn {
+
+// Shapes of one job, computed on the host.
+struct Plan {
+    int n, d, m;          // d already clamped to n-1
+    int64_t K;            // families per node
+    int W;                // 64-bit words per bit plane (ceil(m/64), >= 1)
+    int rmax;             // max arity
+    int rows;             // rows of the lgamma table
+    int b_up;             // low dims done in shared memory by the up-zeta tile
+    int b_g;              // low dims of the Gamma phase-1 tile
+    int hc_g;             // high dims per Gamma phase-2 chunk
+    uint32_t nlow_g;      // subsets of b_g dims with at most d elements
+    int wb;               // in-warp bits of the F / R' tiles
+    int prec;             // 0 = FP64, 1 = FP32
+};
+
+cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int W,
+                               uint64_t* planes, cudaStream_t s);
+cudaError_t launch_check_data(const uint8_t* data, const uint8_t* arity, int n, int m,
+                              int* err, cudaStream_t s);
+cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T,
+                                cudaStream_t s);
+cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* planes,
+                          const double* Dvals, const double* T, const double* log_rho,
+                          int64_t x_begin, int64_t x_count, uint32_t* masks,
+                          uint32_t* cmasks, double* logB, int64_t* debug_counts,
+                          cudaStream_t s);
+cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s);
+cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double* cmax,
+                                void* lbs, cudaStream_t s);
+cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* A,
+                          cudaStream_t s);
+cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
+cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s,
+                            int* launches);
+cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc, void* W,
+                            cudaStream_t s);
+cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam_v, cudaStream_t s);
+cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
+                         const uint32_t* masks, const void* Gam, const void* F,
+                         const int* err, double* post, double* log_PD, cudaStream_t s);
+
+size_t upzeta_smem_bytes(const Plan& P);
+size_t gamma_p1_smem_bytes(const Plan& P);
+size_t gamma_p2_smem_bytes(const Plan& P);
+cudaError_t set_kernel_attributes();
+
+}  // namespace bn

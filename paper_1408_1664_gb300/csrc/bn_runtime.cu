@@ -1,0 +1,890 @@
+// bn_runtime.cu -- host runtime behind the C ABI of include/bnedge.h:
+// validation, job planning, the device workspace, the launch sequence of
+// Algorithm 1, and the serving queue (bn_submit / bn_poll / bn_wait).
+#include "bnedge.h"
+#include "bn_kernels.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <set>
+#include <thread>
+#include <vector>
+
+namespace {
+
+using bn::Plan;
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+int64_t host_binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int t = 1; t <= k; ++t) r = r * (n - k + t) / t;
+    return r;
+}
+
+int64_t families(int n, int d)
+{
+    if (n < 1 || d < 0) return 0;
+    d = std::min(d, n - 1);
+    int64_t k = 0;
+    for (int s = 0; s <= d; ++s) k += host_binom(n - 1, s);
+    return k;
+}
+
+// Host copy of one job's inputs plus its plan.
+struct HostJob {
+    Plan P{};
+    double ess = 1.0;
+    std::vector<uint8_t> arity;
+    std::vector<double> log_rho;     // d+1 entries, empty = none
+    std::vector<double> Dvals;       // sorted distinct denominators q, q*r
+    const uint8_t* data = nullptr;   // host or device
+    bool data_on_device = false;
+    std::vector<uint8_t> data_copy;  // owned host copy (served jobs)
+};
+
+// Byte offsets of every array of a job inside one device allocation.
+struct Layout {
+    size_t data, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB, cmax, lbs,
+        A, F, Rc, W, Gam, post, logPD, dbg, total;
+};
+
+Layout make_layout(const Plan& P, size_t dbg_cells)
+{
+    const size_t es = P.prec == 0 ? 8 : 4;
+    const size_t nK = (size_t)P.n * P.K;
+    const int hg = P.n - 1 - P.b_g;
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o += al(std::max<size_t>(bytes, 1)); return at; };
+    L.data = take((size_t)P.m * P.n);
+    L.arity = take(P.n);
+    L.log_rho = take((size_t)(P.d + 1) * 8);
+    L.Dvals = take((size_t)P.rows * 8);
+    L.alpha = take((size_t)P.rows * 8);
+    L.lgT = take((size_t)P.rows * (P.m + 1) * 8);
+    L.planes = take((size_t)P.n * P.rmax * P.W * 8);
+    L.err = take(4);
+    L.masks = take(nK * 4);
+    L.cmasks = take(nK * 4);
+    L.logB = take(nK * 8);
+    L.cmax = take((size_t)P.n * 8);
+    L.lbs = take(nK * es);
+    L.A = take(((size_t)P.n << (P.n - 1)) * es);
+    L.F = take(((size_t)1 << P.n) * es);
+    L.Rc = take(((size_t)1 << P.n) * es);
+    L.W = take(((size_t)1 << hg) * P.nlow_g * es);
+    L.Gam = take(nK * es);
+    L.post = take((size_t)P.n * P.n * 8);
+    L.logPD = take(8);
+    L.dbg = take(dbg_cells * 8);
+    L.total = o;
+    return L;
+}
+
+// Distinct values of q = prod of at most d arities (capped at 65536 cells) and
+// of q * r for every arity r: the rows of the lgamma table.
+std::vector<double> denominators(const std::vector<uint8_t>& arity, int d)
+{
+    std::set<std::pair<uint32_t, int>> st{{1u, 0}};
+    for (uint8_t r : arity) {
+        std::vector<std::pair<uint32_t, int>> add;
+        for (auto& pc : st)
+            if (pc.second < d && (uint64_t)pc.first * r <= 65536u) add.push_back({pc.first * r, pc.second + 1});
+        for (auto& a : add) st.insert(a);
+        if (st.size() > 200000) break;
+    }
+    std::set<uint32_t> qs;
+    for (auto& pc : st) qs.insert(pc.first);
+    std::set<uint32_t> rs(arity.begin(), arity.end());
+    std::set<double> D;
+    for (uint32_t q : qs) {
+        D.insert((double)q);
+        for (uint32_t r : rs)
+            if ((uint64_t)q * r <= 65536u) D.insert((double)q * r);
+    }
+    return std::vector<double>(D.begin(), D.end());
+}
+
+int validate_and_plan(const bn_job_desc* j, HostJob& hj)
+{
+    if (!j) return BN_EINVAL;
+    if (j->n < 1 || j->n > 31 || j->d < 0 || j->m < 0 || !j->arity) return BN_EINVAL;
+    if (j->m > 0 && !j->data) return BN_EINVAL;
+    if (!(j->ess > 0.0) || !std::isfinite(j->ess)) return BN_EINVAL;
+    if (j->precision != BN_FP64 && j->precision != BN_FP32_SHIFTED) return BN_EINVAL;
+    Plan& P = hj.P;
+    P.n = j->n;
+    P.d = std::min(j->d, j->n - 1);
+    P.m = j->m;
+    P.prec = j->precision == BN_FP64 ? 0 : 1;
+    hj.arity.assign(j->arity, j->arity + P.n);
+    for (uint8_t r : hj.arity)
+        if (r < 1) return BN_EINVAL;
+    // largest family: the d+1 largest arities
+    std::vector<uint32_t> sorted(hj.arity.begin(), hj.arity.end());
+    std::sort(sorted.rbegin(), sorted.rend());
+    uint64_t cells = 1;
+    for (int t = 0; t <= P.d && t < P.n; ++t) cells *= sorted[t];
+    if (cells > 65536u) return BN_EINVAL;
+    if (j->log_rho) {
+        hj.log_rho.assign(j->log_rho, j->log_rho + (j->d + 1));
+        hj.log_rho.resize(P.d + 1);
+        for (double x : hj.log_rho)
+            if (!std::isfinite(x)) return BN_EINVAL;
+    }
+    hj.ess = j->ess;
+    hj.data = j->data;
+    hj.data_on_device = j->data_on_device != 0;
+    if (!hj.data_on_device && P.m > 0) {
+        for (size_t s = 0; s < (size_t)P.m * P.n; ++s)
+            if (j->data[s] >= hj.arity[s % P.n]) return BN_EINVAL;
+    }
+    P.K = families(P.n, P.d);
+    P.W = std::max(1, (P.m + 63) / 64);
+    P.rmax = (int)sorted[0];
+    hj.Dvals = denominators(hj.arity, P.d);
+    if (hj.Dvals.size() > 16384) return BN_EINVAL;
+    P.rows = (int)hj.Dvals.size();
+    P.b_up = std::min(P.n - 1, 12);
+    P.b_g = std::min(P.n - 1, 13);
+    const int hg = P.n - 1 - P.b_g;
+    P.hc_g = std::min(hg, 12);
+    uint64_t nl = 0;
+    for (int k = 0; k <= P.d && k <= P.b_g; ++k) nl += host_binom(P.b_g, k);
+    P.nlow_g = (uint32_t)nl;
+    P.wb = std::min(P.n, 5);
+    return BN_OK;
+}
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return BN_ECUDA;       \
+    } while (0)
+
+// Event set of one job: [0] start, [1] scores, [2] up-zeta, [3] F, [4] R',
+// [5 + 2v] Gamma phase 1 of v, [6 + 2v] phase 2 of v, [5 + 2n] edges.
+constexpr int kEvents = 6 + 2 * 31;
+struct Events {
+    cudaEvent_t ev[kEvents] = {};
+    bool ok = false;
+    Plan P{};
+    int launches = 0;
+    int create()
+    {
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return BN_ECUDA;
+        ok = true;
+        return BN_OK;
+    }
+    void destroy()
+    {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        ok = false;
+    }
+    cudaEvent_t last() const { return ev[5 + 2 * P.n]; }
+};
+
+struct Bufs {
+    char* base = nullptr;
+    Layout L{};
+    template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+};
+
+// Enqueue steps 1-5 on stream s.  Small host arrays go through `stage`
+// (pinned, >= stage_bytes) when given, else through pageable copies.
+int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_dev,
+            cudaStream_t s, Events* ev, int* launches, char* stage, size_t stage_bytes,
+            bool upload_tables = true)
+{
+    const Plan& P = hj.P;
+    const Layout& L = B.L;
+    int nl = 0;
+    if (ev) CK(cudaEventRecord(ev->ev[0], s));
+    // inputs
+    const uint8_t* data_dev = B.at<uint8_t>(L.data);
+    if (P.m > 0) {
+        if (hj.data_on_device) {
+            data_dev = hj.data;
+        } else {
+            CK(cudaMemcpyAsync(B.at<uint8_t>(L.data), hj.data, (size_t)P.m * P.n,
+                               cudaMemcpyHostToDevice, s));
+        }
+    }
+    // small tables: arity | log_rho | Dvals | alpha
+    std::vector<char> small;
+    const size_t n_ar = al(P.n), n_lr = al((size_t)(P.d + 1) * 8), n_dv = al((size_t)P.rows * 8);
+    small.resize(n_ar + n_lr + 2 * n_dv);
+    std::memcpy(small.data(), hj.arity.data(), P.n);
+    std::vector<double> lr(P.d + 1, 0.0);
+    for (size_t t = 0; t < hj.log_rho.size(); ++t) lr[t] = hj.log_rho[t];
+    std::memcpy(small.data() + n_ar, lr.data(), lr.size() * 8);
+    std::memcpy(small.data() + n_ar + n_lr, hj.Dvals.data(), hj.Dvals.size() * 8);
+    std::vector<double> alpha(P.rows);
+    for (int r = 0; r < P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
+    std::memcpy(small.data() + n_ar + n_lr + n_dv, alpha.data(), alpha.size() * 8);
+    const char* src = small.data();
+    if (upload_tables && stage && stage_bytes >= small.size()) {
+        std::memcpy(stage, small.data(), small.size());
+        src = stage;
+    }
+    if (upload_tables) {
+        CK(cudaMemcpyAsync(B.at<char>(L.arity), src, n_ar, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(B.at<char>(L.log_rho), src + n_ar, n_lr, cudaMemcpyHostToDevice, s));
+        // L.alpha directly follows L.Dvals (both rows*8 rounded to 256)
+        CK(cudaMemcpyAsync(B.at<char>(L.Dvals), src + n_ar + n_lr, 2 * n_dv,
+                           cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemsetAsync(B.at<int>(L.err), 0, 4, s));
+    int* err = B.at<int>(L.err);
+    const uint8_t* ar = B.at<uint8_t>(L.arity);
+    if (hj.data_on_device) { CK(bn::launch_check_data(data_dev, ar, P.n, P.m, err, s)); ++nl; }
+    CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s)); ++nl;
+    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, B.at<double>(L.lgT), s)); ++nl;
+    CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals),
+                         B.at<double>(L.lgT), hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho),
+                         0, (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
+                         B.at<double>(L.logB), nullptr, s)); ++nl;
+    CK(bn::launch_node_max(P, B.at<double>(L.logB), B.at<double>(L.cmax), s)); ++nl;
+    CK(bn::launch_shift_scores(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<void>(L.lbs), s)); ++nl;
+    if (ev) CK(cudaEventRecord(ev->ev[1], s));
+    CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), B.at<void>(L.lbs), B.at<void>(L.A), s)); ++nl;
+    if (ev) CK(cudaEventRecord(ev->ev[2], s));
+    CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
+    if (ev) CK(cudaEventRecord(ev->ev[3], s));
+    CK(bn::launch_backward(P, B.at<void>(L.A), B.at<void>(L.Rc), s, &nl));
+    if (ev) CK(cudaEventRecord(ev->ev[4], s));
+    const size_t es = P.prec == 0 ? 8 : 4;
+    for (int v = 0; v < P.n; ++v) {
+        CK(bn::launch_gamma_p1(P, v, B.at<void>(L.F), B.at<void>(L.Rc), B.at<void>(L.W), s));
+        if (ev) CK(cudaEventRecord(ev->ev[5 + 2 * v], s));
+        CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<char>(L.Gam) + (size_t)v * P.K * es, s));
+        if (ev) CK(cudaEventRecord(ev->ev[6 + 2 * v], s));
+        nl += 2;
+    }
+    CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
+                        B.at<void>(L.Gam), B.at<void>(L.F), err, post_dev, logPD_dev, s)); ++nl;
+    if (ev) CK(cudaEventRecord(ev->ev[5 + 2 * P.n], s));
+    if (launches) *launches = nl;
+    if (ev) {
+        ev->P = P;
+        ev->launches = nl;
+    }
+    return BN_OK;
+}
+
+double alg_bytes(const Plan& P)
+{
+    const double es = P.prec == 0 ? 8.0 : 4.0;
+    const double N = std::ldexp(1.0, P.n);
+    // A written once and read by F and by R'; F and R' written and read once;
+    // the halves of F and R' read for every endpoint v.
+    return es * (1.5 * P.n * N + 4.0 * N + P.n * N);
+}
+
+void fill_stats(const Plan& P, Events& ev, int launches, bn_stats* st)
+{
+    std::memset(st, 0, sizeof(*st));
+    auto el = [&](int a, int b) {
+        float t = 0;
+        cudaEventElapsedTime(&t, ev.ev[a], ev.ev[b]);
+        return (double)t;
+    };
+    st->ms_scores = el(0, 1);
+    st->ms_upzeta = el(1, 2);
+    st->ms_forward = el(2, 3);
+    st->ms_backward = el(3, 4);
+    for (int v = 0; v < P.n; ++v) {
+        st->ms_gamma_p1 += el(v == 0 ? 4 : 4 + 2 * v, 5 + 2 * v);
+        st->ms_gamma_p2 += el(5 + 2 * v, 6 + 2 * v);
+    }
+    st->ms_edges = el(4 + 2 * P.n, 5 + 2 * P.n);
+    st->ms_total = el(0, 5 + 2 * P.n);
+    st->cells = (double)P.n * std::ldexp(1.0, P.n);
+    st->alg_bytes = alg_bytes(P);
+    st->kernels = launches;
+    st->precision = P.prec == 0 ? BN_FP64 : BN_FP32_SHIFTED;
+}
+
+enum JobState { Q_QUEUED, Q_RUNNING, Q_DONE };
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    Events ev;
+    cudaEvent_t done = nullptr;  // after the result copies
+    char* dev = nullptr;         // allocation of the running job (stream-ordered)
+    size_t bytes = 0;
+    char* pin = nullptr;         // pinned host: outputs + small-table staging
+    size_t pin_bytes = 0;
+    uint64_t job = 0;            // 0 = free
+    int launches = 0;
+};
+
+struct ServedJob {
+    HostJob hj;
+    int state = Q_QUEUED;
+    int rc = BN_OK;
+    int slot = -1;
+    size_t bytes = 0;
+    std::vector<double> post;
+    double logPD = 0;
+    bn_stats stats{};
+};
+
+}  // namespace
+
+struct bn_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    int fail_after = -1;
+    int allocs = 0;
+    cudaStream_t stream = nullptr;
+    // direct path workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    char* pin = nullptr;
+    size_t pin_bytes = 0;
+    static constexpr int kRing = 32;
+    Events ring[kRing];
+    int ring_pos = 0;            // next set to use
+    int ring_count = 0;
+    Plan last{};
+    Layout last_layout{};
+    bool have_last = false;
+    int last_launches = 0;
+    bn_stats last_stats{};
+    std::vector<char> tables_sig;   // inputs of the small tables now in ws
+    // serving
+    std::mutex mu;
+    std::vector<Slot> slots;
+    std::map<uint64_t, ServedJob> jobs;
+    std::deque<uint64_t> queue;
+    uint64_t next_id = 1;
+    uint64_t reserved = 0;
+};
+
+namespace {
+
+int dev_alloc(bn_ctx* c, void** p, size_t bytes, cudaStream_t s)
+{
+    if (c->fail_after >= 0 && c->allocs >= c->fail_after) return BN_ENOMEM;
+    cudaError_t e = s ? cudaMallocAsync(p, bytes, s) : cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return BN_ENOMEM;
+    }
+    ++c->allocs;
+    return BN_OK;
+}
+
+int ensure_ws(bn_ctx* c, size_t bytes)
+{
+    if (c->ws_bytes >= bytes) return BN_OK;
+    if (bytes > c->budget) return BN_ENOMEM;
+    if (c->ws) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    void* p = nullptr;
+    int rc = dev_alloc(c, &p, bytes, nullptr);
+    if (rc) return rc;
+    c->ws = (char*)p;
+    c->ws_bytes = bytes;
+    return BN_OK;
+}
+
+int ensure_pin(char** pin, size_t* have, size_t bytes)
+{
+    if (*have >= bytes) return BN_OK;
+    if (*pin) cudaFreeHost(*pin);
+    *pin = nullptr;
+    *have = 0;
+    if (cudaMallocHost((void**)pin, bytes) != cudaSuccess) return BN_ENOMEM;
+    *have = bytes;
+    return BN_OK;
+}
+
+size_t small_bytes(const Plan& P)
+{
+    return al(P.n) + al((size_t)(P.d + 1) * 8) + 2 * al((size_t)P.rows * 8) + 1024;
+}
+
+int run_direct(bn_ctx* c, const bn_job_desc* job, HostJob& hj, double* post_dev,
+               double* logPD_dev, cudaStream_t s)
+{
+    const Layout L = make_layout(hj.P, 0);
+    char* old_ws = c->ws;
+    int rc = ensure_ws(c, L.total);
+    if (rc) return rc;
+    rc = ensure_pin(&c->pin, &c->pin_bytes, small_bytes(hj.P) + 64);
+    if (rc) return rc;
+    Events& ev = c->ring[c->ring_pos % bn_ctx::kRing];
+    if (!ev.ok && (rc = ev.create())) return rc;
+    Bufs B{c->ws, L};
+    // The small tables (arity, log rho, lgamma rows) are uploaded only when
+    // they differ from the ones already in the workspace; the pinned staging
+    // buffer is rewritten only after earlier work has drained.
+    std::vector<char> sig;
+    auto put = [&](const void* p, size_t nb) {
+        const char* q = (const char*)p;
+        sig.insert(sig.end(), q, q + nb);
+    };
+    put(&hj.P, sizeof(Plan));
+    put(&hj.ess, sizeof(double));
+    put(hj.arity.data(), hj.arity.size());
+    put(hj.log_rho.data(), hj.log_rho.size() * 8);
+    put(hj.Dvals.data(), hj.Dvals.size() * 8);
+    const bool upload = (old_ws != c->ws) || sig != c->tables_sig;
+    if (upload) {
+        if (s != c->stream) cudaStreamSynchronize(c->stream);
+        cudaStreamSynchronize(s);
+    }
+    c->tables_sig.clear();
+    rc = enqueue(hj, B, post_dev ? post_dev : B.at<double>(L.post),
+                 logPD_dev ? logPD_dev : B.at<double>(L.logPD), s, &ev, &c->last_launches,
+                 c->pin, c->pin_bytes, upload);
+    if (rc == BN_OK) {
+        c->tables_sig = sig;
+        c->ring_pos = (c->ring_pos + 1) % bn_ctx::kRing;
+        c->ring_count = std::min(c->ring_count + 1, bn_ctx::kRing);
+    }
+    if (rc) return rc;
+    c->last = hj.P;
+    c->last_layout = L;
+    c->have_last = true;
+    (void)job;
+    return BN_OK;
+}
+
+void pump(bn_ctx* c);
+
+}  // namespace
+
+extern "C" {
+
+const char* bn_strerror(int code)
+{
+    switch (code) {
+    case BN_OK: return "ok";
+    case BN_EINVAL: return "invalid argument";
+    case BN_ENOMEM: return "out of memory (device budget)";
+    case BN_EAGAIN: return "job not finished";
+    case BN_ETIMEOUT: return "timed out";
+    case BN_EDEVICE_TIMEOUT: return "device-side wait gave up";
+    case BN_ECUDA: return "CUDA error";
+    case BN_ECANCELED: return "canceled";
+    case BN_ENOTFOUND: return "unknown job id";
+    default: return "unknown error";
+    }
+}
+
+int64_t bn_num_families(int32_t n, int32_t d) { return families(n, d); }
+
+int bn_ctx_create(bn_ctx** out, const bn_ctx_opts* o)
+{
+    if (!out) return BN_EINVAL;
+    *out = nullptr;
+    bn_ctx_opts opts{};
+    opts.device = 0;
+    opts.slots = 4;
+    opts.mem_budget = 0;
+    opts.fail_alloc_after = -1;
+    if (o) opts = *o;
+    if (opts.slots < 1 || opts.slots > 64 || opts.device < 0) return BN_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || opts.device >= ndev) {
+        cudaGetLastError();
+        return BN_ECUDA;
+    }
+    if (cudaSetDevice(opts.device) != cudaSuccess) return BN_ECUDA;
+    if (bn::set_kernel_attributes() != cudaSuccess) return BN_ECUDA;
+    bn_ctx* c = new bn_ctx();
+    c->device = opts.device;
+    c->fail_after = opts.fail_alloc_after;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->budget = opts.mem_budget ? opts.mem_budget : (uint64_t)(0.9 * (double)fr);
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return BN_ECUDA;
+    }
+    c->slots.resize(opts.slots);
+    for (auto& sl : c->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            sl.ev.create() != BN_OK || cudaEventCreate(&sl.done) != cudaSuccess) {
+            bn_ctx_destroy(c);
+            return BN_ECUDA;
+        }
+    }
+    // keep freed stream-ordered memory in the pool between served jobs
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, opts.device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return BN_OK;
+}
+
+int bn_ctx_destroy(bn_ctx* c)
+{
+    if (!c) return BN_EINVAL;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& sl : c->slots) {
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.pin) cudaFreeHost(sl.pin);
+        sl.ev.destroy();
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    if (c->ws) cudaFree(c->ws);
+    if (c->pin) cudaFreeHost(c->pin);
+    for (auto& e : c->ring) e.destroy();
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return BN_OK;
+}
+
+int bn_edge_posteriors_async(bn_ctx* c, const bn_job_desc* job, double* post_dev,
+                             double* log_PD_dev, void* stream)
+{
+    if (!c || !post_dev) return BN_EINVAL;
+    HostJob hj;
+    int rc = validate_and_plan(job, hj);
+    if (rc) return rc;
+    if (cudaSetDevice(c->device) != cudaSuccess) return BN_ECUDA;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    return run_direct(c, job, hj, post_dev, log_PD_dev, s);
+}
+
+int bn_edge_posteriors(bn_ctx* c, const bn_job_desc* job, double* post, double* log_PD)
+{
+    if (!c || !post) return BN_EINVAL;
+    HostJob hj;
+    int rc = validate_and_plan(job, hj);
+    if (rc) return rc;
+    if (cudaSetDevice(c->device) != cudaSuccess) return BN_ECUDA;
+    rc = run_direct(c, job, hj, nullptr, nullptr, c->stream);
+    if (rc) return rc;
+    const Layout& L = c->last_layout;
+    const Plan& P = hj.P;
+    int err = 0;
+    CK(cudaMemcpyAsync(post, c->ws + L.post, (size_t)P.n * P.n * 8, cudaMemcpyDeviceToHost, c->stream));
+    double lpd = 0;
+    CK(cudaMemcpyAsync(&lpd, c->ws + L.logPD, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&err, c->ws + L.err, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (err) return BN_EINVAL;
+    if (log_PD) *log_PD = lpd;
+    Events& ev = c->ring[(c->ring_pos + bn_ctx::kRing - 1) % bn_ctx::kRing];
+    fill_stats(P, ev, c->last_launches, &c->last_stats);
+    return BN_OK;
+}
+
+int bn_scores(bn_ctx* c, const bn_job_desc* job, uint32_t* parent_mask, double* log_B)
+{
+    if (!c || !parent_mask || !log_B) return BN_EINVAL;
+    HostJob hj;
+    int rc = validate_and_plan(job, hj);
+    if (rc) return rc;
+    if (cudaSetDevice(c->device) != cudaSuccess) return BN_ECUDA;
+    // scores only: a workspace big enough for step 1
+    Plan P = hj.P;
+    Layout L = make_layout(P, 0);
+    const size_t need = L.cmax;   // everything up to and including logB
+    rc = ensure_ws(c, need + al((size_t)P.n * 8));
+    if (rc) return rc;
+    rc = ensure_pin(&c->pin, &c->pin_bytes, small_bytes(P) + 64);
+    if (rc) return rc;
+    cudaStreamSynchronize(c->stream);
+    Bufs B{c->ws, L};
+    cudaStream_t s = c->stream;
+    const uint8_t* data_dev = B.at<uint8_t>(L.data);
+    if (P.m > 0) {
+        if (hj.data_on_device) data_dev = hj.data;
+        else CK(cudaMemcpyAsync(B.at<uint8_t>(L.data), hj.data, (size_t)P.m * P.n, cudaMemcpyHostToDevice, s));
+    }
+    std::vector<double> lr(P.d + 1, 0.0);
+    for (size_t t = 0; t < hj.log_rho.size(); ++t) lr[t] = hj.log_rho[t];
+    std::vector<double> alpha(P.rows);
+    for (int r = 0; r < P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
+    CK(cudaMemcpyAsync(B.at<char>(L.arity), hj.arity.data(), P.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.log_rho), lr.data(), lr.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.Dvals), hj.Dvals.data(), hj.Dvals.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.alpha), alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(B.at<int>(L.err), 0, 4, s));
+    const uint8_t* ar = B.at<uint8_t>(L.arity);
+    if (hj.data_on_device) CK(bn::launch_check_data(data_dev, ar, P.n, P.m, B.at<int>(L.err), s));
+    CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s));
+    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, B.at<double>(L.lgT), s));
+    CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals), B.at<double>(L.lgT),
+                         hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho), 0,
+                         (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
+                         B.at<double>(L.logB), nullptr, s));
+    int err = 0;
+    CK(cudaMemcpyAsync(parent_mask, B.at<char>(L.masks), (size_t)P.n * P.K * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(log_B, B.at<char>(L.logB), (size_t)P.n * P.K * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&err, B.at<char>(L.err), 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->have_last = false;
+    c->tables_sig.clear();
+    return err ? BN_EINVAL : BN_OK;
+}
+
+int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask, int64_t* counts,
+                    int64_t cells)
+{
+    if (!c || !counts) return BN_EINVAL;
+    HostJob hj;
+    int rc = validate_and_plan(job, hj);
+    if (rc) return rc;
+    Plan& P = hj.P;
+    if (i < 0 || i >= P.n || (mask >> i & 1u) || (P.n < 32 && (mask >> P.n))) return BN_EINVAL;
+    const int k = __builtin_popcount(mask);
+    if (k > P.d) return BN_EINVAL;
+    int64_t want = hj.arity[i];
+    for (int p = 0; p < P.n; ++p)
+        if (mask >> p & 1u) want *= hj.arity[p];
+    if (want != cells) return BN_EINVAL;
+    // family index in canonical order
+    const uint32_t low = (1u << i) - 1u;
+    const uint32_t cm = (mask & low) | ((mask >> 1) & ~low);
+    int64_t f = 0;
+    for (int s = 0; s < k; ++s) f += host_binom(P.n - 1, s);
+    int t = 1;
+    for (uint32_t x = cm; x; x &= x - 1, ++t) f += host_binom(__builtin_ctz(x), t);
+    if (cudaSetDevice(c->device) != cudaSuccess) return BN_ECUDA;
+    Layout L = make_layout(P, (size_t)cells);
+    rc = ensure_ws(c, L.total);
+    if (rc) return rc;
+    cudaStreamSynchronize(c->stream);
+    Bufs B{c->ws, L};
+    cudaStream_t s = c->stream;
+    const uint8_t* data_dev = B.at<uint8_t>(L.data);
+    if (P.m > 0) {
+        if (hj.data_on_device) data_dev = hj.data;
+        else CK(cudaMemcpyAsync(B.at<uint8_t>(L.data), hj.data, (size_t)P.m * P.n, cudaMemcpyHostToDevice, s));
+    }
+    std::vector<double> alpha(P.rows);
+    for (int r = 0; r < P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
+    CK(cudaMemcpyAsync(B.at<char>(L.arity), hj.arity.data(), P.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.Dvals), hj.Dvals.data(), hj.Dvals.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.alpha), alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s));
+    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, B.at<double>(L.lgT), s));
+    CK(bn::launch_scores(P, B.at<uint8_t>(L.arity), B.at<uint64_t>(L.planes), B.at<double>(L.Dvals),
+                         B.at<double>(L.lgT), nullptr, (int64_t)i * P.K + f, 1,
+                         B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks), B.at<double>(L.logB),
+                         B.at<int64_t>(L.dbg), s));
+    CK(cudaMemcpyAsync(counts, B.at<char>(L.dbg), (size_t)cells * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->have_last = false;
+    c->tables_sig.clear();
+    return BN_OK;
+}
+
+int bn_debug_stage(bn_ctx* c, int32_t stage, void* host_out, size_t bytes)
+{
+    if (!c || !host_out || !c->have_last) return BN_EINVAL;
+    const Plan& P = c->last;
+    const Layout& L = c->last_layout;
+    const size_t es = P.prec == 0 ? 8 : 4;
+    const size_t nK = (size_t)P.n * P.K;
+    size_t off = 0, want = 0;
+    switch (stage) {
+    case BN_STAGE_LOGB: off = L.logB; want = nK * 8; break;
+    case BN_STAGE_MASKS: off = L.masks; want = nK * 4; break;
+    case BN_STAGE_SHIFT: off = L.cmax; want = (size_t)P.n * 8; break;
+    case BN_STAGE_A: off = L.A; want = ((size_t)P.n << (P.n - 1)) * es; break;
+    case BN_STAGE_F: off = L.F; want = ((size_t)1 << P.n) * es; break;
+    case BN_STAGE_RC: off = L.Rc; want = ((size_t)1 << P.n) * es; break;
+    case BN_STAGE_GAMMA: off = L.Gam; want = nK * es; break;
+    default: return BN_EINVAL;
+    }
+    if (bytes != want) return BN_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(host_out, c->ws + off, want, cudaMemcpyDeviceToHost));
+    return BN_OK;
+}
+
+int bn_job_stats(bn_ctx* c, uint64_t id, bn_stats* st)
+{
+    if (!c || !st) return BN_EINVAL;
+    if (id == 0) {
+        *st = c->last_stats;
+        return BN_OK;
+    }
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->jobs.find(id);
+    if (it == c->jobs.end()) return BN_ENOTFOUND;
+    *st = it->second.stats;
+    return BN_OK;
+}
+
+int bn_stats_history(bn_ctx* c, bn_stats* out, int32_t max, int32_t* count)
+{
+    if (!c || !out || !count || max < 0) return BN_EINVAL;
+    const int k = std::min<int>(max, c->ring_count);
+    for (int t = 0; t < k; ++t) {
+        const int idx = (c->ring_pos - k + t + 2 * bn_ctx::kRing) % bn_ctx::kRing;
+        Events& ev = c->ring[idx];
+        if (cudaEventSynchronize(ev.last()) != cudaSuccess) return BN_ECUDA;
+        fill_stats(ev.P, ev, ev.launches, &out[t]);
+    }
+    *count = k;
+    return BN_OK;
+}
+
+// ---------------------------------------------------------------- serving --
+
+int bn_submit(bn_ctx* c, const bn_job_desc* job, uint64_t* id)
+{
+    if (!c || !id || !job) return BN_EINVAL;
+    if (job->data_on_device) return BN_EINVAL;   // served jobs copy host inputs
+    ServedJob sj;
+    int rc = validate_and_plan(job, sj.hj);
+    if (rc) return rc;
+    const Plan& P = sj.hj.P;
+    sj.hj.data_copy.assign(job->data ? job->data : (const uint8_t*)"",
+                           job->data ? job->data + (size_t)P.m * P.n : (const uint8_t*)"");
+    sj.hj.data = sj.hj.data_copy.data();
+    sj.bytes = make_layout(P, 0).total;
+    if (sj.bytes > c->budget) return BN_ENOMEM;
+    std::lock_guard<std::mutex> g(c->mu);
+    const uint64_t jid = c->next_id++;
+    c->jobs.emplace(jid, std::move(sj));
+    c->queue.push_back(jid);
+    *id = jid;
+    pump(c);
+    return BN_OK;
+}
+
+int bn_poll(bn_ctx* c, uint64_t id, double* post, double* log_PD)
+{
+    if (!c) return BN_EINVAL;
+    std::lock_guard<std::mutex> g(c->mu);
+    pump(c);
+    auto it = c->jobs.find(id);
+    if (it == c->jobs.end()) return BN_ENOTFOUND;
+    ServedJob& sj = it->second;
+    if (sj.state != Q_DONE) return BN_EAGAIN;
+    const int rc = sj.rc;
+    if (rc == BN_OK) {
+        if (post) std::memcpy(post, sj.post.data(), sj.post.size() * 8);
+        if (log_PD) *log_PD = sj.logPD;
+    }
+    c->last_stats = sj.stats;
+    c->jobs.erase(it);
+    return rc;
+}
+
+int bn_wait(bn_ctx* c, uint64_t id, double timeout_s, double* post, double* log_PD)
+{
+    if (!c) return BN_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const int rc = bn_poll(c, id, post, log_PD);
+        if (rc != BN_EAGAIN) return rc;
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el >= timeout_s) return BN_ETIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int bn_cancel(bn_ctx* c, uint64_t id)
+{
+    if (!c) return BN_EINVAL;
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->jobs.find(id);
+    if (it == c->jobs.end()) return BN_ENOTFOUND;
+    if (it->second.state != Q_QUEUED) return BN_EAGAIN;
+    c->queue.erase(std::find(c->queue.begin(), c->queue.end(), id));
+    it->second.state = Q_DONE;
+    it->second.rc = BN_ECANCELED;
+    return BN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Retire finished jobs, then admit queued jobs (first fit) while a slot and
+// enough of the memory budget are free.  Called with c->mu held.
+void pump(bn_ctx* c)
+{
+    cudaSetDevice(c->device);
+    for (size_t k = 0; k < c->slots.size(); ++k) {
+        Slot& sl = c->slots[k];
+        if (!sl.job) continue;
+        if (cudaEventQuery(sl.done) == cudaErrorNotReady) continue;
+        cudaGetLastError();
+        ServedJob& sj = c->jobs[sl.job];
+        const Plan& P = sj.hj.P;
+        cudaStreamSynchronize(sl.stream);
+        int err = 0;
+        std::memcpy(&err, sl.pin + (size_t)P.n * P.n * 8 + 8, 4);
+        sj.post.assign((double*)sl.pin, (double*)sl.pin + (size_t)P.n * P.n);
+        std::memcpy(&sj.logPD, sl.pin + (size_t)P.n * P.n * 8, 8);
+        fill_stats(P, sl.ev, sl.launches, &sj.stats);
+        sj.rc = err ? BN_EINVAL : sj.rc;
+        sj.state = Q_DONE;
+        c->reserved -= sl.bytes;
+        sl.bytes = 0;
+        sl.dev = nullptr;
+        sl.job = 0;
+    }
+    for (auto it = c->queue.begin(); it != c->queue.end();) {
+        int free_slot = -1;
+        for (size_t k = 0; k < c->slots.size(); ++k)
+            if (!c->slots[k].job) { free_slot = (int)k; break; }
+        if (free_slot < 0) break;
+        ServedJob& sj = c->jobs[*it];
+        if (c->reserved + sj.bytes > c->budget) { ++it; continue; }
+        Slot& sl = c->slots[free_slot];
+        const Plan& P = sj.hj.P;
+        const size_t out_bytes = (size_t)P.n * P.n * 8 + 16;
+        int rc = ensure_pin(&sl.pin, &sl.pin_bytes, out_bytes + small_bytes(P) + 64);
+        void* dev = nullptr;
+        if (!rc) rc = dev_alloc(c, &dev, sj.bytes, sl.stream);
+        if (!rc) {
+            Layout L = make_layout(P, 0);
+            Bufs B{(char*)dev, L};
+            rc = enqueue(sj.hj, B, B.at<double>(L.post), B.at<double>(L.logPD), sl.stream, &sl.ev,
+                         &sl.launches, sl.pin + al(out_bytes), sl.pin_bytes - al(out_bytes));
+            if (!rc) {
+                if (cudaMemcpyAsync(sl.pin, B.at<char>(L.post), (size_t)P.n * P.n * 8, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+                    cudaMemcpyAsync(sl.pin + (size_t)P.n * P.n * 8, B.at<char>(L.logPD), 8, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+                    cudaMemcpyAsync(sl.pin + (size_t)P.n * P.n * 8 + 8, B.at<char>(L.err), 4, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+                    cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
+                    rc = BN_ECUDA;
+            }
+            cudaFreeAsync(dev, sl.stream);   // stream-ordered: after the job's work
+        }
+        if (rc) {
+            sj.state = Q_DONE;
+            sj.rc = rc;
+            it = c->queue.erase(it);
+            continue;
+        }
+        sl.job = *it;
+        sl.bytes = sj.bytes;
+        c->reserved += sj.bytes;
+        sj.state = Q_RUNNING;
+        sj.slot = free_slot;
+        it = c->queue.erase(it);
+    }
+}
+
+}  // namespace

@@ -1,0 +1,74 @@
+"""CPU checks of the C-ABI library: it loads, exports every function that
+include/bnedge.h declares, and its host-only entry points behave.  No compute
+call is made (there is no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import oracle as orc
+from paper_1408_1664_gb300 import binding as B
+from paper_1408_1664_gb300 import build as Bld
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(bn_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    Bld.build()
+    return B.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert "bn_edge_posteriors" in names and "bn_submit" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(B.EXPORTS) <= set(names)
+
+
+def test_num_families_matches_oracle(lib):
+    for n in range(1, 32):
+        for d in range(0, 6):
+            assert B.bn_num_families(n, d) == orc.num_families(n, d)
+    assert B.bn_num_families(0, 1) == 0 and B.bn_num_families(5, -1) == 0
+
+
+def test_strerror_names_codes(lib):
+    assert B.bn_strerror(0) == "ok"
+    for code in range(-8, 0):
+        assert B.bn_strerror(code) not in ("", "unknown error")
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.bn_ctx_create(None, None) == B.BN_EINVAL
+    assert lib.bn_ctx_destroy(None) == B.BN_EINVAL
+    assert lib.bn_edge_posteriors(None, None, None, None) == B.BN_EINVAL
+    assert lib.bn_job_stats(None, 0, None) == B.BN_EINVAL
+
+
+def test_structure_layouts_match_header(lib):
+    # 4 int32 + 2 pointers + double + pointer + 2 int32 on LP64
+    assert ctypes.sizeof(B.bn_job_desc) == 16 + 16 + 8 + 8 + 8
+    assert ctypes.sizeof(B.bn_ctx_opts) == 4 + 4 + 8 + 4 + 4
+    assert ctypes.sizeof(B.bn_stats) == 10 * 8 + 8
+
+
+def test_product_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1408_1664_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower() or f == "datagen.py", f
