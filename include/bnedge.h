@@ -142,6 +142,30 @@ int bn_edge_posteriors_async(bn_ctx* ctx, const bn_job_desc* job,
                              double* post_dev, double* log_PD_dev,
                              void* stream);
 
+/* No-allocation variant of bn_edge_posteriors_async (the paper has no
+ * counterpart; this serves callers that must not allocate device memory:
+ * code running inside a CUDA graph capture, where cudaMalloc is not allowed;
+ * applications that own and partition all GPU memory themselves; loops that
+ * cannot afford the device-wide synchronisation of cudaFree).
+ *
+ * Needs no context.  Every intermediate array lives in one file-scope device
+ * array of BN_STATIC_SCRATCH_BYTES (64 MiB) that every GPU loading this
+ * library holds until the process exits.  Jobs whose arrays do not fit it
+ * (roughly n > 19 on the FP64 path, n > 20 on the FP32 path) are rejected
+ * with BN_ENOMEM before any GPU work.  Runs on the current device, enqueued
+ * on `stream` (a cudaStream_t, NULL = the legacy default stream).  The first
+ * call on a device looks up the array's device address for that device; make
+ * that first call before any stream capture begins.  job->data may be host
+ * or device memory (host data and the small tables are copied with
+ * cudaMemcpyAsync from pageable memory); post_dev (n*n doubles) and
+ * log_PD_dev (one double, or NULL) are device memory owned by the caller.
+ * All calls on a device share the array and it keeps the previous call's
+ * contents: calls whose GPU work may overlap (different streams without
+ * ordering) race and give undefined results. */
+#define BN_STATIC_SCRATCH_BYTES (64u << 20)
+int bn_edge_posteriors_static(const bn_job_desc* job, double* post_dev,
+                              double* log_PD_dev, void* stream);
+
 /* Serving.  bn_submit copies the inputs, admits the job when a slot and
  * enough device memory (by its n*2^n footprint) are free -- queuing it
  * otherwise -- and returns at once.  Jobs in different slots run

@@ -56,7 +56,7 @@ _lib = None
 EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_edge_posteriors", "bn_edge_posteriors_async", "bn_submit", "bn_poll", "bn_wait",
            "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror", "bn_debug_stage",
-           "bn_debug_counts"]
+           "bn_debug_counts", "bn_edge_posteriors_static"]
 
 
 def library_path() -> str:
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_scores": (C.c_int, [P, C.POINTER(bn_job_desc), P, P]),
         "bn_edge_posteriors": (C.c_int, [P, C.POINTER(bn_job_desc), P, P]),
         "bn_edge_posteriors_async": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
+        "bn_edge_posteriors_static": (C.c_int, [C.POINTER(bn_job_desc), P, P, P]),
         "bn_submit": (C.c_int, [P, C.POINTER(bn_job_desc), C.POINTER(C.c_uint64)]),
         "bn_poll": (C.c_int, [P, C.c_uint64, P, P]),
         "bn_wait": (C.c_int, [P, C.c_uint64, C.c_double, P, P]),
@@ -184,6 +185,15 @@ def bn_edge_posteriors_async(ctx: int, job: Job, post_dev, log_PD_dev=None, stre
                                          _ptr(log_PD_dev), _ptr(stream))
     if rc:
         raise BnError(rc, "bn_edge_posteriors_async")
+
+
+def bn_edge_posteriors_static(job: Job, post_dev, log_PD_dev=None, stream=None) -> None:
+    """No-allocation variant: all intermediates in the library's fixed device
+    scratch array (for callers that cannot allocate device memory)."""
+    rc = load().bn_edge_posteriors_static(C.byref(job.desc), _ptr(post_dev), _ptr(log_PD_dev),
+                                          _ptr(stream))
+    if rc:
+        raise BnError(rc, "bn_edge_posteriors_static")
 
 
 def bn_scores(ctx: int, job: Job):
