@@ -210,12 +210,12 @@ def large_runs(ctx):
 def test_large_properties_and_fp32_vs_fp64(large_runs):
     ds, d, p32, l32, p64, l64 = large_runs
     n = ds.n
-    for P in (p32, p64):
+    for P, tol in ((p32, 1e-4), (p64, 1e-9)):
         assert np.all(np.isfinite(P))
-        assert np.all(P >= 0) and np.all(P <= 1 + 1e-9)
+        assert np.all(P >= 0) and np.all(P <= 1 + tol)
         assert np.all(np.diag(P) == 0)
-        assert np.all(P + P.T <= 1 + 1e-6)
-        assert np.all(P.sum(axis=0) <= d + 1e-6)
+        assert np.all(P + P.T <= 1 + 2 * tol)           # acyclic: not both ways
+        assert np.all(P.sum(axis=0) <= d + n * tol)     # in-degree bound
     err = float(np.abs(p32 - p64).max())
     print(f"n=26 max |fp32 - fp64| = {err:.3e}")
     assert err < 1e-4
