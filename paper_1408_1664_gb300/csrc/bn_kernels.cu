@@ -173,6 +173,197 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
     (void)d;
 }
 
+// Scores with one warp per family and one lane per 64-sample word (m <= 2048):
+// every lane keeps its word of each parent plane and child plane in
+// registers, so a cell costs an AND chain, a popc and one warp reduction.
+// Lane c % 32 keeps the count of cell c and adds its lgamma-table term when a
+// run of 32 cells is complete (FP64 adds in a fixed order).
+template <int MP, int MR>
+__global__ void __launch_bounds__(256)
+k_scores_w(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__ arity,
+           const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
+           const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
+           int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
+           double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool has_word = lane < W;
+    for (int64_t xi = warp0; xi < x_count; xi += nwarps) {
+        const int64_t x = x_begin + xi;
+        const int i = (int)(x / K);
+        uint32_t f = (uint32_t)(x % K);
+        int k = 0;
+        while (f >= binom(n - 1, k)) { f -= binom(n - 1, k); ++k; }
+        const uint32_t cm = colex_unrank(f, k, n - 1);
+        const uint32_t G = expand(cm, i);
+        uint64_t pw[MP][MR];
+        int rad[MP];
+        uint32_t g = G;
+        int q = 1;
+#pragma unroll
+        for (int t = 0; t < MP; ++t) {
+            rad[t] = 1;
+#pragma unroll
+            for (int v = 0; v < MR; ++v) pw[t][v] = (v == 0) ? ~0ull : 0ull;
+            if (t < k) {
+                const int p = __ffs(g) - 1;
+                g &= g - 1;
+                rad[t] = arity[p];
+                q *= rad[t];
+#pragma unroll
+                for (int v = 0; v < MR; ++v)
+                    pw[t][v] = (v < rad[t] && has_word) ? planes[((size_t)p * rmax + v) * W + lane] : 0ull;
+            }
+        }
+        const int ri = arity[i];
+        uint64_t cw[MR];
+#pragma unroll
+        for (int v = 0; v < MR; ++v)
+            cw[v] = (v < ri && has_word) ? planes[((size_t)i * rmax + v) * W + lane] : 0ull;
+        const double* Tq = T + (size_t)find_row(Dvals, rows, (double)q) * (m + 1);
+        const double* Tqr = T + (size_t)find_row(Dvals, rows, (double)q * ri) * (m + 1);
+        int dig[MP];
+#pragma unroll
+        for (int t = 0; t < MP; ++t) dig[t] = 0;
+        double acc = 0.0;
+        uint32_t cur = 0, curj = 0;
+        int cell = 0;
+        for (int cfg = 0; cfg < q; ++cfg) {
+            uint64_t M = ~0ull;
+#pragma unroll
+            for (int t = 0; t < MP; ++t) {
+                uint64_t w = pw[t][0];
+#pragma unroll
+                for (int v = 1; v < MR; ++v)
+                    if (dig[t] == v) w = pw[t][v];
+                M &= w;
+            }
+            uint32_t Nj = 0;
+#pragma unroll
+            for (int v = 0; v < MR; ++v) {
+                if (v < ri) {
+                    const uint32_t N = __reduce_add_sync(FULL, (uint32_t)__popcll(M & cw[v]));
+                    Nj += N;
+                    if (lane == (cell & 31)) {
+                        cur = N;
+                        if (debug_counts) debug_counts[cell] = N;
+                    }
+                    if ((cell & 31) == 31) acc += Tqr[cur];
+                    ++cell;
+                }
+            }
+            if (lane == (cfg & 31)) curj = Nj;
+            if ((cfg & 31) == 31) acc -= Tq[curj];
+            bool carry = true;
+#pragma unroll
+            for (int t = 0; t < MP; ++t) {
+                if (carry) {
+                    if (++dig[t] < rad[t]) carry = false;
+                    else dig[t] = 0;
+                }
+            }
+        }
+        if ((cell & 31) != 0 && lane < (cell & 31)) acc += Tqr[cur];
+        if ((q & 31) != 0 && lane < (q & 31)) acc -= Tq[curj];
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+            masks[x] = G;
+            cmasks[x] = cm;
+        }
+    }
+}
+
+// Register version of k_scores for at most 8 parents and child arity at most
+// 8: one warp per family, one lane per parent configuration j.  The lane
+// ANDs the planes of its configuration's parent values word by word and
+// counts each child value with popc, then adds its own BDeu terms
+//   -T_q(N_j) + sum_k T_qr(N_jk);
+// the warp sum gives log B.  No cross-lane step per cell.
+constexpr int SC_MP = 8, SC_MR = 8;
+__global__ void __launch_bounds__(256)
+k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__ arity,
+             const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
+             const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
+             int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
+             double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t xi = warp0; xi < x_count; xi += nwarps) {
+        const int64_t x = x_begin + xi;
+        const int i = (int)(x / K);
+        uint32_t f = (uint32_t)(x % K);
+        int k = 0;
+        while (f >= binom(n - 1, k)) { f -= binom(n - 1, k); ++k; }
+        const uint32_t cm = colex_unrank(f, k, n - 1);
+        const uint32_t G = expand(cm, i);
+        int par[SC_MP], rad[SC_MP];
+        uint32_t g = G;
+        int q = 1;
+#pragma unroll
+        for (int t = 0; t < SC_MP; ++t) {
+            par[t] = 0;
+            rad[t] = 1;
+            if (g) {
+                par[t] = __ffs(g) - 1;
+                g &= g - 1;
+                rad[t] = arity[par[t]];
+                q *= rad[t];
+            }
+        }
+        const int ri = arity[i];
+        const double* Tq = T + (size_t)find_row(Dvals, rows, (double)q) * (m + 1);
+        const double* Tqr = T + (size_t)find_row(Dvals, rows, (double)q * ri) * (m + 1);
+        const uint64_t* cp = planes + (size_t)i * rmax * W;
+        double acc = 0.0;
+        for (int j0 = 0; j0 < q; j0 += 32) {
+            const int j = j0 + lane;
+            if (j < q) {
+                const uint64_t* pp[SC_MP];
+                int jj = j;
+#pragma unroll
+                for (int t = 0; t < SC_MP; ++t) {
+                    const int dg = jj % rad[t];
+                    jj /= rad[t];
+                    pp[t] = planes + ((size_t)par[t] * rmax + dg) * W;
+                }
+                uint32_t N[SC_MR];
+#pragma unroll
+                for (int xv = 0; xv < SC_MR; ++xv) N[xv] = 0;
+                for (int w = 0; w < W; ++w) {
+                    uint64_t M = ~0ull;
+#pragma unroll
+                    for (int t = 0; t < SC_MP; ++t)
+                        if (t < k) M &= pp[t][w];
+#pragma unroll
+                    for (int xv = 0; xv < SC_MR; ++xv)
+                        if (xv < ri) N[xv] += (uint32_t)__popcll(M & cp[(size_t)xv * W + w]);
+                }
+                uint32_t Nj = 0;
+#pragma unroll
+                for (int xv = 0; xv < SC_MR; ++xv) {
+                    if (xv < ri) {
+                        acc += Tqr[N[xv]];
+                        Nj += N[xv];
+                        if (debug_counts) debug_counts[(int64_t)j * ri + xv] = N[xv];
+                    }
+                }
+                acc -= Tq[Nj];
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+            masks[x] = G;
+            cmasks[x] = cm;
+        }
+    }
+}
+
 // cmax[i] = max_f logB[i*K + f]; one block per node.
 __global__ void k_node_max(int64_t K, const double* __restrict__ logB, double* __restrict__ cmax)
 {
@@ -286,94 +477,158 @@ k_upzeta(int n, int b, int64_t K, int qbits, const uint32_t* __restrict__ cmasks
 //   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),       R'(V) = 1
 // where R'(T) = R(V - T) turns Eq. 10 into a recursion over T.
 // ===========================================================================
+// Next subset with the same number of elements in increasing value order
+// (the colexicographic successor); x != 0.
+__device__ __forceinline__ uint32_t colex_next(uint32_t x)
+{
+    const uint32_t u = x & (0u - x);
+    const uint32_t v = x + u;
+    return v | (((v ^ x) >> 2) >> (__ffs(u) - 1));
+}
+
+// log-sum-exp of the in-tile terms of one lane: X and a[i] + nb[i] for the
+// in-tile bits selected by `use` (at most 5).
+template <typename T>
+__device__ __forceinline__ T lse_in_tile(T X, const T (&a)[5], const T (&nb)[5], uint32_t use)
+{
+    using L = LogOps<T>;
+    T t[5];
+    T m = X;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        t[i] = (use >> i & 1u) ? a[i] + nb[i] : L::ninf();
+        m = t[i] > m ? t[i] : m;
+    }
+    if (m == L::ninf()) return m;
+    T s = L::ex(X - m);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) s += L::ex(t[i] - m);
+    return m + L::lg(s);
+}
+
+// A warp owns 2^wb consecutive subsets (one per lane); the tile's high bits
+// Ht are the same for every lane, so the terms across tiles run over the set
+// bits of Ht with warp-uniform addresses.  Each warp walks `tpw` tiles in
+// colexicographic order of Ht.  A is read once, with a streaming hint so
+// that F and R' stay in L2 for the next level.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_forward_level(int n, int wb, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ F)
+k_forward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __restrict__ A,
+                T* __restrict__ F)
 {
     using L = LogOps<T>;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp >= ntiles) return;
-    const uint32_t Ht = colex_unrank(warp, hl, n - wb);
+    const uint32_t first = warp * (uint32_t)tpw;
+    if (first >= ntiles) return;
+    const int nh = n - wb;
     const uint32_t lb = (uint32_t)lane & ((1u << wb) - 1u);
     const bool active = lane < (1 << wb);
-    const uint32_t S = (Ht << wb) | lb;
     const size_t half = (size_t)1 << (n - 1);
-    LseAcc<T> X;
-    T a[5];
-    if (active) {
-        for (int i = wb; i < n; ++i) {
-            if (S >> i & 1u) {
-                const uint32_t Si = S & ~(1u << i);
-                X.add(A[(size_t)i * half + squeeze(Si, i)] + F[Si]);
+    uint32_t Ht = colex_unrank(first, hl, nh);
+    for (uint32_t tile = first; tile < ntiles && tile < first + (uint32_t)tpw; ++tile) {
+        const uint32_t S = (Ht << wb) | lb;
+        // terms across tiles: i = wb + j for the set bits j of Ht
+        T m = L::ninf(), sum = T(0);
+        {
+            T x[26];
+            int cnt = 0;
+            uint32_t rest = Ht;
+#pragma unroll
+            for (int q = 0; q < 26; ++q) {
+                if (!rest) break;
+                const int j = __ffs(rest) - 1;
+                rest &= rest - 1;
+                const int i = wb + j;
+                const uint32_t Hm = Ht & ~(1u << j);
+                const T* Ai = A + (size_t)i * half + ((size_t)squeeze(Hm, j) << wb);
+                const T* Fi = F + ((size_t)Hm << wb);
+                x[q] = active ? __ldcs(Ai + lb) + Fi[lb] : L::ninf();
+                m = x[q] > m ? x[q] : m;
+                cnt = q + 1;
             }
+#pragma unroll
+            for (int q = 0; q < 26; ++q)
+                if (q < cnt) sum += L::ex(x[q] - m);
         }
-    }
+        const T X = (m == L::ninf()) ? m : m + L::lg(sum);
+        T a[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        a[i] = L::ninf();
-        if (i < wb && active && (S >> i & 1u))
-            a[i] = A[(size_t)i * half + squeeze(S & ~(1u << i), i)];
-    }
-    T Fv = (S == 0u) ? T(0) : X.value();
-    for (int l = 1; l <= wb; ++l) {
-        T nb[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Fv, 1 << i);
-        if (active && __popc(lb) == l) {
-            LseAcc<T> acc = X;
-#pragma unroll
-            for (int i = 0; i < 5; ++i)
-                if (i < wb && (lb >> i & 1u)) acc.add(a[i] + nb[i]);
-            Fv = acc.value();
+        for (int i = 0; i < 5; ++i) {
+            a[i] = L::ninf();
+            if (i < wb && active && (S >> i & 1u))
+                a[i] = __ldcs(A + (size_t)i * half + squeeze(S & ~(1u << i), i));
         }
+        T Fv = (S == 0u) ? T(0) : X;
+        for (int l = 1; l <= wb; ++l) {
+            T nb[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Fv, 1 << i);
+            if (active && __popc(lb) == l) Fv = lse_in_tile(X, a, nb, lb);
+        }
+        if (active) F[S] = Fv;
+        if (Ht) Ht = colex_next(Ht);
     }
-    if (active) F[S] = Fv;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_backward_level(int n, int wb, int hl, uint32_t ntiles, const T* __restrict__ A,
+k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __restrict__ A,
                  T* __restrict__ Rc)
 {
     using L = LogOps<T>;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp >= ntiles) return;
-    const uint32_t Ht = colex_unrank(warp, hl, n - wb);
+    const uint32_t first = warp * (uint32_t)tpw;
+    if (first >= ntiles) return;
+    const int nh = n - wb;
     const uint32_t wmask = (1u << wb) - 1u;
     const uint32_t lb = (uint32_t)lane & wmask;
     const bool active = lane < (1 << wb);
-    const uint32_t Tm = (Ht << wb) | lb;
-    const uint32_t full = (n == 32) ? 0xffffffffu : ((1u << n) - 1u);
+    const uint32_t full = (1u << n) - 1u;
+    const uint32_t hmask = (nh == 32) ? 0xffffffffu : ((1u << nh) - 1u);
     const size_t half = (size_t)1 << (n - 1);
-    LseAcc<T> X;
-    T a[5];
-    if (active) {
-        for (int i = wb; i < n; ++i) {
-            if (!(Tm >> i & 1u))
-                X.add(A[(size_t)i * half + squeeze(Tm, i)] + Rc[Tm | (1u << i)]);
+    uint32_t Ht = colex_unrank(first, hl, nh);
+    for (uint32_t tile = first; tile < ntiles && tile < first + (uint32_t)tpw; ++tile) {
+        const uint32_t Tm = (Ht << wb) | lb;
+        T m = L::ninf(), sum = T(0);
+        {
+            T x[26];
+            int cnt = 0;
+            uint32_t rest = ~Ht & hmask;
+#pragma unroll
+            for (int q = 0; q < 26; ++q) {
+                if (!rest) break;
+                const int j = __ffs(rest) - 1;
+                rest &= rest - 1;
+                const int i = wb + j;
+                const T* Ai = A + (size_t)i * half + ((size_t)squeeze(Ht, j) << wb);
+                const T* Ri = Rc + ((size_t)(Ht | (1u << j)) << wb);
+                x[q] = active ? __ldcs(Ai + lb) + Ri[lb] : L::ninf();
+                m = x[q] > m ? x[q] : m;
+                cnt = q + 1;
+            }
+#pragma unroll
+            for (int q = 0; q < 26; ++q)
+                if (q < cnt) sum += L::ex(x[q] - m);
         }
-    }
+        const T X = (m == L::ninf()) ? m : m + L::lg(sum);
+        T a[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        a[i] = L::ninf();
-        if (i < wb && active && !(Tm >> i & 1u)) a[i] = A[(size_t)i * half + squeeze(Tm, i)];
-    }
-    T Rv = (Tm == full) ? T(0) : X.value();
-    for (int l = wb - 1; l >= 0; --l) {
-        T nb[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Rv, 1 << i);
-        if (active && __popc(lb) == l) {
-            LseAcc<T> acc = X;
-#pragma unroll
-            for (int i = 0; i < 5; ++i)
-                if (i < wb && !(lb >> i & 1u)) acc.add(a[i] + nb[i]);
-            Rv = acc.value();
+        for (int i = 0; i < 5; ++i) {
+            a[i] = L::ninf();
+            if (i < wb && active && !(Tm >> i & 1u)) a[i] = __ldcs(A + (size_t)i * half + squeeze(Tm, i));
         }
+        T Rv = (Tm == full) ? T(0) : X;
+        for (int l = wb - 1; l >= 0; --l) {
+            T nb[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Rv, 1 << i);
+            if (active && __popc(lb) == l) Rv = lse_in_tile(X, a, nb, ~lb & wmask);
+        }
+        if (active) Rc[Tm] = Rv;
+        if (Ht) Ht = colex_next(Ht);
     }
-    if (active) Rc[Tm] = Rv;
 }
 
 // ===========================================================================
@@ -584,9 +839,26 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
     const int threads = 256;
     const int64_t warps_wanted = x_count;
     int grid = grid_for(warps_wanted * 32, threads, 152 * 64);
-    k_scores<<<grid, threads, 0, s>>>(P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
-                                      P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
-                                      logB, debug_counts);
+    if (P.W <= 32 && P.d <= 4 && P.rmax <= 2)
+        k_scores_w<4, 2><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+                                                  P.rows, T, log_rho, x_begin, x_count, masks,
+                                                  cmasks, logB, debug_counts);
+    else if (P.W <= 32 && P.d <= 4 && P.rmax <= 4)
+        k_scores_w<4, 4><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+                                                  P.rows, T, log_rho, x_begin, x_count, masks,
+                                                  cmasks, logB, debug_counts);
+    else if (P.W <= 32 && P.d <= 8 && P.rmax <= 4)
+        k_scores_w<8, 4><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+                                                  P.rows, T, log_rho, x_begin, x_count, masks,
+                                                  cmasks, logB, debug_counts);
+    else if (P.d <= SC_MP && P.rmax <= SC_MR)
+        k_scores_cfg<<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+                                              P.rows, T, log_rho, x_begin, x_count, masks,
+                                              cmasks, logB, debug_counts);
+    else
+        k_scores<<<grid, threads, 0, s>>>(P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+                                          P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
+                                          logB, debug_counts);
     return cudaGetLastError();
 }
 
@@ -623,9 +895,14 @@ static int fixed_bits(int64_t terms)
     return 63 - b;
 }
 
-cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* A,
-                          cudaStream_t s)
+cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
+                          const uint16_t* rk13, void* A, cudaStream_t s)
 {
+    if (use_tile13_up(P)) {
+        cudaError_t e = launch_reorder_up(P, lbs, tab, s);
+        if (e != cudaSuccess) return e;
+        return launch_upzeta13(P, tab, rk13 + 8192, A, s);
+    }
     const int h = P.n - 1 - P.b_up;
     const unsigned grid = (unsigned)P.n << h;
     const size_t sm = upzeta_smem_bytes(P);
@@ -646,17 +923,27 @@ static uint32_t host_binom(int n, int k)
     return (uint32_t)r;
 }
 
+// Tiles per warp: enough warps to fill the GPU a few times over, at most 8.
+static int tiles_per_warp(uint32_t ntiles)
+{
+    int tpw = 1;
+    while (tpw < 8 && (uint64_t)ntiles >= (uint64_t)tpw * 2 * 152 * 64 * 4) tpw *= 2;
+    return tpw;
+}
+
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches)
 {
     const int nh = P.n - P.wb;
     for (int hl = 0; hl <= nh; ++hl) {
         const uint32_t nt = host_binom(nh, hl);
-        const unsigned grid = (unsigned)(((uint64_t)nt * 32 + 255) / 256);
+        const int tpw = tiles_per_warp(nt);
+        const uint32_t warps = (nt + tpw - 1) / tpw;
+        const unsigned grid = (unsigned)(((uint64_t)warps * 32 + 255) / 256);
         if (P.prec == 0)
-            k_forward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const double*)A,
+            k_forward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const double*)A,
                                                          (double*)F);
         else
-            k_forward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const float*)A,
+            k_forward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const float*)A,
                                                         (float*)F);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -670,12 +957,14 @@ cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t
     const int nh = P.n - P.wb;
     for (int hl = nh; hl >= 0; --hl) {
         const uint32_t nt = host_binom(nh, hl);
-        const unsigned grid = (unsigned)(((uint64_t)nt * 32 + 255) / 256);
+        const int tpw = tiles_per_warp(nt);
+        const uint32_t warps = (nt + tpw - 1) / tpw;
+        const unsigned grid = (unsigned)(((uint64_t)warps * 32 + 255) / 256);
         if (P.prec == 0)
-            k_backward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const double*)A,
-                                                          (double*)Rc);
+            k_backward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw,
+                                                          (const double*)A, (double*)Rc);
         else
-            k_backward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, (const float*)A,
+            k_backward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const float*)A,
                                                          (float*)Rc);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -698,9 +987,10 @@ size_t gamma_p2_smem_bytes(const Plan& P)
     return ((size_t)1 << P.hc_g) * es + nout * es + nout * 4 + 16;
 }
 
-cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc, void* W,
-                            cudaStream_t s)
+cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc,
+                            const uint16_t* rk13, void* W, cudaStream_t s)
 {
+    if (use_tile13_gamma(P)) return launch_gamma13_p1(P, v, F, Rc, rk13, W, s);
     const int h = P.n - 1 - P.b_g;
     const size_t sm1 = gamma_p1_smem_bytes(P);
     if (P.prec == 0)
@@ -755,7 +1045,7 @@ cudaError_t set_kernel_attributes()
     SETA(k_gamma_p2<double>)
     SETA(k_gamma_p2<float>)
 #undef SETA
-    return cudaSuccess;
+    return set_tile13_attributes();
 }
 
 }  // namespace bn

@@ -35,19 +35,37 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
 cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s);
 cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double* cmax,
                                 void* lbs, cudaStream_t s);
-cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* A,
-                          cudaStream_t s);
+// Step 2.  n >= 14 uses the 13-dimension register tiles and needs `tab`
+// (n*K values, the scores reordered by high and low parts); smaller n use
+// one shared-memory tile per node slice and ignore `tab`.
+// `rk13` points at the two 8192-entry uint16 subset-rank tables (rank, then
+// inverse) of the 13-dimension tiles, filled by launch_rank13_tables.
+cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
+                          const uint16_t* rk13, void* A, cudaStream_t s);
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
 cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s,
                             int* launches);
-cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc, void* W,
-                            cudaStream_t s);
+cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc,
+                            const uint16_t* rk13, void* W, cudaStream_t s);
 cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam_v, cudaStream_t s);
 cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                          const uint32_t* masks, const void* Gam, const void* F,
                          const int* err, double* post, double* log_PD, cudaStream_t s);
 
 size_t upzeta_smem_bytes(const Plan& P);
+// bn_tile13.cu
+cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s);
+cudaError_t launch_rank13_tables(uint16_t* rank13, uint16_t* unrank13, cudaStream_t s);
+cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
+                            cudaStream_t s);
+cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* Rc,
+                              const uint16_t* rank13, void* W, cudaStream_t s);
+constexpr size_t kRank13Bytes = 2 * 8192 * sizeof(uint16_t);
+size_t upzeta13_smem_bytes(const Plan& P);
+size_t gamma13_smem_bytes(const Plan& P);
+cudaError_t set_tile13_attributes();
+bool use_tile13_up(const Plan& P);   // n >= 14 and the tile's shared memory fits
+inline bool use_tile13_gamma(const Plan& P) { return P.n >= 14; }
 size_t gamma_p1_smem_bytes(const Plan& P);
 size_t gamma_p2_smem_bytes(const Plan& P);
 cudaError_t set_kernel_attributes();

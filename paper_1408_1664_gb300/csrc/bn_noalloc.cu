@@ -179,6 +179,8 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                  o_pl = take((size_t)P.n * P.rmax * P.W * 8), o_err = take(4),
                  o_masks = take(nK * 4), o_cm = take(nK * 4), o_logB = take(nK * 8),
                  o_cmax = take((size_t)P.n * 8), o_lbs = take(nK * es),
+                 o_reo = take(bn::use_tile13_up(P) ? nK * es : 0),
+                 o_rk = take(bn::use_tile13_gamma(P) ? bn::kRank13Bytes : 0),
                  o_A = take(((size_t)P.n << (P.n - 1)) * es), o_F = take(((size_t)1 << P.n) * es),
                  o_Rc = take(((size_t)1 << P.n) * es),
                  o_W = take(((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es);
@@ -218,11 +220,13 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                           (int64_t)P.n * P.K, masks, cm, logB, nullptr, s));
     CKS(bn::launch_node_max(P, logB, cmax, s));
     CKS(bn::launch_shift_scores(P, logB, cmax, base + o_lbs, s));
-    CKS(bn::launch_upzeta(P, cm, base + o_lbs, base + o_A, s));
+    uint16_t* rk13 = reinterpret_cast<uint16_t*>(base + o_rk);
+    if (bn::use_tile13_gamma(P)) CKS(bn::launch_rank13_tables(rk13, rk13 + 8192, s));
+    CKS(bn::launch_upzeta(P, cm, base + o_lbs, base + o_reo, rk13, base + o_A, s));
     CKS(bn::launch_forward(P, base + o_A, base + o_F, s, nullptr));
     CKS(bn::launch_backward(P, base + o_A, base + o_Rc, s, nullptr));
     for (int v = 0; v < P.n; ++v) {
-        CKS(bn::launch_gamma_p1(P, v, base + o_F, base + o_Rc, base + o_W, s));
+        CKS(bn::launch_gamma_p1(P, v, base + o_F, base + o_Rc, rk13, base + o_W, s));
         CKS(bn::launch_gamma_p2(P, base + o_W, base + o_G + (size_t)v * P.K * es, s));
     }
     CKS(bn::launch_edges(P, logB, cmax, masks, base + o_G, base + o_F, err, post_dev,

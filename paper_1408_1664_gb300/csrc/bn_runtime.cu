@@ -53,7 +53,7 @@ struct HostJob {
 // Byte offsets of every array of a job inside one device allocation.
 struct Layout {
     size_t data, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB, cmax, lbs,
-        A, F, Rc, W, Gam, post, logPD, dbg, total;
+        tab, rk13, A, F, Rc, W, Gam, post, logPD, dbg, total;
 };
 
 Layout make_layout(const Plan& P, size_t dbg_cells)
@@ -77,6 +77,8 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     L.logB = take(nK * 8);
     L.cmax = take((size_t)P.n * 8);
     L.lbs = take(nK * es);
+    L.tab = take(bn::use_tile13_up(P) ? nK * es : 0);
+    L.rk13 = take(bn::use_tile13_gamma(P) ? bn::kRank13Bytes : 0);
     L.A = take(((size_t)P.n << (P.n - 1)) * es);
     L.F = take(((size_t)1 << P.n) * es);
     L.Rc = take(((size_t)1 << P.n) * es);
@@ -256,8 +258,15 @@ int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_de
                          B.at<double>(L.logB), nullptr, s)); ++nl;
     CK(bn::launch_node_max(P, B.at<double>(L.logB), B.at<double>(L.cmax), s)); ++nl;
     CK(bn::launch_shift_scores(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<void>(L.lbs), s)); ++nl;
+    if (bn::use_tile13_gamma(P)) {
+        uint16_t* rk = B.at<uint16_t>(L.rk13);
+        CK(bn::launch_rank13_tables(rk, rk + 8192, s));
+        ++nl;
+    }
     if (ev) CK(cudaEventRecord(ev->ev[1], s));
-    CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), B.at<void>(L.lbs), B.at<void>(L.A), s)); ++nl;
+    CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), B.at<void>(L.lbs), B.at<void>(L.tab),
+                         B.at<uint16_t>(L.rk13), B.at<void>(L.A), s));
+    nl += bn::use_tile13_up(P) ? 2 : 1;
     if (ev) CK(cudaEventRecord(ev->ev[2], s));
     CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
     if (ev) CK(cudaEventRecord(ev->ev[3], s));
@@ -265,7 +274,8 @@ int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_de
     if (ev) CK(cudaEventRecord(ev->ev[4], s));
     const size_t es = P.prec == 0 ? 8 : 4;
     for (int v = 0; v < P.n; ++v) {
-        CK(bn::launch_gamma_p1(P, v, B.at<void>(L.F), B.at<void>(L.Rc), B.at<void>(L.W), s));
+        CK(bn::launch_gamma_p1(P, v, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
+                               B.at<void>(L.W), s));
         if (ev) CK(cudaEventRecord(ev->ev[5 + 2 * v], s));
         CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<char>(L.Gam) + (size_t)v * P.K * es, s));
         if (ev) CK(cudaEventRecord(ev->ev[6 + 2 * v], s));

@@ -1,0 +1,600 @@
+// bn_tile13.cu -- register-blocked 13-dimension tiles for the two truncated
+// zeta transforms (Eq. 7 / Algorithm 2 and Eq. 12 / Algorithm 3) when n >= 14.
+//
+// A tile is the 2^13 subsets that share their high bits.  256 threads hold 32
+// values each.  A transform over the 13 tile dimensions runs in three
+// register layouts (dims 8..12, dims 3..7, dims 0..2), exchanging through a
+// swizzled shared-memory array between layouts, so every butterfly is a
+// register operation.
+//
+// Arithmetic is exact to working precision without a log-sum-exp per
+// butterfly.  A first pass computes the max-plus transform m(L) (the largest
+// single term of every output; a max per butterfly).  Each value is then held
+// as x(L) * 2^(BW*e(L)) with the band e(L) = floor(m(L) / BW): x(L) lies in
+// [1, 2^BW * 8192) and never overflows (BW = 112 bits in FP32, 600 nats in
+// FP64).  A butterfly adds a partner from the same band unchanged, one band
+// lower times 2^-BW, and drops partners two or more bands lower (they are
+// below 2^-BW * 2^-13 of the result: under one rounding unit).  Bands are monotone along butterflies (m is), so the
+// largest term of every output reaches it unscaled and x(L) >= 1.  One
+// exponential enters per input and one logarithm leaves per output.
+#include "bn_device.cuh"
+#include "bn_kernels.cuh"
+
+namespace bn {
+namespace {
+
+constexpr int TB = 13;            // tile dimensions
+constexpr int TN = 1 << TB;       // tile elements
+constexpr int TT = 256;           // threads per tile
+constexpr int TR = 32;            // values per thread
+constexpr unsigned FULLMASK = 0xffffffffu;
+
+// Band width in the value's log units and the factor one band down.
+template <typename T> struct Band;
+template <> struct Band<float> {
+    static constexpr float width = 112.0f;         // base-2 logs: x < 2^(112+13) < 2^127
+    static __device__ __forceinline__ float down1() { return 0x1p-112f; }
+};
+template <> struct Band<double> {
+    static constexpr double width = 600.0;          // natural logs
+    static __device__ __forceinline__ double down1() { return 2.6503965530043108e-261; }  // e^-600
+};
+
+template <typename T> __device__ __forceinline__ T band_factor(int dd)
+{
+    return dd == 0 ? T(1) : (dd == 1 ? Band<T>::down1() : T(0));
+}
+
+// a*b + c in the value's own precision (no promotion to double).
+__device__ __forceinline__ float madd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Shared-memory position of tile element e.  Flips bits 3,4 by bits 8,9 and
+// bit 2 by bit 5, which makes all three layouts' accesses free of bank
+// conflicts (32-bit accesses in layouts 1 and 2, 128-bit in layout 3).
+__device__ __forceinline__ uint32_t swz(uint32_t e)
+{
+    return e ^ (((e >> 8) & 3u) << 3) ^ (((e >> 5) & 1u) << 2);
+}
+
+// Element held in register r by thread t.
+__device__ __forceinline__ uint32_t el1(int r, int t) { return ((uint32_t)r << 8) | (uint32_t)t; }
+__device__ __forceinline__ uint32_t el2(int r, int t)
+{
+    return ((uint32_t)t & 7u) | ((uint32_t)r << 3) | (((uint32_t)t >> 3) << 8);
+}
+__device__ __forceinline__ uint32_t el3(int r, int t)
+{
+    return ((uint32_t)r & 7u) | ((uint32_t)t << 3) | (((uint32_t)r >> 3) << 11);
+}
+
+// Butterflies over register bits [k0, k0+nk): UP adds a subset into its
+// superset (upward zeta), DOWN adds a superset into its subset.
+template <bool UP, typename T>
+__device__ __forceinline__ void bfly_max(T (&v)[TR], int k0, int nk)
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        if (k < k0 || k >= k0 + nk) continue;
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            if (r & (1 << k)) continue;
+            const int s = r | (1 << k);
+            if (UP) v[s] = v[s] > v[r] ? v[s] : v[r];
+            else v[r] = v[r] > v[s] ? v[r] : v[s];
+        }
+    }
+}
+
+// Sum butterflies with bands e (exact small integers held as T).  Three
+// cases per thread: all its bands equal (plain adds); two adjacent bands
+// (factor 1 or 2^-BW, one fused multiply-add); otherwise the full rule
+// (1, 2^-BW, or 0 for partners two or more bands down).
+template <bool UP, typename T>
+__device__ __forceinline__ void bfly_sum(T (&x)[TR], const T (&e)[TR], int k0, int nk)
+{
+    T lo = e[0], hi = e[0];
+#pragma unroll
+    for (int r = 1; r < TR; ++r) {
+        lo = e[r] < lo ? e[r] : lo;
+        hi = e[r] > hi ? e[r] : hi;
+    }
+    const T gap = hi - lo;
+    if (gap == T(0)) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if (k < k0 || k >= k0 + nk) continue;
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                if (r & (1 << k)) continue;
+                const int s = r | (1 << k);
+                if (UP) x[s] += x[r];
+                else x[r] += x[s];
+            }
+        }
+    } else if (gap == T(1)) {
+        // partner bands differ by 0 or 1: factor 1 or 2^-BW
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if (k < k0 || k >= k0 + nk) continue;
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                if (r & (1 << k)) continue;
+                const int s = r | (1 << k);
+                if (UP) x[s] = madd(x[r], e[s] == e[r] ? T(1) : Band<T>::down1(), x[s]);
+                else x[r] = madd(x[s], e[r] == e[s] ? T(1) : Band<T>::down1(), x[r]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if (k < k0 || k >= k0 + nk) continue;
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                if (r & (1 << k)) continue;
+                const int s = r | (1 << k);
+                const T dd = UP ? e[s] - e[r] : e[r] - e[s];
+                const T f = dd == T(0) ? T(1) : (dd == T(1) ? Band<T>::down1() : T(0));
+                if (UP) x[s] = madd(x[r], f, x[s]);
+                else x[r] = madd(x[s], f, x[r]);
+            }
+        }
+    }
+}
+
+// Layout loads and stores through the swizzled array.
+template <typename T> __device__ __forceinline__ void ld1(const T* a, T (&v)[TR], int t)
+{
+#pragma unroll
+    for (int r = 0; r < TR; ++r) v[r] = a[swz(el1(r, t))];
+}
+template <typename T> __device__ __forceinline__ void st1(T* a, const T (&v)[TR], int t)
+{
+#pragma unroll
+    for (int r = 0; r < TR; ++r) a[swz(el1(r, t))] = v[r];
+}
+template <typename T> __device__ __forceinline__ void ld2(const T* a, T (&v)[TR], int t)
+{
+#pragma unroll
+    for (int r = 0; r < TR; ++r) v[r] = a[swz(el2(r, t))];
+}
+template <typename T> __device__ __forceinline__ void st2(T* a, const T (&v)[TR], int t)
+{
+#pragma unroll
+    for (int r = 0; r < TR; ++r) a[swz(el2(r, t))] = v[r];
+}
+// Layout 3: thread t owns four runs of 8 consecutive elements.
+template <typename T> __device__ __forceinline__ void ld3(const T* a, T (&v)[TR], int t)
+{
+#pragma unroll
+    for (int r = 0; r < TR; ++r) v[r] = a[swz(el3(r, t))];
+}
+template <> __device__ __forceinline__ void ld3<float>(const float* a, float (&v)[TR], int t)
+{
+    const bool flip = (t >> 2) & 1;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const uint32_t base = swz(el3(8 * x, t)) & ~7u;
+        float4 p = *reinterpret_cast<const float4*>(a + base);
+        float4 q = *reinterpret_cast<const float4*>(a + base + 4);
+        if (flip) { float4 w = p; p = q; q = w; }
+        v[8 * x + 0] = p.x; v[8 * x + 1] = p.y; v[8 * x + 2] = p.z; v[8 * x + 3] = p.w;
+        v[8 * x + 4] = q.x; v[8 * x + 5] = q.y; v[8 * x + 6] = q.z; v[8 * x + 7] = q.w;
+    }
+}
+template <typename T> __device__ __forceinline__ void st3(T* a, const T (&v)[TR], int t)
+{
+#pragma unroll
+    for (int r = 0; r < TR; ++r) a[swz(el3(r, t))] = v[r];
+}
+template <> __device__ __forceinline__ void st3<float>(float* a, const float (&v)[TR], int t)
+{
+    const bool flip = (t >> 2) & 1;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const uint32_t base = swz(el3(8 * x, t)) & ~7u;
+        float4 p = make_float4(v[8 * x + 0], v[8 * x + 1], v[8 * x + 2], v[8 * x + 3]);
+        float4 q = make_float4(v[8 * x + 4], v[8 * x + 5], v[8 * x + 6], v[8 * x + 7]);
+        if (flip) { float4 w = p; p = q; q = w; }
+        *reinterpret_cast<float4*>(a + base) = p;
+        *reinterpret_cast<float4*>(a + base + 4) = q;
+    }
+}
+// Binomial coefficients C(a, b), a < 32, b <= 8, in shared memory (indices
+// differ across lanes, which would serialise constant-cache reads).
+struct SBinom {
+    uint32_t v[32][9];
+};
+__device__ __forceinline__ void fill_sbinom(SBinom& sb)
+{
+    for (int x = threadIdx.x; x < 32 * 9; x += blockDim.x) sb.v[x / 9][x % 9] = binom(x / 9, x % 9);
+}
+__device__ __forceinline__ uint32_t sb_binom(const SBinom& sb, int a, int b)
+{
+    if (b < 0 || b > a) return 0u;
+    return b > 8 ? binom(a, b) : sb.v[a][b];
+}
+__device__ __forceinline__ uint32_t sb_unrank(const SBinom& sb, uint32_t r, int nb, int* kout)
+{
+    int k = 0;
+    while (r >= sb_binom(sb, nb, k)) { r -= sb_binom(sb, nb, k); ++k; }
+    uint32_t x = 0;
+    int c = nb - 1;
+    for (int t = k; t >= 1; --t) {
+        while (sb_binom(sb, c, t) > r) --c;
+        x |= 1u << c;
+        r -= sb_binom(sb, c, t);
+        --c;
+    }
+    if (kout) *kout = k;
+    return x;
+}
+
+
+uint64_t binom_host(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int t = 1; t <= k; ++t) r = r * (uint64_t)(n - k + t) / (uint64_t)t;
+    return r;
+}
+
+__device__ __forceinline__ float floor_div(float m, float w) { return floorf(m * (1.0f / w)); }
+__device__ __forceinline__ double floor_div(double m, double w) { return floor(m / w); }
+
+}  // namespace
+
+// ===========================================================================
+// Families reordered by (high part G_H, low part g_L) for the tile scatter:
+// row = rank of G_H among the subsets of the h = n-14 high index bits with at
+// most d elements, column = rank of g_L among the subsets of the 13 low bits
+// with at most d - |G_H| elements.  Row r of size k holds C13(<= d-k)
+// columns, so the table holds exactly the K families of the node.
+// ===========================================================================
+__device__ __forceinline__ uint32_t row_offset(int h, int d, int kh, uint32_t rank_in_class)
+{
+    uint32_t off = 0;
+    for (int k = 0; k < kh; ++k) off += binom(h, k) * num_small_subsets(TB, d - k);
+    return off + rank_in_class * num_small_subsets(TB, d - kh);
+}
+
+template <typename T>
+__global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs, T* __restrict__ tab)
+{
+    const int h = n - 1 - TB;
+    const int64_t total = (int64_t)n * K;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(x / K);
+        uint32_t f = (uint32_t)(x % K);
+        int k = 0;
+        while (f >= binom(n - 1, k)) { f -= binom(n - 1, k); ++k; }
+        const uint32_t cm = colex_unrank(f, k, n - 1);
+        const uint32_t gl = cm & (TN - 1u), gh = cm >> TB;
+        const int kh = __popc(gh);
+        // colex rank of gh within its size class
+        uint32_t rk = 0;
+        int t = 1;
+        for (uint32_t y = gh; y; y &= y - 1, ++t) rk += binom(__ffs(y) - 1, t);
+        const uint32_t col = small_subset_rank(gl, TB);
+        tab[(size_t)i * K + row_offset(h, d, kh, rk) + col] = lbs[x];
+    }
+}
+
+// ===========================================================================
+// Step 2 for n >= 14: one block per tile (i, H) of A_i.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(TT, 2)
+k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* __restrict__ unrank13,
+           T* __restrict__ A)
+{
+    using Lg = LogOps<T>;
+    constexpr T BW = Band<T>::width;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* A0 = reinterpret_cast<T*>(smem_raw);
+    T* A1 = A0 + TN;
+    T* E = A1 + TN;
+    SBinom* sb = reinterpret_cast<SBinom*>(E + TN);
+    int* meta = reinterpret_cast<int*>(sb + 1);  // [0,32) class counts, [32,64) class starts, [64,72) warp sums
+    uint32_t* off13 = reinterpret_cast<uint32_t*>(meta + 80);   // 16 entries
+    const uint32_t ncol = num_small_subsets(TB, d);
+    const int h = n - 1 - TB;
+    const uint32_t nrow = num_small_subsets(h, d);
+    uint32_t* rowbase = off13 + 16;
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int i = (int)(blockIdx.x >> h);
+    const uint32_t H = blockIdx.x & ((1u << h) - 1u);
+    const T* tb = tab + (size_t)i * K;
+
+    fill_sbinom(*sb);
+    if (t < 80) meta[t] = 0;
+    if (t < 16) {
+        uint32_t o = 0;
+        for (int k = 0; k < t && k <= TB; ++k) o += binom(TB, k);
+        off13[t] = o;
+    }
+    for (int r = 0; r < TR; ++r) A0[swz(el1(r, t))] = Lg::ninf();   // no term: zero
+    __syncthreads();
+
+    // --- rows whose high part lies inside H (size-major order), with the
+    //     offset of each row in the node's reordered table ------------------
+    const uint32_t chunk = (nrow + TT - 1) / TT;
+    const uint32_t r0 = min(nrow, (uint32_t)t * chunk), r1 = min(nrow, r0 + chunk);
+    int cnt = 0;
+    for (uint32_t r = r0; r < r1; ++r) {
+        int k;
+        const uint32_t G = sb_unrank(*sb, r, h, &k);
+        if ((G & ~H) == 0u) { ++cnt; atomicAdd(&meta[k], 1); }
+    }
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULLMASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) meta[64 + warp] = incl;
+    __syncthreads();
+    int pos = incl - cnt;
+    for (int w = 0; w < warp; ++w) pos += meta[64 + w];
+    for (uint32_t r = r0; r < r1; ++r) {
+        int k;
+        const uint32_t G = sb_unrank(*sb, r, h, &k);
+        if ((G & ~H) == 0u) {
+            // offset = sum over smaller classes of C(h,k') * C13(<= d-k') + rank in class * C13(<= d-k)
+            uint32_t base = 0;
+            for (int kk = 0; kk < k; ++kk) base += sb_binom(*sb, h, kk) * off13[min(d - kk, TB) + 1];
+            const uint32_t rin = r - (k == 0 ? 0u : num_small_subsets(h, k - 1));
+            rowbase[pos++] = base + rin * off13[min(d - k, TB) + 1];
+        }
+    }
+    if (t == 0) {
+        int s2 = 0;
+        for (int k = 0; k <= d + 1 && k < 32; ++k) { meta[32 + k] = s2; if (k <= d) s2 += meta[k]; }
+    }
+    __syncthreads();
+
+    // --- per-column log-sum over the admissible rows, in a fixed order ------
+    // column c (low pattern of size j) takes the rows of classes k <= d - j:
+    // the list prefix up to the start of class d - j + 1.
+    for (uint32_t c = warp; c < 32 && c < ncol; c += TT / 32) {          // heavy columns: a warp each
+        int j = 0;
+        while (off13[j + 1] <= c) ++j;
+        const int rend = meta[32 + min(d - j + 1, 31)];
+        T mx = Lg::ninf();
+        for (int rp = lane; rp < rend; rp += 32) {
+            const T val = tb[rowbase[rp] + c];
+            mx = val > mx ? val : mx;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const T y = __shfl_xor_sync(FULLMASK, mx, o);
+            mx = y > mx ? y : mx;
+        }
+        T sm = T(0);
+        for (int rp = lane; rp < rend; rp += 32) sm += Lg::ex(tb[rowbase[rp] + c] - mx);
+        for (int o = 16; o; o >>= 1) sm += __shfl_xor_sync(FULLMASK, sm, o);
+        if (lane == 0) {
+            const uint32_t sw = swz(unrank13[c]);
+            A0[sw] = A1[sw] = mx + Lg::lg(sm);
+        }
+    }
+    for (uint32_t c = 32 + t; c < ncol; c += TT) {                       // light columns: a thread each
+        int j = 0;
+        while (off13[j + 1] <= c) ++j;
+        const int rend = meta[32 + min(d - j + 1, 31)];
+        T mx = Lg::ninf();
+        for (int rp = 0; rp < rend; ++rp) {
+            const T val = tb[rowbase[rp] + c];
+            mx = val > mx ? val : mx;
+        }
+        T sm = T(0);
+        for (int rp = 0; rp < rend; ++rp) sm += Lg::ex(tb[rowbase[rp] + c] - mx);
+        const uint32_t sw = swz(unrank13[c]);
+        A0[sw] = A1[sw] = mx + Lg::lg(sm);
+    }
+    __syncthreads();
+
+    // --- max-plus pass: layouts 1, 2, 3 ------------------------------------
+    T v[TR];
+    ld1(A0, v, t);
+    bfly_max<true>(v, 0, 5);
+    st1(A0, v, t);
+    __syncthreads();
+    ld2(A0, v, t);
+    bfly_max<true>(v, 0, 5);
+    st2(A0, v, t);
+    __syncthreads();
+    ld3(A0, v, t);
+    bfly_max<true>(v, 0, 3);
+
+    // --- bands and scaled inputs (layout 3) --------------------------------
+    T e[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) e[r] = floor_div(v[r], BW);
+    st3(E, e, t);                         // bands, read again in layouts 2 and 1
+    ld3(A1, v, t);                        // C at the slots, garbage elsewhere
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+        v[r] = (__popc(el3(r, t)) <= d) ? Lg::ex(v[r] - BW * e[r]) : T(0);
+    // --- sum pass: layouts 3, 2, 1 ------------------------------------------
+    bfly_sum<true>(v, e, 0, 3);
+    __syncthreads();
+    st3(A0, v, t);
+    __syncthreads();
+    ld2(A0, v, t);
+    ld2(E, e, t);
+    bfly_sum<true>(v, e, 0, 5);
+    __syncthreads();
+    st2(A0, v, t);
+    __syncthreads();
+    ld1(A0, v, t);
+    ld1(E, e, t);
+    bfly_sum<true>(v, e, 0, 5);
+    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
+#pragma unroll
+    for (int r = 0; r < TR; ++r) out[el1(r, t)] = madd(BW, e[r], Lg::lg(v[r]));
+}
+
+// ===========================================================================
+// Step 4, phase 1 for n >= 14: one block per tile H of the n-1 bits of S
+// (bit v removed); s_v(S) = F(S) + R'(S + {v}); keeps the outputs with at
+// most d low elements in row H of W.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(TT, 2)
+k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
+             const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W)
+{
+    using Lg = LogOps<T>;
+    constexpr T BW = Band<T>::width;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* A0 = reinterpret_cast<T*>(smem_raw);
+    T* A1 = A0 + TN;
+    T* E = A1 + TN;
+    const int t = threadIdx.x;
+    const uint32_t H = blockIdx.x;
+    const uint32_t bv = 1u << v;
+
+    T x[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const uint32_t el = el1(r, t);
+        const uint32_t S = expand((H << TB) | el, v);
+        x[r] = F[S] + Rc[S | bv];
+        A1[swz(el)] = x[r];
+    }
+    bfly_max<false>(x, 0, 5);
+    st1(A0, x, t);
+    __syncthreads();
+    ld2(A0, x, t);
+    bfly_max<false>(x, 0, 5);
+    st2(A0, x, t);
+    __syncthreads();
+    ld3(A0, x, t);
+    bfly_max<false>(x, 0, 3);
+
+    T e[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) e[r] = floor_div(x[r], BW);
+    st3(E, e, t);
+    ld3(A1, x, t);                        // s_v in layout 3
+#pragma unroll
+    for (int r = 0; r < TR; ++r) x[r] = Lg::ex(x[r] - BW * e[r]);
+    bfly_sum<false>(x, e, 0, 3);
+    __syncthreads();
+    st3(A0, x, t);
+    __syncthreads();
+    ld2(A0, x, t);
+    ld2(E, e, t);
+    bfly_sum<false>(x, e, 0, 5);
+    __syncthreads();
+    st2(A0, x, t);
+    __syncthreads();
+    ld1(A0, x, t);
+    ld1(E, e, t);
+    bfly_sum<false>(x, e, 0, 5);
+    T* row = W + (size_t)H * nlow;
+    const int pt = __popc((uint32_t)t);
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+        if (pt + __popc((uint32_t)r) <= d) row[rank13[el1(r, t)]] = madd(BW, e[r], Lg::lg(x[r]));
+}
+
+// rank13[L] = position of L among the subsets of 13 bits ordered by size then
+// value; unrank13 is its inverse.
+__global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restrict__ unrank13)
+{
+    const uint32_t L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= (uint32_t)TN) return;
+    const uint32_t r = small_subset_rank(L, TB);
+    rank13[L] = (uint16_t)r;
+    unrank13[r] = (uint16_t)L;
+}
+
+// ===========================================================================
+// Launchers.
+// ===========================================================================
+size_t upzeta13_smem_bytes(const Plan& P)
+{
+    const size_t es = P.prec == 0 ? 8 : 4;
+    const int h = P.n - 1 - TB;
+    uint64_t ncol = 0, nrow = 0;
+    for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
+    for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
+    (void)ncol;
+    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + nrow * 4 + 16;
+}
+
+bool use_tile13_up(const Plan& P)
+{
+    return P.n >= 14 && upzeta13_smem_bytes(P) <= 227 * 1024;
+}
+
+size_t gamma13_smem_bytes(const Plan& P)
+{
+    const size_t es = P.prec == 0 ? 8 : 4;
+    return (size_t)TN * (3 * es) + 16;
+}
+
+cudaError_t launch_rank13_tables(uint16_t* rank13, uint16_t* unrank13, cudaStream_t s)
+{
+    k_rank13_tables<<<TN / 256, 256, 0, s>>>(rank13, unrank13);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s)
+{
+    const int64_t total = (int64_t)P.n * P.K;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (P.prec == 0)
+        k_reorder_up<double><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const double*)lbs, (double*)tab);
+    else
+        k_reorder_up<float><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const float*)lbs, (float*)tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
+                            cudaStream_t s)
+{
+    const int h = P.n - 1 - TB;
+    const unsigned grid = (unsigned)P.n << h;
+    const size_t sm = upzeta13_smem_bytes(P);
+    if (P.prec == 0)
+        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const double*)tab, unrank13,
+                                                (double*)A);
+    else
+        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const float*)tab, unrank13,
+                                               (float*)A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* Rc,
+                              const uint16_t* rank13, void* W, cudaStream_t s)
+{
+    const int h = P.n - 1 - TB;
+    const size_t sm = gamma13_smem_bytes(P);
+    if (P.prec == 0)
+        k_gamma13_p1<double><<<1u << h, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const double*)F,
+                                                      (const double*)Rc, rank13, (double*)W);
+    else
+        k_gamma13_p1<float><<<1u << h, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const float*)F,
+                                                     (const float*)Rc, rank13, (float*)W);
+    return cudaGetLastError();
+}
+
+cudaError_t set_tile13_attributes()
+{
+    cudaError_t e;
+    const int big = 227 * 1024;
+#define SETA(k)                                                                      \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+    if (e != cudaSuccess) return e;
+    SETA(k_upzeta13<double>)
+    SETA(k_upzeta13<float>)
+    SETA(k_gamma13_p1<double>)
+    SETA(k_gamma13_p1<float>)
+#undef SETA
+    return cudaSuccess;
+}
+
+}  // namespace bn
