@@ -486,24 +486,15 @@ __device__ __forceinline__ uint32_t colex_next(uint32_t x)
     return v | (((v ^ x) >> 2) >> (__ffs(u) - 1));
 }
 
-// log-sum-exp of the in-tile terms of one lane: X and a[i] + nb[i] for the
-// in-tile bits selected by `use` (at most 5).
+// Branchless online log-sum-exp step: (m, s) represents m + lg(s).
 template <typename T>
-__device__ __forceinline__ T lse_in_tile(T X, const T (&a)[5], const T (&nb)[5], uint32_t use)
+__device__ __forceinline__ void lse_step(T& m, T& s, T x)
 {
     using L = LogOps<T>;
-    T t[5];
-    T m = X;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        t[i] = (use >> i & 1u) ? a[i] + nb[i] : L::ninf();
-        m = t[i] > m ? t[i] : m;
-    }
-    if (m == L::ninf()) return m;
-    T s = L::ex(X - m);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) s += L::ex(t[i] - m);
-    return m + L::lg(s);
+    const T mn = x > m ? x : m;
+    if (mn == L::ninf()) return;
+    s = s * L::ex(m - mn) + L::ex(x - mn);
+    m = mn;
 }
 
 // A warp owns 2^wb consecutive subsets (one per lane); the tile's high bits
@@ -528,30 +519,20 @@ k_forward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __rest
     uint32_t Ht = colex_unrank(first, hl, nh);
     for (uint32_t tile = first; tile < ntiles && tile < first + (uint32_t)tpw; ++tile) {
         const uint32_t S = (Ht << wb) | lb;
-        // terms across tiles: i = wb + j for the set bits j of Ht
-        T m = L::ninf(), sum = T(0);
-        {
-            T x[26];
-            int cnt = 0;
-            uint32_t rest = Ht;
-#pragma unroll
-            for (int q = 0; q < 26; ++q) {
-                if (!rest) break;
-                const int j = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const int i = wb + j;
-                const uint32_t Hm = Ht & ~(1u << j);
-                const T* Ai = A + (size_t)i * half + ((size_t)squeeze(Hm, j) << wb);
-                const T* Fi = F + ((size_t)Hm << wb);
-                x[q] = active ? __ldcs(Ai + lb) + Fi[lb] : L::ninf();
-                m = x[q] > m ? x[q] : m;
-                cnt = q + 1;
-            }
-#pragma unroll
-            for (int q = 0; q < 26; ++q)
-                if (q < cnt) sum += L::ex(x[q] - m);
+        // terms across tiles: i = wb + j for the set bits j of Ht (same for all lanes)
+        T m = L::ninf(), sm = T(0);
+        uint32_t rest = Ht;
+        const int cnt = __popc(Ht);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+            const int j = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const uint32_t Hm = Ht & ~(1u << j);
+            const T* Ai = A + (size_t)(wb + j) * half + ((size_t)squeeze(Hm, j) << wb);
+            const T* Fi = F + ((size_t)Hm << wb);
+            if (active) lse_step(m, sm, __ldcs(Ai + lb) + Fi[lb]);
         }
-        const T X = (m == L::ninf()) ? m : m + L::lg(sum);
+        const T X = (m == L::ninf()) ? m : m + L::lg(sm);
         T a[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -564,7 +545,13 @@ k_forward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __rest
             T nb[5];
 #pragma unroll
             for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Fv, 1 << i);
-            if (active && __popc(lb) == l) Fv = lse_in_tile(X, a, nb, lb);
+            if (active && __popc(lb) == l) {
+                T mm = X, ss = (X == L::ninf()) ? T(0) : T(1);
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+                    if (lb >> i & 1u) lse_step(mm, ss, a[i] + nb[i]);
+                Fv = mm + L::lg(ss);
+            }
         }
         if (active) F[S] = Fv;
         if (Ht) Ht = colex_next(Ht);
@@ -586,33 +573,23 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
     const uint32_t lb = (uint32_t)lane & wmask;
     const bool active = lane < (1 << wb);
     const uint32_t full = (1u << n) - 1u;
-    const uint32_t hmask = (nh == 32) ? 0xffffffffu : ((1u << nh) - 1u);
+    const uint32_t hmask = (1u << nh) - 1u;
     const size_t half = (size_t)1 << (n - 1);
     uint32_t Ht = colex_unrank(first, hl, nh);
     for (uint32_t tile = first; tile < ntiles && tile < first + (uint32_t)tpw; ++tile) {
         const uint32_t Tm = (Ht << wb) | lb;
-        T m = L::ninf(), sum = T(0);
-        {
-            T x[26];
-            int cnt = 0;
-            uint32_t rest = ~Ht & hmask;
-#pragma unroll
-            for (int q = 0; q < 26; ++q) {
-                if (!rest) break;
-                const int j = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const int i = wb + j;
-                const T* Ai = A + (size_t)i * half + ((size_t)squeeze(Ht, j) << wb);
-                const T* Ri = Rc + ((size_t)(Ht | (1u << j)) << wb);
-                x[q] = active ? __ldcs(Ai + lb) + Ri[lb] : L::ninf();
-                m = x[q] > m ? x[q] : m;
-                cnt = q + 1;
-            }
-#pragma unroll
-            for (int q = 0; q < 26; ++q)
-                if (q < cnt) sum += L::ex(x[q] - m);
+        T m = L::ninf(), sm = T(0);
+        uint32_t rest = ~Ht & hmask;
+        const int cnt = __popc(rest);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+            const int j = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const T* Ai = A + (size_t)(wb + j) * half + ((size_t)squeeze(Ht, j) << wb);
+            const T* Ri = Rc + ((size_t)(Ht | (1u << j)) << wb);
+            if (active) lse_step(m, sm, __ldcs(Ai + lb) + Ri[lb]);
         }
-        const T X = (m == L::ninf()) ? m : m + L::lg(sum);
+        const T X = (m == L::ninf()) ? m : m + L::lg(sm);
         T a[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -624,7 +601,13 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
             T nb[5];
 #pragma unroll
             for (int i = 0; i < 5; ++i) nb[i] = __shfl_xor_sync(FULL, Rv, 1 << i);
-            if (active && __popc(lb) == l) Rv = lse_in_tile(X, a, nb, ~lb & wmask);
+            if (active && __popc(lb) == l) {
+                T mm = X, ss = (X == L::ninf()) ? T(0) : T(1);
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+                    if (i < wb && !(lb >> i & 1u)) lse_step(mm, ss, a[i] + nb[i]);
+                Rv = mm + L::lg(ss);
+            }
         }
         if (active) Rc[Tm] = Rv;
         if (Ht) Ht = colex_next(Ht);
@@ -1034,9 +1017,8 @@ cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
 cudaError_t set_kernel_attributes()
 {
     cudaError_t e;
-    const int big = 227 * 1024;
-#define SETA(k)                                                                      \
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+#define SETA(k)                      \
+    e = allow_max_dynamic_smem(k); \
     if (e != cudaSuccess) return e;
     SETA(k_upzeta<double>)
     SETA(k_upzeta<float>)

@@ -70,4 +70,18 @@ size_t gamma_p1_smem_bytes(const Plan& P);
 size_t gamma_p2_smem_bytes(const Plan& P);
 cudaError_t set_kernel_attributes();
 
+// Allow a kernel the largest dynamic shared memory the device gives one block
+// next to the kernel's own static shared memory.
+template <typename K> inline cudaError_t allow_max_dynamic_smem(K kernel)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 }  // namespace bn

@@ -142,6 +142,42 @@ __device__ __forceinline__ void bfly_sum(T (&x)[TR], const T (&e)[TR], int k0, i
     }
 }
 
+// Online log-sum-exp step (branchless): (m, s) stands for m + lg(s).
+template <typename T>
+__device__ __forceinline__ void lse_online(T& m, T& s, T x)
+{
+    using Lg = LogOps<T>;
+    const T mn = x > m ? x : m;
+    if (mn == Lg::ninf()) return;
+    s = s * Lg::ex(m - mn) + Lg::ex(x - mn);
+    m = mn;
+}
+
+// Sum butterflies without bands (every value in one common scale).
+template <bool UP, typename T>
+__device__ __forceinline__ void bfly_plain(T (&x)[TR], int k0, int nk)
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        if (k < k0 || k >= k0 + nk) continue;
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            if (r & (1 << k)) continue;
+            const int s = r | (1 << k);
+            if (UP) x[s] += x[r];
+            else x[r] += x[s];
+        }
+    }
+}
+
+// A tile whose values span less than FastSpan (log units) below its maximum
+// is summed in one scale relative to that maximum: every output is at least
+// 2^-FastSpan of it, and a partial sum flushed below the smallest normal is
+// under 2^-46 of any output, also summed over the 8192 elements.
+template <typename T> struct FastSpan;
+template <> struct FastSpan<float> { static constexpr float value = 80.0f; };      // bits
+template <> struct FastSpan<double> { static constexpr double value = 640.0; };    // nats
+
 // Layout loads and stores through the swizzled array.
 template <typename T> __device__ __forceinline__ void ld1(const T* a, T (&v)[TR], int t)
 {
@@ -285,7 +321,7 @@ __global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs,
 // Step 2 for n >= 14: one block per tile (i, H) of A_i.
 // ===========================================================================
 template <typename T>
-__global__ void __launch_bounds__(TT, 2)
+__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* __restrict__ unrank13,
            T* __restrict__ A)
 {
@@ -296,7 +332,7 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
     T* A1 = A0 + TN;
     T* E = A1 + TN;
     SBinom* sb = reinterpret_cast<SBinom*>(E + TN);
-    int* meta = reinterpret_cast<int*>(sb + 1);  // [0,32) class counts, [32,64) class starts, [64,72) warp sums
+    int* meta = reinterpret_cast<int*>(sb + 1);  // [0,32) class counts, [32,64) class starts, [64,72) warp sums, [72] tile max
     uint32_t* off13 = reinterpret_cast<uint32_t*>(meta + 80);   // 16 entries
     const uint32_t ncol = num_small_subsets(TB, d);
     const int h = n - 1 - TB;
@@ -308,8 +344,11 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
     const uint32_t H = blockIdx.x & ((1u << h) - 1u);
     const T* tb = tab + (size_t)i * K;
 
+    using O = typename OrdInt<T>::type;
+    O* tmax = reinterpret_cast<O*>(meta + 72);   // max over the slots (8-byte aligned)
     fill_sbinom(*sb);
-    if (t < 80) meta[t] = 0;
+    if (t < 72) meta[t] = 0;
+    if (t == 0) *tmax = ord_enc(Lg::ninf());
     if (t < 16) {
         uint32_t o = 0;
         for (int k = 0; k < t && k <= TB; ++k) o += binom(TB, k);
@@ -361,38 +400,64 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
         int j = 0;
         while (off13[j + 1] <= c) ++j;
         const int rend = meta[32 + min(d - j + 1, 31)];
-        T mx = Lg::ninf();
-        for (int rp = lane; rp < rend; rp += 32) {
-            const T val = tb[rowbase[rp] + c];
-            mx = val > mx ? val : mx;
-        }
+        T mx = Lg::ninf(), sm = T(0);
+#pragma unroll 4
+        for (int rp = lane; rp < rend; rp += 32) lse_online(mx, sm, tb[rowbase[rp] + c]);
+        // combine the lanes' (max, sum) pairs in a fixed tree order
         for (int o = 16; o; o >>= 1) {
-            const T y = __shfl_xor_sync(FULLMASK, mx, o);
-            mx = y > mx ? y : mx;
+            const T m2 = __shfl_xor_sync(FULLMASK, mx, o);
+            const T s2 = __shfl_xor_sync(FULLMASK, sm, o);
+            const T mn = m2 > mx ? m2 : mx;
+            if (mn != Lg::ninf()) {
+                sm = sm * Lg::ex(mx - mn) + s2 * Lg::ex(m2 - mn);
+                mx = mn;
+            }
         }
-        T sm = T(0);
-        for (int rp = lane; rp < rend; rp += 32) sm += Lg::ex(tb[rowbase[rp] + c] - mx);
-        for (int o = 16; o; o >>= 1) sm += __shfl_xor_sync(FULLMASK, sm, o);
         if (lane == 0) {
             const uint32_t sw = swz(unrank13[c]);
             A0[sw] = A1[sw] = mx + Lg::lg(sm);
+            atomicMax(tmax, ord_enc(mx));
         }
     }
     for (uint32_t c = 32 + t; c < ncol; c += TT) {                       // light columns: a thread each
         int j = 0;
         while (off13[j + 1] <= c) ++j;
         const int rend = meta[32 + min(d - j + 1, 31)];
-        T mx = Lg::ninf();
-        for (int rp = 0; rp < rend; ++rp) {
-            const T val = tb[rowbase[rp] + c];
-            mx = val > mx ? val : mx;
-        }
-        T sm = T(0);
-        for (int rp = 0; rp < rend; ++rp) sm += Lg::ex(tb[rowbase[rp] + c] - mx);
+        T mx = Lg::ninf(), sm = T(0);
+#pragma unroll 8
+        for (int rp = 0; rp < rend; ++rp) lse_online(mx, sm, tb[rowbase[rp] + c]);
         const uint32_t sw = swz(unrank13[c]);
         A0[sw] = A1[sw] = mx + Lg::lg(sm);
+        atomicMax(tmax, ord_enc(mx));
     }
     __syncthreads();
+
+    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
+    // --- fast path: the tile spans less than FastSpan below its maximum -----
+    // (the smallest output is C(empty) and every output is at most
+    // 13 bits above the largest slot value)
+    {
+        const T M = ord_dec(*tmax) + T(TB);
+        if (M - A1[0] < FastSpan<T>::value) {
+            T x[TR];
+            ld1(A1, x, t);
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+                x[r] = (__popc(el1(r, t)) <= d) ? Lg::ex(x[r] - M) : T(0);
+            bfly_plain<true>(x, 0, 5);
+            st1(A0, x, t);
+            __syncthreads();
+            ld2(A0, x, t);
+            bfly_plain<true>(x, 0, 5);
+            st2(A0, x, t);
+            __syncthreads();
+            ld3(A0, x, t);
+            bfly_plain<true>(x, 0, 3);
+#pragma unroll
+            for (int r = 0; r < TR; ++r) out[el3(r, t)] = M + Lg::lg(x[r]);
+            return;
+        }
+    }
 
     // --- max-plus pass: layouts 1, 2, 3 ------------------------------------
     T v[TR];
@@ -430,7 +495,6 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
     ld1(A0, v, t);
     ld1(E, e, t);
     bfly_sum<true>(v, e, 0, 5);
-    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
 #pragma unroll
     for (int r = 0; r < TR; ++r) out[el1(r, t)] = madd(BW, e[r], Lg::lg(v[r]));
 }
@@ -441,7 +505,7 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
 // most d low elements in row H of W.
 // ===========================================================================
 template <typename T>
-__global__ void __launch_bounds__(TT, 2)
+__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W)
 {
@@ -455,14 +519,53 @@ k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
     const uint32_t H = blockIdx.x;
     const uint32_t bv = 1u << v;
 
+    using O = typename OrdInt<T>::type;
+    __shared__ O tmax_s;
+    __shared__ T sfull_s;
+    if (t == 0) tmax_s = ord_enc(Lg::ninf());
+    __syncthreads();
     T x[TR];
+    T mx = Lg::ninf();
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
         const uint32_t el = el1(r, t);
         const uint32_t S = expand((H << TB) | el, v);
         x[r] = F[S] + Rc[S | bv];
-        A1[swz(el)] = x[r];
+        mx = x[r] > mx ? x[r] : mx;
     }
+    for (int o = 16; o; o >>= 1) {
+        const T y = __shfl_xor_sync(FULLMASK, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((t & 31) == 0) atomicMax(&tmax_s, ord_enc(mx));
+    if (t == TT - 1) sfull_s = x[TR - 1];            // s of the full tile set (element 8191)
+    __syncthreads();
+    T* row = W + (size_t)H * nlow;
+    {
+        // every output T (|T| <= d) sums s over its supersets, the full set
+        // included: it is at least s(full)
+        const T M = ord_dec(tmax_s) + T(TB);
+        if (M - sfull_s < FastSpan<T>::value) {
+#pragma unroll
+            for (int r = 0; r < TR; ++r) x[r] = Lg::ex(x[r] - M);
+            bfly_plain<false>(x, 0, 5);
+            st1(A0, x, t);
+            __syncthreads();
+            ld2(A0, x, t);
+            bfly_plain<false>(x, 0, 5);
+            st2(A0, x, t);
+            __syncthreads();
+            ld3(A0, x, t);
+            bfly_plain<false>(x, 0, 3);
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const uint32_t el = el3(r, t);
+                if (__popc(el) <= d) row[rank13[el]] = M + Lg::lg(x[r]);
+            }
+            return;
+        }
+    }
+    st1(A1, x, t);                        // s_v kept for the band pass
     bfly_max<false>(x, 0, 5);
     st1(A0, x, t);
     __syncthreads();
@@ -493,7 +596,6 @@ k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
     ld1(A0, x, t);
     ld1(E, e, t);
     bfly_sum<false>(x, e, 0, 5);
-    T* row = W + (size_t)H * nlow;
     const int pt = __popc((uint32_t)t);
 #pragma unroll
     for (int r = 0; r < TR; ++r)
@@ -522,12 +624,12 @@ size_t upzeta13_smem_bytes(const Plan& P)
     for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
     for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
     (void)ncol;
-    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + nrow * 4 + 16;
+    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + nrow * 4 + 16;  // meta[72..73] holds the tile max
 }
 
 bool use_tile13_up(const Plan& P)
 {
-    return P.n >= 14 && upzeta13_smem_bytes(P) <= 227 * 1024;
+    return P.n >= 14 && upzeta13_smem_bytes(P) <= 227 * 1024 - 64;
 }
 
 size_t gamma13_smem_bytes(const Plan& P)
@@ -585,9 +687,8 @@ cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* R
 cudaError_t set_tile13_attributes()
 {
     cudaError_t e;
-    const int big = 227 * 1024;
-#define SETA(k)                                                                      \
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+#define SETA(k)                      \
+    e = allow_max_dynamic_smem(k); \
     if (e != cudaSuccess) return e;
     SETA(k_upzeta13<double>)
     SETA(k_upzeta13<float>)
