@@ -52,6 +52,8 @@ def parse():
                     help="skip the secondary FP64-path measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
     ap.add_argument("--subset-n", type=int, default=0,
                     help="use only the first N variables of the workload (profiling)")
     return ap.parse_args()
@@ -216,6 +218,117 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- serving --
+def serving_trace(duration_s: float, rate: float = 200.0):
+    """Seeded Poisson arrivals of small jobs (n 8..22, d=3, binary, m=500)
+    with one n=29, m=2000 job at t=1 s."""
+    arr = datagen.poisson_arrivals(rate, duration_s, seed=7)
+    jobs = [(float(t),) + datagen.served_job(j) for j, t in enumerate(arr)]
+    jobs.append((1.0,) + datagen.served_job(0, big=True))
+    jobs.sort(key=lambda x: x[0])
+    return jobs
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if xs else None
+
+
+def run_serving(binding, device: int, duration_s: float) -> dict:
+    """Served FP32 path (bn_submit/bn_poll, 8 slots) against the plain FP64
+    one-job-at-a-time path on the same arrival trace."""
+    trace = serving_trace(duration_s)
+    descs = [binding.Job(ds.data, ds.arity, d, precision="fp32") for _, ds, d in trace]
+    out = {}
+    # served: continuous batching
+    lat, res = [], {}
+    with binding.Context(device, slots=8) as ctx:
+        pending = {}
+        k = 0
+        t0 = time.perf_counter()
+        while k < len(trace) or pending:
+            now = time.perf_counter() - t0
+            while k < len(trace) and trace[k][0] <= now:
+                pending[binding.bn_submit(ctx.h, descs[k])] = k
+                k += 1
+            for jid in list(pending):
+                kk = pending[jid]
+                rc, post, _ = binding.bn_poll(ctx.h, jid, trace[kk][1].n)
+                if rc == binding.BN_EAGAIN:
+                    continue
+                if rc != binding.BN_OK:
+                    raise binding.BnError(rc, "served job")
+                lat.append(time.perf_counter() - t0 - trace[kk][0])
+                res[kk] = post
+                del pending[jid]
+        span = time.perf_counter() - t0
+    out["served_fp32"] = {"jobs": len(lat), "jobs_per_s": len(lat) / span,
+                          "p50_ms": _pct(lat, 50) * 1e3, "p99_ms": _pct(lat, 99) * 1e3,
+                          "slots": 8}
+    # plain: FP64, one job at a time, first come first served
+    lat64, err = [], 0.0
+    with binding.Context(device, slots=1) as ctx:
+        t0 = time.perf_counter()
+        for kk, (t_arr, ds, d) in enumerate(trace):
+            wait = t_arr - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            post, _ = binding.bn_edge_posteriors(ctx.h, binding.Job(ds.data, ds.arity, d,
+                                                                    precision="fp64"))
+            lat64.append(time.perf_counter() - t0 - t_arr)
+            err = max(err, float(np.abs(post - res[kk]).max()))
+        span64 = time.perf_counter() - t0
+    out["plain_fp64"] = {"jobs": len(lat64), "jobs_per_s": len(lat64) / span64,
+                         "p50_ms": _pct(lat64, 50) * 1e3, "p99_ms": _pct(lat64, 99) * 1e3}
+    out["max_abs_err_fp32_vs_fp64"] = err
+    out["trace"] = (f"Poisson 200 jobs/s for {duration_s:g} s (seed 7): n~U[8,22], d=3, binary, "
+                    f"m=500, plus one n=29, m=2000 job at t=1 s; {len(trace)} jobs")
+    return out
+
+
+# ------------------------------------------------------------- batches --
+def run_batched(binding, torch, device: int, jobs_n: int = 256, reps: int = 5) -> dict:
+    """The batched workload (job j: seed 1000+j, n~U[10,18], d=3, arity
+    U{2,3}, m~U[100,1000]) as one CUDA graph in FP32, against the plain FP64
+    path running the same jobs one at a time."""
+    jobs = [datagen.batched_job(j) for j in range(jobs_n)]
+    cells = sum(ds.n * 2 ** ds.n for ds, _ in jobs)
+    out = {}
+    with binding.Context(device) as ctx:
+        descs = [binding.Job(ds.data, ds.arity, d, precision="fp32") for ds, d in jobs]
+        t0 = time.perf_counter()
+        batch = binding.Batch(ctx.h, descs)
+        build_s = time.perf_counter() - t0
+        stream = torch.cuda.Stream()
+        for _ in range(2):
+            batch.run(stream)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            batch.run(stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res = [batch.results(k)[0] for k in range(jobs_n)]
+        batch.close()
+        out["batched_fp32_graph"] = {"jobs": jobs_n, "ms_per_batch": ms,
+                                     "jobs_per_s": jobs_n / (ms / 1e3),
+                                     "cells_per_s": cells / (ms / 1e3),
+                                     "build_ms": build_s * 1e3}
+        err = 0.0
+        t0 = time.perf_counter()
+        for k, (ds, d) in enumerate(jobs):
+            post, _ = binding.bn_edge_posteriors(ctx.h, binding.Job(ds.data, ds.arity, d,
+                                                                    precision="fp64"))
+            err = max(err, float(np.abs(post - res[k]).max()))
+        s64 = time.perf_counter() - t0
+        out["plain_fp64_one_at_a_time"] = {"jobs": jobs_n, "s": s64, "jobs_per_s": jobs_n / s64,
+                                           "cells_per_s": cells / s64}
+        out["max_abs_err_fp32_vs_fp64"] = err
+    return out
+
+
 # ---------------------------------------------------------------- ours --
 def run_ours(args):
     import torch
@@ -359,6 +472,10 @@ def run_ours(args):
                                                   "ms_backward", "ms_gamma_p1", "ms_gamma_p2",
                                                   "ms_edges")},
             "max_abs_diff_vs_fp32": err}
+
+    if rank == 0 and not args.no_serve:
+        extra["serving"] = run_serving(binding, local, args.serve_seconds)
+        extra["batched"] = run_batched(binding, torch, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

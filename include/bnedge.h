@@ -121,6 +121,12 @@ int bn_ctx_destroy(bn_ctx* ctx);
  * 0 for invalid n or d. */
 int64_t bn_num_families(int32_t n, int32_t d);
 
+/* Device bytes one job needs (its DP arrays A, F, R', the Gamma scratch and
+ * the score tables; A alone is n * 2^(n-1) values).  bn_submit admits a job
+ * only while the sum of the footprints of the jobs it runs stays within the
+ * context's budget.  BN_EINVAL for an invalid job. */
+int bn_job_footprint(const bn_job_desc* job, uint64_t* bytes);
+
 /* Step 1 only (Eq. 6, Algorithm 1 step 1): parent_mask[i*K+f] and
  * log_B[i*K+f] (FP64, natural log, including log_rho) on the host.  Blocks
  * until done. */
@@ -165,6 +171,21 @@ int bn_edge_posteriors_async(bn_ctx* ctx, const bn_job_desc* job,
 #define BN_STATIC_SCRATCH_BYTES (64u << 20)
 int bn_edge_posteriors_static(const bn_job_desc* job, double* post_dev,
                               double* log_PD_dev, void* stream);
+
+/* Batches.  Many independent jobs (typically small n) planned together:
+ * bn_batch_create validates every job, copies its host inputs into one
+ * device arena, and records the kernels of all jobs into one CUDA graph, the
+ * jobs spread over up to 32 concurrent branches.  bn_batch_run replays the
+ * graph on `stream` (NULL = the context's stream) without host
+ * synchronisation: one launch runs the whole batch.  bn_batch_results waits
+ * for the last run and copies job k's posteriors (n*n doubles) and log P(D).
+ * Device data pointers are not accepted (BN_EINVAL).  The arena counts
+ * against the context's budget (BN_ENOMEM). */
+typedef struct bn_batch bn_batch;
+int bn_batch_create(bn_ctx* ctx, const bn_job_desc* jobs, int32_t count, bn_batch** batch);
+int bn_batch_run(bn_batch* batch, void* stream);
+int bn_batch_results(bn_batch* batch, int32_t k, double* post, double* log_PD);
+int bn_batch_destroy(bn_batch* batch);
 
 /* Serving.  bn_submit copies the inputs, admits the job when a slot and
  * enough device memory (by its n*2^n footprint) are free -- queuing it

@@ -56,7 +56,8 @@ _lib = None
 EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_edge_posteriors", "bn_edge_posteriors_async", "bn_submit", "bn_poll", "bn_wait",
            "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror", "bn_debug_stage",
-           "bn_debug_counts", "bn_edge_posteriors_static"]
+           "bn_debug_counts", "bn_edge_posteriors_static", "bn_job_footprint", "bn_batch_create",
+           "bn_batch_run", "bn_batch_results", "bn_batch_destroy"]
 
 
 def library_path() -> str:
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_ctx_create": (C.c_int, [C.POINTER(P), C.POINTER(bn_ctx_opts)]),
         "bn_ctx_destroy": (C.c_int, [P]),
         "bn_num_families": (C.c_int64, [C.c_int32, C.c_int32]),
+        "bn_job_footprint": (C.c_int, [C.POINTER(bn_job_desc), C.POINTER(C.c_uint64)]),
         "bn_scores": (C.c_int, [P, C.POINTER(bn_job_desc), P, P]),
         "bn_edge_posteriors": (C.c_int, [P, C.POINTER(bn_job_desc), P, P]),
         "bn_edge_posteriors_async": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
@@ -92,6 +94,10 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_stats_history": (C.c_int, [P, C.POINTER(bn_stats), C.c_int32,
                                        C.POINTER(C.c_int32)]),
         "bn_strerror": (C.c_char_p, [C.c_int]),
+        "bn_batch_create": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.POINTER(P)]),
+        "bn_batch_run": (C.c_int, [P, P]),
+        "bn_batch_results": (C.c_int, [P, C.c_int32, P, P]),
+        "bn_batch_destroy": (C.c_int, [P]),
         "bn_debug_stage": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
         "bn_debug_counts": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_uint32, P,
                                       C.c_int64]),
@@ -129,6 +135,14 @@ def bn_strerror(code: int) -> str:
 
 def bn_num_families(n: int, d: int) -> int:
     return int(load().bn_num_families(n, d))
+
+
+def bn_job_footprint(job: "Job") -> int:
+    out = C.c_uint64()
+    rc = load().bn_job_footprint(C.byref(job.desc), C.byref(out))
+    if rc:
+        raise BnError(rc, "bn_job_footprint")
+    return int(out.value)
 
 
 def bn_ctx_create(device: int = 0, slots: int = 4, mem_budget: int = 0,
@@ -264,6 +278,45 @@ def bn_debug_counts(ctx: int, job: Job, i: int, mask: int, cells: int) -> np.nda
     if rc:
         raise BnError(rc, "bn_debug_counts")
     return out
+
+
+class Batch:
+    """Owns one bn_batch: many independent jobs replayed as one CUDA graph."""
+
+    def __init__(self, ctx: int, jobs: list):
+        self.jobs = list(jobs)
+        arr = (bn_job_desc * len(self.jobs))(*[j.desc for j in self.jobs])
+        self._arr = arr
+        h = C.c_void_p()
+        rc = load().bn_batch_create(ctx, arr, len(self.jobs), C.byref(h))
+        if rc:
+            raise BnError(rc, "bn_batch_create")
+        self.h = h.value
+
+    def run(self, stream=None) -> None:
+        rc = load().bn_batch_run(self.h, _ptr(stream))
+        if rc:
+            raise BnError(rc, "bn_batch_run")
+
+    def results(self, k: int):
+        n = self.jobs[k].n
+        post = np.zeros((n, n))
+        lpd = np.zeros(1)
+        rc = load().bn_batch_results(self.h, k, _ptr(post), _ptr(lpd))
+        if rc:
+            raise BnError(rc, "bn_batch_results")
+        return post, float(lpd[0])
+
+    def close(self):
+        if self.h:
+            load().bn_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Context:

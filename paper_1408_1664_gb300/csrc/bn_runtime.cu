@@ -202,6 +202,9 @@ struct Bufs {
     template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
 };
 
+int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, double* post_dev,
+                    double* logPD_dev, cudaStream_t s, Events* ev, int* launches);
+
 // Enqueue steps 1-5 on stream s.  Small host arrays go through `stage`
 // (pinned, >= stage_bytes) when given, else through pageable copies.
 int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_dev,
@@ -210,7 +213,6 @@ int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_de
 {
     const Plan& P = hj.P;
     const Layout& L = B.L;
-    int nl = 0;
     if (ev) CK(cudaEventRecord(ev->ev[0], s));
     // inputs
     const uint8_t* data_dev = B.at<uint8_t>(L.data);
@@ -246,6 +248,16 @@ int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_de
         CK(cudaMemcpyAsync(B.at<char>(L.Dvals), src + n_ar + n_lr, 2 * n_dv,
                            cudaMemcpyHostToDevice, s));
     }
+    return enqueue_kernels(hj, B, data_dev, post_dev, logPD_dev, s, ev, launches);
+}
+
+// Enqueue the kernels of steps 1-5 on stream s (inputs already on the device).
+int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, double* post_dev,
+                    double* logPD_dev, cudaStream_t s, Events* ev, int* launches)
+{
+    const Plan& P = hj.P;
+    const Layout& L = B.L;
+    int nl = 0;
     CK(cudaMemsetAsync(B.at<int>(L.err), 0, 4, s));
     int* err = B.at<int>(L.err);
     const uint8_t* ar = B.at<uint8_t>(L.arity);
@@ -291,6 +303,7 @@ int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_de
     }
     return BN_OK;
 }
+
 
 double alg_bytes(const Plan& P)
 {
@@ -380,6 +393,22 @@ struct bn_ctx {
     std::deque<uint64_t> queue;
     uint64_t next_id = 1;
     uint64_t reserved = 0;
+};
+
+struct bn_batch {
+    bn_ctx* ctx = nullptr;
+    std::vector<HostJob> jobs;
+    std::vector<Layout> layouts;
+    std::vector<size_t> offs, out_off;
+    char* arena = nullptr;
+    char* out = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last = nullptr;
+    bool ran = false;
 };
 
 namespace {
@@ -500,6 +529,16 @@ const char* bn_strerror(int code)
 }
 
 int64_t bn_num_families(int32_t n, int32_t d) { return families(n, d); }
+
+int bn_job_footprint(const bn_job_desc* job, uint64_t* bytes)
+{
+    if (!bytes) return BN_EINVAL;
+    HostJob hj;
+    const int rc = validate_and_plan(job, hj);
+    if (rc) return rc;
+    *bytes = make_layout(hj.P, 0).total;
+    return BN_OK;
+}
 
 int bn_ctx_create(bn_ctx** out, const bn_ctx_opts* o)
 {
@@ -754,6 +793,127 @@ int bn_stats_history(bn_ctx* c, bn_stats* out, int32_t max, int32_t* count)
         fill_stats(ev.P, ev, ev.launches, &out[t]);
     }
     *count = k;
+    return BN_OK;
+}
+
+// ---------------------------------------------------------------- batches --
+
+int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch** out)
+{
+    if (!c || !jobs || !out || count < 1) return BN_EINVAL;
+    *out = nullptr;
+    bn_batch* b = new bn_batch();
+    b->ctx = c;
+    b->jobs.resize(count);
+    size_t total = 0, outs = 0;
+    for (int k = 0; k < count; ++k) {
+        HostJob& hj = b->jobs[k];
+        int rc = jobs[k].data_on_device ? BN_EINVAL : validate_and_plan(&jobs[k], hj);
+        if (rc) { delete b; return rc; }
+        const Plan& P = hj.P;
+        hj.data_copy.assign(jobs[k].data ? jobs[k].data : (const uint8_t*)"",
+                            jobs[k].data ? jobs[k].data + (size_t)P.m * P.n : (const uint8_t*)"");
+        hj.data = hj.data_copy.data();
+        b->layouts.push_back(make_layout(P, 0));
+        b->offs.push_back(total);
+        total += b->layouts.back().total;
+        b->out_off.push_back(outs);
+        outs += al((size_t)P.n * P.n * 8 + 8);
+    }
+    if (total + outs > c->budget) { delete b; return BN_ENOMEM; }
+    if (cudaSetDevice(c->device) != cudaSuccess) { delete b; return BN_ECUDA; }
+    void* p = nullptr;
+    int rc = dev_alloc(c, &p, total + outs, nullptr);
+    if (rc) { delete b; return rc; }
+    b->arena = (char*)p;
+    b->out = b->arena + total;
+    rc = BN_ECUDA;
+    cudaStream_t cap = c->stream;
+    const int nb = std::min(count, 32);
+    b->streams.assign(nb, nullptr);
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (auto& st : b->streams) ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    b->joins.assign(nb, nullptr);
+    for (auto& e : b->joins) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    // inputs go to the device now; only kernels are captured
+    for (int k = 0; ok && k < count; ++k) {
+        const HostJob& hj = b->jobs[k];
+        const Layout& L = b->layouts[k];
+        Bufs B{b->arena + b->offs[k], L};
+        std::vector<double> lr(hj.P.d + 1, 0.0), alpha(hj.P.rows);
+        for (size_t t = 0; t < hj.log_rho.size(); ++t) lr[t] = hj.log_rho[t];
+        for (int r = 0; r < hj.P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
+        ok = (hj.P.m == 0 || cudaMemcpy(B.at<char>(L.data), hj.data, (size_t)hj.P.m * hj.P.n,
+                                        cudaMemcpyHostToDevice) == cudaSuccess) &&
+             cudaMemcpy(B.at<char>(L.arity), hj.arity.data(), hj.P.n, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(B.at<char>(L.log_rho), lr.data(), lr.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(B.at<char>(L.Dvals), hj.Dvals.data(), hj.Dvals.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(B.at<char>(L.alpha), alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    ok = ok && cudaStreamSynchronize(cap) == cudaSuccess;
+    if (ok && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        bool cap_ok = cudaEventRecord(b->fork, cap) == cudaSuccess;
+        for (auto st : b->streams) cap_ok = cap_ok && cudaStreamWaitEvent(st, b->fork, 0) == cudaSuccess;
+        for (int k = 0; cap_ok && k < count; ++k) {
+            const HostJob& hj = b->jobs[k];
+            Bufs B{b->arena + b->offs[k], b->layouts[k]};
+            double* post = reinterpret_cast<double*>(b->out + b->out_off[k]);
+            cap_ok = enqueue_kernels(hj, B, B.at<uint8_t>(B.L.data), post, post + hj.P.n * hj.P.n,
+                                     b->streams[k % nb], nullptr, nullptr) == BN_OK;
+        }
+        for (int q = 0; cap_ok && q < nb; ++q)
+            cap_ok = cudaEventRecord(b->joins[q], b->streams[q]) == cudaSuccess &&
+                     cudaStreamWaitEvent(cap, b->joins[q], 0) == cudaSuccess;
+        cudaGraph_t g = nullptr;
+        const bool end_ok = cudaStreamEndCapture(cap, &g) == cudaSuccess;
+        if (cap_ok && end_ok && g && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+            b->graph = g;
+            rc = BN_OK;
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    cudaGetLastError();
+    if (rc) { bn_batch_destroy(b); return rc; }
+    *out = b;
+    return BN_OK;
+}
+
+int bn_batch_run(bn_batch* b, void* stream)
+{
+    if (!b || !b->exec) return BN_EINVAL;
+    cudaSetDevice(b->ctx->device);
+    b->last = stream ? (cudaStream_t)stream : b->ctx->stream;
+    CK(cudaGraphLaunch(b->exec, b->last));
+    b->ran = true;
+    return BN_OK;
+}
+
+int bn_batch_results(bn_batch* b, int32_t k, double* post, double* log_PD)
+{
+    if (!b || !post || k < 0 || k >= (int32_t)b->jobs.size() || !b->ran) return BN_EINVAL;
+    const Plan& P = b->jobs[k].P;
+    CK(cudaStreamSynchronize(b->last));
+    const char* src = b->out + b->out_off[k];
+    CK(cudaMemcpy(post, src, (size_t)P.n * P.n * 8, cudaMemcpyDeviceToHost));
+    if (log_PD) CK(cudaMemcpy(log_PD, src + (size_t)P.n * P.n * 8, 8, cudaMemcpyDeviceToHost));
+    int err = 0;
+    CK(cudaMemcpy(&err, b->arena + b->offs[k] + b->layouts[k].err, 4, cudaMemcpyDeviceToHost));
+    return err ? BN_EINVAL : BN_OK;
+}
+
+int bn_batch_destroy(bn_batch* b)
+{
+    if (!b) return BN_EINVAL;
+    cudaSetDevice(b->ctx->device);
+    if (b->ran) cudaStreamSynchronize(b->last);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto st : b->streams) if (st) cudaStreamDestroy(st);
+    for (auto e : b->joins) if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->arena) cudaFree(b->arena);
+    delete b;
     return BN_OK;
 }
 
