@@ -323,6 +323,7 @@ __global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs,
 template <typename T>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* __restrict__ unrank13,
+           const uint32_t* __restrict__ rowmask, const uint32_t* __restrict__ rowoff,
            T* __restrict__ A)
 {
     using Lg = LogOps<T>;
@@ -357,45 +358,53 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
     for (int r = 0; r < TR; ++r) A0[swz(el1(r, t))] = Lg::ninf();   // no term: zero
     __syncthreads();
 
-    // --- rows whose high part lies inside H (size-major order), with the
-    //     offset of each row in the node's reordered table ------------------
-    const uint32_t chunk = (nrow + TT - 1) / TT;
-    const uint32_t r0 = min(nrow, (uint32_t)t * chunk), r1 = min(nrow, r0 + chunk);
+    // --- rows whose high part lies inside H, kept in row order (size-major):
+    //     warp w scans a contiguous range of rows, 32 at a time (ballot), and
+    //     the warps' counts are scanned so the list stays in row order.  The
+    //     list holds each row's table offset; rowsr holds its row index.
+    uint32_t* rowsr = rowbase + nrow;
+    const uint32_t per_warp = (nrow + (TT / 32) - 1) / (TT / 32);
+    const uint32_t wr0 = min(nrow, (uint32_t)warp * per_warp), wr1 = min(nrow, wr0 + per_warp);
     int cnt = 0;
-    for (uint32_t r = r0; r < r1; ++r) {
-        int k;
-        const uint32_t G = sb_unrank(*sb, r, h, &k);
-        if ((G & ~H) == 0u) { ++cnt; atomicAdd(&meta[k], 1); }
+    for (uint32_t b = wr0; b < wr1; b += 32) {
+        const uint32_t r = b + lane;
+        const bool hit = r < wr1 && (rowmask[r] & ~H) == 0u;
+        cnt += __popc(__ballot_sync(FULLMASK, hit));
     }
-    int incl = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULLMASK, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) meta[64 + warp] = incl;
+    if (lane == 0) meta[64 + warp] = cnt;
     __syncthreads();
-    int pos = incl - cnt;
+    int pos = 0;
     for (int w = 0; w < warp; ++w) pos += meta[64 + w];
-    for (uint32_t r = r0; r < r1; ++r) {
-        int k;
-        const uint32_t G = sb_unrank(*sb, r, h, &k);
-        if ((G & ~H) == 0u) {
-            // offset = sum over smaller classes of C(h,k') * C13(<= d-k') + rank in class * C13(<= d-k)
-            uint32_t base = 0;
-            for (int kk = 0; kk < k; ++kk) base += sb_binom(*sb, h, kk) * off13[min(d - kk, TB) + 1];
-            const uint32_t rin = r - (k == 0 ? 0u : num_small_subsets(h, k - 1));
-            rowbase[pos++] = base + rin * off13[min(d - k, TB) + 1];
+    for (uint32_t b = wr0; b < wr1; b += 32) {
+        const uint32_t r = b + lane;
+        const bool hit = r < wr1 && (rowmask[r] & ~H) == 0u;
+        const uint32_t bal = __ballot_sync(FULLMASK, hit);
+        if (hit) {
+            const int at = pos + __popc(bal & ((1u << lane) - 1u));
+            rowbase[at] = rowoff[r];
+            rowsr[at] = r;
         }
+        pos += __popc(bal);
     }
-    if (t == 0) {
-        int s2 = 0;
-        for (int k = 0; k <= d + 1 && k < 32; ++k) { meta[32 + k] = s2; if (k <= d) s2 += meta[k]; }
+    __syncthreads();
+    int total = 0;
+    for (int w = 0; w < TT / 32; ++w) total += meta[64 + w];
+    // class k starts at the first listed row with index >= first row of class k
+    if (t <= d + 1 && t < 32) {
+        const uint32_t rs = num_small_subsets(h, t - 1);
+        int lo = 0, hi = total;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (rowsr[mid] < rs) lo = mid + 1; else hi = mid;
+        }
+        meta[32 + t] = lo;
     }
     __syncthreads();
 
     // --- per-column log-sum over the admissible rows, in a fixed order ------
     // column c (low pattern of size j) takes the rows of classes k <= d - j:
     // the list prefix up to the start of class d - j + 1.
+    T tm = Lg::ninf();                      // this thread's largest column maximum
     for (uint32_t c = warp; c < 32 && c < ncol; c += TT / 32) {          // heavy columns: a warp each
         int j = 0;
         while (off13[j + 1] <= c) ++j;
@@ -416,8 +425,8 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
         if (lane == 0) {
             const uint32_t sw = swz(unrank13[c]);
             A0[sw] = A1[sw] = mx + Lg::lg(sm);
-            atomicMax(tmax, ord_enc(mx));
         }
+        tm = mx > tm ? mx : tm;
     }
     for (uint32_t c = 32 + t; c < ncol; c += TT) {                       // light columns: a thread each
         int j = 0;
@@ -428,8 +437,14 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
         for (int rp = 0; rp < rend; ++rp) lse_online(mx, sm, tb[rowbase[rp] + c]);
         const uint32_t sw = swz(unrank13[c]);
         A0[sw] = A1[sw] = mx + Lg::lg(sm);
-        atomicMax(tmax, ord_enc(mx));
+        tm = mx > tm ? mx : tm;
     }
+    // one shared atomic per warp for the tile maximum
+    for (int o = 16; o; o >>= 1) {
+        const T o2 = __shfl_xor_sync(FULLMASK, tm, o);
+        tm = o2 > tm ? o2 : tm;
+    }
+    if (lane == 0) atomicMax(tmax, ord_enc(tm));
     __syncthreads();
 
     T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
@@ -613,6 +628,21 @@ __global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restr
     unrank13[r] = (uint16_t)L;
 }
 
+// Rows of the reordered score table: rowmask[r] = the high part G_H of row r
+// (subsets of the h high bits with at most d elements, by size then value)
+// and rowoff[r] = the row's offset in a node's table.
+__global__ void k_row_tables(int h, int d, uint32_t nrow, uint32_t* __restrict__ rowmask,
+                             uint32_t* __restrict__ rowoff)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrow) return;
+    uint32_t rr = r;
+    int k = 0;
+    while (rr >= binom(h, k)) { rr -= binom(h, k); ++k; }
+    rowmask[r] = colex_unrank(rr, k, h);
+    rowoff[r] = row_offset(h, d, k, rr);
+}
+
 // ===========================================================================
 // Launchers.
 // ===========================================================================
@@ -624,7 +654,7 @@ size_t upzeta13_smem_bytes(const Plan& P)
     for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
     for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
     (void)ncol;
-    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + nrow * 4 + 16;  // meta[72..73] holds the tile max
+    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + 2 * nrow * 4 + 16;
 }
 
 bool use_tile13_up(const Plan& P)
@@ -655,18 +685,32 @@ cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
-                            cudaStream_t s)
+size_t row_tables_bytes(const Plan& P)
 {
     const int h = P.n - 1 - TB;
+    uint64_t nrow = 0;
+    for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
+    return (size_t)nrow * 8;
+}
+
+cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13,
+                            uint32_t* rowtabs, void* A, cudaStream_t s)
+{
+    const int h = P.n - 1 - TB;
+    uint64_t nrow = 0;
+    for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
+    k_row_tables<<<(unsigned)((nrow + 255) / 256), 256, 0, s>>>(h, P.d, (uint32_t)nrow, rowtabs,
+                                                                rowtabs + nrow);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
     const unsigned grid = (unsigned)P.n << h;
     const size_t sm = upzeta13_smem_bytes(P);
     if (P.prec == 0)
         k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const double*)tab, unrank13,
-                                                (double*)A);
+                                                rowtabs, rowtabs + nrow, (double*)A);
     else
         k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const float*)tab, unrank13,
-                                               (float*)A);
+                                               rowtabs, rowtabs + nrow, (float*)A);
     return cudaGetLastError();
 }
 
