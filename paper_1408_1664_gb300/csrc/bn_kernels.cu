@@ -884,10 +884,7 @@ cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs
     if (use_tile13_up(P)) {
         cudaError_t e = launch_reorder_up(P, lbs, tab, s);
         if (e != cudaSuccess) return e;
-        const size_t es = P.prec == 0 ? 8 : 4;
-        uint32_t* rowtabs = reinterpret_cast<uint32_t*>(
-            static_cast<char*>(tab) + (((size_t)P.n * P.K * es + 255) & ~(size_t)255));
-        return launch_upzeta13(P, tab, rk13 + 8192, rowtabs, A, s);
+        return launch_upzeta13(P, tab, rk13 + 8192, A, s);
     }
     const int h = P.n - 1 - P.b_up;
     const unsigned grid = (unsigned)P.n << h;

@@ -36,9 +36,8 @@ cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cud
 cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double* cmax,
                                 void* lbs, cudaStream_t s);
 // Step 2.  n >= 14 uses the 13-dimension register tiles and needs `tab`
-// (n*K values, the scores reordered by high and low parts, followed by
-// row_tables_bytes(P) bytes of row tables); smaller n use one shared-memory
-// tile per node slice and ignore `tab`.
+// (n*K values, the scores reordered by high and low parts); smaller n use
+// one shared-memory tile per node slice and ignore `tab`.
 // `rk13` points at the two 8192-entry uint16 subset-rank tables (rank, then
 // inverse) of the 13-dimension tiles, filled by launch_rank13_tables.
 cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
@@ -57,9 +56,8 @@ size_t upzeta_smem_bytes(const Plan& P);
 // bn_tile13.cu
 cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s);
 cudaError_t launch_rank13_tables(uint16_t* rank13, uint16_t* unrank13, cudaStream_t s);
-cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13,
-                            uint32_t* rowtabs, void* A, cudaStream_t s);
-size_t row_tables_bytes(const Plan& P);   // appended to the reordered table
+cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
+                            cudaStream_t s);
 cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* Rc,
                               const uint16_t* rank13, void* W, cudaStream_t s);
 constexpr size_t kRank13Bytes = 2 * 8192 * sizeof(uint16_t);

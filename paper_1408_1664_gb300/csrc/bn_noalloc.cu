@@ -179,7 +179,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                  o_pl = take((size_t)P.n * P.rmax * P.W * 8), o_err = take(4),
                  o_masks = take(nK * 4), o_cm = take(nK * 4), o_logB = take(nK * 8),
                  o_cmax = take((size_t)P.n * 8), o_lbs = take(nK * es),
-                 o_reo = take(bn::use_tile13_up(P) ? al(nK * es) + bn::row_tables_bytes(P) : 0),
+                 o_reo = take(bn::use_tile13_up(P) ? nK * es : 0),
                  o_rk = take(bn::use_tile13_gamma(P) ? bn::kRank13Bytes : 0),
                  o_A = take(((size_t)P.n << (P.n - 1)) * es), o_F = take(((size_t)1 << P.n) * es),
                  o_Rc = take(((size_t)1 << P.n) * es),

@@ -77,7 +77,7 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     L.logB = take(nK * 8);
     L.cmax = take((size_t)P.n * 8);
     L.lbs = take(nK * es);
-    L.tab = take(bn::use_tile13_up(P) ? al(nK * es) + bn::row_tables_bytes(P) : 0);
+    L.tab = take(bn::use_tile13_up(P) ? nK * es : 0);
     L.rk13 = take(bn::use_tile13_gamma(P) ? bn::kRank13Bytes : 0);
     L.A = take(((size_t)P.n << (P.n - 1)) * es);
     L.F = take(((size_t)1 << P.n) * es);

@@ -236,19 +236,22 @@ template <> __device__ __forceinline__ void st3<float>(float* a, const float (&v
         *reinterpret_cast<float4*>(a + base + 4) = q;
     }
 }
-// Binomial coefficients C(a, b), a < 32, b <= 8, in shared memory (indices
-// differ across lanes, which would serialise constant-cache reads).
+// Binomial coefficients C(a, b), a < 32, in shared memory, stored for
+// b <= a / 2 only (C(a, b) = C(a, a - b)).  Lanes look up different entries,
+// which would serialise constant-cache reads; the table is copied from a
+// global-memory image with coalesced loads.
+__device__ const BinomTable g_binom_image = make_binom_table();
 struct SBinom {
-    uint32_t v[32][9];
+    uint32_t v[32][16];
 };
 __device__ __forceinline__ void fill_sbinom(SBinom& sb)
 {
-    for (int x = threadIdx.x; x < 32 * 9; x += blockDim.x) sb.v[x / 9][x % 9] = binom(x / 9, x % 9);
+    for (int x = threadIdx.x; x < 32 * 16; x += blockDim.x) sb.v[x >> 4][x & 15] = g_binom_image.v[x >> 4][x & 15];
 }
 __device__ __forceinline__ uint32_t sb_binom(const SBinom& sb, int a, int b)
 {
     if (b < 0 || b > a) return 0u;
-    return b > 8 ? binom(a, b) : sb.v[a][b];
+    return sb.v[a][min(b, a - b)];
 }
 __device__ __forceinline__ uint32_t sb_unrank(const SBinom& sb, uint32_t r, int nb, int* kout)
 {
@@ -323,7 +326,6 @@ __global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs,
 template <typename T>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* __restrict__ unrank13,
-           const uint32_t* __restrict__ rowmask, const uint32_t* __restrict__ rowoff,
            T* __restrict__ A)
 {
     using Lg = LogOps<T>;
@@ -358,86 +360,143 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
     for (int r = 0; r < TR; ++r) A0[swz(el1(r, t))] = Lg::ninf();   // no term: zero
     __syncthreads();
 
-    // --- rows whose high part lies inside H, kept in row order (size-major):
-    //     warp w scans a contiguous range of rows, 32 at a time (ballot), and
-    //     the warps' counts are scanned so the list stays in row order.  The
-    //     list holds each row's table offset; rowsr holds its row index.
-    uint32_t* rowsr = rowbase + nrow;
-    const uint32_t per_warp = (nrow + (TT / 32) - 1) / (TT / 32);
-    const uint32_t wr0 = min(nrow, (uint32_t)warp * per_warp), wr1 = min(nrow, wr0 + per_warp);
-    int cnt = 0;
-    for (uint32_t b = wr0; b < wr1; b += 32) {
-        const uint32_t r = b + lane;
-        const bool hit = r < wr1 && (rowmask[r] & ~H) == 0u;
-        cnt += __popc(__ballot_sync(FULLMASK, hit));
-    }
-    if (lane == 0) meta[64 + warp] = cnt;
-    __syncthreads();
-    int pos = 0;
-    for (int w = 0; w < warp; ++w) pos += meta[64 + w];
-    for (uint32_t b = wr0; b < wr1; b += 32) {
-        const uint32_t r = b + lane;
-        const bool hit = r < wr1 && (rowmask[r] & ~H) == 0u;
-        const uint32_t bal = __ballot_sync(FULLMASK, hit);
-        if (hit) {
-            const int at = pos + __popc(bal & ((1u << lane) - 1u));
-            rowbase[at] = rowoff[r];
-            rowsr[at] = r;
-        }
-        pos += __popc(bal);
+    // --- rows whose high part lies inside H, in row order (by size, then
+    //     colex): the k-element subsets of H in increasing mask order.  Entry
+    //     p of the list is unranked among the subsets of H's hc positions,
+    //     its positions are mapped onto the bits of H, and the row's offset in
+    //     the node's table follows from its colex rank among all h-bit sets.
+    const int hc = __popc(H);
+    const int kmax = min(d, hc);
+    if (t < 32) {
+        // meta[32 + k]: first list entry of class k (entries of size k)
+        meta[32 + t] = (int)num_small_subsets(hc, min(t, d + 1) - 1);
+        // meta[k]: offset of the first class-k row in the node's table
+        uint32_t o = 0;
+        for (int k = 0; k < t && k <= min(d, h); ++k) o += binom(h, k) * off13[min(d - k, TB) + 1];
+        meta[t] = (int)o;
     }
     __syncthreads();
-    int total = 0;
-    for (int w = 0; w < TT / 32; ++w) total += meta[64 + w];
-    // class k starts at the first listed row with index >= first row of class k
-    if (t <= d + 1 && t < 32) {
-        const uint32_t rs = num_small_subsets(h, t - 1);
-        int lo = 0, hi = total;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (rowsr[mid] < rs) lo = mid + 1; else hi = mid;
+    const int total = meta[32 + kmax + 1];
+    for (int p = t; p < total; p += TT) {
+        int k;
+        const uint32_t loc = sb_unrank(*sb, (uint32_t)p, hc, &k);
+        uint32_t rk = 0, hh = H;
+        int q = 0, idx = 1;
+        while (hh) {
+            const int b = __ffs(hh) - 1;
+            hh &= hh - 1;
+            if (loc >> q & 1u) rk += sb_binom(*sb, b, idx++);
+            ++q;
         }
-        meta[32 + t] = lo;
+        rowbase[p] = (uint32_t)meta[k] + rk * off13[min(d - k, TB) + 1];
     }
     __syncthreads();
 
     // --- per-column log-sum over the admissible rows, in a fixed order ------
-    // column c (low pattern of size j) takes the rows of classes k <= d - j:
-    // the list prefix up to the start of class d - j + 1.
+    // Column c (low pattern of size j) takes the rows of size at most d - j,
+    // i.e. the list prefix before the first row of size d - j + 1; a row of
+    // size k holds the first W_k = off13[d - k + 1] columns.
     T tm = Lg::ninf();                      // this thread's largest column maximum
-    for (uint32_t c = warp; c < 32 && c < ncol; c += TT / 32) {          // heavy columns: a warp each
-        int j = 0;
-        while (off13[j + 1] <= c) ++j;
-        const int rend = meta[32 + min(d - j + 1, 31)];
-        T mx = Lg::ninf(), sm = T(0);
-#pragma unroll 4
-        for (int rp = lane; rp < rend; rp += 32) lse_online(mx, sm, tb[rowbase[rp] + c]);
-        // combine the lanes' (max, sum) pairs in a fixed tree order
-        for (int o = 16; o; o >>= 1) {
-            const T m2 = __shfl_xor_sync(FULLMASK, mx, o);
-            const T s2 = __shfl_xor_sync(FULLMASK, sm, o);
-            const T mn = m2 > mx ? m2 : mx;
-            if (mn != Lg::ninf()) {
-                sm = sm * Lg::ex(mx - mn) + s2 * Lg::ex(m2 - mn);
-                mx = mn;
+    // Long columns (at most d - 2 low elements, many rows): warp w takes the
+    // rows w, w + 8, ... and its lanes the columns of a 96-column block
+    // (coalesced reads along the row); the eight warp partials are combined
+    // in warp order.
+    const uint32_t nlong = d >= 2 ? off13[min(d - 2, TB) + 1] : 0u;
+    T* part = E;                            // 2 * 8 * 96 partial (max, sum) pairs
+    for (uint32_t cb = 0; cb < nlong; cb += 96) {
+        T m[3], sm[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { m[q] = Lg::ninf(); sm[q] = T(0); }
+        // rows of size k hold W_k columns; only sizes with W_k > cb reach this block
+        int kb = 0;
+        while (kb < kmax && off13[min(d - kb - 1, TB) + 1] > cb) ++kb;
+        const int pend = meta[32 + kb + 1];
+        int k = 0;
+        for (int p0 = warp; p0 < pend; p0 += 4 * (TT / 32)) {
+            T x[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + u * (TT / 32);
+                while (k < kb && p >= meta[32 + k + 1]) ++k;
+                const uint32_t W = p < pend ? min(nlong, off13[min(d - k, TB) + 1]) : 0u;
+                const T* src = tb + (p < pend ? rowbase[p] : 0u);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const uint32_t c = cb + lane + 32 * q;
+                    x[u][q] = c < W ? src[c] : Lg::ninf();
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) lse_online(m[q], sm[q], x[u][q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            part[(warp * 96 + lane + 32 * q) * 2] = m[q];
+            part[(warp * 96 + lane + 32 * q) * 2 + 1] = sm[q];
+        }
+        __syncthreads();
+        if (t < 96 && cb + t < nlong) {
+            T mx = Lg::ninf(), s2 = T(0);
+#pragma unroll
+            for (int w = 0; w < TT / 32; ++w) {
+                const T mw = part[(w * 96 + t) * 2], sw = part[(w * 96 + t) * 2 + 1];
+                const T mn = mw > mx ? mw : mx;
+                if (mn != Lg::ninf()) {
+                    s2 = s2 * Lg::ex(mx - mn) + sw * Lg::ex(mw - mn);
+                    mx = mn;
+                }
+            }
+            const uint32_t sw = swz(unrank13[cb + t]);
+            A0[sw] = A1[sw] = mx + Lg::lg(s2);
+            tm = mx > tm ? mx : tm;
+        }
+        __syncthreads();
+    }
+    // Short columns (d - 1 or d low elements): only the row of the empty set
+    // and the 1-element rows, at most 1 + hc; a thread per column, four
+    // columns at a time and eight rows per batch so the loads overlap.
+    for (uint32_t c0 = nlong + t; c0 < ncol; c0 += 4 * TT) {
+        T mx[4], sm[4];
+        int re[4];
+        int rmax = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t c = c0 + q * TT;
+            int rend = 0;
+            if (c < ncol) {
+                int j = 0;
+                while (off13[j + 1] <= c) ++j;
+                rend = meta[32 + min(d - j + 1, 31)];
+            }
+            re[q] = rend;
+            rmax = max(rmax, rend);
+            mx[q] = Lg::ninf();
+            sm[q] = T(0);
+        }
+        for (int rp0 = 0; rp0 < rmax; rp0 += 8) {
+            T x[8][4];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int rp = rp0 + u;
+                const T* src = tb + (rp < rmax ? rowbase[rp] : 0u) + c0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x[u][q] = rp < re[q] ? src[q * TT] : Lg::ninf();
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) lse_online(mx[q], sm[q], x[u][q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (c0 + q * TT < ncol) {
+                const uint32_t sw = swz(unrank13[c0 + q * TT]);
+                A0[sw] = A1[sw] = mx[q] + Lg::lg(sm[q]);
+                tm = mx[q] > tm ? mx[q] : tm;
             }
         }
-        if (lane == 0) {
-            const uint32_t sw = swz(unrank13[c]);
-            A0[sw] = A1[sw] = mx + Lg::lg(sm);
-        }
-        tm = mx > tm ? mx : tm;
-    }
-    for (uint32_t c = 32 + t; c < ncol; c += TT) {                       // light columns: a thread each
-        int j = 0;
-        while (off13[j + 1] <= c) ++j;
-        const int rend = meta[32 + min(d - j + 1, 31)];
-        T mx = Lg::ninf(), sm = T(0);
-#pragma unroll 8
-        for (int rp = 0; rp < rend; ++rp) lse_online(mx, sm, tb[rowbase[rp] + c]);
-        const uint32_t sw = swz(unrank13[c]);
-        A0[sw] = A1[sw] = mx + Lg::lg(sm);
-        tm = mx > tm ? mx : tm;
     }
     // one shared atomic per warp for the tile maximum
     for (int o = 16; o; o >>= 1) {
@@ -628,21 +687,6 @@ __global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restr
     unrank13[r] = (uint16_t)L;
 }
 
-// Rows of the reordered score table: rowmask[r] = the high part G_H of row r
-// (subsets of the h high bits with at most d elements, by size then value)
-// and rowoff[r] = the row's offset in a node's table.
-__global__ void k_row_tables(int h, int d, uint32_t nrow, uint32_t* __restrict__ rowmask,
-                             uint32_t* __restrict__ rowoff)
-{
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrow) return;
-    uint32_t rr = r;
-    int k = 0;
-    while (rr >= binom(h, k)) { rr -= binom(h, k); ++k; }
-    rowmask[r] = colex_unrank(rr, k, h);
-    rowoff[r] = row_offset(h, d, k, rr);
-}
-
 // ===========================================================================
 // Launchers.
 // ===========================================================================
@@ -654,7 +698,7 @@ size_t upzeta13_smem_bytes(const Plan& P)
     for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
     for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
     (void)ncol;
-    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + 2 * nrow * 4 + 16;
+    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + nrow * 4 + 16;
 }
 
 bool use_tile13_up(const Plan& P)
@@ -685,32 +729,18 @@ cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStr
     return cudaGetLastError();
 }
 
-size_t row_tables_bytes(const Plan& P)
+cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
+                            cudaStream_t s)
 {
     const int h = P.n - 1 - TB;
-    uint64_t nrow = 0;
-    for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
-    return (size_t)nrow * 8;
-}
-
-cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13,
-                            uint32_t* rowtabs, void* A, cudaStream_t s)
-{
-    const int h = P.n - 1 - TB;
-    uint64_t nrow = 0;
-    for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
-    k_row_tables<<<(unsigned)((nrow + 255) / 256), 256, 0, s>>>(h, P.d, (uint32_t)nrow, rowtabs,
-                                                                rowtabs + nrow);
-    cudaError_t e0 = cudaGetLastError();
-    if (e0 != cudaSuccess) return e0;
     const unsigned grid = (unsigned)P.n << h;
     const size_t sm = upzeta13_smem_bytes(P);
     if (P.prec == 0)
         k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const double*)tab, unrank13,
-                                                rowtabs, rowtabs + nrow, (double*)A);
+                                                (double*)A);
     else
         k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const float*)tab, unrank13,
-                                               rowtabs, rowtabs + nrow, (float*)A);
+                                               (float*)A);
     return cudaGetLastError();
 }
 

@@ -127,6 +127,23 @@ def test_posteriors_fp32_match_oracle(ctx, n, d, arity, m, seed):
     np.testing.assert_allclose(post, ref["post"], atol=1e-4, rtol=0)
 
 
+# In-degree bounds across the whole range on the 13-dimension tile path
+# (n >= 14): no parents, single parents, bounds that make some tile columns
+# long and others short, and d = n - 1 (every subset is a parent set).
+TILE_CASES = [(14, 0), (14, 1), (14, 5), (15, 7), (15, 14), (17, 2)]
+
+
+@pytest.mark.parametrize("n,d", TILE_CASES)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+def test_tile_path_in_degree_range(ctx, n, d, precision, tol):
+    ds = datagen.random_dag_data(n, 300, 2, min(max(d, 1), 3), 1.0, seed=40 + n + d)
+    ref = orc.edge_posteriors(ds.data, ds.arity, d)
+    post, lpd = ctx.edge_posteriors(ds.data, ds.arity, d, precision=precision)
+    np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
+    if precision == "fp64":
+        assert abs(lpd - ref["log_PD"]) <= 1e-9 * max(1.0, abs(ref["log_PD"]))
+
+
 def test_small_config_both_paths(ctx):
     ds, d = datagen.config_small()
     ref = orc.edge_posteriors(ds.data, ds.arity, d)
