@@ -178,6 +178,23 @@ template <typename T> struct FastSpan;
 template <> struct FastSpan<float> { static constexpr float value = 80.0f; };      // bits
 template <> struct FastSpan<double> { static constexpr double value = 640.0; };    // nats
 
+// Single-scale windows for the upward zeta.  Pass p scales the terms by
+// s_p = M - top - p * win (M bounds every output from above) and writes the
+// outputs whose scaled value is at least 2^lo (e^lo): terms flushed below the
+// smallest normal number (2^-126; e^-708) number at most 8192, under 2^-113
+// (e^-699) in total, which is below 2^-33 (e^-99) of such an output.  An
+// output left over has scaled value below 2^lo in pass p, hence below 2^top
+// in pass p + 1, so no term of it overflows there (2^128; e^709).
+template <typename T> struct Window;
+template <> struct Window<float> {                 // bits
+    static constexpr float top = 126.0f, lo = -80.0f, win = 206.0f;
+    static constexpr int max_pass = 3;
+};
+template <> struct Window<double> {                // nats
+    static constexpr double top = 700.0, lo = -600.0, win = 1300.0;
+    static constexpr int max_pass = 3;
+};
+
 // Layout loads and stores through the swizzled array.
 template <typename T> __device__ __forceinline__ void ld1(const T* a, T (&v)[TR], int t)
 {
@@ -321,43 +338,40 @@ __global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs,
 }
 
 // ===========================================================================
-// Step 2 for n >= 14: one block per tile (i, H) of A_i.
+// Step 2 for n >= 14, part 1: the column sums of tile (i, H) of A_i,
+//   C_H(G_L) = log sum of B_i(G_H + G_L) over G_H inside H, |G_H| <= d - |G_L|,
+// for every low pattern G_L (13 bits) with at most d elements, in column
+// order (by size, then colex).  They go to the first ncol slots of the
+// tile's own slice of A, which part 2 reads and then overwrites.  Small
+// shared memory and register use keep many blocks resident, which hides the
+// latency of the gathers from the score table.
 // ===========================================================================
 template <typename T>
-__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
-k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* __restrict__ unrank13,
-           T* __restrict__ A)
+__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 4 : 2)
+k_upzeta13_cols(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A)
 {
     using Lg = LogOps<T>;
-    constexpr T BW = Band<T>::width;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* A0 = reinterpret_cast<T*>(smem_raw);
-    T* A1 = A0 + TN;
-    T* E = A1 + TN;
-    SBinom* sb = reinterpret_cast<SBinom*>(E + TN);
-    int* meta = reinterpret_cast<int*>(sb + 1);  // [0,32) class counts, [32,64) class starts, [64,72) warp sums, [72] tile max
-    uint32_t* off13 = reinterpret_cast<uint32_t*>(meta + 80);   // 16 entries
+    T* part = reinterpret_cast<T*>(smem_raw);            // 2 * 8 * 96 partial (max, sum) pairs
+    SBinom* sb = reinterpret_cast<SBinom*>(part + 2 * 8 * 96);
+    int* meta = reinterpret_cast<int*>(sb + 1);          // [0,32) row offsets, [32,64) list starts
+    uint32_t* off13 = reinterpret_cast<uint32_t*>(meta + 64);   // 16 entries
+    uint32_t* rowbase = off13 + 16;                      // up to nrow entries
     const uint32_t ncol = num_small_subsets(TB, d);
     const int h = n - 1 - TB;
-    const uint32_t nrow = num_small_subsets(h, d);
-    uint32_t* rowbase = off13 + 16;
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int i = (int)(blockIdx.x >> h);
     const uint32_t H = blockIdx.x & ((1u << h) - 1u);
     const T* tb = tab + (size_t)i * K;
+    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
 
-    using O = typename OrdInt<T>::type;
-    O* tmax = reinterpret_cast<O*>(meta + 72);   // max over the slots (8-byte aligned)
     fill_sbinom(*sb);
-    if (t < 72) meta[t] = 0;
-    if (t == 0) *tmax = ord_enc(Lg::ninf());
     if (t < 16) {
         uint32_t o = 0;
         for (int k = 0; k < t && k <= TB; ++k) o += binom(TB, k);
         off13[t] = o;
     }
-    for (int r = 0; r < TR; ++r) A0[swz(el1(r, t))] = Lg::ninf();   // no term: zero
     __syncthreads();
 
     // --- rows whose high part lies inside H, in row order (by size, then
@@ -396,13 +410,11 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
     // Column c (low pattern of size j) takes the rows of size at most d - j,
     // i.e. the list prefix before the first row of size d - j + 1; a row of
     // size k holds the first W_k = off13[d - k + 1] columns.
-    T tm = Lg::ninf();                      // this thread's largest column maximum
     // Long columns (at most d - 2 low elements, many rows): warp w takes the
     // rows w, w + 8, ... and its lanes the columns of a 96-column block
     // (coalesced reads along the row); the eight warp partials are combined
     // in warp order.
     const uint32_t nlong = d >= 2 ? off13[min(d - 2, TB) + 1] : 0u;
-    T* part = E;                            // 2 * 8 * 96 partial (max, sum) pairs
     for (uint32_t cb = 0; cb < nlong; cb += 96) {
         T m[3], sm[3];
 #pragma unroll
@@ -448,9 +460,7 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
                     mx = mn;
                 }
             }
-            const uint32_t sw = swz(unrank13[cb + t]);
-            A0[sw] = A1[sw] = mx + Lg::lg(s2);
-            tm = mx > tm ? mx : tm;
+            out[cb + t] = mx + Lg::lg(s2);
         }
         __syncthreads();
     }
@@ -491,44 +501,95 @@ k_upzeta13(int n, int d, int64_t K, const T* __restrict__ tab, const uint16_t* _
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (c0 + q * TT < ncol) {
-                const uint32_t sw = swz(unrank13[c0 + q * TT]);
-                A0[sw] = A1[sw] = mx[q] + Lg::lg(sm[q]);
-                tm = mx[q] > tm ? mx[q] : tm;
-            }
+            if (c0 + q * TT < ncol) out[c0 + q * TT] = mx[q] + Lg::lg(sm[q]);
         }
     }
-    // one shared atomic per warp for the tile maximum
+}
+
+// ===========================================================================
+// Step 2 for n >= 14, part 2: one block per tile (i, H) of A_i.  The column
+// sums of part 1 are placed at their low patterns (every other slot holds
+// zero) and the truncated upward zeta over the 13 low bits follows.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
+k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ A)
+{
+    using Lg = LogOps<T>;
+    constexpr T BW = Band<T>::width;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* A0 = reinterpret_cast<T*>(smem_raw);
+    T* A1 = A0 + TN;
+    T* E = A1 + TN;
+    using O = typename OrdInt<T>::type;
+    O* tmax = reinterpret_cast<O*>(E + TN);      // largest column sum
+    const uint32_t ncol = num_small_subsets(TB, d);
+    const int h = n - 1 - TB;
+    const int t = threadIdx.x, lane = t & 31;
+    const int i = (int)(blockIdx.x >> h);
+    const uint32_t H = blockIdx.x & ((1u << h) - 1u);
+    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
+
+    if (t == 0) *tmax = ord_enc(Lg::ninf());
+#pragma unroll
+    for (int r = 0; r < TR; ++r)                 // no term: zero (slots that are no column)
+        if (__popc(el1(r, t)) > d) A0[swz(el1(r, t))] = Lg::ninf();
+    T tm = Lg::ninf();
+    for (uint32_t c = t; c < ncol; c += TT) {
+        const T v = out[c];
+        const uint32_t sw = swz(unrank13[c]);
+        A0[sw] = A1[sw] = v;
+        tm = v > tm ? v : tm;
+    }
     for (int o = 16; o; o >>= 1) {
         const T o2 = __shfl_xor_sync(FULLMASK, tm, o);
         tm = o2 > tm ? o2 : tm;
     }
+    __syncthreads();                             // tmax initialised; column reads done
     if (lane == 0) atomicMax(tmax, ord_enc(tm));
     __syncthreads();
 
-    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
-    // --- fast path: the tile spans less than FastSpan below its maximum -----
-    // (the smallest output is C(empty) and every output is at most
-    // 13 bits above the largest slot value)
+    // --- single-scale passes (Window): pass p sums linear values 2^(x - s_p)
+    //     (e^(x - s_p) in FP64) with s_p = M - top - p * win and writes the
+    //     outputs it resolves; the last pass writes every output left.  Every
+    //     output is at least C(empty) and at most M, so ceil((M - C(empty)) /
+    //     win) passes resolve the tile.  Tiles that need more than
+    //     Window::max_pass passes take the banded path below.
     {
+        using Wn = Window<T>;
         const T M = ord_dec(*tmax) + T(TB);
-        if (M - A1[0] < FastSpan<T>::value) {
-            T x[TR];
-            ld1(A1, x, t);
+        const T span = M - A1[0];
+        const int npass = span < Wn::win ? 1 : (int)ceil(span / Wn::win);
+        if (npass <= Wn::max_pass) {
+            uint32_t done = 0u;                  // bit r: output el3(r, t) written
+            T sp = M - Wn::top;
+            for (int p = 0; p < npass; ++p, sp -= Wn::win) {
+                const bool last = p + 1 == npass;
+                T x[TR];
+                ld1(A1, x, t);
 #pragma unroll
-            for (int r = 0; r < TR; ++r)
-                x[r] = (__popc(el1(r, t)) <= d) ? Lg::ex(x[r] - M) : T(0);
-            bfly_plain<true>(x, 0, 5);
-            st1(A0, x, t);
-            __syncthreads();
-            ld2(A0, x, t);
-            bfly_plain<true>(x, 0, 5);
-            st2(A0, x, t);
-            __syncthreads();
-            ld3(A0, x, t);
-            bfly_plain<true>(x, 0, 3);
+                for (int r = 0; r < TR; ++r)
+                    x[r] = (__popc(el1(r, t)) <= d) ? Lg::ex(x[r] - sp) : T(0);
+                bfly_plain<true>(x, 0, 5);
+                st1(A0, x, t);
+                __syncthreads();
+                ld2(A0, x, t);
+                bfly_plain<true>(x, 0, 5);
+                st2(A0, x, t);
+                __syncthreads();
+                ld3(A0, x, t);
+                bfly_plain<true>(x, 0, 3);
 #pragma unroll
-            for (int r = 0; r < TR; ++r) out[el3(r, t)] = M + Lg::lg(x[r]);
+                for (int r = 0; r < TR; ++r) {
+                    const T lx = Lg::lg(x[r]);
+                    if (!(done >> r & 1u) && (last || lx >= Wn::lo)) {
+                        out[el3(r, t)] = sp + lx;
+                        done |= 1u << r;
+                    }
+                }
+                if (last) break;
+                if (__syncthreads_and(done == 0xffffffffu)) break;   // also guards A0 reuse
+            }
             return;
         }
     }
@@ -690,20 +751,24 @@ __global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restr
 // ===========================================================================
 // Launchers.
 // ===========================================================================
-size_t upzeta13_smem_bytes(const Plan& P)
+size_t upzeta13_cols_smem_bytes(const Plan& P)
 {
     const size_t es = P.prec == 0 ? 8 : 4;
     const int h = P.n - 1 - TB;
-    uint64_t ncol = 0, nrow = 0;
-    for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
+    uint64_t nrow = 0;
     for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
-    (void)ncol;
-    return (size_t)TN * (3 * es) + sizeof(SBinom) + 80 * 4 + 16 * 4 + nrow * 4 + 16;
+    return 2 * 8 * 96 * es + sizeof(SBinom) + 64 * 4 + 16 * 4 + nrow * 4;
+}
+
+size_t upzeta13_smem_bytes(const Plan& P)
+{
+    const size_t es = P.prec == 0 ? 8 : 4;
+    return (size_t)TN * (3 * es) + 16;
 }
 
 bool use_tile13_up(const Plan& P)
 {
-    return P.n >= 14 && upzeta13_smem_bytes(P) <= 227 * 1024 - 64;
+    return P.n >= 14 && upzeta13_cols_smem_bytes(P) <= 227 * 1024 - 64;
 }
 
 size_t gamma13_smem_bytes(const Plan& P)
@@ -734,13 +799,14 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
 {
     const int h = P.n - 1 - TB;
     const unsigned grid = (unsigned)P.n << h;
-    const size_t sm = upzeta13_smem_bytes(P);
-    if (P.prec == 0)
-        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const double*)tab, unrank13,
-                                                (double*)A);
-    else
-        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, P.K, (const float*)tab, unrank13,
-                                               (float*)A);
+    const size_t sc = upzeta13_cols_smem_bytes(P), sm = upzeta13_smem_bytes(P);
+    if (P.prec == 0) {
+        k_upzeta13_cols<double><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const double*)tab, (double*)A);
+        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A);
+    } else {
+        k_upzeta13_cols<float><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const float*)tab, (float*)A);
+        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A);
+    }
     return cudaGetLastError();
 }
 
@@ -764,6 +830,8 @@ cudaError_t set_tile13_attributes()
 #define SETA(k)                      \
     e = allow_max_dynamic_smem(k); \
     if (e != cudaSuccess) return e;
+    SETA(k_upzeta13_cols<double>)
+    SETA(k_upzeta13_cols<float>)
     SETA(k_upzeta13<double>)
     SETA(k_upzeta13<float>)
     SETA(k_gamma13_p1<double>)

@@ -144,6 +144,36 @@ def test_tile_path_in_degree_range(ctx, n, d, precision, tol):
         assert abs(lpd - ref["log_PD"]) <= 1e-9 * max(1.0, abs(ref["log_PD"]))
 
 
+# A structure prior that grows steeply with the parent-set size spreads the
+# values of an upward-zeta tile over thousands of log units: tiles whose high
+# part H has few elements then span one, two, three or more single-scale
+# windows of the 13-dimension tile (or fall back to its banded path),
+# depending on |H|.  The windows are 206 bits (FP32) and 1300 nats (FP64).
+@pytest.mark.parametrize("precision,step", [("fp64", 1000.0), ("fp32", 150.0)])
+def test_stage_A_wide_spans(ctx, precision, step):
+    n, d = 18, 4
+    ds = _ds(n, 200, 2, 3, seed=77)
+    rho = [step * k for k in range(d + 1)]
+    ref = orc.edge_posteriors(ds.data, ds.arity, d, log_rho=rho, stages=True)
+    post, lpd = ctx.edge_posteriors(ds.data, ds.arity, d, log_rho=rho, precision=precision)
+    N = 1 << n
+    c = B.bn_debug_stage(ctx.h, B.BN_STAGE_SHIFT, (n,), np.float64)
+    dt = np.float64 if precision == "fp64" else np.float32
+    A = B.bn_debug_stage(ctx.h, B.BN_STAGE_A, (n, N // 2), dt).astype(np.float64)
+    assert np.all(np.isfinite(A))
+    for i in range(n):
+        low = (1 << i) - 1
+        cidx = np.arange(N // 2)
+        want = ref["A"][i][(cidx & low) | ((cidx & ~low) << 1)] - c[i]
+        if precision == "fp64":
+            np.testing.assert_allclose(A[i], want, atol=1e-9, rtol=0)
+        else:                                   # log2 units, FP32 inputs
+            want2 = want / np.log(2.0)
+            np.testing.assert_allclose(A[i], want2, atol=1e-4, rtol=2e-6)
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
+
+
 def test_small_config_both_paths(ctx):
     ds, d = datagen.config_small()
     ref = orc.edge_posteriors(ds.data, ds.arity, d)
