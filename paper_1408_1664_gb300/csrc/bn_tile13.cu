@@ -8,15 +8,20 @@
 // register operation.
 //
 // Arithmetic is exact to working precision without a log-sum-exp per
-// butterfly.  A first pass computes the max-plus transform m(L) (the largest
-// single term of every output; a max per butterfly).  Each value is then held
-// as x(L) * 2^(BW*e(L)) with the band e(L) = floor(m(L) / BW): x(L) lies in
-// [1, 2^BW * 8192) and never overflows (BW = 112 bits in FP32, 600 nats in
-// FP64).  A butterfly adds a partner from the same band unchanged, one band
-// lower times 2^-BW, and drops partners two or more bands lower (they are
-// below 2^-BW * 2^-13 of the result: under one rounding unit).  Bands are monotone along butterflies (m is), so the
-// largest term of every output reaches it unscaled and x(L) >= 1.  One
-// exponential enters per input and one logarithm leaves per output.
+// butterfly.  Most tiles are summed in linear scale, in one or a few
+// single-scale passes (Window).  The others first compute the max-plus
+// transform m(L), the largest single term of every output (a max per
+// butterfly), and hold each value as y(L) * 2^m(L) (e^m(L) in FP64): every
+// partial sum at L is at most the final output, so y(L) <= 8192, and a
+// butterfly adds its partner scaled by 2^(m(partner) - m(L)) <= 1 (m is
+// monotone along the butterflies).  A term can only underflow there when it
+// is below 2^-126 of the output it belongs to.  One exponential enters per
+// input and per butterfly, one logarithm leaves per output.  FP64 avoids a
+// full-precision exponential per butterfly: it holds each value as
+// x(L) * e^(BW*e(L)) with the band e(L) = floor(m(L) / BW), BW = 600 nats, so
+// x(L) lies in [1, e^BW * 8192); a butterfly adds a partner from the same
+// band unchanged, one band lower times e^-BW, and drops partners two or more
+// bands lower (below e^-BW * 2^-13 of the result: under one rounding unit).
 #include "bn_device.cuh"
 #include "bn_kernels.cuh"
 
@@ -29,21 +34,11 @@ constexpr int TT = 256;           // threads per tile
 constexpr int TR = 32;            // values per thread
 constexpr unsigned FULLMASK = 0xffffffffu;
 
-// Band width in the value's log units and the factor one band down.
-template <typename T> struct Band;
-template <> struct Band<float> {
-    static constexpr float width = 112.0f;         // base-2 logs: x < 2^(112+13) < 2^127
-    static __device__ __forceinline__ float down1() { return 0x1p-112f; }
-};
-template <> struct Band<double> {
-    static constexpr double width = 600.0;          // natural logs
+// Band width (natural logs) and the factor one band down, FP64 only.
+struct Band64 {
+    static constexpr double width = 600.0;
     static __device__ __forceinline__ double down1() { return 2.6503965530043108e-261; }  // e^-600
 };
-
-template <typename T> __device__ __forceinline__ T band_factor(int dd)
-{
-    return dd == 0 ? T(1) : (dd == 1 ? Band<T>::down1() : T(0));
-}
 
 // a*b + c in the value's own precision (no promotion to double).
 __device__ __forceinline__ float madd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -86,10 +81,29 @@ __device__ __forceinline__ void bfly_max(T (&v)[TR], int k0, int nk)
     }
 }
 
+// Sum butterflies on values held relative to their own scales m (the final
+// max-plus transform): the partner is scaled by exp(m(partner) - m(self)).
+template <bool UP, typename T>
+__device__ __forceinline__ void bfly_scaled(T (&x)[TR], const T (&m)[TR], int k0, int nk)
+{
+    using Lg = LogOps<T>;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        if (k < k0 || k >= k0 + nk) continue;
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            if (r & (1 << k)) continue;
+            const int s = r | (1 << k);
+            if (UP) x[s] = madd(x[r], Lg::ex(m[r] - m[s]), x[s]);
+            else x[r] = madd(x[s], Lg::ex(m[s] - m[r]), x[r]);
+        }
+    }
+}
+
 // Sum butterflies with bands e (exact small integers held as T).  Three
 // cases per thread: all its bands equal (plain adds); two adjacent bands
-// (factor 1 or 2^-BW, one fused multiply-add); otherwise the full rule
-// (1, 2^-BW, or 0 for partners two or more bands down).
+// (factor 1 or e^-BW, one fused multiply-add); otherwise the full rule
+// (1, e^-BW, or 0 for partners two or more bands down).
 template <bool UP, typename T>
 __device__ __forceinline__ void bfly_sum(T (&x)[TR], const T (&e)[TR], int k0, int nk)
 {
@@ -113,7 +127,7 @@ __device__ __forceinline__ void bfly_sum(T (&x)[TR], const T (&e)[TR], int k0, i
             }
         }
     } else if (gap == T(1)) {
-        // partner bands differ by 0 or 1: factor 1 or 2^-BW
+        // partner bands differ by 0 or 1: factor 1 or e^-BW
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             if (k < k0 || k >= k0 + nk) continue;
@@ -121,8 +135,8 @@ __device__ __forceinline__ void bfly_sum(T (&x)[TR], const T (&e)[TR], int k0, i
             for (int r = 0; r < TR; ++r) {
                 if (r & (1 << k)) continue;
                 const int s = r | (1 << k);
-                if (UP) x[s] = madd(x[r], e[s] == e[r] ? T(1) : Band<T>::down1(), x[s]);
-                else x[r] = madd(x[s], e[r] == e[s] ? T(1) : Band<T>::down1(), x[r]);
+                if (UP) x[s] = madd(x[r], e[s] == e[r] ? T(1) : Band64::down1(), x[s]);
+                else x[r] = madd(x[s], e[r] == e[s] ? T(1) : Band64::down1(), x[r]);
             }
         }
     } else {
@@ -134,12 +148,28 @@ __device__ __forceinline__ void bfly_sum(T (&x)[TR], const T (&e)[TR], int k0, i
                 if (r & (1 << k)) continue;
                 const int s = r | (1 << k);
                 const T dd = UP ? e[s] - e[r] : e[r] - e[s];
-                const T f = dd == T(0) ? T(1) : (dd == T(1) ? Band<T>::down1() : T(0));
+                const T f = dd == T(0) ? T(1) : (dd == T(1) ? Band64::down1() : T(0));
                 if (UP) x[s] = madd(x[r], f, x[s]);
                 else x[r] = madd(x[s], f, x[r]);
             }
         }
     }
+}
+
+template <bool UP>
+__device__ __forceinline__ void sum_bfly(float (&x)[TR], const float (&m)[TR], int k0, int nk)
+{
+    bfly_scaled<UP>(x, m, k0, nk);
+}
+template <bool UP>
+__device__ __forceinline__ void sum_bfly(double (&x)[TR], const double (&e)[TR], int k0, int nk)
+{
+    bfly_sum<UP>(x, e, k0, nk);
+}
+__device__ __forceinline__ float scaled_log(float y, float m) { return m + LogOps<float>::lg(y); }
+__device__ __forceinline__ double scaled_log(double x, double e)
+{
+    return madd(Band64::width, e, LogOps<double>::lg(x));
 }
 
 // Online log-sum-exp step (branchless): (m, s) stands for m + lg(s).
@@ -253,6 +283,41 @@ template <> __device__ __forceinline__ void st3<float>(float* a, const float (&v
         *reinterpret_cast<float4*>(a + base + 4) = q;
     }
 }
+// The exact sum pass after the max-plus pass.  On entry v holds m (layout
+// 3); A1 holds the transform's inputs (for UP only the slots with at most d
+// elements are inputs).  On exit v and sc hold, in layout 1, each output as
+// scaled_log(v, sc): FP32 keeps y relative to its own scale m, FP64 keeps x
+// in its band.
+template <bool UP, typename T>
+__device__ __forceinline__ void sum_pass(T (&v)[TR], T (&sc)[TR], const T* A1, T* A0, T* E,
+                                         int t, int d)
+{
+    using Lg = LogOps<T>;
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+        sc[r] = sizeof(T) == 4 ? v[r] : floor(v[r] / T(Band64::width));
+    st3(E, sc, t);                        // scales, read again in layouts 2 and 1
+    ld3(A1, v, t);
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const T base = sizeof(T) == 4 ? sc[r] : T(Band64::width) * sc[r];
+        v[r] = (!UP || __popc(el3(r, t)) <= d) ? Lg::ex(v[r] - base) : T(0);
+    }
+    sum_bfly<UP>(v, sc, 0, 3);
+    __syncthreads();
+    st3(A0, v, t);
+    __syncthreads();
+    ld2(A0, v, t);
+    ld2(E, sc, t);
+    sum_bfly<UP>(v, sc, 0, 5);
+    __syncthreads();
+    st2(A0, v, t);
+    __syncthreads();
+    ld1(A0, v, t);
+    ld1(E, sc, t);
+    sum_bfly<UP>(v, sc, 0, 5);
+}
+
 // Binomial coefficients C(a, b), a < 32, in shared memory, stored for
 // b <= a / 2 only (C(a, b) = C(a, a - b)).  Lanes look up different entries,
 // which would serialise constant-cache reads; the table is copied from a
@@ -295,8 +360,6 @@ uint64_t binom_host(int n, int k)
     return r;
 }
 
-__device__ __forceinline__ float floor_div(float m, float w) { return floorf(m * (1.0f / w)); }
-__device__ __forceinline__ double floor_div(double m, double w) { return floor(m / w); }
 
 }  // namespace
 
@@ -516,7 +579,6 @@ __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ A)
 {
     using Lg = LogOps<T>;
-    constexpr T BW = Band<T>::width;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
     T* A1 = A0 + TN;
@@ -607,31 +669,11 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     ld3(A0, v, t);
     bfly_max<true>(v, 0, 3);
 
-    // --- bands and scaled inputs (layout 3) --------------------------------
-    T e[TR];
+    // --- exact sum pass: layouts 3, 2, 1 ------------------------------------
+    T sc[TR];
+    sum_pass<true>(v, sc, A1, A0, E, t, d);
 #pragma unroll
-    for (int r = 0; r < TR; ++r) e[r] = floor_div(v[r], BW);
-    st3(E, e, t);                         // bands, read again in layouts 2 and 1
-    ld3(A1, v, t);                        // C at the slots, garbage elsewhere
-#pragma unroll
-    for (int r = 0; r < TR; ++r)
-        v[r] = (__popc(el3(r, t)) <= d) ? Lg::ex(v[r] - BW * e[r]) : T(0);
-    // --- sum pass: layouts 3, 2, 1 ------------------------------------------
-    bfly_sum<true>(v, e, 0, 3);
-    __syncthreads();
-    st3(A0, v, t);
-    __syncthreads();
-    ld2(A0, v, t);
-    ld2(E, e, t);
-    bfly_sum<true>(v, e, 0, 5);
-    __syncthreads();
-    st2(A0, v, t);
-    __syncthreads();
-    ld1(A0, v, t);
-    ld1(E, e, t);
-    bfly_sum<true>(v, e, 0, 5);
-#pragma unroll
-    for (int r = 0; r < TR; ++r) out[el1(r, t)] = madd(BW, e[r], Lg::lg(v[r]));
+    for (int r = 0; r < TR; ++r) out[el1(r, t)] = scaled_log(v[r], sc[r]);
 }
 
 // ===========================================================================
@@ -645,7 +687,6 @@ k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W)
 {
     using Lg = LogOps<T>;
-    constexpr T BW = Band<T>::width;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
     T* A1 = A0 + TN;
@@ -711,30 +752,12 @@ k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
     ld3(A0, x, t);
     bfly_max<false>(x, 0, 3);
 
-    T e[TR];
-#pragma unroll
-    for (int r = 0; r < TR; ++r) e[r] = floor_div(x[r], BW);
-    st3(E, e, t);
-    ld3(A1, x, t);                        // s_v in layout 3
-#pragma unroll
-    for (int r = 0; r < TR; ++r) x[r] = Lg::ex(x[r] - BW * e[r]);
-    bfly_sum<false>(x, e, 0, 3);
-    __syncthreads();
-    st3(A0, x, t);
-    __syncthreads();
-    ld2(A0, x, t);
-    ld2(E, e, t);
-    bfly_sum<false>(x, e, 0, 5);
-    __syncthreads();
-    st2(A0, x, t);
-    __syncthreads();
-    ld1(A0, x, t);
-    ld1(E, e, t);
-    bfly_sum<false>(x, e, 0, 5);
+    T sc[TR];
+    sum_pass<false>(x, sc, A1, A0, E, t, d);
     const int pt = __popc((uint32_t)t);
 #pragma unroll
     for (int r = 0; r < TR; ++r)
-        if (pt + __popc((uint32_t)r) <= d) row[rank13[el1(r, t)]] = madd(BW, e[r], Lg::lg(x[r]));
+        if (pt + __popc((uint32_t)r) <= d) row[rank13[el1(r, t)]] = scaled_log(x[r], sc[r]);
 }
 
 // rank13[L] = position of L among the subsets of 13 bits ordered by size then
