@@ -120,7 +120,7 @@ def measured_peaks() -> tuple[float, str]:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha1()
-    for f in ("bn_kernels.cu", "bn_device.cuh"):
+    for f in ("bn_kernels.cu", "bn_tile13.cu", "bn_device.cuh"):
         with open(os.path.join(ROOT, "paper_1408_1664_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -143,20 +143,36 @@ def committed_traffic(kernel: str, workload: str, precision: str):
     return None
 
 
-def stage_table(n: int, es: int) -> dict:
-    """Algorithmic HBM bytes per launch of each kernel (minimal traffic)."""
+def stage_table(n: int, d: int, es: int) -> dict:
+    """Per kernel: algorithmic HBM bytes per launch (minimal traffic),
+    launches per job and how to read its device time from bn_stats."""
+    from math import comb
     N = 2 ** n
-    return {
-        # A written once: n 2^(n-1) values
-        "k_upzeta": {"bytes": n * N / 2 * es, "launches": 1, "field": "ms_upzeta"},
-        # A read once, F written once (cross-tile F reads are L2 hits)
-        "k_forward_level": {"bytes": (n * N / 2 + N) * es, "launches": None,
-                            "field": "ms_forward"},
-        "k_backward_level": {"bytes": (n * N / 2 + N) * es, "launches": None,
-                             "field": "ms_backward"},
-        # per endpoint v: the halves of F and R' (2^(n-1) values each)
-        "k_gamma_p1": {"bytes": N * es, "launches": n, "field": "ms_gamma_p1"},
+    A_bytes = n * N / 2 * es                      # A: n 2^(n-1) values, written once
+    nh = n - min(n, 5) + 1                        # F / R' launches (one per level)
+    tab = {
+        # A read once, F written once and read once by the next level
+        "k_forward_level": {"bytes": (A_bytes + 2 * N * es) / nh, "launches": nh,
+                            "ms": lambda h: h["ms_forward"]},
+        "k_backward_level": {"bytes": (A_bytes + 2 * N * es) / nh, "launches": nh,
+                             "ms": lambda h: h["ms_backward"]},
     }
+    if n >= 14:
+        h = n - 1 - 13
+        ncol = sum(comb(13, k) for k in range(min(d, 13) + 1))
+        K = sum(comb(n - 1, k) for k in range(min(d, n - 1) + 1))
+        C_bytes = n * 2 ** h * ncol * es          # column sums handed to the tile kernel
+        tab["k_upzeta13"] = {"bytes": A_bytes + C_bytes, "launches": 1,
+                             "ms": lambda h: h["ms_upzeta"] - h["ms_upzeta_sums"]}
+        tab["k_upzeta13_cols"] = {"bytes": C_bytes + 2 * n * K * es, "launches": 1,
+                                  "ms": lambda h: h["ms_upzeta_sums"]}
+        # per endpoint v: the halves of F and R' read, one row of W per tile written
+        tab["k_gamma13_p1"] = {"bytes": (N + 2 ** h * ncol) * es, "launches": n,
+                               "ms": lambda h: h["ms_gamma_p1"]}
+    else:
+        tab["k_upzeta"] = {"bytes": A_bytes, "launches": 1, "ms": lambda h: h["ms_upzeta"]}
+        tab["k_gamma_p1"] = {"bytes": N * es, "launches": n, "ms": lambda h: h["ms_gamma_p1"]}
+    return tab
 
 
 # ------------------------------------------------------------- CPU oracle --
@@ -400,15 +416,13 @@ def run_ours(args):
     # roofline of the dominant kernel, from the per-kernel CUDA events of the
     # timed steps
     peak, peak_kind = measured_peaks()
-    tab = stage_table(n, es)
+    tab = stage_table(n, d, es)
     launches_per_step = hist[-1]["kernels"] if hist else None
-    nh = n - min(n, 5) + 1
-    tab["k_forward_level"]["launches"] = nh
-    tab["k_backward_level"]["launches"] = nh
     per_stage = {}
     for k, row in tab.items():
-        ms = statistics.mean(h[row["field"]] for h in hist)
+        ms = statistics.mean(row["ms"](h) for h in hist)
         per_stage[k] = {"ms_per_step": ms, "launches_per_step": row["launches"],
+                        "alg_bytes_per_launch": row["bytes"],
                         "alg_gbs": row["bytes"] * row["launches"] / (ms / 1e3) / 1e9}
     other = {f: statistics.mean(h[f] for h in hist) for f in ("ms_scores", "ms_gamma_p2",
                                                               "ms_edges", "ms_total")}

@@ -99,7 +99,7 @@ typedef struct bn_job_desc {
 typedef struct bn_stats {
     double ms_scores;        /* device time of each stage, CUDA events on the
                                 launching stream                              */
-    double ms_upzeta;        /* the single up-zeta launch                     */
+    double ms_upzeta;        /* step 2: all of its launches                   */
     double ms_forward;       /* all F level launches                          */
     double ms_backward;      /* all R' level launches                         */
     double ms_gamma_p1;      /* sum over v of the Gamma phase-1 launches      */
@@ -110,6 +110,9 @@ typedef struct bn_stats {
     double alg_bytes;        /* algorithmic HBM bytes of the DP arrays        */
     int32_t kernels;         /* kernel launches of the job                    */
     int32_t precision;
+    double ms_upzeta_sums;   /* the part of ms_upzeta spent before the tile
+                                butterflies (score reordering and column sums
+                                of the 13-dimension tiles; 0 for n < 14)      */
 } bn_stats;
 
 /* Context.  bn_ctx_create returns BN_EINVAL for a NULL pointer or bad

@@ -46,7 +46,8 @@ class bn_stats(C.Structure):
                 ("ms_forward", C.c_double), ("ms_backward", C.c_double),
                 ("ms_gamma_p1", C.c_double), ("ms_gamma_p2", C.c_double),
                 ("ms_edges", C.c_double), ("ms_total", C.c_double), ("cells", C.c_double),
-                ("alg_bytes", C.c_double), ("kernels", C.c_int32), ("precision", C.c_int32)]
+                ("alg_bytes", C.c_double), ("kernels", C.c_int32), ("precision", C.c_int32),
+                ("ms_upzeta_sums", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -879,12 +879,12 @@ static int fixed_bits(int64_t terms)
 }
 
 cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
-                          const uint16_t* rk13, void* A, cudaStream_t s)
+                          const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done)
 {
     if (use_tile13_up(P)) {
         cudaError_t e = launch_reorder_up(P, lbs, tab, s);
         if (e != cudaSuccess) return e;
-        return launch_upzeta13(P, tab, rk13 + 8192, A, s);
+        return launch_upzeta13(P, tab, rk13 + 8192, A, s, sums_done);
     }
     const int h = P.n - 1 - P.b_up;
     const unsigned grid = (unsigned)P.n << h;

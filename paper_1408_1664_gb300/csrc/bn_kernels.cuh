@@ -41,7 +41,7 @@ cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double*
 // `rk13` points at the two 8192-entry uint16 subset-rank tables (rank, then
 // inverse) of the 13-dimension tiles, filled by launch_rank13_tables.
 cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
-                          const uint16_t* rk13, void* A, cudaStream_t s);
+                          const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done = nullptr);
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
 cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s,
                             int* launches);
@@ -57,7 +57,7 @@ size_t upzeta_smem_bytes(const Plan& P);
 cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s);
 cudaError_t launch_rank13_tables(uint16_t* rank13, uint16_t* unrank13, cudaStream_t s);
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
-                            cudaStream_t s);
+                            cudaStream_t s, cudaEvent_t sums_done = nullptr);
 cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* Rc,
                               const uint16_t* rank13, void* W, cudaStream_t s);
 constexpr size_t kRank13Bytes = 2 * 8192 * sizeof(uint16_t);

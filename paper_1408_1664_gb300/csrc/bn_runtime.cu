@@ -174,7 +174,7 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
 
 // Event set of one job: [0] start, [1] scores, [2] up-zeta, [3] F, [4] R',
 // [5 + 2v] Gamma phase 1 of v, [6 + 2v] phase 2 of v, [5 + 2n] edges.
-constexpr int kEvents = 6 + 2 * 31;
+constexpr int kEvents = 7 + 2 * 31;   // the last one ends the column sums of step 2
 struct Events {
     cudaEvent_t ev[kEvents] = {};
     bool ok = false;
@@ -277,8 +277,9 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     }
     if (ev) CK(cudaEventRecord(ev->ev[1], s));
     CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), B.at<void>(L.lbs), B.at<void>(L.tab),
-                         B.at<uint16_t>(L.rk13), B.at<void>(L.A), s));
-    nl += bn::use_tile13_up(P) ? 2 : 1;
+                         B.at<uint16_t>(L.rk13), B.at<void>(L.A), s,
+                         ev && bn::use_tile13_up(P) ? ev->ev[kEvents - 1] : nullptr));
+    nl += bn::use_tile13_up(P) ? 3 : 1;
     if (ev) CK(cudaEventRecord(ev->ev[2], s));
     CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
     if (ev) CK(cudaEventRecord(ev->ev[3], s));
@@ -324,6 +325,7 @@ void fill_stats(const Plan& P, Events& ev, int launches, bn_stats* st)
     };
     st->ms_scores = el(0, 1);
     st->ms_upzeta = el(1, 2);
+    st->ms_upzeta_sums = bn::use_tile13_up(P) ? el(1, kEvents - 1) : 0.0;
     st->ms_forward = el(2, 3);
     st->ms_backward = el(3, 4);
     for (int v = 0; v < P.n; ++v) {

@@ -818,18 +818,25 @@ cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStr
 }
 
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
-                            cudaStream_t s)
+                            cudaStream_t s, cudaEvent_t sums_done)
 {
     const int h = P.n - 1 - TB;
     const unsigned grid = (unsigned)P.n << h;
     const size_t sc = upzeta13_cols_smem_bytes(P), sm = upzeta13_smem_bytes(P);
-    if (P.prec == 0) {
+    if (P.prec == 0)
         k_upzeta13_cols<double><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const double*)tab, (double*)A);
-        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A);
-    } else {
+    else
         k_upzeta13_cols<float><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const float*)tab, (float*)A);
-        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (sums_done) {
+        e = cudaEventRecord(sums_done, s);
+        if (e != cudaSuccess) return e;
     }
+    if (P.prec == 0)
+        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A);
+    else
+        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A);
     return cudaGetLastError();
 }
 
