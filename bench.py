@@ -149,13 +149,16 @@ def stage_table(n: int, d: int, es: int) -> dict:
     from math import comb
     N = 2 ** n
     A_bytes = n * N / 2 * es                      # A: n 2^(n-1) values, written once
-    nh = n - min(n, 5) + 1                        # F / R' launches (one per level)
+    nh = (n - 4 + 1) if (es == 4 and n >= 5) else (n - min(n, 5) + 1)   # F / R' launches (one per level)
+    rows = es == 4 and n >= 5                     # FP32: one thread per 16-subset tile
+    fwd, bwd = ("k_forward_rows", "k_backward_rows") if rows else ("k_forward_level",
+                                                                   "k_backward_level")
     tab = {
         # A read once, F written once and read once by the next level
-        "k_forward_level": {"bytes": (A_bytes + 2 * N * es) / nh, "launches": nh,
-                            "ms": lambda h: h["ms_forward"]},
-        "k_backward_level": {"bytes": (A_bytes + 2 * N * es) / nh, "launches": nh,
-                             "ms": lambda h: h["ms_backward"]},
+        fwd: {"bytes": (A_bytes + 2 * N * es) / nh, "launches": nh,
+              "ms": lambda h: h["ms_forward"]},
+        bwd: {"bytes": (A_bytes + 2 * N * es) / nh, "launches": nh,
+              "ms": lambda h: h["ms_backward"]},
     }
     if n >= 14:
         h = n - 1 - 13

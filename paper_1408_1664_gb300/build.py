@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUTDIR, "libbnedge.so")
-SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_runtime.cu", "bn_noalloc.cu"]
+SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_runtime.cu", "bn_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

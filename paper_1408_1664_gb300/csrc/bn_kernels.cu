@@ -916,6 +916,7 @@ static int tiles_per_warp(uint32_t ntiles)
 
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches)
 {
+    if (use_rows_levels(P)) return launch_forward_rows(P, A, F, s, launches);
     const int nh = P.n - P.wb;
     for (int hl = 0; hl <= nh; ++hl) {
         const uint32_t nt = host_binom(nh, hl);
@@ -937,6 +938,7 @@ cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s
 
 cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s, int* launches)
 {
+    if (use_rows_levels(P)) return launch_backward_rows(P, A, Rc, s, launches);
     const int nh = P.n - P.wb;
     for (int hl = nh; hl >= 0; --hl) {
         const uint32_t nt = host_binom(nh, hl);

@@ -42,6 +42,11 @@ cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double*
 // inverse) of the 13-dimension tiles, filled by launch_rank13_tables.
 cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
                           const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done = nullptr);
+// Step 3 in FP32 with one thread per 16-subset tile (bn_levels.cu).
+bool use_rows_levels(const Plan& P);
+cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
+cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStream_t s,
+                                 int* launches);
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
 cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s,
                             int* launches);
