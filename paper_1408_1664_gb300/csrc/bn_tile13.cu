@@ -527,46 +527,18 @@ k_upzeta13_cols(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
         }
         __syncthreads();
     }
-    // Short columns (d - 1 or d low elements): only the row of the empty set
-    // and the 1-element rows, at most 1 + hc; a thread per column, four
-    // columns at a time and eight rows per batch so the loads overlap.
-    for (uint32_t c0 = nlong + t; c0 < ncol; c0 += 4 * TT) {
-        T mx[4], sm[4];
-        int re[4];
-        int rmax = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t c = c0 + q * TT;
-            int rend = 0;
-            if (c < ncol) {
-                int j = 0;
-                while (off13[j + 1] <= c) ++j;
-                rend = meta[32 + min(d - j + 1, 31)];
-            }
-            re[q] = rend;
-            rmax = max(rmax, rend);
-            mx[q] = Lg::ninf();
-            sm[q] = T(0);
-        }
-        for (int rp0 = 0; rp0 < rmax; rp0 += 8) {
-            T x[8][4];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int rp = rp0 + u;
-                const T* src = tb + (rp < rmax ? rowbase[rp] : 0u) + c0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) x[u][q] = rp < re[q] ? src[q * TT] : Lg::ninf();
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) lse_online(mx[q], sm[q], x[u][q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (c0 + q * TT < ncol) out[c0 + q * TT] = mx[q] + Lg::lg(sm[q]);
-        }
+    // Columns with d - 1 low elements: the row of the empty set and the
+    // 1-element rows, 1 + hc of them; a thread per column.
+    const uint32_t ncopy = off13[min(d, TB + 1)];     // first column with d low elements
+    const int rmid = meta[32 + 2];
+    for (uint32_t c = nlong + t; c < ncopy; c += TT) {
+        T mx = Lg::ninf(), sm = T(0);
+#pragma unroll 8
+        for (int rp = 0; rp < rmid; ++rp) lse_online(mx, sm, tb[rowbase[rp] + c]);
+        out[c] = mx + Lg::lg(sm);
     }
+    // Columns with d low elements take the row of the empty set alone (offset 0).
+    for (uint32_t c = ncopy + t; c < ncol; c += TT) out[c] = tb[c];
 }
 
 // ===========================================================================
