@@ -120,7 +120,7 @@ def measured_peaks() -> tuple[float, str]:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha1()
-    for f in ("bn_kernels.cu", "bn_tile13.cu", "bn_device.cuh"):
+    for f in ("bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_device.cuh"):
         with open(os.path.join(ROOT, "paper_1408_1664_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

@@ -96,6 +96,8 @@ __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
     for (int x = threadIdx.x; x < BT * BT; x += blockDim.x) bt[x / BT][x % BT] = g_binom_lanes.v[x / BT][x % BT];
 }
 
+}  // namespace
+
 //   F(S) = sum_{i in S} A_i(S - {i}) F(S - {i}),  F(empty) = 1
 __global__ void __launch_bounds__(256)
 k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ F)
@@ -180,6 +182,8 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, flo
     }
     store16(Rc + ((size_t)Ht << LB), Rv);
 }
+
+namespace {
 
 uint64_t choose(int n, int k)
 {
