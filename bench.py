@@ -178,6 +178,23 @@ def stage_table(n: int, d: int, es: int) -> dict:
     return tab
 
 
+# ------------------------------------------------------------- replicas --
+def replica_value(local_s: float, units_per_rank: float, dist=None, device="cpu"):
+    """Independent replicas, one per rank: the job time is the maximum over
+    ranks, and the value is the units of all ranks over that time.  Returns
+    (max seconds, units per second).  `dist` is torch.distributed (None for
+    one process); `device` holds the reduction tensor (the rank's GPU under
+    NCCL, the CPU under gloo)."""
+    world = 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(local_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_s = float(t.item())
+        world = dist.get_world_size()
+    return local_s, world * units_per_rank / local_s
+
+
 # ------------------------------------------------------------- CPU oracle --
 def oracle_sample(ds, d, budget_s: float):
     """Time the oracle on sub-problems (the first n_s variables of the same
@@ -409,11 +426,8 @@ def run_ours(args):
     clocks = sampler.stop()
     t_ms = e0.elapsed_time(e1)
     hist = binding.bn_stats_history(ctx.h, min(args.steps, 32))
-    if dist:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * args.steps * cells / (t_ms / 1e3)
+    t_s, value = replica_value(t_ms / 1e3, args.steps * cells, dist, "cuda")
+    t_ms = t_s * 1e3
     post = post_dev.cpu().numpy()
 
     # roofline of the dominant kernel, from the per-kernel CUDA events of the
@@ -458,8 +472,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             binding.bn_edge_posteriors(ctx.h, job_h, post_host)
-        e2e_s = time.perf_counter() - t0
-        e2e = {"value": e2e_steps * cells / e2e_s * world, "unit": UNIT,
+        e2e_s, e2e_value = replica_value(time.perf_counter() - t0, e2e_steps * cells, dist, "cuda")
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(ds.m * n + n),
                "d2h_bytes_per_step": int(n * n * 8 + 8),
                "ms_per_step": e2e_s / e2e_steps * 1e3}
