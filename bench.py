@@ -329,7 +329,8 @@ def run_batched(binding, torch, device: int, jobs_n: int = 256, reps: int = 5) -
     jobs = [datagen.batched_job(j) for j in range(jobs_n)]
     cells = sum(ds.n * 2 ** ds.n for ds, _ in jobs)
     out = {}
-    with binding.Context(device) as ctx:
+
+    def timed_batch(ctx):
         descs = [binding.Job(ds.data, ds.arity, d, precision="fp32") for ds, d in jobs]
         t0 = time.perf_counter()
         batch = binding.Batch(ctx.h, descs)
@@ -347,11 +348,20 @@ def run_batched(binding, torch, device: int, jobs_n: int = 256, reps: int = 5) -
         stream.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res = [batch.results(k)[0] for k in range(jobs_n)]
+        sched = batch.describe().strip().splitlines()
         batch.close()
+        return ms, build_s, res, sched
+
+    with binding.Context(device, autotune=False) as ctx0:
+        ms0, _, _, _ = timed_batch(ctx0)
+    with binding.Context(device) as ctx:
+        ms, build_s, res, sched = timed_batch(ctx)
         out["batched_fp32_graph"] = {"jobs": jobs_n, "ms_per_batch": ms,
                                      "jobs_per_s": jobs_n / (ms / 1e3),
                                      "cells_per_s": cells / (ms / 1e3),
-                                     "build_ms": build_s * 1e3}
+                                     "build_ms_incl_autotune": build_s * 1e3,
+                                     "groups": len(sched), "schedule": sched,
+                                     "ms_per_batch_default_schedule": ms0}
         err = 0.0
         t0 = time.perf_counter()
         for k, (ds, d) in enumerate(jobs):

@@ -79,8 +79,12 @@ typedef struct bn_ctx_opts {
                                 the free memory at creation                   */
     int32_t fail_alloc_after;/* test hook: allocations after this many fail
                                 with BN_ENOMEM; < 0 disables                  */
-    int32_t reserved;
+    int32_t flags;           /* BN_CTX_* bits, 0 = defaults                   */
 } bn_ctx_opts;
+
+/* bn_ctx_opts.flags: batches keep the default schedule instead of timing the
+ * alternatives (see bn_batch_create). */
+#define BN_CTX_NO_AUTOTUNE 1
 
 typedef struct bn_job_desc {
     int32_t n;               /* number of variables                           */
@@ -175,19 +179,34 @@ int bn_edge_posteriors_async(bn_ctx* ctx, const bn_job_desc* job,
 int bn_edge_posteriors_static(const bn_job_desc* job, double* post_dev,
                               double* log_PD_dev, void* stream);
 
-/* Batches.  Many independent jobs (typically small n) planned together:
- * bn_batch_create validates every job, copies its host inputs into one
- * device arena, and records the kernels of all jobs into one CUDA graph, the
- * jobs spread over up to 32 concurrent branches.  bn_batch_run replays the
- * graph on `stream` (NULL = the context's stream) without host
- * synchronisation: one launch runs the whole batch.  bn_batch_results waits
- * for the last run and copies job k's posteriors (n*n doubles) and log P(D).
- * Device data pointers are not accepted (BN_EINVAL).  The arena counts
- * against the context's budget (BN_ENOMEM). */
+/* Batches.  Many independent jobs (typically small n) planned together
+ * (Algorithm 1 for each job; the paper has no batch form).
+ * bn_batch_create validates every job and copies its host inputs into one
+ * device arena.  Jobs with equal n, d and precision form a group: their
+ * arrays lie at a fixed stride, and every launch of steps 2-5 covers the
+ * whole group (step 1 runs per job: its sizes depend on m and the arities).
+ * Unless the context has BN_CTX_NO_AUTOTUNE, the schedule of each group --
+ * the kernels of the up-zeta (13-dimension tiles or shared-memory tiles), of
+ * F and R' (16-subset rows or warp tiles, FP32) and of the down-zeta phase 1
+ * -- is chosen by timing each alternative on the group's own data, and the
+ * choice is cached in the context for later batches with the same group
+ * shape.  Every schedule gives the same values up to rounding (within the
+ * stated tolerances, 1e-9 FP64 and 1e-4 FP32, of the job run alone; equal
+ * bit for bit under the default schedule).  The launches of all groups are
+ * recorded into one CUDA graph, one branch per group.  bn_batch_run replays
+ * the graph on `stream` (NULL = the context's stream) without host
+ * synchronisation: one graph launch runs the whole batch.  bn_batch_results
+ * waits for the last run and copies job k's posteriors (n*n doubles) and
+ * log P(D).  Device data pointers are not accepted (BN_EINVAL).  The arena
+ * counts against the context's budget (BN_ENOMEM). */
 typedef struct bn_batch bn_batch;
 int bn_batch_create(bn_ctx* ctx, const bn_job_desc* jobs, int32_t count, bn_batch** batch);
 int bn_batch_run(bn_batch* batch, void* stream);
 int bn_batch_results(bn_batch* batch, int32_t k, double* post, double* log_PD);
+/* One line per group into buf (NUL-terminated, truncated to len): its n, d,
+ * precision, jobs and the schedule it runs, and whether that was timed.
+ * BN_EINVAL for NULL arguments. */
+int bn_batch_describe(bn_batch* batch, char* buf, size_t len);
 int bn_batch_destroy(bn_batch* batch);
 
 /* Serving.  bn_submit copies the inputs, admits the job when a slot and

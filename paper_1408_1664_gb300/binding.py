@@ -32,7 +32,7 @@ class BnError(RuntimeError):
 
 class bn_ctx_opts(C.Structure):
     _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("mem_budget", C.c_uint64),
-                ("fail_alloc_after", C.c_int32), ("reserved", C.c_int32)]
+                ("fail_alloc_after", C.c_int32), ("flags", C.c_int32)]
 
 
 class bn_job_desc(C.Structure):
@@ -58,7 +58,7 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_edge_posteriors", "bn_edge_posteriors_async", "bn_submit", "bn_poll", "bn_wait",
            "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror", "bn_debug_stage",
            "bn_debug_counts", "bn_edge_posteriors_static", "bn_job_footprint", "bn_batch_create",
-           "bn_batch_run", "bn_batch_results", "bn_batch_destroy"]
+           "bn_batch_run", "bn_batch_results", "bn_batch_describe", "bn_batch_destroy"]
 
 
 def library_path() -> str:
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_batch_create": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.POINTER(P)]),
         "bn_batch_run": (C.c_int, [P, P]),
         "bn_batch_results": (C.c_int, [P, C.c_int32, P, P]),
+        "bn_batch_describe": (C.c_int, [P, C.c_char_p, C.c_size_t]),
         "bn_batch_destroy": (C.c_int, [P]),
         "bn_debug_stage": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
         "bn_debug_counts": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_uint32, P,
@@ -146,10 +147,13 @@ def bn_job_footprint(job: "Job") -> int:
     return int(out.value)
 
 
+BN_CTX_NO_AUTOTUNE = 1
+
+
 def bn_ctx_create(device: int = 0, slots: int = 4, mem_budget: int = 0,
-                  fail_alloc_after: int = -1) -> int:
+                  fail_alloc_after: int = -1, flags: int = 0) -> int:
     h = C.c_void_p()
-    opts = bn_ctx_opts(device, slots, mem_budget, fail_alloc_after, 0)
+    opts = bn_ctx_opts(device, slots, mem_budget, fail_alloc_after, flags)
     rc = load().bn_ctx_create(C.byref(h), C.byref(opts))
     if rc:
         raise BnError(rc, "bn_ctx_create")
@@ -299,6 +303,13 @@ class Batch:
         if rc:
             raise BnError(rc, "bn_batch_run")
 
+    def describe(self) -> str:
+        buf = C.create_string_buffer(1 << 14)
+        rc = load().bn_batch_describe(self.h, buf, len(buf))
+        if rc:
+            raise BnError(rc, "bn_batch_describe")
+        return buf.value.decode()
+
     def results(self, k: int):
         n = self.jobs[k].n
         post = np.zeros((n, n))
@@ -324,8 +335,9 @@ class Context:
     """Owns one bn_ctx."""
 
     def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0,
-                 fail_alloc_after: int = -1):
-        self.h = bn_ctx_create(device, slots, mem_budget, fail_alloc_after)
+                 fail_alloc_after: int = -1, autotune: bool = True):
+        self.h = bn_ctx_create(device, slots, mem_budget, fail_alloc_after,
+                               0 if autotune else BN_CTX_NO_AUTOTUNE)
 
     def close(self):
         if self.h:

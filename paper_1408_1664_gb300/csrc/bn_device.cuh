@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace bn {
@@ -31,6 +32,17 @@ static __constant__ BinomTable c_binom = make_binom_table();
 __device__ __forceinline__ uint32_t binom(int n, int k)
 {
     return (k < 0 || k > n) ? 0u : c_binom.v[n][k];
+}
+
+// Jobs of one batch group share a launch: the arrays of job blockIdx.y lie
+// js bytes after those of job blockIdx.y - 1 (js = 0 for a single job).
+template <typename P>
+__device__ __forceinline__ P* job_ptr(P* p, size_t js)
+{
+    // byte arithmetic on the pointer itself (no round trip through an
+    // integer), so the result stays based on p for alias analysis
+    using B = typename std::conditional<std::is_const<P>::value, const char, char>::type;
+    return reinterpret_cast<P*>(reinterpret_cast<B*>(p) + (size_t)blockIdx.y * js);
 }
 
 // Number of subsets of an nb-element set with at most d elements.

@@ -365,8 +365,11 @@ k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict
 }
 
 // cmax[i] = max_f logB[i*K + f]; one block per node.
-__global__ void k_node_max(int64_t K, const double* __restrict__ logB, double* __restrict__ cmax)
+__global__ void k_node_max(int64_t K, const double* __restrict__ logB, double* __restrict__ cmax,
+                           size_t js)
 {
+    logB = job_ptr(logB, js);
+    cmax = job_ptr(cmax, js);
     __shared__ double red[32];
     const int i = blockIdx.x;
     double mx = -INFINITY;
@@ -383,8 +386,11 @@ __global__ void k_node_max(int64_t K, const double* __restrict__ logB, double* _
 
 template <typename T>
 __global__ void k_shift_scores(int64_t total, int64_t K, const double* __restrict__ logB,
-                               const double* __restrict__ cmax, T* __restrict__ lbs)
+                               const double* __restrict__ cmax, T* __restrict__ lbs, size_t js)
 {
+    logB = job_ptr(logB, js);
+    cmax = job_ptr(cmax, js);
+    lbs = job_ptr(lbs, js);
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
          x += (int64_t)gridDim.x * blockDim.x)
         lbs[x] = (T)LogOps<T>::from_ln(logB[x] - cmax[x / K]);
@@ -405,8 +411,11 @@ __global__ void k_shift_scores(int64_t total, int64_t K, const double* __restric
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_upzeta(int n, int b, int64_t K, int qbits, const uint32_t* __restrict__ cmasks,
-         const T* __restrict__ lbs, T* __restrict__ A)
+         const T* __restrict__ lbs, T* __restrict__ A, size_t js)
 {
+    cmasks = job_ptr(cmasks, js);
+    lbs = job_ptr(lbs, js);
+    A = job_ptr(A, js);
     using O = typename OrdInt<T>::type;
     using U = unsigned long long;
     using L = LogOps<T>;
@@ -505,8 +514,10 @@ __device__ __forceinline__ void lse_step(T& m, T& s, T x)
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_forward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __restrict__ A,
-                T* __restrict__ F)
+                T* __restrict__ F, size_t js)
 {
+    A = job_ptr(A, js);
+    F = job_ptr(F, js);
     using L = LogOps<T>;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -561,8 +572,10 @@ k_forward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __rest
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __restrict__ A,
-                 T* __restrict__ Rc)
+                 T* __restrict__ Rc, size_t js)
 {
+    A = job_ptr(A, js);
+    Rc = job_ptr(Rc, js);
     using L = LogOps<T>;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -630,8 +643,11 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gamma_p1(int n, int d, int v, int b, uint32_t nlow, const T* __restrict__ F,
-           const T* __restrict__ Rc, T* __restrict__ W)
+           const T* __restrict__ Rc, T* __restrict__ W, size_t js)
 {
+    F = job_ptr(F, js);
+    Rc = job_ptr(Rc, js);
+    W = job_ptr(W, js);
     using L = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* vals = reinterpret_cast<T*>(smem_raw);
@@ -659,8 +675,10 @@ k_gamma_p1(int n, int d, int v, int b, uint32_t nlow, const T* __restrict__ F,
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, const T* __restrict__ W,
-           T* __restrict__ Gam)
+           T* __restrict__ Gam, size_t js)
 {
+    W = job_ptr(W, js);
+    Gam = job_ptr(Gam, js);
     using L = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int h = n - 1 - b;
@@ -728,8 +746,16 @@ __global__ void __launch_bounds__(256)
 k_edges(int n, int64_t K, int use_z, int qbits, const double* __restrict__ logB,
         const double* __restrict__ cmax, const uint32_t* __restrict__ masks,
         const T* __restrict__ Gam, const T* __restrict__ F, const int* __restrict__ err,
-        double* __restrict__ post, double* __restrict__ log_PD)
+        double* __restrict__ post, double* __restrict__ log_PD, size_t js)
 {
+    logB = job_ptr(logB, js);
+    cmax = job_ptr(cmax, js);
+    masks = job_ptr(masks, js);
+    Gam = job_ptr(Gam, js);
+    F = job_ptr(F, js);
+    err = job_ptr(err, js);
+    post = job_ptr(post, js);
+    log_PD = job_ptr(log_PD, js);
     using L = LogOps<T>;
     __shared__ unsigned long long Nu[32];
     __shared__ double red[32];
@@ -847,7 +873,7 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
 
 cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s)
 {
-    k_node_max<<<P.n, 256, 0, s>>>(P.K, logB, cmax);
+    k_node_max<<<dim3(P.n, P.nj), 256, 0, s>>>(P.K, logB, cmax, P.js);
     return cudaGetLastError();
 }
 
@@ -855,12 +881,11 @@ cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double*
                                 cudaStream_t s)
 {
     const int64_t total = (int64_t)P.n * P.K;
+    const dim3 grid(grid_for(total, 256), P.nj);
     if (P.prec == 0)
-        k_shift_scores<double><<<grid_for(total, 256), 256, 0, s>>>(total, P.K, logB, cmax,
-                                                                    (double*)lbs);
+        k_shift_scores<double><<<grid, 256, 0, s>>>(total, P.K, logB, cmax, (double*)lbs, P.js);
     else
-        k_shift_scores<float><<<grid_for(total, 256), 256, 0, s>>>(total, P.K, logB, cmax,
-                                                                   (float*)lbs);
+        k_shift_scores<float><<<grid, 256, 0, s>>>(total, P.K, logB, cmax, (float*)lbs, P.js);
     return cudaGetLastError();
 }
 
@@ -887,14 +912,14 @@ cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs
         return launch_upzeta13(P, tab, rk13 + 8192, A, s, sums_done);
     }
     const int h = P.n - 1 - P.b_up;
-    const unsigned grid = (unsigned)P.n << h;
+    const dim3 grid((unsigned)P.n << h, P.nj);
     const size_t sm = upzeta_smem_bytes(P);
     if (P.prec == 0)
         k_upzeta<double><<<grid, 256, sm, s>>>(P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
-                                               (const double*)lbs, (double*)A);
+                                               (const double*)lbs, (double*)A, P.js);
     else
         k_upzeta<float><<<grid, 256, sm, s>>>(P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
-                                              (const float*)lbs, (float*)A);
+                                              (const float*)lbs, (float*)A, P.js);
     return cudaGetLastError();
 }
 
@@ -922,13 +947,13 @@ cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s
         const uint32_t nt = host_binom(nh, hl);
         const int tpw = tiles_per_warp(nt);
         const uint32_t warps = (nt + tpw - 1) / tpw;
-        const unsigned grid = (unsigned)(((uint64_t)warps * 32 + 255) / 256);
+        const dim3 grid((unsigned)(((uint64_t)warps * 32 + 255) / 256), P.nj);
         if (P.prec == 0)
             k_forward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const double*)A,
-                                                         (double*)F);
+                                                         (double*)F, P.js);
         else
             k_forward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const float*)A,
-                                                        (float*)F);
+                                                        (float*)F, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
@@ -944,13 +969,13 @@ cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t
         const uint32_t nt = host_binom(nh, hl);
         const int tpw = tiles_per_warp(nt);
         const uint32_t warps = (nt + tpw - 1) / tpw;
-        const unsigned grid = (unsigned)(((uint64_t)warps * 32 + 255) / 256);
+        const dim3 grid((unsigned)(((uint64_t)warps * 32 + 255) / 256), P.nj);
         if (P.prec == 0)
             k_backward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw,
-                                                          (const double*)A, (double*)Rc);
+                                                          (const double*)A, (double*)Rc, P.js);
         else
             k_backward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const float*)A,
-                                                         (float*)Rc);
+                                                         (float*)Rc, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
@@ -978,26 +1003,28 @@ cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc,
     if (use_tile13_gamma(P)) return launch_gamma13_p1(P, v, F, Rc, rk13, W, s);
     const int h = P.n - 1 - P.b_g;
     const size_t sm1 = gamma_p1_smem_bytes(P);
+    const dim3 grid(1u << h, P.nj);
     if (P.prec == 0)
-        k_gamma_p1<double><<<1u << h, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
-                                                     (const double*)F, (const double*)Rc,
-                                                     (double*)W);
+        k_gamma_p1<double><<<grid, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
+                                                  (const double*)F, (const double*)Rc,
+                                                  (double*)W, P.js);
     else
-        k_gamma_p1<float><<<1u << h, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
-                                                    (const float*)F, (const float*)Rc,
-                                                    (float*)W);
+        k_gamma_p1<float><<<grid, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
+                                                 (const float*)F, (const float*)Rc,
+                                                 (float*)W, P.js);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam_v, cudaStream_t s)
 {
     const size_t sm2 = gamma_p2_smem_bytes(P);
+    const dim3 grid(P.nlow_g, P.nj);
     if (P.prec == 0)
-        k_gamma_p2<double><<<P.nlow_g, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
-                                                      (const double*)W, (double*)Gam_v);
+        k_gamma_p2<double><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
+                                                  (const double*)W, (double*)Gam_v, P.js);
     else
-        k_gamma_p2<float><<<P.nlow_g, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
-                                                     (const float*)W, (float*)Gam_v);
+        k_gamma_p2<float><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
+                                                 (const float*)W, (float*)Gam_v, P.js);
     return cudaGetLastError();
 }
 
@@ -1005,14 +1032,15 @@ cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                          const uint32_t* masks, const void* Gam, const void* F, const int* err,
                          double* post, double* log_PD, cudaStream_t s)
 {
+    const dim3 grid(P.n, P.nj);
     if (P.prec == 0)
-        k_edges<double><<<P.n, 256, 0, s>>>(P.n, P.K, 0, fixed_bits(P.K), logB, cmax, masks,
-                                            (const double*)Gam,
-                                            (const double*)F, err, post, log_PD);
+        k_edges<double><<<grid, 256, 0, s>>>(P.n, P.K, 0, fixed_bits(P.K), logB, cmax, masks,
+                                             (const double*)Gam,
+                                             (const double*)F, err, post, log_PD, P.js);
     else
-        k_edges<float><<<P.n, 256, 0, s>>>(P.n, P.K, 1, fixed_bits(P.K), logB, cmax, masks,
-                                           (const float*)Gam,
-                                           (const float*)F, err, post, log_PD);
+        k_edges<float><<<grid, 256, 0, s>>>(P.n, P.K, 1, fixed_bits(P.K), logB, cmax, masks,
+                                            (const float*)Gam,
+                                            (const float*)F, err, post, log_PD, P.js);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,14 @@ struct Plan {
     uint32_t nlow_g;      // subsets of b_g dims with at most d elements
     int wb;               // in-warp bits of the F / R' tiles
     int prec;             // 0 = FP64, 1 = FP32
+    // Schedule (set by the planner, changed by the batch autotuner):
+    int up13 = 0;         // step 2 by the 13-dimension tiles (n >= 14)
+    int g13 = 0;          // step 4 phase 1 by the 13-dimension tiles (n >= 14)
+    int frows = 0;        // FP32 step 3 by the 16-subset row kernels
+    // Batch groups: nj jobs with equal plans, their arrays js bytes apart;
+    // the launches of steps 2-5 cover all of them (gridDim.y = nj).
+    int nj = 1;
+    size_t js = 0;
 };
 
 cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int W,
@@ -43,7 +51,7 @@ cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double*
 cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
                           const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done = nullptr);
 // Step 3 in FP32 with one thread per 16-subset tile (bn_levels.cu).
-bool use_rows_levels(const Plan& P);
+bool rows_levels_fit(const Plan& P);      // FP32 and 5 <= n < 32
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
 cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStream_t s,
                                  int* launches);
@@ -60,7 +68,7 @@ cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
 size_t upzeta_smem_bytes(const Plan& P);
 // bn_tile13.cu
 cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s);
-cudaError_t launch_rank13_tables(uint16_t* rank13, uint16_t* unrank13, cudaStream_t s);
+cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unrank13, cudaStream_t s);
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
                             cudaStream_t s, cudaEvent_t sums_done = nullptr);
 cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* Rc,
@@ -69,8 +77,22 @@ constexpr size_t kRank13Bytes = 2 * 8192 * sizeof(uint16_t);
 size_t upzeta13_smem_bytes(const Plan& P);
 size_t gamma13_smem_bytes(const Plan& P);
 cudaError_t set_tile13_attributes();
-bool use_tile13_up(const Plan& P);   // n >= 14 and the tile's shared memory fits
-inline bool use_tile13_gamma(const Plan& P) { return P.n >= 14; }
+bool tile13_up_fits(const Plan& P);   // n >= 14 and the column kernel's shared memory fits
+inline bool tile13_gamma_fits(const Plan& P) { return P.n >= 14; }
+
+// The schedule a plan runs: which kernels do steps 2, 3 and 4.  Every choice
+// that fits computes the same values up to rounding.
+inline bool use_tile13_up(const Plan& P) { return P.up13 != 0; }
+inline bool use_tile13_gamma(const Plan& P) { return P.g13 != 0; }
+inline bool use_rows_levels(const Plan& P) { return P.frows != 0; }
+inline bool needs_rank13(const Plan& P) { return P.up13 || P.g13; }
+// The default schedule: every specialised kernel that fits.
+inline void default_schedule(Plan& P)
+{
+    P.up13 = tile13_up_fits(P);
+    P.g13 = tile13_gamma_fits(P);
+    P.frows = rows_levels_fit(P);
+}
 size_t gamma_p1_smem_bytes(const Plan& P);
 size_t gamma_p2_smem_bytes(const Plan& P);
 cudaError_t set_kernel_attributes();

@@ -99,9 +99,12 @@ __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
 }  // namespace
 
 //   F(S) = sum_{i in S} A_i(S - {i}) F(S - {i}),  F(empty) = 1
-__global__ void __launch_bounds__(256)
-k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ F)
+__global__ void __launch_bounds__(256, 3)
+k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ F,
+               size_t js)
 {
+    A = job_ptr(A, js);
+    F = job_ptr(F, js);
     __shared__ uint32_t bt[BT][BT];
     fill_table(bt);
     __syncthreads();
@@ -142,9 +145,12 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, floa
 }
 
 //   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),  R'(V) = 1
-__global__ void __launch_bounds__(256)
-k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ Rc)
+__global__ void __launch_bounds__(256, 3)
+k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ Rc,
+                size_t js)
 {
+    A = job_ptr(A, js);
+    Rc = job_ptr(Rc, js);
     __shared__ uint32_t bt[BT][BT];
     fill_table(bt);
     __syncthreads();
@@ -195,7 +201,7 @@ uint64_t choose(int n, int k)
 
 }  // namespace
 
-bool use_rows_levels(const Plan& P)
+bool rows_levels_fit(const Plan& P)
 {
     return P.prec != 0 && P.n >= LB + 1 && P.n - LB < BT;
 }
@@ -205,7 +211,8 @@ cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStrea
     const int nh = P.n - LB;
     for (int hl = 0; hl <= nh; ++hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        k_forward_rows<<<(nt + 255) / 256, 256, 0, s>>>(P.n, hl, nt, (const float*)A, (float*)F);
+        k_forward_rows<<<dim3((nt + 255) / 256, P.nj), 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+                                                                   (float*)F, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
@@ -219,7 +226,8 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
     const int nh = P.n - LB;
     for (int hl = nh; hl >= 0; --hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        k_backward_rows<<<(nt + 255) / 256, 256, 0, s>>>(P.n, hl, nt, (const float*)A, (float*)Rc);
+        k_backward_rows<<<dim3((nt + 255) / 256, P.nj), 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+                                                                    (float*)Rc, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;

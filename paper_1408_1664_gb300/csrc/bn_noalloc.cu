@@ -167,6 +167,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     for (int k = 0; k <= P.d && k <= P.b_g; ++k) nl += (uint64_t)binom64(P.b_g, k);
     P.nlow_g = (uint32_t)nl;
     P.wb = P.n < 5 ? P.n : 5;
+    bn::default_schedule(P);
 
     // layout inside the static array
     const size_t es = P.prec == 0 ? 8 : 4;
@@ -180,7 +181,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                  o_masks = take(nK * 4), o_cm = take(nK * 4), o_logB = take(nK * 8),
                  o_cmax = take((size_t)P.n * 8), o_lbs = take(nK * es),
                  o_reo = take(bn::use_tile13_up(P) ? nK * es : 0),
-                 o_rk = take(bn::use_tile13_gamma(P) ? bn::kRank13Bytes : 0),
+                 o_rk = take(bn::needs_rank13(P) ? bn::kRank13Bytes : 0),
                  o_A = take(((size_t)P.n << (P.n - 1)) * es), o_F = take(((size_t)1 << P.n) * es),
                  o_Rc = take(((size_t)1 << P.n) * es),
                  o_W = take(((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es);
@@ -221,7 +222,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     CKS(bn::launch_node_max(P, logB, cmax, s));
     CKS(bn::launch_shift_scores(P, logB, cmax, base + o_lbs, s));
     uint16_t* rk13 = reinterpret_cast<uint16_t*>(base + o_rk);
-    if (bn::use_tile13_gamma(P)) CKS(bn::launch_rank13_tables(rk13, rk13 + 8192, s));
+    if (bn::needs_rank13(P)) CKS(bn::launch_rank13_tables(P, rk13, rk13 + 8192, s));
     CKS(bn::launch_upzeta(P, cm, base + o_lbs, base + o_reo, rk13, base + o_A, s));
     CKS(bn::launch_forward(P, base + o_A, base + o_F, s, nullptr));
     CKS(bn::launch_backward(P, base + o_A, base + o_Rc, s, nullptr));

@@ -9,9 +9,11 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <array>
 #include <map>
 #include <mutex>
 #include <set>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -77,8 +79,9 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     L.logB = take(nK * 8);
     L.cmax = take((size_t)P.n * 8);
     L.lbs = take(nK * es);
-    L.tab = take(bn::use_tile13_up(P) ? nK * es : 0);
-    L.rk13 = take(bn::use_tile13_gamma(P) ? bn::kRank13Bytes : 0);
+    // sized for every schedule that fits, so that a plan can switch kernels
+    L.tab = take(bn::tile13_up_fits(P) ? nK * es : 0);
+    L.rk13 = take(bn::tile13_gamma_fits(P) ? bn::kRank13Bytes : 0);
     L.A = take(((size_t)P.n << (P.n - 1)) * es);
     L.F = take(((size_t)1 << P.n) * es);
     L.Rc = take(((size_t)1 << P.n) * es);
@@ -163,6 +166,7 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
     for (int k = 0; k <= P.d && k <= P.b_g; ++k) nl += host_binom(P.b_g, k);
     P.nlow_g = (uint32_t)nl;
     P.wb = std::min(P.n, 5);
+    bn::default_schedule(P);
     return BN_OK;
 }
 
@@ -270,9 +274,9 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
                          B.at<double>(L.logB), nullptr, s)); ++nl;
     CK(bn::launch_node_max(P, B.at<double>(L.logB), B.at<double>(L.cmax), s)); ++nl;
     CK(bn::launch_shift_scores(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<void>(L.lbs), s)); ++nl;
-    if (bn::use_tile13_gamma(P)) {
+    if (bn::needs_rank13(P)) {
         uint16_t* rk = B.at<uint16_t>(L.rk13);
-        CK(bn::launch_rank13_tables(rk, rk + 8192, s));
+        CK(bn::launch_rank13_tables(P, rk, rk + 8192, s));
         ++nl;
     }
     if (ev) CK(cudaEventRecord(ev->ev[1], s));
@@ -395,15 +399,29 @@ struct bn_ctx {
     std::deque<uint64_t> queue;
     uint64_t next_id = 1;
     uint64_t reserved = 0;
+    // batches
+    int flags = 0;
+    std::map<std::array<int, 4>, std::array<int, 3>> tuned;   // (n, d, prec, jobs) -> schedule
+};
+
+// Jobs of a batch with equal n, d and precision: their arrays lie js bytes
+// apart from base on (each job in the same padded layout), and the launches
+// of steps 2-5 cover all of them.
+struct BatchGroup {
+    Plan P{};                  // n, d, K, precision, schedule; nj and js
+    Layout L{};                // the padded layout of one job
+    size_t base = 0;           // arena offset of the group's first job
+    std::vector<int> members;  // indices into bn_batch::jobs
+    bool timed = false;        // schedule chosen by timing (else default or cached)
+    float ms[3][2] = {};       // timings of the alternatives: up-zeta, F/R', Gamma
 };
 
 struct bn_batch {
     bn_ctx* ctx = nullptr;
     std::vector<HostJob> jobs;
-    std::vector<Layout> layouts;
-    std::vector<size_t> offs, out_off;
+    std::vector<int> group_of, slot_of;
+    std::vector<BatchGroup> groups;
     char* arena = nullptr;
-    char* out = nullptr;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> joins;
     cudaEvent_t fork = nullptr;
@@ -563,6 +581,7 @@ int bn_ctx_create(bn_ctx** out, const bn_ctx_opts* o)
     bn_ctx* c = new bn_ctx();
     c->device = opts.device;
     c->fail_after = opts.fail_alloc_after;
+    c->flags = opts.flags;
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->budget = opts.mem_budget ? opts.mem_budget : (uint64_t)(0.9 * (double)fr);
@@ -800,6 +819,123 @@ int bn_stats_history(bn_ctx* c, bn_stats* out, int32_t max, int32_t* count)
 
 // ---------------------------------------------------------------- batches --
 
+namespace {
+
+// Steps 1-5 of every job of group g on stream s; `stages` selects the parts:
+// bit 0 step 1 (per job) and the score shift, bit 1 step 2, bit 2 step 3,
+// bit 3 step 4, bit 4 step 5.
+int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsigned stages)
+{
+    const Plan& G = g.P;
+    const Layout& L = g.L;
+    char* base = b->arena + g.base;
+    auto at = [&](size_t off) { return base + off; };
+    if (stages & 1u) {
+        for (size_t q = 0; q < g.members.size(); ++q) {
+            const HostJob& hj = b->jobs[g.members[q]];
+            const Plan& P = hj.P;
+            char* jb = base + q * G.js;
+            CK(bn::launch_pack_planes(reinterpret_cast<const uint8_t*>(jb + L.data), P.n, P.m,
+                                      P.rmax, P.W, reinterpret_cast<uint64_t*>(jb + L.planes), s));
+            CK(bn::launch_lgamma_table(reinterpret_cast<const double*>(jb + L.alpha), P.rows, P.m,
+                                       reinterpret_cast<double*>(jb + L.lgT), s));
+            CK(bn::launch_scores(P, reinterpret_cast<const uint8_t*>(jb + L.arity),
+                                 reinterpret_cast<const uint64_t*>(jb + L.planes),
+                                 reinterpret_cast<const double*>(jb + L.Dvals),
+                                 reinterpret_cast<const double*>(jb + L.lgT),
+                                 reinterpret_cast<const double*>(jb + L.log_rho), 0,
+                                 (int64_t)P.n * P.K, reinterpret_cast<uint32_t*>(jb + L.masks),
+                                 reinterpret_cast<uint32_t*>(jb + L.cmasks),
+                                 reinterpret_cast<double*>(jb + L.logB), nullptr, s));
+        }
+        CK(bn::launch_node_max(G, reinterpret_cast<const double*>(at(L.logB)),
+                               reinterpret_cast<double*>(at(L.cmax)), s));
+        CK(bn::launch_shift_scores(G, reinterpret_cast<const double*>(at(L.logB)),
+                                   reinterpret_cast<const double*>(at(L.cmax)), at(L.lbs), s));
+        if (bn::tile13_gamma_fits(G)) {
+            uint16_t* rk = reinterpret_cast<uint16_t*>(at(L.rk13));
+            CK(bn::launch_rank13_tables(G, rk, rk + 8192, s));
+        }
+    }
+    if (stages & 2u)
+        CK(bn::launch_upzeta(G, reinterpret_cast<const uint32_t*>(at(L.cmasks)), at(L.lbs),
+                             at(L.tab), reinterpret_cast<const uint16_t*>(at(L.rk13)), at(L.A), s));
+    if (stages & 4u) {
+        CK(bn::launch_forward(G, at(L.A), at(L.F), s, nullptr));
+        CK(bn::launch_backward(G, at(L.A), at(L.Rc), s, nullptr));
+    }
+    if (stages & 8u) {
+        const size_t es = G.prec == 0 ? 8 : 4;
+        for (int v = 0; v < G.n; ++v) {
+            CK(bn::launch_gamma_p1(G, v, at(L.F), at(L.Rc),
+                                   reinterpret_cast<const uint16_t*>(at(L.rk13)), at(L.W), s));
+            CK(bn::launch_gamma_p2(G, at(L.W), at(L.Gam) + (size_t)v * G.K * es, s));
+        }
+    }
+    if (stages & 16u)
+        CK(bn::launch_edges(G, reinterpret_cast<const double*>(at(L.logB)),
+                            reinterpret_cast<const double*>(at(L.cmax)),
+                            reinterpret_cast<const uint32_t*>(at(L.masks)), at(L.Gam), at(L.F),
+                            reinterpret_cast<const int*>(at(L.err)),
+                            reinterpret_cast<double*>(at(L.post)),
+                            reinterpret_cast<double*>(at(L.logPD)), s));
+    return BN_OK;
+}
+
+// Mean device time (ms) of `stages` of group g under plan P: one warm-up run
+// and three timed runs on stream s.
+int time_stages(const bn_batch* b, const BatchGroup& g, const Plan& P, unsigned stages,
+                cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* ms)
+{
+    BatchGroup t = g;
+    t.P = P;
+    int rc = enqueue_group(b, t, s, stages);
+    if (rc) return rc;
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) {
+        rc = enqueue_group(b, t, s, stages);
+        if (rc) return rc;
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= 3.0f;
+    return BN_OK;
+}
+
+// The autotuner: for every stage with alternatives that fit, time each on
+// the group's own data (steps before it computed once with the default
+// schedule) and keep the fastest.  The stages are independent given their
+// inputs, so they are tuned one at a time.
+int tune_group(const bn_batch* b, BatchGroup& g, cudaStream_t s)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return BN_ECUDA;
+    }
+    int rc = enqueue_group(b, g, s, 31u);
+    struct Knob { int Plan::*flag; bool fits; unsigned stage; };
+    const Knob knobs[3] = {{&Plan::up13, bn::tile13_up_fits(g.P), 2u},
+                           {&Plan::frows, bn::rows_levels_fit(g.P), 4u},
+                           {&Plan::g13, bn::tile13_gamma_fits(g.P), 8u}};
+    for (int k = 0; rc == BN_OK && k < 3; ++k) {
+        if (!knobs[k].fits) continue;
+        for (int alt = 0; rc == BN_OK && alt < 2; ++alt) {
+            Plan P = g.P;
+            P.*(knobs[k].flag) = alt;
+            rc = time_stages(b, g, P, knobs[k].stage, s, e0, e1, &g.ms[k][alt]);
+        }
+        if (rc == BN_OK) g.P.*(knobs[k].flag) = g.ms[k][1] <= g.ms[k][0] ? 1 : 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == BN_OK) g.timed = true;
+    return rc;
+}
+
+}  // namespace
+
 int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch** out)
 {
     if (!c || !jobs || !out || count < 1) return BN_EINVAL;
@@ -807,7 +943,9 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
     bn_batch* b = new bn_batch();
     b->ctx = c;
     b->jobs.resize(count);
-    size_t total = 0, outs = 0;
+    b->group_of.assign(count, -1);
+    b->slot_of.assign(count, -1);
+    std::map<std::array<int, 3>, int> key_to_group;
     for (int k = 0; k < count; ++k) {
         HostJob& hj = b->jobs[k];
         int rc = jobs[k].data_on_device ? BN_EINVAL : validate_and_plan(&jobs[k], hj);
@@ -816,63 +954,93 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
         hj.data_copy.assign(jobs[k].data ? jobs[k].data : (const uint8_t*)"",
                             jobs[k].data ? jobs[k].data + (size_t)P.m * P.n : (const uint8_t*)"");
         hj.data = hj.data_copy.data();
-        b->layouts.push_back(make_layout(P, 0));
-        b->offs.push_back(total);
-        total += b->layouts.back().total;
-        b->out_off.push_back(outs);
-        outs += al((size_t)P.n * P.n * 8 + 8);
+        const std::array<int, 3> key{P.n, P.d, P.prec};
+        auto it = key_to_group.find(key);
+        if (it == key_to_group.end()) {
+            it = key_to_group.emplace(key, (int)b->groups.size()).first;
+            b->groups.emplace_back();
+            b->groups.back().P = P;
+        }
+        BatchGroup& g = b->groups[it->second];
+        b->group_of[k] = it->second;
+        b->slot_of[k] = (int)g.members.size();
+        g.members.push_back(k);
+        // the padded plan: the largest step-1 tables of the group
+        g.P.m = std::max(g.P.m, P.m);
+        g.P.W = std::max(g.P.W, P.W);
+        g.P.rmax = std::max(g.P.rmax, P.rmax);
+        g.P.rows = std::max(g.P.rows, P.rows);
     }
-    if (total + outs > c->budget) { delete b; return BN_ENOMEM; }
+    size_t total = 0;
+    for (auto& g : b->groups) {
+        g.L = make_layout(g.P, 0);
+        g.P.nj = (int)g.members.size();
+        g.P.js = g.L.total;
+        g.base = total;
+        total += (size_t)g.P.nj * g.P.js;
+    }
+    if (total > c->budget) { delete b; return BN_ENOMEM; }
     if (cudaSetDevice(c->device) != cudaSuccess) { delete b; return BN_ECUDA; }
     void* p = nullptr;
-    int rc = dev_alloc(c, &p, total + outs, nullptr);
+    int rc = dev_alloc(c, &p, total, nullptr);
     if (rc) { delete b; return rc; }
     b->arena = (char*)p;
-    b->out = b->arena + total;
     rc = BN_ECUDA;
     cudaStream_t cap = c->stream;
-    const int nb = std::min(count, 32);
+    const int nb = std::min((int)b->groups.size(), 32);
     b->streams.assign(nb, nullptr);
     bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
     for (auto& st : b->streams) ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
     b->joins.assign(nb, nullptr);
     for (auto& e : b->joins) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
     // inputs go to the device now; only kernels are captured
+    ok = ok && cudaMemset(b->arena, 0, total) == cudaSuccess;
     for (int k = 0; ok && k < count; ++k) {
         const HostJob& hj = b->jobs[k];
-        const Layout& L = b->layouts[k];
-        Bufs B{b->arena + b->offs[k], L};
+        const BatchGroup& g = b->groups[b->group_of[k]];
+        const Layout& L = g.L;
+        char* jb = b->arena + g.base + (size_t)b->slot_of[k] * g.P.js;
         std::vector<double> lr(hj.P.d + 1, 0.0), alpha(hj.P.rows);
         for (size_t t = 0; t < hj.log_rho.size(); ++t) lr[t] = hj.log_rho[t];
         for (int r = 0; r < hj.P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
-        ok = (hj.P.m == 0 || cudaMemcpy(B.at<char>(L.data), hj.data, (size_t)hj.P.m * hj.P.n,
+        ok = (hj.P.m == 0 || cudaMemcpy(jb + L.data, hj.data, (size_t)hj.P.m * hj.P.n,
                                         cudaMemcpyHostToDevice) == cudaSuccess) &&
-             cudaMemcpy(B.at<char>(L.arity), hj.arity.data(), hj.P.n, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(B.at<char>(L.log_rho), lr.data(), lr.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(B.at<char>(L.Dvals), hj.Dvals.data(), hj.Dvals.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(B.at<char>(L.alpha), alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+             cudaMemcpy(jb + L.arity, hj.arity.data(), hj.P.n, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(jb + L.log_rho, lr.data(), lr.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(jb + L.Dvals, hj.Dvals.data(), hj.Dvals.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(jb + L.alpha, alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    // schedules: cached, timed, or the default
+    for (auto& g : b->groups) {
+        if (!ok) break;
+        if (c->flags & BN_CTX_NO_AUTOTUNE) continue;
+        const std::array<int, 4> key{g.P.n, g.P.d, g.P.prec, g.P.nj};
+        auto it = c->tuned.find(key);
+        if (it != c->tuned.end()) {
+            g.P.up13 = it->second[0];
+            g.P.frows = it->second[1];
+            g.P.g13 = it->second[2];
+            continue;
+        }
+        ok = tune_group(b, g, cap) == BN_OK;
+        if (ok) c->tuned[key] = {g.P.up13, g.P.frows, g.P.g13};
     }
     ok = ok && cudaStreamSynchronize(cap) == cudaSuccess;
     if (ok && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         bool cap_ok = cudaEventRecord(b->fork, cap) == cudaSuccess;
         for (auto st : b->streams) cap_ok = cap_ok && cudaStreamWaitEvent(st, b->fork, 0) == cudaSuccess;
-        for (int k = 0; cap_ok && k < count; ++k) {
-            const HostJob& hj = b->jobs[k];
-            Bufs B{b->arena + b->offs[k], b->layouts[k]};
-            double* post = reinterpret_cast<double*>(b->out + b->out_off[k]);
-            cap_ok = enqueue_kernels(hj, B, B.at<uint8_t>(B.L.data), post, post + hj.P.n * hj.P.n,
-                                     b->streams[k % nb], nullptr, nullptr) == BN_OK;
-        }
+        for (size_t q = 0; cap_ok && q < b->groups.size(); ++q)
+            cap_ok = enqueue_group(b, b->groups[q], b->streams[q % nb], 31u) == BN_OK;
         for (int q = 0; cap_ok && q < nb; ++q)
             cap_ok = cudaEventRecord(b->joins[q], b->streams[q]) == cudaSuccess &&
                      cudaStreamWaitEvent(cap, b->joins[q], 0) == cudaSuccess;
-        cudaGraph_t g = nullptr;
-        const bool end_ok = cudaStreamEndCapture(cap, &g) == cudaSuccess;
-        if (cap_ok && end_ok && g && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
-            b->graph = g;
+        cudaGraph_t gr = nullptr;
+        const bool end_ok = cudaStreamEndCapture(cap, &gr) == cudaSuccess;
+        if (cap_ok && end_ok && gr && cudaGraphInstantiate(&b->exec, gr, 0) == cudaSuccess) {
+            b->graph = gr;
             rc = BN_OK;
-        } else if (g) {
-            cudaGraphDestroy(g);
+        } else if (gr) {
+            cudaGraphDestroy(gr);
         }
     }
     cudaGetLastError();
@@ -895,13 +1063,32 @@ int bn_batch_results(bn_batch* b, int32_t k, double* post, double* log_PD)
 {
     if (!b || !post || k < 0 || k >= (int32_t)b->jobs.size() || !b->ran) return BN_EINVAL;
     const Plan& P = b->jobs[k].P;
+    const BatchGroup& g = b->groups[b->group_of[k]];
+    const char* jb = b->arena + g.base + (size_t)b->slot_of[k] * g.P.js;
     CK(cudaStreamSynchronize(b->last));
-    const char* src = b->out + b->out_off[k];
-    CK(cudaMemcpy(post, src, (size_t)P.n * P.n * 8, cudaMemcpyDeviceToHost));
-    if (log_PD) CK(cudaMemcpy(log_PD, src + (size_t)P.n * P.n * 8, 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(post, jb + g.L.post, (size_t)P.n * P.n * 8, cudaMemcpyDeviceToHost));
+    if (log_PD) CK(cudaMemcpy(log_PD, jb + g.L.logPD, 8, cudaMemcpyDeviceToHost));
     int err = 0;
-    CK(cudaMemcpy(&err, b->arena + b->offs[k] + b->layouts[k].err, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&err, jb + g.L.err, 4, cudaMemcpyDeviceToHost));
     return err ? BN_EINVAL : BN_OK;
+}
+
+int bn_batch_describe(bn_batch* b, char* buf, size_t len)
+{
+    if (!b || !buf || len == 0) return BN_EINVAL;
+    std::string s;
+    char line[256];
+    for (const auto& g : b->groups) {
+        std::snprintf(line, sizeof line,
+                      "n=%d d=%d %s jobs=%d up13=%d frows=%d g13=%d %s"
+                      " ms(up %.3f/%.3f fr %.3f/%.3f g %.3f/%.3f)\n",
+                      g.P.n, g.P.d, g.P.prec == 0 ? "fp64" : "fp32", g.P.nj, g.P.up13, g.P.frows,
+                      g.P.g13, g.timed ? "timed" : "default-or-cached", g.ms[0][0], g.ms[0][1],
+                      g.ms[1][0], g.ms[1][1], g.ms[2][0], g.ms[2][1]);
+        s += line;
+    }
+    std::snprintf(buf, len, "%s", s.c_str());
+    return BN_OK;
 }
 
 int bn_batch_destroy(bn_batch* b)

@@ -378,8 +378,11 @@ __device__ __forceinline__ uint32_t row_offset(int h, int d, int kh, uint32_t ra
 }
 
 template <typename T>
-__global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs, T* __restrict__ tab)
+__global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs, T* __restrict__ tab,
+                             size_t js)
 {
+    lbs = job_ptr(lbs, js);
+    tab = job_ptr(tab, js);
     const int h = n - 1 - TB;
     const int64_t total = (int64_t)n * K;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
@@ -411,8 +414,10 @@ __global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs,
 // ===========================================================================
 template <typename T>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 4 : 2)
-k_upzeta13_cols(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A)
+k_upzeta13_cols(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A, size_t js)
 {
+    tab = job_ptr(tab, js);
+    A = job_ptr(A, js);
     using Lg = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* part = reinterpret_cast<T*>(smem_raw);            // 2 * 8 * 96 partial (max, sum) pairs
@@ -548,8 +553,10 @@ k_upzeta13_cols(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
 // ===========================================================================
 template <typename T>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
-k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ A)
+k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ A, size_t js)
 {
+    unrank13 = job_ptr(unrank13, js);
+    A = job_ptr(A, js);
     using Lg = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
@@ -656,8 +663,13 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
-             const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W)
+             const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W,
+             size_t js)
 {
+    F = job_ptr(F, js);
+    Rc = job_ptr(Rc, js);
+    rank13 = job_ptr(rank13, js);
+    W = job_ptr(W, js);
     using Lg = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
@@ -734,8 +746,11 @@ k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
 
 // rank13[L] = position of L among the subsets of 13 bits ordered by size then
 // value; unrank13 is its inverse.
-__global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restrict__ unrank13)
+__global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restrict__ unrank13,
+                                size_t js)
 {
+    rank13 = job_ptr(rank13, js);
+    unrank13 = job_ptr(unrank13, js);
     const uint32_t L = blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= (uint32_t)TN) return;
     const uint32_t r = small_subset_rank(L, TB);
@@ -761,7 +776,7 @@ size_t upzeta13_smem_bytes(const Plan& P)
     return (size_t)TN * (3 * es) + 16;
 }
 
-bool use_tile13_up(const Plan& P)
+bool tile13_up_fits(const Plan& P)
 {
     return P.n >= 14 && upzeta13_cols_smem_bytes(P) <= 227 * 1024 - 64;
 }
@@ -772,20 +787,22 @@ size_t gamma13_smem_bytes(const Plan& P)
     return (size_t)TN * (3 * es) + 16;
 }
 
-cudaError_t launch_rank13_tables(uint16_t* rank13, uint16_t* unrank13, cudaStream_t s)
+cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unrank13, cudaStream_t s)
 {
-    k_rank13_tables<<<TN / 256, 256, 0, s>>>(rank13, unrank13);
+    k_rank13_tables<<<dim3(TN / 256, P.nj), 256, 0, s>>>(rank13, unrank13, P.js);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s)
 {
     const int64_t total = (int64_t)P.n * P.K;
-    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    const dim3 grid((unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), P.nj);
     if (P.prec == 0)
-        k_reorder_up<double><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const double*)lbs, (double*)tab);
+        k_reorder_up<double><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const double*)lbs, (double*)tab,
+                                                  P.js);
     else
-        k_reorder_up<float><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const float*)lbs, (float*)tab);
+        k_reorder_up<float><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const float*)lbs, (float*)tab,
+                                                 P.js);
     return cudaGetLastError();
 }
 
@@ -793,12 +810,14 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
                             cudaStream_t s, cudaEvent_t sums_done)
 {
     const int h = P.n - 1 - TB;
-    const unsigned grid = (unsigned)P.n << h;
+    const dim3 grid((unsigned)P.n << h, P.nj);
     const size_t sc = upzeta13_cols_smem_bytes(P), sm = upzeta13_smem_bytes(P);
     if (P.prec == 0)
-        k_upzeta13_cols<double><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const double*)tab, (double*)A);
+        k_upzeta13_cols<double><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const double*)tab, (double*)A,
+                                                     P.js);
     else
-        k_upzeta13_cols<float><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const float*)tab, (float*)A);
+        k_upzeta13_cols<float><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const float*)tab, (float*)A,
+                                                    P.js);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (sums_done) {
@@ -806,9 +825,9 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         if (e != cudaSuccess) return e;
     }
     if (P.prec == 0)
-        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A);
+        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A, P.js);
     else
-        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A);
+        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A, P.js);
     return cudaGetLastError();
 }
 
@@ -817,12 +836,13 @@ cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* R
 {
     const int h = P.n - 1 - TB;
     const size_t sm = gamma13_smem_bytes(P);
+    const dim3 grid(1u << h, P.nj);
     if (P.prec == 0)
-        k_gamma13_p1<double><<<1u << h, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const double*)F,
-                                                      (const double*)Rc, rank13, (double*)W);
+        k_gamma13_p1<double><<<grid, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const double*)F,
+                                                   (const double*)Rc, rank13, (double*)W, P.js);
     else
-        k_gamma13_p1<float><<<1u << h, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const float*)F,
-                                                     (const float*)Rc, rank13, (float*)W);
+        k_gamma13_p1<float><<<grid, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const float*)F,
+                                                  (const float*)Rc, rank13, (float*)W, P.js);
     return cudaGetLastError();
 }
 
