@@ -200,15 +200,7 @@ __device__ __forceinline__ void bfly_plain(T (&x)[TR], int k0, int nk)
     }
 }
 
-// A tile whose values span less than FastSpan (log units) below its maximum
-// is summed in one scale relative to that maximum: every output is at least
-// 2^-FastSpan of it, and a partial sum flushed below the smallest normal is
-// under 2^-46 of any output, also summed over the 8192 elements.
-template <typename T> struct FastSpan;
-template <> struct FastSpan<float> { static constexpr float value = 80.0f; };      // bits
-template <> struct FastSpan<double> { static constexpr double value = 640.0; };    // nats
-
-// Single-scale windows for the upward zeta.  Pass p scales the terms by
+// Single-scale windows for both zeta tiles.  Pass p scales the terms by
 // s_p = M - top - p * win (M bounds every output from above) and writes the
 // outputs whose scaled value is at least 2^lo (e^lo): terms flushed below the
 // smallest normal number (2^-126; e^-708) number at most 8192, under 2^-113
@@ -218,7 +210,7 @@ template <> struct FastSpan<double> { static constexpr double value = 640.0; }; 
 template <typename T> struct Window;
 template <> struct Window<float> {                 // bits
     static constexpr float top = 126.0f, lo = -80.0f, win = 206.0f;
-    static constexpr int max_pass = 3;
+    static constexpr int max_pass = 2;     // a third pass costs more than the exact path
 };
 template <> struct Window<double> {                // nats
     static constexpr double top = 700.0, lo = -600.0, win = 1300.0;
@@ -703,11 +695,13 @@ k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
     T* row = W + (size_t)H * nlow;
     {
         // every output T (|T| <= d) sums s over its supersets, the full set
-        // included: it is at least s(full)
+        // included: it lies between s(full) and M, so a tile that spans
+        // less than one window resolves in one single-scale pass (Window)
         const T M = ord_dec(tmax_s) + T(TB);
-        if (M - sfull_s < FastSpan<T>::value) {
+        if (M - sfull_s < Window<T>::win) {
+            const T sp = M - Window<T>::top;
 #pragma unroll
-            for (int r = 0; r < TR; ++r) x[r] = Lg::ex(x[r] - M);
+            for (int r = 0; r < TR; ++r) x[r] = Lg::ex(x[r] - sp);
             bfly_plain<false>(x, 0, 5);
             st1(A0, x, t);
             __syncthreads();
@@ -720,7 +714,7 @@ k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
                 const uint32_t el = el3(r, t);
-                if (__popc(el) <= d) row[rank13[el]] = M + Lg::lg(x[r]);
+                if (__popc(el) <= d) row[rank13[el]] = sp + Lg::lg(x[r]);
             }
             return;
         }
