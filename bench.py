@@ -169,12 +169,13 @@ def stage_table(n: int, d: int, es: int) -> dict:
                              "ms": lambda h: h["ms_upzeta"] - h["ms_upzeta_sums"]}
         tab["k_upzeta13_cols"] = {"bytes": C_bytes + 2 * n * K * es, "launches": 1,
                                   "ms": lambda h: h["ms_upzeta_sums"]}
-        # per endpoint v: the halves of F and R' read, one row of W per tile written
-        tab["k_gamma13_p1"] = {"bytes": (N + 2 ** h * ncol) * es, "launches": n,
+        # every endpoint v in one launch: the halves of F and R' read per v,
+        # one row of W per tile written
+        tab["k_gamma13_p1"] = {"bytes": n * (N + 2 ** h * ncol) * es, "launches": 1,
                                "ms": lambda h: h["ms_gamma_p1"]}
     else:
         tab["k_upzeta"] = {"bytes": A_bytes, "launches": 1, "ms": lambda h: h["ms_upzeta"]}
-        tab["k_gamma_p1"] = {"bytes": N * es, "launches": n, "ms": lambda h: h["ms_gamma_p1"]}
+        tab["k_gamma_p1"] = {"bytes": n * N * es, "launches": 1, "ms": lambda h: h["ms_gamma_p1"]}
     return tab
 
 

@@ -642,12 +642,13 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
 // ===========================================================================
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_gamma_p1(int n, int d, int v, int b, uint32_t nlow, const T* __restrict__ F,
+k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
            const T* __restrict__ Rc, T* __restrict__ W, size_t js)
 {
+    const int v = blockIdx.z;                       // endpoint: one slice of W each
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
-    W = job_ptr(W, js);
+    W = job_ptr(W, js) + (size_t)v * gridDim.x * nlow;
     using L = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* vals = reinterpret_cast<T*>(smem_raw);
@@ -674,11 +675,12 @@ k_gamma_p1(int n, int d, int v, int b, uint32_t nlow, const T* __restrict__ F,
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, const T* __restrict__ W,
+k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, int64_t K, const T* __restrict__ W,
            T* __restrict__ Gam, size_t js)
 {
-    W = job_ptr(W, js);
-    Gam = job_ptr(Gam, js);
+    const int v = blockIdx.z;                       // endpoint: its slice of W, its K outputs
+    W = job_ptr(W, js) + ((size_t)v << (n - 1 - b)) * nlow;
+    Gam = job_ptr(Gam, js) + (size_t)v * K;
     using L = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int h = n - 1 - b;
@@ -997,34 +999,34 @@ size_t gamma_p2_smem_bytes(const Plan& P)
     return ((size_t)1 << P.hc_g) * es + nout * es + nout * 4 + 16;
 }
 
-cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc,
-                            const uint16_t* rk13, void* W, cudaStream_t s)
+cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
+                            void* W, cudaStream_t s)
 {
-    if (use_tile13_gamma(P)) return launch_gamma13_p1(P, v, F, Rc, rk13, W, s);
+    if (use_tile13_gamma(P)) return launch_gamma13_p1(P, F, Rc, rk13, W, s);
     const int h = P.n - 1 - P.b_g;
     const size_t sm1 = gamma_p1_smem_bytes(P);
-    const dim3 grid(1u << h, P.nj);
+    const dim3 grid(1u << h, P.nj, P.n);
     if (P.prec == 0)
-        k_gamma_p1<double><<<grid, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
+        k_gamma_p1<double><<<grid, 256, sm1, s>>>(P.n, P.d, P.b_g, P.nlow_g,
                                                   (const double*)F, (const double*)Rc,
                                                   (double*)W, P.js);
     else
-        k_gamma_p1<float><<<grid, 256, sm1, s>>>(P.n, P.d, v, P.b_g, P.nlow_g,
+        k_gamma_p1<float><<<grid, 256, sm1, s>>>(P.n, P.d, P.b_g, P.nlow_g,
                                                  (const float*)F, (const float*)Rc,
                                                  (float*)W, P.js);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam_v, cudaStream_t s)
+cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s)
 {
     const size_t sm2 = gamma_p2_smem_bytes(P);
-    const dim3 grid(P.nlow_g, P.nj);
+    const dim3 grid(P.nlow_g, P.nj, P.n);
     if (P.prec == 0)
-        k_gamma_p2<double><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
-                                                  (const double*)W, (double*)Gam_v, P.js);
+        k_gamma_p2<double><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
+                                                  (const double*)W, (double*)Gam, P.js);
     else
-        k_gamma_p2<float><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g,
-                                                 (const float*)W, (float*)Gam_v, P.js);
+        k_gamma_p2<float><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
+                                                 (const float*)W, (float*)Gam, P.js);
     return cudaGetLastError();
 }
 

@@ -58,9 +58,11 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
 cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s,
                             int* launches);
-cudaError_t launch_gamma_p1(const Plan& P, int v, const void* F, const void* Rc,
-                            const uint16_t* rk13, void* W, cudaStream_t s);
-cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam_v, cudaStream_t s);
+// Step 4 for every endpoint v in one launch per phase (gridDim.z = n): W
+// holds n slices of 2^(n-1-b_g) * nlow_g values, Gam the n * K outputs.
+cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
+                            void* W, cudaStream_t s);
+cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s);
 cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                          const uint32_t* masks, const void* Gam, const void* F,
                          const int* err, double* post, double* log_PD, cudaStream_t s);
@@ -71,7 +73,7 @@ cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStr
 cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unrank13, cudaStream_t s);
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
                             cudaStream_t s, cudaEvent_t sums_done = nullptr);
-cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* Rc,
+cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
                               const uint16_t* rank13, void* W, cudaStream_t s);
 constexpr size_t kRank13Bytes = 2 * 8192 * sizeof(uint16_t);
 size_t upzeta13_smem_bytes(const Plan& P);

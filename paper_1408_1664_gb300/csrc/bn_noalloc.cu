@@ -184,7 +184,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                  o_rk = take(bn::needs_rank13(P) ? bn::kRank13Bytes : 0),
                  o_A = take(((size_t)P.n << (P.n - 1)) * es), o_F = take(((size_t)1 << P.n) * es),
                  o_Rc = take(((size_t)1 << P.n) * es),
-                 o_W = take(((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es);
+                 o_W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es);
     if (o > (size_t)BN_STATIC_SCRATCH_BYTES) return BN_ENOMEM;   // job too large
 
     int dev = 0;
@@ -226,10 +226,8 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     CKS(bn::launch_upzeta(P, cm, base + o_lbs, base + o_reo, rk13, base + o_A, s));
     CKS(bn::launch_forward(P, base + o_A, base + o_F, s, nullptr));
     CKS(bn::launch_backward(P, base + o_A, base + o_Rc, s, nullptr));
-    for (int v = 0; v < P.n; ++v) {
-        CKS(bn::launch_gamma_p1(P, v, base + o_F, base + o_Rc, rk13, base + o_W, s));
-        CKS(bn::launch_gamma_p2(P, base + o_W, base + o_G + (size_t)v * P.K * es, s));
-    }
+    CKS(bn::launch_gamma_p1(P, base + o_F, base + o_Rc, rk13, base + o_W, s));
+    CKS(bn::launch_gamma_p2(P, base + o_W, base + o_G, s));
     CKS(bn::launch_edges(P, logB, cmax, masks, base + o_G, base + o_F, err, post_dev,
                          log_PD_dev, s));
 #undef CKS

@@ -85,7 +85,7 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     L.A = take(((size_t)P.n << (P.n - 1)) * es);
     L.F = take(((size_t)1 << P.n) * es);
     L.Rc = take(((size_t)1 << P.n) * es);
-    L.W = take(((size_t)1 << hg) * P.nlow_g * es);
+    L.W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es);   // one slice per endpoint
     L.Gam = take(nK * es);
     L.post = take((size_t)P.n * P.n * 8);
     L.logPD = take(8);
@@ -177,8 +177,10 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
     } while (0)
 
 // Event set of one job: [0] start, [1] scores, [2] up-zeta, [3] F, [4] R',
-// [5 + 2v] Gamma phase 1 of v, [6 + 2v] phase 2 of v, [5 + 2n] edges.
-constexpr int kEvents = 7 + 2 * 31;   // the last one ends the column sums of step 2
+// [5] Gamma phase 1, [6] Gamma phase 2, [7] edges, [8] the column sums of
+// step 2 (13-dimension tiles only).
+constexpr int kEvents = 9;
+constexpr int kEvEdges = 7, kEvSums = 8;
 struct Events {
     cudaEvent_t ev[kEvents] = {};
     bool ok = false;
@@ -197,7 +199,7 @@ struct Events {
             if (e) cudaEventDestroy(e);
         ok = false;
     }
-    cudaEvent_t last() const { return ev[5 + 2 * P.n]; }
+    cudaEvent_t last() const { return ev[kEvEdges]; }
 };
 
 struct Bufs {
@@ -282,25 +284,22 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     if (ev) CK(cudaEventRecord(ev->ev[1], s));
     CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), B.at<void>(L.lbs), B.at<void>(L.tab),
                          B.at<uint16_t>(L.rk13), B.at<void>(L.A), s,
-                         ev && bn::use_tile13_up(P) ? ev->ev[kEvents - 1] : nullptr));
+                         ev && bn::use_tile13_up(P) ? ev->ev[kEvSums] : nullptr));
     nl += bn::use_tile13_up(P) ? 3 : 1;
     if (ev) CK(cudaEventRecord(ev->ev[2], s));
     CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
     if (ev) CK(cudaEventRecord(ev->ev[3], s));
     CK(bn::launch_backward(P, B.at<void>(L.A), B.at<void>(L.Rc), s, &nl));
     if (ev) CK(cudaEventRecord(ev->ev[4], s));
-    const size_t es = P.prec == 0 ? 8 : 4;
-    for (int v = 0; v < P.n; ++v) {
-        CK(bn::launch_gamma_p1(P, v, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
-                               B.at<void>(L.W), s));
-        if (ev) CK(cudaEventRecord(ev->ev[5 + 2 * v], s));
-        CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<char>(L.Gam) + (size_t)v * P.K * es, s));
-        if (ev) CK(cudaEventRecord(ev->ev[6 + 2 * v], s));
-        nl += 2;
-    }
+    CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
+                           B.at<void>(L.W), s));
+    if (ev) CK(cudaEventRecord(ev->ev[5], s));
+    CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
+    if (ev) CK(cudaEventRecord(ev->ev[6], s));
+    nl += 2;
     CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
                         B.at<void>(L.Gam), B.at<void>(L.F), err, post_dev, logPD_dev, s)); ++nl;
-    if (ev) CK(cudaEventRecord(ev->ev[5 + 2 * P.n], s));
+    if (ev) CK(cudaEventRecord(ev->ev[kEvEdges], s));
     if (launches) *launches = nl;
     if (ev) {
         ev->P = P;
@@ -329,15 +328,13 @@ void fill_stats(const Plan& P, Events& ev, int launches, bn_stats* st)
     };
     st->ms_scores = el(0, 1);
     st->ms_upzeta = el(1, 2);
-    st->ms_upzeta_sums = bn::use_tile13_up(P) ? el(1, kEvents - 1) : 0.0;
+    st->ms_upzeta_sums = bn::use_tile13_up(P) ? el(1, kEvSums) : 0.0;
     st->ms_forward = el(2, 3);
     st->ms_backward = el(3, 4);
-    for (int v = 0; v < P.n; ++v) {
-        st->ms_gamma_p1 += el(v == 0 ? 4 : 4 + 2 * v, 5 + 2 * v);
-        st->ms_gamma_p2 += el(5 + 2 * v, 6 + 2 * v);
-    }
-    st->ms_edges = el(4 + 2 * P.n, 5 + 2 * P.n);
-    st->ms_total = el(0, 5 + 2 * P.n);
+    st->ms_gamma_p1 = el(4, 5);
+    st->ms_gamma_p2 = el(5, 6);
+    st->ms_edges = el(6, kEvEdges);
+    st->ms_total = el(0, kEvEdges);
     st->cells = (double)P.n * std::ldexp(1.0, P.n);
     st->alg_bytes = alg_bytes(P);
     st->kernels = launches;
@@ -865,12 +862,9 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
         CK(bn::launch_backward(G, at(L.A), at(L.Rc), s, nullptr));
     }
     if (stages & 8u) {
-        const size_t es = G.prec == 0 ? 8 : 4;
-        for (int v = 0; v < G.n; ++v) {
-            CK(bn::launch_gamma_p1(G, v, at(L.F), at(L.Rc),
-                                   reinterpret_cast<const uint16_t*>(at(L.rk13)), at(L.W), s));
-            CK(bn::launch_gamma_p2(G, at(L.W), at(L.Gam) + (size_t)v * G.K * es, s));
-        }
+        CK(bn::launch_gamma_p1(G, at(L.F), at(L.Rc), reinterpret_cast<const uint16_t*>(at(L.rk13)),
+                               at(L.W), s));
+        CK(bn::launch_gamma_p2(G, at(L.W), at(L.Gam), s));
     }
     if (stages & 16u)
         CK(bn::launch_edges(G, reinterpret_cast<const double*>(at(L.logB)),

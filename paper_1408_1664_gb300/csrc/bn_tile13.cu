@@ -654,14 +654,15 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 // ===========================================================================
 template <typename T>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
-k_gamma13_p1(int n, int d, int v, uint32_t nlow, const T* __restrict__ F,
+k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W,
              size_t js)
 {
+    const int v = blockIdx.z;                       // endpoint: one slice of W each
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
     rank13 = job_ptr(rank13, js);
-    W = job_ptr(W, js);
+    W = job_ptr(W, js) + (size_t)v * gridDim.x * nlow;
     using Lg = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
@@ -825,17 +826,17 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
     return cudaGetLastError();
 }
 
-cudaError_t launch_gamma13_p1(const Plan& P, int v, const void* F, const void* Rc,
+cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
                               const uint16_t* rank13, void* W, cudaStream_t s)
 {
     const int h = P.n - 1 - TB;
     const size_t sm = gamma13_smem_bytes(P);
-    const dim3 grid(1u << h, P.nj);
+    const dim3 grid(1u << h, P.nj, P.n);
     if (P.prec == 0)
-        k_gamma13_p1<double><<<grid, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const double*)F,
+        k_gamma13_p1<double><<<grid, TT, sm, s>>>(P.n, P.d, P.nlow_g, (const double*)F,
                                                    (const double*)Rc, rank13, (double*)W, P.js);
     else
-        k_gamma13_p1<float><<<grid, TT, sm, s>>>(P.n, P.d, v, P.nlow_g, (const float*)F,
+        k_gamma13_p1<float><<<grid, TT, sm, s>>>(P.n, P.d, P.nlow_g, (const float*)F,
                                                   (const float*)Rc, rank13, (float*)W, P.js);
     return cudaGetLastError();
 }
