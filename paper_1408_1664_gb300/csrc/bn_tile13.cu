@@ -81,12 +81,18 @@ __device__ __forceinline__ void bfly_max(T (&v)[TR], int k0, int nk)
     }
 }
 
-// Sum butterflies on values held relative to their own scales m (the final
-// max-plus transform): the partner is scaled by exp(m(partner) - m(self)).
-template <bool UP, typename T>
-__device__ __forceinline__ void bfly_scaled(T (&x)[TR], const T (&m)[TR], int k0, int nk)
+// 2^e for an integer e <= 0, built in the exponent bits (0 below 2^-126).
+__device__ __forceinline__ float pow2i(int e)
 {
-    using Lg = LogOps<T>;
+    return __int_as_float(max(e + 127, 0) << 23);
+}
+
+// FP32 sum butterflies on values held relative to their own integer scales
+// (the bits of `m` are ints: floor of the final max-plus transform): the
+// partner is scaled by the exact power of two 2^(m(partner) - m(self)) <= 1.
+template <bool UP>
+__device__ __forceinline__ void bfly_pow2(float (&x)[TR], const float (&m)[TR], int k0, int nk)
+{
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         if (k < k0 || k >= k0 + nk) continue;
@@ -94,8 +100,9 @@ __device__ __forceinline__ void bfly_scaled(T (&x)[TR], const T (&m)[TR], int k0
         for (int r = 0; r < TR; ++r) {
             if (r & (1 << k)) continue;
             const int s = r | (1 << k);
-            if (UP) x[s] = madd(x[r], Lg::ex(m[r] - m[s]), x[s]);
-            else x[r] = madd(x[s], Lg::ex(m[s] - m[r]), x[r]);
+            const int mr = __float_as_int(m[r]), ms = __float_as_int(m[s]);
+            if (UP) x[s] = madd(x[r], pow2i(mr - ms), x[s]);
+            else x[r] = madd(x[s], pow2i(ms - mr), x[r]);
         }
     }
 }
@@ -159,14 +166,24 @@ __device__ __forceinline__ void bfly_sum(T (&x)[TR], const T (&e)[TR], int k0, i
 template <bool UP>
 __device__ __forceinline__ void sum_bfly(float (&x)[TR], const float (&m)[TR], int k0, int nk)
 {
-    bfly_scaled<UP>(x, m, k0, nk);
+    bfly_pow2<UP>(x, m, k0, nk);
 }
 template <bool UP>
 __device__ __forceinline__ void sum_bfly(double (&x)[TR], const double (&e)[TR], int k0, int nk)
 {
     bfly_sum<UP>(x, e, k0, nk);
 }
-__device__ __forceinline__ float scaled_log(float y, float m) { return m + LogOps<float>::lg(y); }
+// Scale of an output from its max-plus value, the log that the scale stands
+// for, and an output's log from its scaled value.  FP32: an integer (kept as
+// the bits of a float); FP64: a band of BW nats.
+__device__ __forceinline__ float scale_of(float m) { return __int_as_float(__float2int_rd(m)); }
+__device__ __forceinline__ double scale_of(double m) { return floor(m / Band64::width); }
+__device__ __forceinline__ float scale_base(float sc) { return (float)__float_as_int(sc); }
+__device__ __forceinline__ double scale_base(double sc) { return Band64::width * sc; }
+__device__ __forceinline__ float scaled_log(float y, float sc)
+{
+    return scale_base(sc) + LogOps<float>::lg(y);
+}
 __device__ __forceinline__ double scaled_log(double x, double e)
 {
     return madd(Band64::width, e, LogOps<double>::lg(x));
@@ -278,23 +295,20 @@ template <> __device__ __forceinline__ void st3<float>(float* a, const float (&v
 // The exact sum pass after the max-plus pass.  On entry v holds m (layout
 // 3); A1 holds the transform's inputs (for UP only the slots with at most d
 // elements are inputs).  On exit v and sc hold, in layout 1, each output as
-// scaled_log(v, sc): FP32 keeps y relative to its own scale m, FP64 keeps x
-// in its band.
+// scaled_log(v, sc): FP32 keeps y relative to 2^floor(m), FP64 keeps x in
+// its band.
 template <bool UP, typename T>
 __device__ __forceinline__ void sum_pass(T (&v)[TR], T (&sc)[TR], const T* A1, T* A0, T* E,
                                          int t, int d)
 {
     using Lg = LogOps<T>;
 #pragma unroll
-    for (int r = 0; r < TR; ++r)
-        sc[r] = sizeof(T) == 4 ? v[r] : floor(v[r] / T(Band64::width));
+    for (int r = 0; r < TR; ++r) sc[r] = scale_of(v[r]);
     st3(E, sc, t);                        // scales, read again in layouts 2 and 1
     ld3(A1, v, t);
 #pragma unroll
-    for (int r = 0; r < TR; ++r) {
-        const T base = sizeof(T) == 4 ? sc[r] : T(Band64::width) * sc[r];
-        v[r] = (!UP || __popc(el3(r, t)) <= d) ? Lg::ex(v[r] - base) : T(0);
-    }
+    for (int r = 0; r < TR; ++r)
+        v[r] = (!UP || __popc(el3(r, t)) <= d) ? Lg::ex(v[r] - scale_base(sc[r])) : T(0);
     sum_bfly<UP>(v, sc, 0, 3);
     __syncthreads();
     st3(A0, v, t);
