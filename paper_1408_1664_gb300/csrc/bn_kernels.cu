@@ -173,6 +173,100 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
     (void)d;
 }
 
+// Scores with one thread per family, for binary data (every arity 2) and at
+// most 4 parents: at most 16 parent configurations and 32 cells.  Word by
+// word the thread builds the masks of all 16 configurations as a product
+// tree of the parent planes (configuration index: digit t = value of parent
+// t, parent 0 least significant; a missing parent t >= |G| contributes the
+// planes (all ones, none), so the configurations with digit 1 there stay
+// empty), counts every cell with popc, and adds the BDeu terms in FP64 in
+// the order (configuration, child value).  Empty cells add
+// lgamma(a) - lgamma(a) = 0 exactly, so the padding changes nothing.
+// The bit planes (n * 2 * W words) stay in L1.
+__global__ void __launch_bounds__(128)
+k_scores_bin(int n, int m, int W, int64_t K, const uint64_t* __restrict__ planes,
+             const double* __restrict__ Dvals, int rows, const double* __restrict__ T,
+             const double* __restrict__ log_rho, int64_t x_begin, int64_t x_count,
+             uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
+             double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+{
+    __shared__ uint32_t bt[32][5];                  // C(a, b), b <= 4, for the unrank
+    for (int e = threadIdx.x; e < 32 * 5; e += blockDim.x) bt[e / 5][e % 5] = binom(e / 5, e % 5);
+    __syncthreads();
+    const int64_t xi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (xi >= x_count) return;
+    const int64_t x = x_begin + xi;
+    const int i = (int)(x / K);
+    uint32_t f = (uint32_t)(x % K);
+    int k = 0;
+    while (f >= bt[n - 1][k]) { f -= bt[n - 1][k]; ++k; }
+    uint32_t cm = 0;                                // colex unrank of f among k-subsets
+    {
+        int c = n - 2;
+        for (int t = k; t >= 1; --t) {
+            while (bt[c][t] > f) --c;
+            cm |= 1u << c;
+            f -= bt[c][t];
+            --c;
+        }
+    }
+    const uint32_t G = expand(cm, i);
+    int par[4];
+    {
+        uint32_t g = G;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            par[t] = g ? __ffs(g) - 1 : -1;
+            g &= g - 1;
+        }
+    }
+    uint32_t cnt[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) cnt[c] = 0;
+    for (int w = 0; w < W; ++w) {
+        uint64_t E[16];
+        E[0] = ~0ull;
+#pragma unroll
+        for (int t = 3; t >= 0; --t) {              // most significant digit first
+            const uint64_t p0 = par[t] >= 0 ? planes[((size_t)par[t] * 2) * W + w] : ~0ull;
+            const uint64_t p1 = par[t] >= 0 ? planes[((size_t)par[t] * 2 + 1) * W + w] : 0ull;
+            const int size = 1 << (3 - t);
+#pragma unroll
+            for (int j = size - 1; j >= 0; --j) {
+                const uint64_t e = E[j];
+                E[2 * j] = e & p0;
+                E[2 * j + 1] = e & p1;
+            }
+        }
+        const uint64_t c0 = planes[((size_t)i * 2) * W + w];
+        const uint64_t c1 = planes[((size_t)i * 2 + 1) * W + w];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            cnt[2 * j] += (uint32_t)__popcll(E[j] & c0);
+            cnt[2 * j + 1] += (uint32_t)__popcll(E[j] & c1);
+        }
+    }
+    const double q = (double)(1 << k);
+    const double* Tq = T + (size_t)find_row(Dvals, rows, q) * (m + 1);
+    const double* Tqr = T + (size_t)find_row(Dvals, rows, 2.0 * q) * (m + 1);
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        acc -= Tq[cnt[2 * j] + cnt[2 * j + 1]];
+        acc += Tqr[cnt[2 * j]];
+        acc += Tqr[cnt[2 * j + 1]];
+    }
+    if (debug_counts) {
+        const int cells = 2 << k;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            if (c < cells) debug_counts[c] = cnt[c];
+    }
+    logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+    masks[x] = G;
+    cmasks[x] = cm;
+}
+
 // Scores with one warp per family and one lane per 64-sample word (m <= 2048):
 // every lane keeps its word of each parent plane and child plane in
 // registers, so a cell costs an AND chain, a popc and one warp reduction.
@@ -850,6 +944,12 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
     const int threads = 256;
     const int64_t warps_wanted = x_count;
     int grid = grid_for(warps_wanted * 32, threads, 152 * 64);
+    if (P.allbin && P.d <= 4) {
+        k_scores_bin<<<(unsigned)((x_count + 127) / 128), 128, 0, s>>>(
+            P.n, P.m, P.W, P.K, planes, Dvals, P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
+            logB, debug_counts);
+        return cudaGetLastError();
+    }
     if (P.W <= 32 && P.d <= 4 && P.rmax <= 2)
         k_scores_w<4, 2><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,

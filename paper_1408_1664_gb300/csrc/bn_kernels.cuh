@@ -19,6 +19,7 @@ struct Plan {
     uint32_t nlow_g;      // subsets of b_g dims with at most d elements
     int wb;               // in-warp bits of the F / R' tiles
     int prec;             // 0 = FP64, 1 = FP32
+    int allbin = 0;       // every variable has arity 2
     // Schedule (set by the planner, changed by the batch autotuner):
     int up13 = 0;         // step 2 by the 13-dimension tiles (n >= 14)
     int g13 = 0;          // step 4 phase 1 by the 13-dimension tiles (n >= 14)

@@ -154,6 +154,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     for (int k = 0; k <= P.d; ++k) P.K += binom64(P.n - 1, k);
     P.W = P.m > 0 ? (P.m + 63) / 64 : 1;
     P.rmax = (int)sorted[0];
+    P.allbin = sorted[0] == 2 && sorted[P.n - 1] == 2;
     double tables[2 * kMaxRows];                        // Dvals | alpha
     const int rows = denominators(arity, P.n, P.d, tables);
     if (rows < 0) return BN_ENOMEM;

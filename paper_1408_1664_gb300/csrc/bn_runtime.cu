@@ -155,6 +155,7 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
     P.K = families(P.n, P.d);
     P.W = std::max(1, (P.m + 63) / 64);
     P.rmax = (int)sorted[0];
+    P.allbin = sorted[0] == 2 && sorted[P.n - 1] == 2;
     hj.Dvals = denominators(hj.arity, P.d);
     if (hj.Dvals.size() > 16384) return BN_EINVAL;
     P.rows = (int)hj.Dvals.size();

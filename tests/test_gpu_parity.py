@@ -40,7 +40,7 @@ def _ds(n, m, arity, d, alpha=1.0, seed=0):
 
 @pytest.mark.parametrize("n,m,arity,seed", [
     (6, 200, 2, 1), (7, 3000, 3, 2), (8, 130, [2, 3, 4, 2, 5, 3, 2, 2], 3), (5, 64, 2, 4),
-    (5, 1, 3, 5)])
+    (5, 1, 3, 5), (9, 2000, 2, 6)])
 def test_counts_bit_exact(ctx, n, m, arity, seed):
     ds = _ds(n, m, arity, 3, seed=seed)
     d = min(3, n - 1)
