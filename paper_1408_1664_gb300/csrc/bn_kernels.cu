@@ -830,75 +830,91 @@ k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, int64_t K, const T* __res
 }
 
 // ===========================================================================
-// Step 5: log P(u->v, D) = log sum_{G: u in G} B_v(G) Gamma_v(G)  (Eq. 11)
-// and P(u->v | D) = P(u->v, D) / P(D).  One block per endpoint v, FP64.
-// P(D) is F(V) on the FP64 path (Algorithm 1) and sum_G B_v(G) Gamma_v(G) on
-// the FP32 path (the same quantity, Eq. 11 summed over all G, computed from
-// the same Gamma_v so that rounding common to numerator and denominator
-// cancels).  Block 0 also writes log P(D) = F~(V) + sum_i c_i.
+// Step 5: P(u->v, D) = sum_{G: u in G} B_v(G) Gamma_v(G)  (Eq. 11) and
+// P(u->v | D) = P(u->v, D) / P(D), in FP64, in three launches.
+// Every term B_v(G) Gamma_v(G) is at most their sum over G, which is F(V)
+// (Eq. 11 summed over all G), so e(G) = B_v(G) Gamma_v(G) / F(V) <= 1 (up to
+// rounding) needs no maximum pass.  Blocks over (families of v, v) add e(G)
+// in fixed point (2^qbits, integer atomics: the sums do not depend on the
+// order of arrival) into acc[v*n + u] for every u in G and into acc[n*n + v]
+// for all G.  The FP64 path divides by F(V) (Algorithm 1), i.e. takes
+// acc[v*n + u] / 2^qbits; the FP32 path divides by Z_v = acc[n*n + v]
+// (the same quantity from the same Gamma_v, so rounding common to numerator
+// and denominator cancels).  log P(D) = F~(V) + sum_i c_i.
 // ===========================================================================
+__global__ void k_edges_zero(int n, unsigned long long* __restrict__ acc, size_t js)
+{
+    acc = job_ptr(acc, js);
+    for (int t = threadIdx.x; t < n * (n + 1); t += blockDim.x) acc[t] = 0ull;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_edges(int n, int64_t K, int use_z, int qbits, const double* __restrict__ logB,
-        const double* __restrict__ cmax, const uint32_t* __restrict__ masks,
-        const T* __restrict__ Gam, const T* __restrict__ F, const int* __restrict__ err,
-        double* __restrict__ post, double* __restrict__ log_PD, size_t js)
+k_edges_acc(int n, int64_t K, int qbits, const double* __restrict__ logB,
+            const double* __restrict__ cmax, const uint32_t* __restrict__ masks,
+            const T* __restrict__ Gam, const T* __restrict__ F,
+            unsigned long long* __restrict__ acc, size_t js)
 {
     logB = job_ptr(logB, js);
     cmax = job_ptr(cmax, js);
     masks = job_ptr(masks, js);
     Gam = job_ptr(Gam, js);
     F = job_ptr(F, js);
-    err = job_ptr(err, js);
-    post = job_ptr(post, js);
-    log_PD = job_ptr(log_PD, js);
+    acc = job_ptr(acc, js);
     using L = LogOps<T>;
-    __shared__ unsigned long long Nu[32];
-    __shared__ double red[32];
-    const double qscale = ldexp(1.0, qbits);
-    const int v = blockIdx.x;
+    __shared__ unsigned long long Nu[32], Nz;
+    const int v = blockIdx.z;
     const int tid = threadIdx.x;
-    const int nw = blockDim.x >> 5;
     if (tid < 32) Nu[tid] = 0ull;
+    if (tid == 0) Nz = 0ull;
+    __syncthreads();
     const uint32_t full = (1u << n) - 1u;
     const double lnFV = L::to_ln((double)F[full]);
-    double mx = -INFINITY;
-    for (int64_t f = tid; f < K; f += blockDim.x) {
+    const double qscale = ldexp(1.0, qbits);
+    const double cv = cmax[v];
+    unsigned long long z = 0ull;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + tid; f < K;
+         f += (int64_t)gridDim.x * blockDim.x) {
         const size_t x = (size_t)v * K + f;
-        mx = fmax(mx, logB[x] - cmax[v] + L::to_ln((double)Gam[x]));
-    }
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
-    if ((tid & 31) == 0) red[tid >> 5] = mx;
-    __syncthreads();
-    mx = -INFINITY;
-    for (int w = 0; w < nw; ++w) mx = fmax(mx, red[w]);
-    __syncthreads();
-    double z = 0.0;
-    for (int64_t f = tid; f < K; f += blockDim.x) {
-        const size_t x = (size_t)v * K + f;
-        const double e = exp(logB[x] - cmax[v] + L::to_ln((double)Gam[x]) - mx);
-        z += e;
-        // e <= 1; fixed point keeps the per-u sums independent of arrival order
+        const double e = exp(logB[x] - cv + L::to_ln((double)Gam[x]) - lnFV);
         const unsigned long long q = __double2ull_rn(e * qscale);
+        z += q;
         for (uint32_t g = masks[x]; g; g &= g - 1) atomicAdd(&Nu[__ffs(g) - 1], q);
     }
-    z = warp_sum(z);
-    if ((tid & 31) == 0) red[tid >> 5] = z;
+    for (int o = 16; o; o >>= 1) z += __shfl_xor_sync(FULL, z, o);
+    if ((tid & 31) == 0) atomicAdd(&Nz, z);
     __syncthreads();
-    z = 0.0;
-    for (int w = 0; w < nw; ++w) z += red[w];
-    const double lognorm = use_z ? mx + log(z) : lnFV;
+    if (tid < n && Nu[tid]) atomicAdd(&acc[(size_t)v * n + tid], Nu[tid]);
+    if (tid == 0) atomicAdd(&acc[(size_t)n * n + v], Nz);
+}
+
+template <typename T>
+__global__ void k_edges_fin(int n, int use_z, int qbits, const double* __restrict__ cmax,
+                            const T* __restrict__ F, const int* __restrict__ err,
+                            const unsigned long long* __restrict__ acc,
+                            double* __restrict__ post, double* __restrict__ log_PD, size_t js)
+{
+    cmax = job_ptr(cmax, js);
+    F = job_ptr(F, js);
+    err = job_ptr(err, js);
+    acc = job_ptr(acc, js);
+    post = job_ptr(post, js);
+    log_PD = job_ptr(log_PD, js);
     const bool bad = err && *err;
-    for (int u = tid; u < n; u += blockDim.x) {
+    const double qscale = ldexp(1.0, qbits);
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int u = t / n, v = t % n;
+        const unsigned long long num = acc[(size_t)v * n + u];
         double p = 0.0;
-        if (u != v && Nu[u] > 0ull)
-            p = exp(mx + log(__ull2double_rn(Nu[u]) / qscale) - lognorm);
-        post[(size_t)u * n + v] = bad ? NAN : p;
+        if (u != v && num > 0ull)
+            p = use_z ? __ull2double_rn(num) / __ull2double_rn(acc[(size_t)n * n + v])
+                      : __ull2double_rn(num) / qscale;
+        post[t] = bad ? NAN : p;
     }
-    if (v == 0 && tid == 0 && log_PD) {
+    if (threadIdx.x == 0 && log_PD) {
         double c = 0.0;
         for (int i = 0; i < n; ++i) c += cmax[i];
-        *log_PD = bad ? NAN : lnFV + c;
+        *log_PD = bad ? NAN : LogOps<T>::to_ln((double)F[(1u << n) - 1u]) + c;
     }
 }
 
@@ -1132,17 +1148,29 @@ cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_
 
 cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                          const uint32_t* masks, const void* Gam, const void* F, const int* err,
-                         double* post, double* log_PD, cudaStream_t s)
+                         unsigned long long* acc, double* post, double* log_PD, cudaStream_t s)
 {
-    const dim3 grid(P.n, P.nj);
+    k_edges_zero<<<dim3(1, P.nj), 256, 0, s>>>(P.n, acc, P.js);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned chunks = (unsigned)std::min<int64_t>((P.K + 1023) / 1024, 64);
+    const dim3 grid(chunks, P.nj, P.n);
     if (P.prec == 0)
-        k_edges<double><<<grid, 256, 0, s>>>(P.n, P.K, 0, fixed_bits(P.K), logB, cmax, masks,
-                                             (const double*)Gam,
-                                             (const double*)F, err, post, log_PD, P.js);
+        k_edges_acc<double><<<grid, 256, 0, s>>>(P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
+                                                 (const double*)Gam, (const double*)F, acc, P.js);
     else
-        k_edges<float><<<grid, 256, 0, s>>>(P.n, P.K, 1, fixed_bits(P.K), logB, cmax, masks,
-                                            (const float*)Gam,
-                                            (const float*)F, err, post, log_PD, P.js);
+        k_edges_acc<float><<<grid, 256, 0, s>>>(P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
+                                                (const float*)Gam, (const float*)F, acc, P.js);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (P.prec == 0)
+        k_edges_fin<double><<<dim3(1, P.nj), 1024, 0, s>>>(P.n, 0, fixed_bits(P.K), cmax,
+                                                           (const double*)F, err, acc, post,
+                                                           log_PD, P.js);
+    else
+        k_edges_fin<float><<<dim3(1, P.nj), 1024, 0, s>>>(P.n, 1, fixed_bits(P.K), cmax,
+                                                          (const float*)F, err, acc, post,
+                                                          log_PD, P.js);
     return cudaGetLastError();
 }
 

@@ -64,9 +64,11 @@ cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t
 cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
                             void* W, cudaStream_t s);
 cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s);
+// Step 5 (three launches); acc: n * (n + 1) scratch words.
 cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                          const uint32_t* masks, const void* Gam, const void* F,
-                         const int* err, double* post, double* log_PD, cudaStream_t s);
+                         const int* err, unsigned long long* acc, double* post, double* log_PD,
+                         cudaStream_t s);
 
 size_t upzeta_smem_bytes(const Plan& P);
 // bn_tile13.cu

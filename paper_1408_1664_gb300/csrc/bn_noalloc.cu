@@ -185,7 +185,8 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                  o_rk = take(bn::needs_rank13(P) ? bn::kRank13Bytes : 0),
                  o_A = take(((size_t)P.n << (P.n - 1)) * es), o_F = take(((size_t)1 << P.n) * es),
                  o_Rc = take(((size_t)1 << P.n) * es),
-                 o_W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es);
+                 o_W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es),
+                 o_ea = take((size_t)P.n * (P.n + 1) * 8);
     if (o > (size_t)BN_STATIC_SCRATCH_BYTES) return BN_ENOMEM;   // job too large
 
     int dev = 0;
@@ -229,7 +230,8 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     CKS(bn::launch_backward(P, base + o_A, base + o_Rc, s, nullptr));
     CKS(bn::launch_gamma_p1(P, base + o_F, base + o_Rc, rk13, base + o_W, s));
     CKS(bn::launch_gamma_p2(P, base + o_W, base + o_G, s));
-    CKS(bn::launch_edges(P, logB, cmax, masks, base + o_G, base + o_F, err, post_dev,
+    CKS(bn::launch_edges(P, logB, cmax, masks, base + o_G, base + o_F, err,
+                         reinterpret_cast<unsigned long long*>(base + o_ea), post_dev,
                          log_PD_dev, s));
 #undef CKS
     return BN_OK;

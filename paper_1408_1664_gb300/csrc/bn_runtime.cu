@@ -55,7 +55,7 @@ struct HostJob {
 // Byte offsets of every array of a job inside one device allocation.
 struct Layout {
     size_t data, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB, cmax, lbs,
-        tab, rk13, A, F, Rc, W, Gam, post, logPD, dbg, total;
+        tab, rk13, A, F, Rc, W, Gam, eacc, post, logPD, dbg, total;
 };
 
 Layout make_layout(const Plan& P, size_t dbg_cells)
@@ -87,6 +87,7 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     L.Rc = take(((size_t)1 << P.n) * es);
     L.W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es);   // one slice per endpoint
     L.Gam = take(nK * es);
+    L.eacc = take((size_t)P.n * (P.n + 1) * 8);
     L.post = take((size_t)P.n * P.n * 8);
     L.logPD = take(8);
     L.dbg = take(dbg_cells * 8);
@@ -299,7 +300,9 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     if (ev) CK(cudaEventRecord(ev->ev[6], s));
     nl += 2;
     CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
-                        B.at<void>(L.Gam), B.at<void>(L.F), err, post_dev, logPD_dev, s)); ++nl;
+                        B.at<void>(L.Gam), B.at<void>(L.F), err,
+                        B.at<unsigned long long>(L.eacc), post_dev, logPD_dev, s));
+    nl += 3;
     if (ev) CK(cudaEventRecord(ev->ev[kEvEdges], s));
     if (launches) *launches = nl;
     if (ev) {
@@ -872,6 +875,7 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
                             reinterpret_cast<const double*>(at(L.cmax)),
                             reinterpret_cast<const uint32_t*>(at(L.masks)), at(L.Gam), at(L.F),
                             reinterpret_cast<const int*>(at(L.err)),
+                            reinterpret_cast<unsigned long long*>(at(L.eacc)),
                             reinterpret_cast<double*>(at(L.post)),
                             reinterpret_cast<double*>(at(L.logPD)), s));
     return BN_OK;
