@@ -552,6 +552,104 @@ k_upzeta13_cols(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
     for (uint32_t c = ncopy + t; c < ncol; c += TT) out[c] = tb[c];
 }
 
+// Log-sum-exp kept lazily: (m, s) stands for m + log(s); s is rescaled only
+// when a term exceeds m by more than 64 log units, so a term costs one
+// exponential (the values are finite).
+template <typename T>
+__device__ __forceinline__ void lse_lazy(T& m, T& s, T x)
+{
+    using Lg = LogOps<T>;
+    const T dd = x - m;                           // +inf while the accumulator is empty
+    const bool big = dd > T(64);
+    const T e = Lg::ex(big ? -dd : dd);
+    s = big ? madd(s, e, T(1)) : s + e;
+    m = big ? x : m;
+}
+
+// Part 1 with one warp per tile: each warp enumerates its tile's rows into
+// its own list and sums the columns lane by lane (consecutive columns:
+// coalesced reads of a row); no block barrier after the tables are filled.
+// Columns with d low elements are copies, those with d - 1 take the 1 + |H|
+// rows of at most one high element, the others every row of size at most
+// d - |G_L|.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A, size_t js)
+{
+    tab = job_ptr(tab, js);
+    A = job_ptr(A, js);
+    using Lg = LogOps<T>;
+    __shared__ SBinom sb;
+    __shared__ uint32_t off13[16];
+    __shared__ uint32_t rowoff_k[32];            // offset of the first size-k row in a node's table
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int h = n - 1 - TB;
+    const uint32_t nrow = num_small_subsets(h, d);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* rowbase = reinterpret_cast<uint32_t*>(smem_raw) + (size_t)warp * nrow;
+    fill_sbinom(sb);
+    if (threadIdx.x < 16) {
+        uint32_t o = 0;
+        for (int k = 0; k < (int)threadIdx.x && k <= TB; ++k) o += binom(TB, k);
+        off13[threadIdx.x] = o;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t o = 0;
+        for (int k = 0; k < (int)threadIdx.x && k <= min(d, h); ++k)
+            o += binom(h, k) * off13[min(d - k, TB) + 1];
+        rowoff_k[threadIdx.x] = o;
+    }
+    __syncthreads();
+    const uint32_t ncol = num_small_subsets(TB, d);
+    const uint32_t nlong = d >= 2 ? off13[min(d - 2, TB) + 1] : 0u;
+    const uint32_t ncopy = off13[min(d, TB + 1)];
+    const uint32_t ntiles = (uint32_t)n << h;
+    const uint32_t wpb = blockDim.x >> 5;
+    for (uint32_t tile = blockIdx.x * wpb + warp; tile < ntiles; tile += gridDim.x * wpb) {
+        const int i = (int)(tile >> h);
+        const uint32_t H = tile & ((1u << h) - 1u);
+        const T* tb = tab + (size_t)i * K;
+        T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
+        const int hc = __popc(H);
+        uint32_t total = 0;                      // rows of size <= d inside H
+        for (int k = 0; k <= d && k <= hc; ++k) total += sb_binom(sb, hc, k);
+        for (uint32_t p = lane; p < total; p += 32) {
+            int k;
+            const uint32_t loc = sb_unrank(sb, p, hc, &k);
+            uint32_t rk = 0, hh = H;
+            int q = 0, idx = 1;
+            while (hh) {
+                const int b = __ffs(hh) - 1;
+                hh &= hh - 1;
+                if (loc >> q & 1u) rk += sb_binom(sb, b, idx++);
+                ++q;
+            }
+            rowbase[p] = rowoff_k[k] + rk * off13[min(d - k, TB) + 1];
+        }
+        __syncwarp();
+        for (uint32_t c = lane; c < nlong; c += 32) {          // at most d - 2 low elements
+            int j = 0;
+            while (off13[j + 1] <= c) ++j;
+            uint32_t rend = 0;
+            for (int k = 0; k <= d - j && k <= hc; ++k) rend += sb_binom(sb, hc, k);
+            T m = Lg::ninf(), s = T(0);
+#pragma unroll 4
+            for (uint32_t rp = 0; rp < rend; ++rp) lse_lazy(m, s, tb[rowbase[rp] + c]);
+            out[c] = m + Lg::lg(s);
+        }
+        const uint32_t rmid = 1u + (uint32_t)hc;               // d - 1 low elements
+        for (uint32_t c = nlong + lane; c < ncopy; c += 32) {
+            T m = Lg::ninf(), s = T(0);
+#pragma unroll 4
+            for (uint32_t rp = 0; rp < rmid; ++rp) lse_lazy(m, s, tb[rowbase[rp] + c]);
+            out[c] = m + Lg::lg(s);
+        }
+        for (uint32_t c = ncopy + lane; c < ncol; c += 32) out[c] = tb[c];   // d low elements
+        __syncwarp();                                          // rowbase is reused
+    }
+}
+
 // ===========================================================================
 // Step 2 for n >= 14, part 2: one block per tile (i, H) of A_i.  The column
 // sums of part 1 are placed at their low patterns (every other slot holds
@@ -821,7 +919,19 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
     const int h = P.n - 1 - TB;
     const dim3 grid((unsigned)P.n << h, P.nj);
     const size_t sc = upzeta13_cols_smem_bytes(P), sm = upzeta13_smem_bytes(P);
-    if (P.prec == 0)
+    uint64_t nrow = 0;
+    for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
+    if (nrow * 4 * 8 <= 160 * 1024) {                 // warp per tile, 8 tiles per block
+        const uint64_t ntiles = (uint64_t)P.n << h;
+        const dim3 gw((unsigned)std::min<uint64_t>((ntiles + 7) / 8, 152 * 16), P.nj);
+        const size_t sw = (size_t)nrow * 4 * 8;
+        if (P.prec == 0)
+            k_upzeta13_colw<double><<<gw, 256, sw, s>>>(P.n, P.d, P.K, (const double*)tab,
+                                                        (double*)A, P.js);
+        else
+            k_upzeta13_colw<float><<<gw, 256, sw, s>>>(P.n, P.d, P.K, (const float*)tab,
+                                                       (float*)A, P.js);
+    } else if (P.prec == 0)
         k_upzeta13_cols<double><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const double*)tab, (double*)A,
                                                      P.js);
     else
@@ -863,6 +973,8 @@ cudaError_t set_tile13_attributes()
     if (e != cudaSuccess) return e;
     SETA(k_upzeta13_cols<double>)
     SETA(k_upzeta13_cols<float>)
+    SETA(k_upzeta13_colw<double>)
+    SETA(k_upzeta13_colw<float>)
     SETA(k_upzeta13<double>)
     SETA(k_upzeta13<float>)
     SETA(k_gamma13_p1<double>)
