@@ -829,6 +829,104 @@ k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, int64_t K, const T* __res
     }
 }
 
+// Family index of the mask cm over the n-1 bits of V - {v}: by size, then
+// colexicographic rank (the canonical order of the scores).
+__device__ __forceinline__ uint32_t family_index(uint32_t cm, int n)
+{
+    const int k = __popc(cm);
+    uint32_t f = 0;
+    for (int s = 0; s < k; ++s) f += binom(n - 1, s);
+    int t = 1;
+    for (uint32_t x = cm; x; x &= x - 1, ++t) f += binom(__ffs(x) - 1, t);
+    return f;
+}
+
+// Lazy log-sum-exp step (one exponential per term): (m, s) is m + log(s).
+template <typename T>
+__device__ __forceinline__ void lse_lazy_k(T& m, T& s, T x)
+{
+    using L = LogOps<T>;
+    const T dd = x - m;                             // +inf while empty
+    const bool big = dd > T(64);
+    const T e = L::ex(big ? -dd : dd);
+    s = big ? s * e + T(1) : s + e;
+    m = big ? x : m;
+}
+
+// Warp-wide log-sum of the lanes' (m, s), in a fixed tree order.
+template <typename T>
+__device__ __forceinline__ T warp_lse(T m, T s)
+{
+    using L = LogOps<T>;
+    for (int o = 16; o; o >>= 1) {
+        const T m2 = __shfl_xor_sync(FULL, m, o);
+        const T s2 = __shfl_xor_sync(FULL, s, o);
+        const T mn = m2 > m ? m2 : m;
+        if (mn != L::ninf()) {
+            s = s * L::ex(m - mn) + s2 * L::ex(m2 - mn);
+            m = mn;
+        }
+    }
+    return m + L::lg(s);
+}
+
+// Phase 2 for the columns whose low pattern g has at least d - 1 elements
+// (d' = d - |g| <= 1, at most one high element left): the outputs are
+// Gamma(g) = log-sum of W[H][g] over every H and, for d' = 1, Gamma(g + {b})
+// = log-sum over the H that contain b, for every high bit b -- the truncated
+// transform over the high dimensions, written out.  One warp per column,
+// eight consecutive columns per block (they share the sectors of W's rows).
+// Lane l takes the rows H = l + 32k: high bits 0-4 are its lane bits, the
+// bits from 5 up are summed per lane.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gamma_p2s(int n, int d, int b, uint32_t nlow, uint32_t c0, int64_t K, const T* __restrict__ W,
+            T* __restrict__ Gam, size_t js)
+{
+    constexpr int MB = 13;                          // high bits from 5 up (h <= 17)
+    const int v = blockIdx.z;
+    W = job_ptr(W, js) + ((size_t)v << (n - 1 - b)) * nlow;
+    Gam = job_ptr(Gam, js) + (size_t)v * K;
+    using L = LogOps<T>;
+    const int h = n - 1 - b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t col = c0 + blockIdx.x * 8 + warp;
+    if (col >= nlow) return;                        // whole warps leave
+    int kg = 0;
+    uint32_t r = col;
+    while (r >= binom(b, kg)) { r -= binom(b, kg); ++kg; }
+    const uint32_t g = colex_unrank(r, kg, b);
+    const bool one = d - kg == 1;
+    T m0 = L::ninf(), s0 = T(0);
+    T mb[MB], sb[MB];
+#pragma unroll
+    for (int q = 0; q < MB; ++q) { mb[q] = L::ninf(); sb[q] = T(0); }
+    const uint32_t nH = 1u << h;
+    for (uint32_t H = lane; H < nH; H += 32) {
+        const T w = W[(size_t)H * nlow + col];
+        lse_lazy_k(m0, s0, w);
+        if (one) {
+#pragma unroll
+            for (int q = 0; q < MB; ++q)
+                if (5 + q < h && (H >> (5 + q) & 1u)) lse_lazy_k(mb[q], sb[q], w);
+        }
+    }
+    const T all = warp_lse(m0, s0);
+    if (lane == 0) Gam[family_index(g, n)] = all;
+    if (!one) return;
+    for (int bb = 0; bb < h && bb < 5; ++bb) {
+        const bool in = lane >> bb & 1;
+        const T x = warp_lse(in ? m0 : L::ninf(), in ? s0 : T(0));
+        if (lane == 0) Gam[family_index(g | (1u << (b + bb)), n)] = x;
+    }
+#pragma unroll
+    for (int q = 0; q < MB; ++q) {
+        if (5 + q >= h) break;
+        const T x = warp_lse(mb[q], sb[q]);
+        if (lane == 0) Gam[family_index(g | (1u << (b + 5 + q)), n)] = x;
+    }
+}
+
 // ===========================================================================
 // Step 5: P(u->v, D) = sum_{G: u in G} B_v(G) Gamma_v(G)  (Eq. 11) and
 // P(u->v | D) = P(u->v, D) / P(D), in FP64, in three launches.
@@ -1135,14 +1233,33 @@ cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const 
 
 cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s)
 {
-    const size_t sm2 = gamma_p2_smem_bytes(P);
-    const dim3 grid(P.nlow_g, P.nj, P.n);
-    if (P.prec == 0)
-        k_gamma_p2<double><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
-                                                  (const double*)W, (double*)Gam, P.js);
-    else
-        k_gamma_p2<float><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
-                                                 (const float*)W, (float*)Gam, P.js);
+    // columns with at least d - 1 low elements: the warp kernel; the others
+    // (at least two high elements left): the block butterfly kernel
+    const int h = P.n - 1 - P.b_g;
+    uint32_t c0 = 0;
+    for (int k = 0; k <= P.d - 2 && k <= P.b_g; ++k) c0 += host_binom(P.b_g, k);
+    if (h > 17) c0 = P.nlow_g;                      // beyond the warp kernel's bit count
+    if (c0 > 0) {
+        const size_t sm2 = gamma_p2_smem_bytes(P);
+        const dim3 grid(c0, P.nj, P.n);
+        if (P.prec == 0)
+            k_gamma_p2<double><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
+                                                      (const double*)W, (double*)Gam, P.js);
+        else
+            k_gamma_p2<float><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
+                                                     (const float*)W, (float*)Gam, P.js);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (c0 < P.nlow_g) {
+        const dim3 grid((P.nlow_g - c0 + 7) / 8, P.nj, P.n);
+        if (P.prec == 0)
+            k_gamma_p2s<double><<<grid, 256, 0, s>>>(P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
+                                                     (const double*)W, (double*)Gam, P.js);
+        else
+            k_gamma_p2s<float><<<grid, 256, 0, s>>>(P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
+                                                    (const float*)W, (float*)Gam, P.js);
+    }
     return cudaGetLastError();
 }
 
