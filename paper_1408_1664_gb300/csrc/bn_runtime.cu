@@ -178,16 +178,40 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
         if (e_ != cudaSuccess) return BN_ECUDA;       \
     } while (0)
 
-// Event set of one job: [0] start, [1] scores, [2] up-zeta, [3] F, [4] R',
-// [5] Gamma phase 1, [6] Gamma phase 2, [7] edges, [8] the column sums of
-// step 2 (13-dimension tiles only).
-constexpr int kEvents = 9;
-constexpr int kEvEdges = 7, kEvSums = 8;
+// Event set of one job: [0] start, [1] scores, [2] up-zeta, [3] F, [4] F and
+// R' both done, [5] Gamma phase 1, [6] Gamma phase 2, [7] edges, [8] the
+// column sums of step 2 (13-dimension tiles only), [9] R' done.
+constexpr int kEvents = 10;
+constexpr int kEvEdges = 7, kEvSums = 8, kEvR = 9;
+
+// A second stream for the steps that may run beside the main one: F and R'
+// depend only on A, so R' runs on the side stream between a fork and a join.
+struct Side {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int create()
+    {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)
+            return BN_ECUDA;
+        return BN_OK;
+    }
+    void destroy()
+    {
+        if (s) cudaStreamDestroy(s);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        s = nullptr;
+        fork = join = nullptr;
+    }
+};
 struct Events {
     cudaEvent_t ev[kEvents] = {};
     bool ok = false;
     Plan P{};
     int launches = 0;
+    bool overlap = false;        // R' ran beside F
     int create()
     {
         for (auto& e : ev)
@@ -211,13 +235,14 @@ struct Bufs {
 };
 
 int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, double* post_dev,
-                    double* logPD_dev, cudaStream_t s, Events* ev, int* launches);
+                    double* logPD_dev, cudaStream_t s, Events* ev, int* launches,
+                    const Side* side = nullptr);
 
 // Enqueue steps 1-5 on stream s.  Small host arrays go through `stage`
 // (pinned, >= stage_bytes) when given, else through pageable copies.
 int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_dev,
             cudaStream_t s, Events* ev, int* launches, char* stage, size_t stage_bytes,
-            bool upload_tables = true)
+            bool upload_tables = true, const Side* side = nullptr)
 {
     const Plan& P = hj.P;
     const Layout& L = B.L;
@@ -256,12 +281,12 @@ int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_de
         CK(cudaMemcpyAsync(B.at<char>(L.Dvals), src + n_ar + n_lr, 2 * n_dv,
                            cudaMemcpyHostToDevice, s));
     }
-    return enqueue_kernels(hj, B, data_dev, post_dev, logPD_dev, s, ev, launches);
+    return enqueue_kernels(hj, B, data_dev, post_dev, logPD_dev, s, ev, launches, side);
 }
 
 // Enqueue the kernels of steps 1-5 on stream s (inputs already on the device).
 int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, double* post_dev,
-                    double* logPD_dev, cudaStream_t s, Events* ev, int* launches)
+                    double* logPD_dev, cudaStream_t s, Events* ev, int* launches, const Side* side)
 {
     const Plan& P = hj.P;
     const Layout& L = B.L;
@@ -289,10 +314,25 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
                          ev && bn::use_tile13_up(P) ? ev->ev[kEvSums] : nullptr));
     nl += bn::use_tile13_up(P) ? 3 : 1;
     if (ev) CK(cudaEventRecord(ev->ev[2], s));
-    CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
-    if (ev) CK(cudaEventRecord(ev->ev[3], s));
-    CK(bn::launch_backward(P, B.at<void>(L.A), B.at<void>(L.Rc), s, &nl));
-    if (ev) CK(cudaEventRecord(ev->ev[4], s));
+    if (side && side->s) {
+        CK(cudaEventRecord(side->fork, s));
+        CK(cudaStreamWaitEvent(side->s, side->fork, 0));
+        CK(bn::launch_backward(P, B.at<void>(L.A), B.at<void>(L.Rc), side->s, &nl));
+        if (ev) CK(cudaEventRecord(ev->ev[kEvR], side->s));
+        CK(cudaEventRecord(side->join, side->s));
+        CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
+        if (ev) CK(cudaEventRecord(ev->ev[3], s));
+        CK(cudaStreamWaitEvent(s, side->join, 0));
+    } else {
+        CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
+        if (ev) CK(cudaEventRecord(ev->ev[3], s));
+        CK(bn::launch_backward(P, B.at<void>(L.A), B.at<void>(L.Rc), s, &nl));
+        if (ev) CK(cudaEventRecord(ev->ev[kEvR], s));
+    }
+    if (ev) {
+        CK(cudaEventRecord(ev->ev[4], s));
+        ev->overlap = side && side->s;
+    }
     CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
                            B.at<void>(L.W), s));
     if (ev) CK(cudaEventRecord(ev->ev[5], s));
@@ -334,7 +374,7 @@ void fill_stats(const Plan& P, Events& ev, int launches, bn_stats* st)
     st->ms_upzeta = el(1, 2);
     st->ms_upzeta_sums = bn::use_tile13_up(P) ? el(1, kEvSums) : 0.0;
     st->ms_forward = el(2, 3);
-    st->ms_backward = el(3, 4);
+    st->ms_backward = ev.overlap ? el(2, kEvR) : el(3, kEvR);   // beside F: from the same start
     st->ms_gamma_p1 = el(4, 5);
     st->ms_gamma_p2 = el(5, 6);
     st->ms_edges = el(6, kEvEdges);
@@ -349,6 +389,7 @@ enum JobState { Q_QUEUED, Q_RUNNING, Q_DONE };
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    Side side;                   // R' beside F
     Events ev;
     cudaEvent_t done = nullptr;  // after the result copies
     char* dev = nullptr;         // allocation of the running job (stream-ordered)
@@ -378,6 +419,7 @@ struct bn_ctx {
     int fail_after = -1;
     int allocs = 0;
     cudaStream_t stream = nullptr;
+    Side side;                   // R' beside F on the direct path
     // direct path workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -424,6 +466,7 @@ struct bn_batch {
     std::vector<BatchGroup> groups;
     char* arena = nullptr;
     std::vector<cudaStream_t> streams;
+    std::vector<Side> sides;                 // R' beside F, one per branch
     std::vector<cudaEvent_t> joins;
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
@@ -513,7 +556,7 @@ int run_direct(bn_ctx* c, const bn_job_desc* job, HostJob& hj, double* post_dev,
     c->tables_sig.clear();
     rc = enqueue(hj, B, post_dev ? post_dev : B.at<double>(L.post),
                  logPD_dev ? logPD_dev : B.at<double>(L.logPD), s, &ev, &c->last_launches,
-                 c->pin, c->pin_bytes, upload);
+                 c->pin, c->pin_bytes, upload, &c->side);
     if (rc == BN_OK) {
         c->tables_sig = sig;
         c->ring_pos = (c->ring_pos + 1) % bn_ctx::kRing;
@@ -586,14 +629,16 @@ int bn_ctx_create(bn_ctx** out, const bn_ctx_opts* o)
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->budget = opts.mem_budget ? opts.mem_budget : (uint64_t)(0.9 * (double)fr);
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete c;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        c->side.create() != BN_OK) {
+        bn_ctx_destroy(c);
         return BN_ECUDA;
     }
     c->slots.resize(opts.slots);
     for (auto& sl : c->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            sl.ev.create() != BN_OK || cudaEventCreate(&sl.done) != cudaSuccess) {
+            sl.ev.create() != BN_OK || cudaEventCreate(&sl.done) != cudaSuccess ||
+            sl.side.create() != BN_OK) {
             bn_ctx_destroy(c);
             return BN_ECUDA;
         }
@@ -617,12 +662,14 @@ int bn_ctx_destroy(bn_ctx* c)
         if (sl.dev) cudaFree(sl.dev);
         if (sl.pin) cudaFreeHost(sl.pin);
         sl.ev.destroy();
+        sl.side.destroy();
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     if (c->ws) cudaFree(c->ws);
     if (c->pin) cudaFreeHost(c->pin);
     for (auto& e : c->ring) e.destroy();
+    c->side.destroy();
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return BN_OK;
@@ -825,7 +872,8 @@ namespace {
 // Steps 1-5 of every job of group g on stream s; `stages` selects the parts:
 // bit 0 step 1 (per job) and the score shift, bit 1 step 2, bit 2 step 3,
 // bit 3 step 4, bit 4 step 5.
-int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsigned stages)
+int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsigned stages,
+                  const Side* side = nullptr)
 {
     const Plan& G = g.P;
     const Layout& L = g.L;
@@ -862,8 +910,17 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
         CK(bn::launch_upzeta(G, reinterpret_cast<const uint32_t*>(at(L.cmasks)), at(L.lbs),
                              at(L.tab), reinterpret_cast<const uint16_t*>(at(L.rk13)), at(L.A), s));
     if (stages & 4u) {
-        CK(bn::launch_forward(G, at(L.A), at(L.F), s, nullptr));
-        CK(bn::launch_backward(G, at(L.A), at(L.Rc), s, nullptr));
+        if (side && side->s) {
+            CK(cudaEventRecord(side->fork, s));
+            CK(cudaStreamWaitEvent(side->s, side->fork, 0));
+            CK(bn::launch_backward(G, at(L.A), at(L.Rc), side->s, nullptr));
+            CK(cudaEventRecord(side->join, side->s));
+            CK(bn::launch_forward(G, at(L.A), at(L.F), s, nullptr));
+            CK(cudaStreamWaitEvent(s, side->join, 0));
+        } else {
+            CK(bn::launch_forward(G, at(L.A), at(L.F), s, nullptr));
+            CK(bn::launch_backward(G, at(L.A), at(L.Rc), s, nullptr));
+        }
     }
     if (stages & 8u) {
         CK(bn::launch_gamma_p1(G, at(L.F), at(L.Rc), reinterpret_cast<const uint16_t*>(at(L.rk13)),
@@ -992,6 +1049,8 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
     for (auto& st : b->streams) ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
     b->joins.assign(nb, nullptr);
     for (auto& e : b->joins) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    b->sides.resize(nb);
+    for (auto& sd : b->sides) ok = ok && sd.create() == BN_OK;
     // inputs go to the device now; only kernels are captured
     ok = ok && cudaMemset(b->arena, 0, total) == cudaSuccess;
     for (int k = 0; ok && k < count; ++k) {
@@ -1029,7 +1088,8 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
         bool cap_ok = cudaEventRecord(b->fork, cap) == cudaSuccess;
         for (auto st : b->streams) cap_ok = cap_ok && cudaStreamWaitEvent(st, b->fork, 0) == cudaSuccess;
         for (size_t q = 0; cap_ok && q < b->groups.size(); ++q)
-            cap_ok = enqueue_group(b, b->groups[q], b->streams[q % nb], 31u) == BN_OK;
+            cap_ok = enqueue_group(b, b->groups[q], b->streams[q % nb], 31u,
+                                   &b->sides[q % nb]) == BN_OK;
         for (int q = 0; cap_ok && q < nb; ++q)
             cap_ok = cudaEventRecord(b->joins[q], b->streams[q]) == cudaSuccess &&
                      cudaStreamWaitEvent(cap, b->joins[q], 0) == cudaSuccess;
@@ -1098,6 +1158,7 @@ int bn_batch_destroy(bn_batch* b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto st : b->streams) if (st) cudaStreamDestroy(st);
+    for (auto& sd : b->sides) sd.destroy();
     for (auto e : b->joins) if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->arena) cudaFree(b->arena);
@@ -1220,7 +1281,8 @@ void pump(bn_ctx* c)
             Layout L = make_layout(P, 0);
             Bufs B{(char*)dev, L};
             rc = enqueue(sj.hj, B, B.at<double>(L.post), B.at<double>(L.logPD), sl.stream, &sl.ev,
-                         &sl.launches, sl.pin + al(out_bytes), sl.pin_bytes - al(out_bytes));
+                         &sl.launches, sl.pin + al(out_bytes), sl.pin_bytes - al(out_bytes), true,
+                         &sl.side);
             if (!rc) {
                 if (cudaMemcpyAsync(sl.pin, B.at<char>(L.post), (size_t)P.n * P.n * 8, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
                     cudaMemcpyAsync(sl.pin + (size_t)P.n * P.n * 8, B.at<char>(L.logPD), 8, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||

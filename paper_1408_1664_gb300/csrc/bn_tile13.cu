@@ -296,16 +296,17 @@ template <> __device__ __forceinline__ void st3<float>(float* a, const float (&v
 // 3); A1 holds the transform's inputs (for UP only the slots with at most d
 // elements are inputs).  On exit v and sc hold, in layout 1, each output as
 // scaled_log(v, sc): FP32 keeps y relative to 2^floor(m), FP64 keeps x in
-// its band.
+// its band.  The scales replace the inputs in A1: every thread reads its
+// layout-3 inputs and writes its layout-3 scales to the same slots.
 template <bool UP, typename T>
-__device__ __forceinline__ void sum_pass(T (&v)[TR], T (&sc)[TR], const T* A1, T* A0, T* E,
-                                         int t, int d)
+__device__ __forceinline__ void sum_pass(T (&v)[TR], T (&sc)[TR], T* A1, T* A0, int t, int d)
 {
     using Lg = LogOps<T>;
+    T* E = A1;
 #pragma unroll
     for (int r = 0; r < TR; ++r) sc[r] = scale_of(v[r]);
+    ld3(A1, v, t);                        // inputs
     st3(E, sc, t);                        // scales, read again in layouts 2 and 1
-    ld3(A1, v, t);
 #pragma unroll
     for (int r = 0; r < TR; ++r)
         v[r] = (!UP || __popc(el3(r, t)) <= d) ? Lg::ex(v[r] - scale_base(sc[r])) : T(0);
@@ -665,9 +666,8 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
     T* A1 = A0 + TN;
-    T* E = A1 + TN;
     using O = typename OrdInt<T>::type;
-    O* tmax = reinterpret_cast<O*>(E + TN);      // largest column sum
+    O* tmax = reinterpret_cast<O*>(A1 + TN);     // largest column sum
     const uint32_t ncol = num_small_subsets(TB, d);
     const int h = n - 1 - TB;
     const int t = threadIdx.x, lane = t & 31;
@@ -754,7 +754,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 
     // --- exact sum pass: layouts 3, 2, 1 ------------------------------------
     T sc[TR];
-    sum_pass<true>(v, sc, A1, A0, E, t, d);
+    sum_pass<true>(v, sc, A1, A0, t, d);
 #pragma unroll
     for (int r = 0; r < TR; ++r) out[el1(r, t)] = scaled_log(v[r], sc[r]);
 }
@@ -765,7 +765,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 // most d low elements in row H of W.
 // ===========================================================================
 template <typename T>
-__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 3 : 1)
 k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W,
              size_t js)
@@ -779,7 +779,6 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
     T* A1 = A0 + TN;
-    T* E = A1 + TN;
     const int t = threadIdx.x;
     const uint32_t H = blockIdx.x;
     const uint32_t bv = 1u << v;
@@ -844,7 +843,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     bfly_max<false>(x, 0, 3);
 
     T sc[TR];
-    sum_pass<false>(x, sc, A1, A0, E, t, d);
+    sum_pass<false>(x, sc, A1, A0, t, d);
     const int pt = __popc((uint32_t)t);
 #pragma unroll
     for (int r = 0; r < TR; ++r)
@@ -880,7 +879,7 @@ size_t upzeta13_cols_smem_bytes(const Plan& P)
 size_t upzeta13_smem_bytes(const Plan& P)
 {
     const size_t es = P.prec == 0 ? 8 : 4;
-    return (size_t)TN * (3 * es) + 16;
+    return (size_t)TN * (2 * es) + 16;
 }
 
 bool tile13_up_fits(const Plan& P)
@@ -891,7 +890,7 @@ bool tile13_up_fits(const Plan& P)
 size_t gamma13_smem_bytes(const Plan& P)
 {
     const size_t es = P.prec == 0 ? 8 : 4;
-    return (size_t)TN * (3 * es) + 16;
+    return (size_t)TN * (2 * es) + 16;
 }
 
 cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unrank13, cudaStream_t s)
