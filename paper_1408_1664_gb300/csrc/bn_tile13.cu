@@ -292,6 +292,27 @@ template <> __device__ __forceinline__ void st3<float>(float* a, const float (&v
         *reinterpret_cast<float4*>(a + base + 4) = q;
     }
 }
+// Layout-3 values to global memory: registers 8q..8q+7 of thread t are the
+// consecutive elements el3(8q, t) .. el3(8q, t) + 7 (32-byte aligned).
+__device__ __forceinline__ void st_out3(float* out, const float (&x)[TR], int t)
+{
+#pragma unroll
+    for (int q = 0; q < TR / 8; ++q) {
+        float4* p = reinterpret_cast<float4*>(out + el3(8 * q, t));
+        p[0] = make_float4(x[8 * q], x[8 * q + 1], x[8 * q + 2], x[8 * q + 3]);
+        p[1] = make_float4(x[8 * q + 4], x[8 * q + 5], x[8 * q + 6], x[8 * q + 7]);
+    }
+}
+__device__ __forceinline__ void st_out3(double* out, const double (&x)[TR], int t)
+{
+#pragma unroll
+    for (int q = 0; q < TR / 8; ++q) {
+        double2* p = reinterpret_cast<double2*>(out + el3(8 * q, t));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p[k] = make_double2(x[8 * q + 2 * k], x[8 * q + 2 * k + 1]);
+    }
+}
+
 // The exact sum pass after the max-plus pass.  On entry v holds m (layout
 // 3); A1 holds the transform's inputs (for UP only the slots with at most d
 // elements are inputs).  On exit v and sc hold, in layout 1, each output as
@@ -705,6 +726,27 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
         const T M = ord_dec(*tmax) + T(TB);
         const T span = M - A1[0];
         const int npass = span < Wn::win ? 1 : (int)ceil(span / Wn::win);
+        if (npass == 1) {                        // one window holds the whole tile
+            const T sp = M - Wn::top;
+            T x[TR];
+            ld1(A1, x, t);
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+                x[r] = (__popc(el1(r, t)) <= d) ? Lg::ex(x[r] - sp) : T(0);
+            bfly_plain<true>(x, 0, 5);
+            st1(A0, x, t);
+            __syncthreads();
+            ld2(A0, x, t);
+            bfly_plain<true>(x, 0, 5);
+            st2(A0, x, t);
+            __syncthreads();
+            ld3(A0, x, t);
+            bfly_plain<true>(x, 0, 3);
+#pragma unroll
+            for (int r = 0; r < TR; ++r) x[r] = sp + Lg::lg(x[r]);
+            st_out3(out, x, t);
+            return;
+        }
         if (npass <= Wn::max_pass) {
             uint32_t done = 0u;                  // bit r: output el3(r, t) written
             T sp = M - Wn::top;
