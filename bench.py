@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--sweep", action="store_true",
+                    help="the n and d sweep of the paper's experiments (prints one JSON table)")
     ap.add_argument("--subset-n", type=int, default=0,
                     help="use only the first N variables of the workload (profiling)")
     return ap.parse_args()
@@ -376,6 +378,53 @@ def run_batched(binding, torch, device: int, jobs_n: int = 256, reps: int = 5) -
     return out
 
 
+# ---------------------------------------------------------------- sweep --
+def run_sweep(args) -> None:
+    """Time the FP32 path over the configurations of the paper's experiments
+    (Section 4.2, Tables 1-2: d in {2, 4, 6, 8} at n = 25; n = 21..31 at
+    d = 4; binary data, m = 500, one seeded random DAG per configuration).
+    Each result is checked for 0 <= P <= 1, sum_u P(u->v) <= d and
+    P(u->v) + P(v->u) <= 1; up to n = 26 also against the FP64 path."""
+    import torch
+
+    from paper_1408_1664_gb300 import binding
+
+    binding.load(build_if_missing=True)
+    grid = [(25, d) for d in (2, 4, 6, 8)] + [(n, 4) for n in range(21, 32)]
+    rows = []
+    with binding.Context(0) as ctx:
+        for n, d in grid:
+            ds = datagen.random_dag_data(n, 500, 2, min(d, 4), 1.0, seed=500 + 10 * n + d)
+            job = binding.Job(ds.data, ds.arity, d, precision="fp32")
+            binding.bn_edge_posteriors(ctx.h, job)                       # warm-up
+            reps = 3 if n <= 28 else 1
+            ts, post, st = [], None, None
+            for _ in range(reps):
+                post, _ = binding.bn_edge_posteriors(ctx.h, job)
+                st = ctx.stats()
+                ts.append(st["ms_total"])
+            ms = statistics.median(ts)
+            eps = 1e-6
+            ok = bool(np.all(post >= -eps) and np.all(post <= 1 + eps)
+                      and np.all(post.sum(axis=0) <= d + 1e-4)
+                      and np.all(post + post.T <= 1 + 1e-4))
+            row = {"n": n, "d": d, "m": 500, "ms": ms, "cells_per_s": n * 2 ** n / (ms / 1e3),
+                   "properties_ok": ok,
+                   "stages_ms": {k: round(st[k], 3) for k in ("ms_scores", "ms_upzeta",
+                                                              "ms_upzeta_sums", "ms_forward",
+                                                              "ms_backward", "ms_gamma_p1",
+                                                              "ms_gamma_p2", "ms_edges")}}
+            if n <= 26:
+                p64, _ = binding.bn_edge_posteriors(ctx.h, binding.Job(ds.data, ds.arity, d,
+                                                                       precision="fp64"))
+                row["max_abs_fp32_vs_fp64"] = float(np.abs(post - p64).max())
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "n and d of Section 4.2 (FP32 path, binary, m=500)",
+                      "rows": rows}))
+
+
 # ---------------------------------------------------------------- ours --
 def run_ours(args):
     import torch
@@ -554,7 +603,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

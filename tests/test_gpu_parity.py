@@ -174,6 +174,26 @@ def test_stage_A_wide_spans(ctx, precision, step):
     np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
 
 
+# Larger in-degree bounds on the 13-dimension tile path (the paper's d = 6
+# and 8 of its sweep): other score kernels, longer row lists and more
+# columns per tile, most phase-2 columns on the butterfly kernel.
+LARGE_D = [(16, 6), (16, 8), (18, 6), (20, 6)]
+_large_d_ref = {}
+
+
+@pytest.mark.parametrize("n,d", LARGE_D)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+def test_large_in_degree_bounds(ctx, n, d, precision, tol):
+    ds = datagen.random_dag_data(n, 500, 2, min(d, 4), 1.0, seed=300 + n + d)
+    if (n, d) not in _large_d_ref:
+        _large_d_ref[(n, d)] = orc.edge_posteriors(ds.data, ds.arity, d)
+    ref = _large_d_ref[(n, d)]
+    post, lpd = ctx.edge_posteriors(ds.data, ds.arity, d, precision=precision)
+    np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
+    if precision == "fp64":
+        assert abs(lpd - ref["log_PD"]) <= 1e-9 * max(1.0, abs(ref["log_PD"]))
+
+
 def test_small_config_both_paths(ctx):
     ds, d = datagen.config_small()
     ref = orc.edge_posteriors(ds.data, ds.arity, d)
