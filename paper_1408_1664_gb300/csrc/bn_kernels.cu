@@ -173,8 +173,11 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
     (void)d;
 }
 
-// Scores with one thread per family, for binary data (every arity 2) and at
-// most 4 parents: at most 16 parent configurations and 32 cells.  Word by
+// Scores with one thread per family, for binary data (every arity 2) and
+// families of at most 4 parents: at most 16 parent configurations and 32
+// cells.  The launch covers the first Kc families of every node (those of
+// at most 4 parents; Kc = K when d <= 4); thread index xc stands for family
+// (xc / Kc) * K + xc % Kc.  Word by
 // word the thread builds the masks of all 16 configurations as a product
 // tree of the parent planes (configuration index: digit t = value of parent
 // t, parent 0 least significant; a missing parent t >= |G| contributes the
@@ -184,7 +187,7 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
 // lgamma(a) - lgamma(a) = 0 exactly, so the padding changes nothing.
 // The bit planes (n * 2 * W words) stay in L1.
 __global__ void __launch_bounds__(128)
-k_scores_bin(int n, int m, int W, int64_t K, const uint64_t* __restrict__ planes,
+k_scores_bin(int n, int m, int W, int64_t K, int64_t Kc, const uint64_t* __restrict__ planes,
              const double* __restrict__ Dvals, int rows, const double* __restrict__ T,
              const double* __restrict__ log_rho, int64_t x_begin, int64_t x_count,
              uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
@@ -195,9 +198,10 @@ k_scores_bin(int n, int m, int W, int64_t K, const uint64_t* __restrict__ planes
     __syncthreads();
     const int64_t xi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (xi >= x_count) return;
-    const int64_t x = x_begin + xi;
-    const int i = (int)(x / K);
-    uint32_t f = (uint32_t)(x % K);
+    const int64_t xc = x_begin + xi;
+    const int i = (int)(xc / Kc);
+    uint32_t f = (uint32_t)(xc % Kc);
+    const int64_t x = (int64_t)i * K + f;
     int k = 0;
     while (f >= bt[n - 1][k]) { f -= bt[n - 1][k]; ++k; }
     uint32_t cm = 0;                                // colex unrank of f among k-subsets
@@ -265,6 +269,116 @@ k_scores_bin(int n, int m, int W, int64_t K, const uint64_t* __restrict__ planes
     logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
     masks[x] = G;
     cmasks[x] = cm;
+}
+
+// Scores of the families with exactly k = 4 + HB parents (5 <= k <= 8), for
+// binary data.  A family takes 2^HB adjacent threads of a warp; thread h
+// owns the 16 configurations whose digits of parents 4..k-1 spell h.  Word
+// by word it ANDs the planes of those high digits into one mask, splits the
+// mask over the four low parents with the product tree of k_scores_bin and
+// counts the 32 cells with popc.  Its FP64 sum of BDeu terms meets those of
+// the family's other threads in an xor butterfly (every lane ends with the
+// same sum, so the order is fixed).  The launch covers families f_begin ..
+// f_begin + f_count - 1 of the n * C(n-1, k) families of this size, family
+// g being rank g % C(n-1, k) of node g / C(n-1, k); off is the index of the
+// first k-parent family inside a node's block of K.
+template <int HB>
+__global__ void __launch_bounds__(128)
+k_scores_bin_hi(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
+                const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
+                const double* __restrict__ T, const double* __restrict__ log_rho, int64_t f_begin,
+                int64_t f_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
+                double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+{
+    constexpr int k = 4 + HB;
+    constexpr int NH = 1 << HB;
+    __shared__ uint32_t bt[32][k + 1];
+    for (int e = threadIdx.x; e < 32 * (k + 1); e += blockDim.x)
+        bt[e / (k + 1)][e % (k + 1)] = binom(e / (k + 1), e % (k + 1));
+    __syncthreads();
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int h = (int)(gt & (NH - 1));
+    const bool live = (gt >> HB) < f_count;
+    // a thread past the end works on the last family (all lanes stay in the
+    // butterfly) and writes nothing
+    const int64_t g = f_begin + (live ? (gt >> HB) : f_count - 1);
+    const int i = (int)(g / Ck);
+    uint32_t r = (uint32_t)(g % Ck);
+    uint32_t cm = 0;                                // colex unrank of r among k-subsets
+    {
+        int c = n - 2;
+        for (int t = k; t >= 1; --t) {
+            while (bt[c][t] > r) --c;
+            cm |= 1u << c;
+            r -= bt[c][t];
+            --c;
+        }
+    }
+    const uint32_t G = expand(cm, i);
+    int par[k];
+    {
+        uint32_t gg = G;
+#pragma unroll
+        for (int t = 0; t < k; ++t) {
+            par[t] = __ffs(gg) - 1;
+            gg &= gg - 1;
+        }
+    }
+    // plane rows of the high digits of configuration block h
+    int hrow[HB];
+#pragma unroll
+    for (int t = 0; t < HB; ++t) hrow[t] = (par[4 + t] * 2 + ((h >> t) & 1)) * W;
+    uint32_t cnt[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) cnt[c] = 0;
+    for (int w = 0; w < W; ++w) {
+        uint64_t E[16];
+        E[0] = planes[hrow[0] + w];
+#pragma unroll
+        for (int t = 1; t < HB; ++t) E[0] &= planes[hrow[t] + w];
+#pragma unroll
+        for (int t = 3; t >= 0; --t) {              // most significant digit first
+            const uint64_t p0 = planes[((size_t)par[t] * 2) * W + w];
+            const uint64_t p1 = planes[((size_t)par[t] * 2 + 1) * W + w];
+            const int size = 1 << (3 - t);
+#pragma unroll
+            for (int j = size - 1; j >= 0; --j) {
+                const uint64_t e = E[j];
+                E[2 * j] = e & p0;
+                E[2 * j + 1] = e & p1;
+            }
+        }
+        const uint64_t c0 = planes[((size_t)i * 2) * W + w];
+        const uint64_t c1 = planes[((size_t)i * 2 + 1) * W + w];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            cnt[2 * j] += (uint32_t)__popcll(E[j] & c0);
+            cnt[2 * j + 1] += (uint32_t)__popcll(E[j] & c1);
+        }
+    }
+    const double q = (double)(1 << k);
+    const double* Tq = T + (size_t)find_row(Dvals, rows, q) * (m + 1);
+    const double* Tqr = T + (size_t)find_row(Dvals, rows, 2.0 * q) * (m + 1);
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        acc -= Tq[cnt[2 * j] + cnt[2 * j + 1]];
+        acc += Tqr[cnt[2 * j]];
+        acc += Tqr[cnt[2 * j + 1]];
+    }
+#pragma unroll
+    for (int o = 1; o < NH; o <<= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (!live) return;
+    if (debug_counts) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) debug_counts[32 * h + c] = cnt[c];
+    }
+    if (h == 0) {
+        const int64_t x = (int64_t)i * K + off + (int64_t)(g % Ck);
+        logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+        masks[x] = G;
+        cmasks[x] = cm;
+    }
 }
 
 // Scores with one warp per family and one lane per 64-sample word (m <= 2048):
@@ -1050,6 +1164,65 @@ cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T,
     return cudaGetLastError();
 }
 
+static uint32_t host_binom(int n, int k);
+
+// Binary data, d <= 8: k_scores_bin for the families of at most 4 parents
+// and one k_scores_bin_hi launch per larger family size.  The range is all
+// families or a single one.
+static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, const double* Dvals,
+                                     const double* T, const double* log_rho, int64_t x_begin,
+                                     int64_t x_count, uint32_t* masks, uint32_t* cmasks,
+                                     double* logB, int64_t* debug_counts, cudaStream_t s)
+{
+    int64_t off[10] = {0};
+    for (int k = 0; k <= P.d; ++k) off[k + 1] = off[k] + host_binom(P.n - 1, k);
+    const int dl = P.d < 4 ? P.d : 4;
+    const int64_t Kc = off[dl + 1];
+    int k1 = 0, klo = 0, khi = P.d;                 // single family: its size only
+    int64_t i1 = 0, f1 = 0;
+    if (x_count == 1) {
+        i1 = x_begin / P.K;
+        f1 = x_begin % P.K;
+        while (f1 >= off[k1 + 1]) ++k1;
+        klo = khi = k1;
+    }
+    if (klo <= 4) {
+        const int64_t xb = x_count == 1 ? i1 * Kc + f1 : 0;
+        const int64_t xn = x_count == 1 ? 1 : (int64_t)P.n * Kc;
+        k_scores_bin<<<(unsigned)((xn + 127) / 128), 128, 0, s>>>(
+            P.n, P.m, P.W, P.K, Kc, planes, Dvals, P.rows, T, log_rho, xb, xn, masks, cmasks, logB,
+            debug_counts);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = klo > 5 ? klo : 5; k <= khi; ++k) {
+        const int64_t Ck = host_binom(P.n - 1, k);
+        const int64_t fb = x_count == 1 ? i1 * Ck + (f1 - off[k]) : 0;
+        const int64_t fn = x_count == 1 ? 1 : (int64_t)P.n * Ck;
+        const int64_t threads = fn << (k - 4);
+        const unsigned grid = (unsigned)((threads + 127) / 128);
+#define BN_BIN_HI(HB)                                                                             \
+    k_scores_bin_hi<HB><<<grid, 128, 0, s>>>(P.n, P.m, P.W, P.K, off[k], Ck, planes, Dvals,      \
+                                             P.rows, T, log_rho, fb, fn, masks, cmasks, logB,    \
+                                             debug_counts)
+        switch (k) {
+        case 5: BN_BIN_HI(1); break;
+        case 6: BN_BIN_HI(2); break;
+        case 7: BN_BIN_HI(3); break;
+        default: BN_BIN_HI(4); break;
+        }
+#undef BN_BIN_HI
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int scores_launches(const Plan& P)
+{
+    return P.allbin && P.d > 4 && P.d <= 8 ? P.d - 3 : 1;
+}
+
 cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* planes,
                           const double* Dvals, const double* T, const double* log_rho,
                           int64_t x_begin, int64_t x_count, uint32_t* masks, uint32_t* cmasks,
@@ -1058,12 +1231,9 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
     const int threads = 256;
     const int64_t warps_wanted = x_count;
     int grid = grid_for(warps_wanted * 32, threads, 152 * 64);
-    if (P.allbin && P.d <= 4) {
-        k_scores_bin<<<(unsigned)((x_count + 127) / 128), 128, 0, s>>>(
-            P.n, P.m, P.W, P.K, planes, Dvals, P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
-            logB, debug_counts);
-        return cudaGetLastError();
-    }
+    if (P.allbin && P.d <= 8 && (x_count == 1 || (x_begin == 0 && x_count == (int64_t)P.n * P.K)))
+        return launch_scores_bin(P, planes, Dvals, T, log_rho, x_begin, x_count, masks, cmasks,
+                                 logB, debug_counts, s);
     if (P.W <= 32 && P.d <= 4 && P.rmax <= 2)
         k_scores_w<4, 2><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,

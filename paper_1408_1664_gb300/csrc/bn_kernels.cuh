@@ -41,6 +41,8 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
                           int64_t x_begin, int64_t x_count, uint32_t* masks,
                           uint32_t* cmasks, double* logB, int64_t* debug_counts,
                           cudaStream_t s);
+// Kernels one launch_scores call over all n * K families starts.
+int scores_launches(const Plan& P);
 cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s);
 cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double* cmax,
                                 void* lbs, cudaStream_t s);

@@ -300,7 +300,8 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals),
                          B.at<double>(L.lgT), hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho),
                          0, (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
-                         B.at<double>(L.logB), nullptr, s)); ++nl;
+                         B.at<double>(L.logB), nullptr, s));
+    nl += bn::scores_launches(P);
     CK(bn::launch_node_max(P, B.at<double>(L.logB), B.at<double>(L.cmax), s)); ++nl;
     CK(bn::launch_shift_scores(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<void>(L.lbs), s)); ++nl;
     if (bn::needs_rank13(P)) {

@@ -56,8 +56,26 @@ def test_counts_bit_exact(ctx, n, m, arity, seed):
         np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("n,m,d,seed", [(10, 700, 8, 11), (12, 130, 6, 12), (9, 2000, 7, 13)])
+def test_counts_bit_exact_binary_large_families(ctx, n, m, d, seed):
+    """Binary data, families of 5..d parents: the counts of every cell, in
+    the cell order (configuration, child value), against the oracle's."""
+    ds = _ds(n, m, 2, 4, seed=seed)
+    job = B.Job(ds.data, ds.arity, d)
+    rng = np.random.default_rng(seed)
+    for k in list(range(5, d + 1)) * 4:
+        i = int(rng.integers(n))
+        cand = [p for p in range(n) if p != i]
+        G = sum(1 << int(p) for p in rng.choice(cand, size=k, replace=False))
+        want = orc.family_counts(ds.data, ds.arity, i, G)
+        got = B.bn_debug_counts(ctx.h, job, i, G, want.shape[0])
+        np.testing.assert_array_equal(got, want)
+
+
 @pytest.mark.parametrize("n,m,arity,d,seed,ess,rho", [
     (12, 200, 2, 3, 0, 1.0, None), (9, 700, 3, 4, 1, 1.0, None),
+    (11, 300, 2, 8, 5, 1.0, None), (13, 97, 2, 6, 6, 3.0, [0.0, -0.5, -1.1, -1.6, -2.3, -2.9, -3.7]),
+    (14, 500, 2, 5, 7, 1.0, None),
     (10, 333, [2, 3, 2, 4, 2, 3, 2, 2, 5, 2], 3, 2, 2.5, [0.0, -0.7, -1.9, -3.3]),
     (6, 0, 2, 2, 3, 1.0, None), (1, 50, 4, 0, 4, 1.0, None)])
 def test_scores_match_oracle(ctx, n, m, arity, d, seed, ess, rho):
