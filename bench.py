@@ -58,6 +58,8 @@ def parse():
                     help="the n and d sweep of the paper's experiments (prints one JSON table)")
     ap.add_argument("--subset-n", type=int, default=0,
                     help="use only the first N variables of the workload (profiling)")
+    ap.add_argument("--degree", type=int, default=0,
+                    help="override the workload's in-degree bound d (profiling)")
     return ap.parse_args()
 
 
@@ -444,6 +446,9 @@ def run_ours(args):
         ds = datagen.Dataset(np.ascontiguousarray(ds.data[:, :args.subset_n]),
                              ds.arity[:args.subset_n].copy(), [], ds.seed)
         name = f"{name}_first{args.subset_n}"
+    if args.degree:
+        d = args.degree
+        name = f"{name}_d{d}"
     n = ds.n
     cells = n * 2 ** n
     prec = args.precision

@@ -182,9 +182,10 @@ int bn_edge_posteriors_static(const bn_job_desc* job, double* post_dev,
 /* Batches.  Many independent jobs (typically small n) planned together
  * (Algorithm 1 for each job; the paper has no batch form).
  * bn_batch_create validates every job and copies its host inputs into one
- * device arena.  Jobs with equal n, d and precision form a group: their
- * arrays lie at a fixed stride, and every launch of steps 2-5 covers the
- * whole group (step 1 runs per job: its sizes depend on m and the arities).
+ * device arena.  Jobs with equal n, d, precision and kind of data (every
+ * arity 2, or not) form a group: their arrays lie at a fixed stride in a
+ * layout padded to the group's largest m, arity and lgamma table, and every
+ * launch of steps 1-5 covers the whole group.
  * Unless the context has BN_CTX_NO_AUTOTUNE, the schedule of each group --
  * the kernels of the up-zeta (13-dimension tiles or shared-memory tiles), of
  * F and R' (16-subset rows or warp tiles, FP32) and of the down-zeta phase 1
@@ -204,7 +205,8 @@ int bn_batch_create(bn_ctx* ctx, const bn_job_desc* jobs, int32_t count, bn_batc
 int bn_batch_run(bn_batch* batch, void* stream);
 int bn_batch_results(bn_batch* batch, int32_t k, double* post, double* log_PD);
 /* One line per group into buf (NUL-terminated, truncated to len): its n, d,
- * precision, jobs and the schedule it runs, and whether that was timed.
+ * precision, kind of data, jobs and the schedule it runs, and whether that
+ * was timed.
  * BN_EINVAL for NULL arguments. */
 int bn_batch_describe(bn_batch* batch, char* buf, size_t len);
 int bn_batch_destroy(bn_batch* batch);

@@ -25,9 +25,14 @@ static constexpr unsigned FULL = 0xffffffffu;
 // ===========================================================================
 
 // planes[(v*rmax + x)*W + w] bit b  <=>  data[(64w + b)*n + v] == x.
+// mj (may be null) holds the job's own sample count at the job stride; m
+// then only bounds the padded group layout.
 __global__ void k_pack_planes(const uint8_t* __restrict__ data, int n, int m, int rmax, int W,
-                              uint64_t* __restrict__ planes)
+                              uint64_t* __restrict__ planes, const int* __restrict__ mj, size_t js)
 {
+    data = job_ptr(data, js);
+    planes = job_ptr(planes, js);
+    if (mj) m = *job_ptr(mj, js);
     const int64_t total = (int64_t)n * rmax * W;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -57,8 +62,10 @@ __global__ void k_check_data(const uint8_t* __restrict__ data, const uint8_t* __
 
 // T[row*(m+1) + N] = lgamma(alpha_row + N) - lgamma(alpha_row), N = 0..m.
 __global__ void k_lgamma_table(const double* __restrict__ alpha, int rows, int m,
-                               double* __restrict__ T)
+                               double* __restrict__ T, size_t js)
 {
+    alpha = job_ptr(alpha, js);
+    T = job_ptr(T, js);
     const int64_t total = (int64_t)rows * (m + 1);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -97,6 +104,19 @@ template <> __device__ __forceinline__ float from_fixed<float>(unsigned long lon
     return __ull2float_rn(u);
 }
 
+// Step-1 kernels of a batch group run for every job of the group at once:
+// job blockIdx.y finds its arrays js bytes after those of job blockIdx.y - 1.
+#define BN_JOB_SCORES()                                                                   \
+    do {                                                                                  \
+        planes = job_ptr(planes, js);                                                     \
+        Dvals = job_ptr(Dvals, js);                                                       \
+        T = job_ptr(T, js);                                                               \
+        if (log_rho) log_rho = job_ptr(log_rho, js);                                      \
+        masks = job_ptr(masks, js);                                                       \
+        cmasks = job_ptr(cmasks, js);                                                     \
+        logB = job_ptr(logB, js);                                                         \
+    } while (0)
+
 // One warp per family x = i*K + f.  Counts N_jk = popc(AND of bit planes),
 // lanes split the words of a plane and the cells of the table lookups.
 //   log B_i(G) = log rho(|G|) + sum_j [ -T_q(N_j) + sum_k T_qr(N_jk) ]
@@ -106,8 +126,10 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
          const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
          const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
          int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-         double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+         double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
 {
+    BN_JOB_SCORES();
+    arity = job_ptr(arity, js);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -191,8 +213,9 @@ k_scores_bin(int n, int m, int W, int64_t K, int64_t Kc, const uint64_t* __restr
              const double* __restrict__ Dvals, int rows, const double* __restrict__ T,
              const double* __restrict__ log_rho, int64_t x_begin, int64_t x_count,
              uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-             double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+             double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
 {
+    BN_JOB_SCORES();
     __shared__ uint32_t bt[32][5];                  // C(a, b), b <= 4, for the unrank
     for (int e = threadIdx.x; e < 32 * 5; e += blockDim.x) bt[e / 5][e % 5] = binom(e / 5, e % 5);
     __syncthreads();
@@ -288,8 +311,9 @@ k_scores_bin_hi(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
                 const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
                 const double* __restrict__ T, const double* __restrict__ log_rho, int64_t f_begin,
                 int64_t f_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-                double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+                double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
 {
+    BN_JOB_SCORES();
     constexpr int k = 4 + HB;
     constexpr int NH = 1 << HB;
     __shared__ uint32_t bt[32][k + 1];
@@ -392,8 +416,10 @@ k_scores_w(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__
            const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
            const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
            int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-           double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+           double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
 {
+    BN_JOB_SCORES();
+    arity = job_ptr(arity, js);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -484,20 +510,23 @@ k_scores_w(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__
     }
 }
 
-// Register version of k_scores for at most 8 parents and child arity at most
-// 8: one warp per family, one lane per parent configuration j.  The lane
-// ANDs the planes of its configuration's parent values word by word and
+// Register version of k_scores for at most MP parents and child arity at
+// most MR: one warp per family, one lane per parent configuration j.  The
+// lane ANDs the planes of its configuration's parent values word by word and
 // counts each child value with popc, then adds its own BDeu terms
 //   -T_q(N_j) + sum_k T_qr(N_jk);
 // the warp sum gives log B.  No cross-lane step per cell.
 constexpr int SC_MP = 8, SC_MR = 8;
+template <int MP, int MR>
 __global__ void __launch_bounds__(256)
 k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__ arity,
              const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
              const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
              int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-             double* __restrict__ logB, int64_t* __restrict__ debug_counts)
+             double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
 {
+    BN_JOB_SCORES();
+    arity = job_ptr(arity, js);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -509,11 +538,11 @@ k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict
         while (f >= binom(n - 1, k)) { f -= binom(n - 1, k); ++k; }
         const uint32_t cm = colex_unrank(f, k, n - 1);
         const uint32_t G = expand(cm, i);
-        int par[SC_MP], rad[SC_MP];
+        int par[MP], rad[MP];
         uint32_t g = G;
         int q = 1;
 #pragma unroll
-        for (int t = 0; t < SC_MP; ++t) {
+        for (int t = 0; t < MP; ++t) {
             par[t] = 0;
             rad[t] = 1;
             if (g) {
@@ -531,29 +560,29 @@ k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict
         for (int j0 = 0; j0 < q; j0 += 32) {
             const int j = j0 + lane;
             if (j < q) {
-                const uint64_t* pp[SC_MP];
+                const uint64_t* pp[MP];
                 int jj = j;
 #pragma unroll
-                for (int t = 0; t < SC_MP; ++t) {
+                for (int t = 0; t < MP; ++t) {
                     const int dg = jj % rad[t];
                     jj /= rad[t];
                     pp[t] = planes + ((size_t)par[t] * rmax + dg) * W;
                 }
-                uint32_t N[SC_MR];
+                uint32_t N[MR];
 #pragma unroll
-                for (int xv = 0; xv < SC_MR; ++xv) N[xv] = 0;
+                for (int xv = 0; xv < MR; ++xv) N[xv] = 0;
                 for (int w = 0; w < W; ++w) {
                     uint64_t M = ~0ull;
 #pragma unroll
-                    for (int t = 0; t < SC_MP; ++t)
+                    for (int t = 0; t < MP; ++t)
                         if (t < k) M &= pp[t][w];
 #pragma unroll
-                    for (int xv = 0; xv < SC_MR; ++xv)
+                    for (int xv = 0; xv < MR; ++xv)
                         if (xv < ri) N[xv] += (uint32_t)__popcll(M & cp[(size_t)xv * W + w]);
                 }
                 uint32_t Nj = 0;
 #pragma unroll
-                for (int xv = 0; xv < SC_MR; ++xv) {
+                for (int xv = 0; xv < MR; ++xv) {
                     if (xv < ri) {
                         acc += Tqr[N[xv]];
                         Nj += N[xv];
@@ -1142,10 +1171,11 @@ static int grid_for(int64_t work, int threads, int cap = 152 * 32)
 }
 
 cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int W,
-                               uint64_t* planes, cudaStream_t s)
+                               uint64_t* planes, cudaStream_t s, const int* mj, int nj, size_t js)
 {
     const int64_t total = (int64_t)n * rmax * W;
-    k_pack_planes<<<grid_for(total, 256), 256, 0, s>>>(data, n, m, rmax, W, planes);
+    k_pack_planes<<<dim3(grid_for(total, 256), nj), 256, 0, s>>>(data, n, m, rmax, W, planes, mj,
+                                                                 js);
     return cudaGetLastError();
 }
 
@@ -1157,10 +1187,11 @@ cudaError_t launch_check_data(const uint8_t* data, const uint8_t* arity, int n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T, cudaStream_t s)
+cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T, cudaStream_t s,
+                                int nj, size_t js)
 {
     const int64_t total = (int64_t)rows * (m + 1);
-    k_lgamma_table<<<grid_for(total, 256), 256, 0, s>>>(alpha, rows, m, T);
+    k_lgamma_table<<<dim3(grid_for(total, 256), nj), 256, 0, s>>>(alpha, rows, m, T, js);
     return cudaGetLastError();
 }
 
@@ -1189,9 +1220,9 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
     if (klo <= 4) {
         const int64_t xb = x_count == 1 ? i1 * Kc + f1 : 0;
         const int64_t xn = x_count == 1 ? 1 : (int64_t)P.n * Kc;
-        k_scores_bin<<<(unsigned)((xn + 127) / 128), 128, 0, s>>>(
+        k_scores_bin<<<dim3((unsigned)((xn + 127) / 128), P.nj), 128, 0, s>>>(
             P.n, P.m, P.W, P.K, Kc, planes, Dvals, P.rows, T, log_rho, xb, xn, masks, cmasks, logB,
-            debug_counts);
+            debug_counts, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1202,9 +1233,9 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
         const int64_t threads = fn << (k - 4);
         const unsigned grid = (unsigned)((threads + 127) / 128);
 #define BN_BIN_HI(HB)                                                                             \
-    k_scores_bin_hi<HB><<<grid, 128, 0, s>>>(P.n, P.m, P.W, P.K, off[k], Ck, planes, Dvals,      \
-                                             P.rows, T, log_rho, fb, fn, masks, cmasks, logB,    \
-                                             debug_counts)
+    k_scores_bin_hi<HB><<<dim3(grid, P.nj), 128, 0, s>>>(                                      \
+        P.n, P.m, P.W, P.K, off[k], Ck, planes, Dvals, P.rows, T, log_rho, fb, fn, masks, cmasks, \
+        logB, debug_counts, P.js)
         switch (k) {
         case 5: BN_BIN_HI(1); break;
         case 6: BN_BIN_HI(2); break;
@@ -1216,6 +1247,11 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+bool scores_cfg_fits(const Plan& P)
+{
+    return !P.allbin && P.d <= SC_MP && P.rmax <= SC_MR;
 }
 
 int scores_launches(const Plan& P)
@@ -1234,26 +1270,34 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
     if (P.allbin && P.d <= 8 && (x_count == 1 || (x_begin == 0 && x_count == (int64_t)P.n * P.K)))
         return launch_scores_bin(P, planes, Dvals, T, log_rho, x_begin, x_count, masks, cmasks,
                                  logB, debug_counts, s);
-    if (P.W <= 32 && P.d <= 4 && P.rmax <= 2)
-        k_scores_w<4, 2><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+    if (P.scfg && scores_cfg_fits(P) && P.d <= 4 && P.rmax <= 4)
+        k_scores_cfg<4, 4><<<dim3(grid, P.nj), threads, 0, s>>>(
+            P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals, P.rows, T, log_rho, x_begin, x_count,
+            masks, cmasks, logB, debug_counts, P.js);
+    else if (P.scfg && scores_cfg_fits(P))
+        k_scores_cfg<SC_MP, SC_MR><<<dim3(grid, P.nj), threads, 0, s>>>(
+            P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals, P.rows, T, log_rho, x_begin, x_count,
+            masks, cmasks, logB, debug_counts, P.js);
+    else if (P.W <= 32 && P.d <= 4 && P.rmax <= 2)
+        k_scores_w<4, 2><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
-                                                  cmasks, logB, debug_counts);
+                                                  cmasks, logB, debug_counts, P.js);
     else if (P.W <= 32 && P.d <= 4 && P.rmax <= 4)
-        k_scores_w<4, 4><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        k_scores_w<4, 4><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
-                                                  cmasks, logB, debug_counts);
+                                                  cmasks, logB, debug_counts, P.js);
     else if (P.W <= 32 && P.d <= 8 && P.rmax <= 4)
-        k_scores_w<8, 4><<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        k_scores_w<8, 4><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
-                                                  cmasks, logB, debug_counts);
+                                                  cmasks, logB, debug_counts, P.js);
     else if (P.d <= SC_MP && P.rmax <= SC_MR)
-        k_scores_cfg<<<grid, threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        k_scores_cfg<SC_MP, SC_MR><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                               P.rows, T, log_rho, x_begin, x_count, masks,
-                                              cmasks, logB, debug_counts);
+                                              cmasks, logB, debug_counts, P.js);
     else
-        k_scores<<<grid, threads, 0, s>>>(P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        k_scores<<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                           P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
-                                          logB, debug_counts);
+                                          logB, debug_counts, P.js);
     return cudaGetLastError();
 }
 

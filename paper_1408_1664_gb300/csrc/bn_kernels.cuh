@@ -24,23 +24,30 @@ struct Plan {
     int up13 = 0;         // step 2 by the 13-dimension tiles (n >= 14)
     int g13 = 0;          // step 4 phase 1 by the 13-dimension tiles (n >= 14)
     int frows = 0;        // FP32 step 3 by the 16-subset row kernels
+    int scfg = 0;         // step 1 by one lane per parent configuration (non-binary data)
     // Batch groups: nj jobs with equal plans, their arrays js bytes apart;
     // the launches of steps 2-5 cover all of them (gridDim.y = nj).
     int nj = 1;
     size_t js = 0;
 };
 
+// Step 1.  A batch group passes nj jobs js bytes apart (mj: each job's own
+// sample count, at the same stride); a single job leaves the defaults.
 cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int W,
-                               uint64_t* planes, cudaStream_t s);
+                               uint64_t* planes, cudaStream_t s, const int* mj = nullptr,
+                               int nj = 1, size_t js = 0);
 cudaError_t launch_check_data(const uint8_t* data, const uint8_t* arity, int n, int m,
                               int* err, cudaStream_t s);
 cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T,
-                                cudaStream_t s);
+                                cudaStream_t s, int nj = 1, size_t js = 0);
 cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* planes,
                           const double* Dvals, const double* T, const double* log_rho,
                           int64_t x_begin, int64_t x_count, uint32_t* masks,
                           uint32_t* cmasks, double* logB, int64_t* debug_counts,
                           cudaStream_t s);
+// Step 1 has the lane-per-configuration alternative (Plan::scfg): data not
+// all binary, at most 8 parents and arity at most 8.
+bool scores_cfg_fits(const Plan& P);
 // Kernels one launch_scores call over all n * K families starts.
 int scores_launches(const Plan& P);
 cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s);
@@ -96,6 +103,8 @@ inline bool needs_rank13(const Plan& P) { return P.up13 || P.g13; }
 // The default schedule: every specialised kernel that fits.
 inline void default_schedule(Plan& P)
 {
+    // lane per configuration where the 4-parent, arity-4 instance applies
+    P.scfg = scores_cfg_fits(P) && P.d <= 4 && P.rmax <= 4;
     P.up13 = tile13_up_fits(P);
     P.g13 = tile13_gamma_fits(P);
     P.frows = rows_levels_fit(P);

@@ -54,8 +54,8 @@ struct HostJob {
 
 // Byte offsets of every array of a job inside one device allocation.
 struct Layout {
-    size_t data, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB, cmax, lbs,
-        tab, rk13, A, F, Rc, W, Gam, eacc, post, logPD, dbg, total;
+    size_t data, mj, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB, cmax,
+        lbs, tab, rk13, A, F, Rc, W, Gam, eacc, post, logPD, dbg, total;
 };
 
 Layout make_layout(const Plan& P, size_t dbg_cells)
@@ -67,6 +67,7 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o += al(std::max<size_t>(bytes, 1)); return at; };
     L.data = take((size_t)P.m * P.n);
+    L.mj = take(4);                  // the job's own m (batch groups pad m)
     L.arity = take(P.n);
     L.log_rho = take((size_t)(P.d + 1) * 8);
     L.Dvals = take((size_t)P.rows * 8);
@@ -445,7 +446,8 @@ struct bn_ctx {
     uint64_t reserved = 0;
     // batches
     int flags = 0;
-    std::map<std::array<int, 4>, std::array<int, 3>> tuned;   // (n, d, prec, jobs) -> schedule
+    // (n, d, prec, binary, jobs) -> schedule (scfg, up13, frows, g13)
+    std::map<std::array<int, 5>, std::array<int, 4>> tuned;
 };
 
 // Jobs of a batch with equal n, d and precision: their arrays lie js bytes
@@ -457,7 +459,7 @@ struct BatchGroup {
     size_t base = 0;           // arena offset of the group's first job
     std::vector<int> members;  // indices into bn_batch::jobs
     bool timed = false;        // schedule chosen by timing (else default or cached)
-    float ms[3][2] = {};       // timings of the alternatives: up-zeta, F/R', Gamma
+    float ms[4][2] = {};       // timings of the alternatives: scores, up-zeta, F/R', Gamma
 };
 
 struct bn_batch {
@@ -881,23 +883,22 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
     char* base = b->arena + g.base;
     auto at = [&](size_t off) { return base + off; };
     if (stages & 1u) {
-        for (size_t q = 0; q < g.members.size(); ++q) {
-            const HostJob& hj = b->jobs[g.members[q]];
-            const Plan& P = hj.P;
-            char* jb = base + q * G.js;
-            CK(bn::launch_pack_planes(reinterpret_cast<const uint8_t*>(jb + L.data), P.n, P.m,
-                                      P.rmax, P.W, reinterpret_cast<uint64_t*>(jb + L.planes), s));
-            CK(bn::launch_lgamma_table(reinterpret_cast<const double*>(jb + L.alpha), P.rows, P.m,
-                                       reinterpret_cast<double*>(jb + L.lgT), s));
-            CK(bn::launch_scores(P, reinterpret_cast<const uint8_t*>(jb + L.arity),
-                                 reinterpret_cast<const uint64_t*>(jb + L.planes),
-                                 reinterpret_cast<const double*>(jb + L.Dvals),
-                                 reinterpret_cast<const double*>(jb + L.lgT),
-                                 reinterpret_cast<const double*>(jb + L.log_rho), 0,
-                                 (int64_t)P.n * P.K, reinterpret_cast<uint32_t*>(jb + L.masks),
-                                 reinterpret_cast<uint32_t*>(jb + L.cmasks),
-                                 reinterpret_cast<double*>(jb + L.logB), nullptr, s));
-        }
+        // one launch per kernel for the whole group, on the padded tables:
+        // words past a job's m are empty and count nothing, rows past its
+        // own are never looked up
+        CK(bn::launch_pack_planes(reinterpret_cast<const uint8_t*>(at(L.data)), G.n, G.m, G.rmax,
+                                  G.W, reinterpret_cast<uint64_t*>(at(L.planes)), s,
+                                  reinterpret_cast<const int*>(at(L.mj)), G.nj, G.js));
+        CK(bn::launch_lgamma_table(reinterpret_cast<const double*>(at(L.alpha)), G.rows, G.m,
+                                   reinterpret_cast<double*>(at(L.lgT)), s, G.nj, G.js));
+        CK(bn::launch_scores(G, reinterpret_cast<const uint8_t*>(at(L.arity)),
+                             reinterpret_cast<const uint64_t*>(at(L.planes)),
+                             reinterpret_cast<const double*>(at(L.Dvals)),
+                             reinterpret_cast<const double*>(at(L.lgT)),
+                             reinterpret_cast<const double*>(at(L.log_rho)), 0,
+                             (int64_t)G.n * G.K, reinterpret_cast<uint32_t*>(at(L.masks)),
+                             reinterpret_cast<uint32_t*>(at(L.cmasks)),
+                             reinterpret_cast<double*>(at(L.logB)), nullptr, s));
         CK(bn::launch_node_max(G, reinterpret_cast<const double*>(at(L.logB)),
                                reinterpret_cast<double*>(at(L.cmax)), s));
         CK(bn::launch_shift_scores(G, reinterpret_cast<const double*>(at(L.logB)),
@@ -973,10 +974,11 @@ int tune_group(const bn_batch* b, BatchGroup& g, cudaStream_t s)
     }
     int rc = enqueue_group(b, g, s, 31u);
     struct Knob { int Plan::*flag; bool fits; unsigned stage; };
-    const Knob knobs[3] = {{&Plan::up13, bn::tile13_up_fits(g.P), 2u},
+    const Knob knobs[4] = {{&Plan::scfg, bn::scores_cfg_fits(g.P), 1u},
+                           {&Plan::up13, bn::tile13_up_fits(g.P), 2u},
                            {&Plan::frows, bn::rows_levels_fit(g.P), 4u},
                            {&Plan::g13, bn::tile13_gamma_fits(g.P), 8u}};
-    for (int k = 0; rc == BN_OK && k < 3; ++k) {
+    for (int k = 0; rc == BN_OK && k < 4; ++k) {
         if (!knobs[k].fits) continue;
         for (int alt = 0; rc == BN_OK && alt < 2; ++alt) {
             Plan P = g.P;
@@ -1002,7 +1004,7 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
     b->jobs.resize(count);
     b->group_of.assign(count, -1);
     b->slot_of.assign(count, -1);
-    std::map<std::array<int, 3>, int> key_to_group;
+    std::map<std::array<int, 4>, int> key_to_group;
     for (int k = 0; k < count; ++k) {
         HostJob& hj = b->jobs[k];
         int rc = jobs[k].data_on_device ? BN_EINVAL : validate_and_plan(&jobs[k], hj);
@@ -1011,7 +1013,9 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
         hj.data_copy.assign(jobs[k].data ? jobs[k].data : (const uint8_t*)"",
                             jobs[k].data ? jobs[k].data + (size_t)P.m * P.n : (const uint8_t*)"");
         hj.data = hj.data_copy.data();
-        const std::array<int, 3> key{P.n, P.d, P.prec};
+        // step 1 of a group is one launch per kernel, so its jobs also share
+        // the choice of score kernel (binary data or not)
+        const std::array<int, 4> key{P.n, P.d, P.prec, P.allbin};
         auto it = key_to_group.find(key);
         if (it == key_to_group.end()) {
             it = key_to_group.emplace(key, (int)b->groups.size()).first;
@@ -1059,30 +1063,39 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
         const BatchGroup& g = b->groups[b->group_of[k]];
         const Layout& L = g.L;
         char* jb = b->arena + g.base + (size_t)b->slot_of[k] * g.P.js;
-        std::vector<double> lr(hj.P.d + 1, 0.0), alpha(hj.P.rows);
+        // the group's tables have g.P.rows rows: the rows past the job's own
+        // hold a denominator no lookup asks for (the table stays sorted) and
+        // alpha = 1
+        std::vector<double> lr(hj.P.d + 1, 0.0), alpha(g.P.rows, 1.0), dv(g.P.rows, 1e300);
         for (size_t t = 0; t < hj.log_rho.size(); ++t) lr[t] = hj.log_rho[t];
-        for (int r = 0; r < hj.P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
+        for (int r = 0; r < hj.P.rows; ++r) {
+            alpha[r] = hj.ess / hj.Dvals[r];
+            dv[r] = hj.Dvals[r];
+        }
+        const int mj = hj.P.m;
         ok = (hj.P.m == 0 || cudaMemcpy(jb + L.data, hj.data, (size_t)hj.P.m * hj.P.n,
                                         cudaMemcpyHostToDevice) == cudaSuccess) &&
+             cudaMemcpy(jb + L.mj, &mj, 4, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(jb + L.arity, hj.arity.data(), hj.P.n, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(jb + L.log_rho, lr.data(), lr.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(jb + L.Dvals, hj.Dvals.data(), hj.Dvals.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(jb + L.Dvals, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(jb + L.alpha, alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
     }
     // schedules: cached, timed, or the default
     for (auto& g : b->groups) {
         if (!ok) break;
         if (c->flags & BN_CTX_NO_AUTOTUNE) continue;
-        const std::array<int, 4> key{g.P.n, g.P.d, g.P.prec, g.P.nj};
+        const std::array<int, 5> key{g.P.n, g.P.d, g.P.prec, g.P.allbin, g.P.nj};
         auto it = c->tuned.find(key);
         if (it != c->tuned.end()) {
-            g.P.up13 = it->second[0];
-            g.P.frows = it->second[1];
-            g.P.g13 = it->second[2];
+            g.P.scfg = it->second[0];
+            g.P.up13 = it->second[1];
+            g.P.frows = it->second[2];
+            g.P.g13 = it->second[3];
             continue;
         }
         ok = tune_group(b, g, cap) == BN_OK;
-        if (ok) c->tuned[key] = {g.P.up13, g.P.frows, g.P.g13};
+        if (ok) c->tuned[key] = {g.P.scfg, g.P.up13, g.P.frows, g.P.g13};
     }
     ok = ok && cudaStreamSynchronize(cap) == cudaSuccess;
     if (ok && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
@@ -1140,11 +1153,12 @@ int bn_batch_describe(bn_batch* b, char* buf, size_t len)
     char line[256];
     for (const auto& g : b->groups) {
         std::snprintf(line, sizeof line,
-                      "n=%d d=%d %s jobs=%d up13=%d frows=%d g13=%d %s"
-                      " ms(up %.3f/%.3f fr %.3f/%.3f g %.3f/%.3f)\n",
-                      g.P.n, g.P.d, g.P.prec == 0 ? "fp64" : "fp32", g.P.nj, g.P.up13, g.P.frows,
+                      "n=%d d=%d %s %s jobs=%d scfg=%d up13=%d frows=%d g13=%d %s"
+                      " ms(sc %.3f/%.3f up %.3f/%.3f fr %.3f/%.3f g %.3f/%.3f)\n",
+                      g.P.n, g.P.d, g.P.prec == 0 ? "fp64" : "fp32",
+                      g.P.allbin ? "binary" : "general", g.P.nj, g.P.scfg, g.P.up13, g.P.frows,
                       g.P.g13, g.timed ? "timed" : "default-or-cached", g.ms[0][0], g.ms[0][1],
-                      g.ms[1][0], g.ms[1][1], g.ms[2][0], g.ms[2][1]);
+                      g.ms[1][0], g.ms[1][1], g.ms[2][0], g.ms[2][1], g.ms[3][0], g.ms[3][1]);
         s += line;
     }
     std::snprintf(buf, len, "%s", s.c_str());

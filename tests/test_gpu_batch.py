@@ -1,12 +1,14 @@
 """Batches: many independent small jobs replayed as one CUDA graph
-(bn_batch_create / bn_batch_run / bn_batch_results).  Jobs with equal n, d
-and precision share the launches of steps 2-5.
+(bn_batch_create / bn_batch_run / bn_batch_results).  Jobs with equal n, d,
+precision and kind of data (binary or not) share every launch of steps 1-5.
 
 Under the default schedule each job's result equals the same job run alone
 bit for bit (the same kernels, every reduction in a fixed order).  With the
 autotuner on, a group may run other kernels for a step; its results then
 agree with the job run alone within the stated tolerances (1e-9 FP64, 1e-4
 FP32), and are identical on every replay."""
+import collections
+
 import numpy as np
 import pytest
 
@@ -58,7 +60,10 @@ def test_autotuned_batch_within_tolerance_and_cached(torch_cuda, precision):
         descs = [B.Job(ds.data, ds.arity, d, precision=precision) for ds, d in jobs]
         with B.Batch(ctx.h, descs) as batch:
             text = batch.describe()
-            assert text.count("timed") == len({(ds.n, d) for ds, d in jobs}), text
+            # groups are (n, d, binary data or not); the autotuner times each
+            groups = collections.Counter((ds.n, d, bool(np.all(ds.arity == 2))) for ds, d in jobs)
+            assert len(text.strip().splitlines()) == len(groups), text
+            assert text.count("timed") == len(groups), text
             first = []
             for rep in range(2):
                 batch.run()
