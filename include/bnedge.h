@@ -82,9 +82,12 @@ typedef struct bn_ctx_opts {
     int32_t flags;           /* BN_CTX_* bits, 0 = defaults                   */
 } bn_ctx_opts;
 
-/* bn_ctx_opts.flags: batches keep the default schedule instead of timing the
- * alternatives (see bn_batch_create). */
+/* bn_ctx_opts.flags: BN_CTX_NO_AUTOTUNE, batches keep the default schedule
+ * instead of timing the alternatives; BN_CTX_CLUSTER_STEP3, every FP32 batch
+ * group with n >= 5 runs step 3 in the persistent cluster kernel whatever
+ * the timing says (see bn_batch_create). */
 #define BN_CTX_NO_AUTOTUNE 1
+#define BN_CTX_CLUSTER_STEP3 2
 
 typedef struct bn_job_desc {
     int32_t n;               /* number of variables                           */
@@ -187,13 +190,21 @@ int bn_edge_posteriors_static(const bn_job_desc* job, double* post_dev,
  * layout padded to the group's largest m, arity and lgamma table, and every
  * launch of steps 1-5 covers the whole group.
  * Unless the context has BN_CTX_NO_AUTOTUNE, the schedule of each group --
- * the kernels of the up-zeta (13-dimension tiles or shared-memory tiles), of
- * F and R' (16-subset rows or warp tiles, FP32) and of the down-zeta phase 1
- * -- is chosen by timing each alternative on the group's own data, and the
- * choice is cached in the context for later batches with the same group
- * shape.  Every schedule gives the same values up to rounding (within the
- * stated tolerances, 1e-9 FP64 and 1e-4 FP32, of the job run alone; equal
- * bit for bit under the default schedule).  The launches of all groups are
+ * the kernel of the scores (one lane per 64-sample word or one lane per
+ * parent configuration, non-binary data), of the up-zeta (13-dimension
+ * tiles or shared-memory tiles), of F and R' (16-subset rows or warp tiles,
+ * FP32; then one launch per popcount level or one persistent launch of
+ * thread-block clusters, each cluster taking F or R' of one job at a time
+ * and running all its levels between cluster barriers) and of the down-zeta
+ * phase 1 -- is chosen by timing: the groups run at the same time, so the
+ * autotuner times the whole batch on its own data, switching one kernel
+ * choice at a time for all groups, the groups with n <= 14 or those with
+ * n > 14, and keeps a switch that makes the batch more than 1% faster.  The
+ * choices are cached in the context; a later batch whose group shapes are
+ * all cached takes them without timing.  Every schedule gives the same
+ * values up to rounding (within the stated tolerances, 1e-9 FP64 and 1e-4
+ * FP32, of the job run alone; equal bit for bit under the default schedule
+ * and with the cluster kernel).  The launches of all groups are
  * recorded into one CUDA graph, one branch per group.  bn_batch_run replays
  * the graph on `stream` (NULL = the context's stream) without host
  * synchronisation: one graph launch runs the whole batch.  bn_batch_results

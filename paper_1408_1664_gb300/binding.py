@@ -148,6 +148,7 @@ def bn_job_footprint(job: "Job") -> int:
 
 
 BN_CTX_NO_AUTOTUNE = 1
+BN_CTX_CLUSTER_STEP3 = 2
 
 
 def bn_ctx_create(device: int = 0, slots: int = 4, mem_budget: int = 0,
@@ -335,9 +336,10 @@ class Context:
     """Owns one bn_ctx."""
 
     def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0,
-                 fail_alloc_after: int = -1, autotune: bool = True):
-        self.h = bn_ctx_create(device, slots, mem_budget, fail_alloc_after,
-                               0 if autotune else BN_CTX_NO_AUTOTUNE)
+                 fail_alloc_after: int = -1, autotune: bool = True,
+                 cluster_step3: bool = False):
+        flags = (0 if autotune else BN_CTX_NO_AUTOTUNE) | (BN_CTX_CLUSTER_STEP3 if cluster_step3 else 0)
+        self.h = bn_ctx_create(device, slots, mem_budget, fail_alloc_after, flags)
 
     def close(self):
         if self.h:

@@ -25,6 +25,7 @@ struct Plan {
     int g13 = 0;          // step 4 phase 1 by the 13-dimension tiles (n >= 14)
     int frows = 0;        // FP32 step 3 by the 16-subset row kernels
     int scfg = 0;         // step 1 by one lane per parent configuration (non-binary data)
+    int frc = 0;          // FP32 step 3 of a batch group by the persistent cluster kernel
     // Batch groups: nj jobs with equal plans, their arrays js bytes apart;
     // the launches of steps 2-5 cover all of them (gridDim.y = nj).
     int nj = 1;
@@ -63,6 +64,10 @@ cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs
 // Step 3 in FP32 with one thread per 16-subset tile (bn_levels.cu).
 bool rows_levels_fit(const Plan& P);      // FP32 and 5 <= n < 32
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
+// F and R' of every job of a batch group in one persistent launch of
+// thread-block clusters (FP32, rows_levels_fit); one launch.
+cudaError_t launch_rows_cluster(const Plan& P, const void* A, void* F, void* Rc, cudaStream_t s,
+                                int* launches);
 cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStream_t s,
                                  int* launches);
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);

@@ -16,6 +16,8 @@
 // term and s rescaled only when a term exceeds m by more than 2^64, so a term
 // costs one exponential.  s stays below 2^64 * 32 and every value entering is
 // finite (A and F are logs of positive sums).
+#include <algorithm>
+
 #include "bn_device.cuh"
 #include "bn_kernels.cuh"
 
@@ -44,12 +46,16 @@ __host__ __device__ constexpr int squeeze4(int x, int i)
     return (x & ((1 << i) - 1)) | ((x >> 1) & ~((1 << i) - 1));
 }
 
-__device__ __forceinline__ void load16(const float* p, float (&v)[LN], bool stream)
+// Load modes: LD_PLAIN, LD_STREAM (read once: evict first), LD_L2 (through
+// L2 only: values another block of the same launch wrote).
+enum { LD_PLAIN = 0, LD_STREAM = 1, LD_L2 = 2 };
+
+__device__ __forceinline__ void load16(const float* p, float (&v)[LN], int mode)
 {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
     for (int k = 0; k < LN / 4; ++k) {
-        const float4 x = stream ? __ldcs(q + k) : q[k];
+        const float4 x = mode == LD_STREAM ? __ldcs(q + k) : mode == LD_L2 ? __ldcg(q + k) : q[k];
         v[4 * k] = x.x;
         v[4 * k + 1] = x.y;
         v[4 * k + 2] = x.z;
@@ -96,22 +102,12 @@ __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
     for (int x = threadIdx.x; x < BT * BT; x += blockDim.x) bt[x / BT][x % BT] = g_binom_lanes.v[x / BT][x % BT];
 }
 
-}  // namespace
-
+// The 16 values of F in tile Ht (its level's tiles of F already written):
 //   F(S) = sum_{i in S} A_i(S - {i}) F(S - {i}),  F(empty) = 1
-__global__ void __launch_bounds__(256, 3)
-k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ F,
-               size_t js)
+template <int FMODE>
+__device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const float* __restrict__ A,
+                                             float* __restrict__ F)
 {
-    A = job_ptr(A, js);
-    F = job_ptr(F, js);
-    __shared__ uint32_t bt[BT][BT];
-    fill_table(bt);
-    __syncthreads();
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ntiles) return;
-    const int nh = n - LB;
-    const uint32_t Ht = tile_of(g, hl, nh, bt);
     const size_t half = (size_t)1 << (n - 1);
     using L = LogOps<float>;
 
@@ -123,8 +119,8 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, floa
         const int j = __ffs(rest) - 1;
         const uint32_t Hm = Ht & ~(1u << j);
         float a[LN], f[LN];
-        load16(A + (size_t)(LB + j) * half + ((size_t)squeeze(Hm, j) << LB), a, true);
-        load16(F + ((size_t)Hm << LB), f, false);
+        load16(A + (size_t)(LB + j) * half + ((size_t)squeeze(Hm, j) << LB), a, LD_STREAM);
+        load16(F + ((size_t)Hm << LB), f, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + f[l]);
     }
@@ -144,21 +140,14 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, floa
     store16(F + ((size_t)Ht << LB), Fv);
 }
 
+// The 16 values of R' in tile Ht (the tiles of the level above written):
 //   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),  R'(V) = 1
-__global__ void __launch_bounds__(256, 3)
-k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ Rc,
-                size_t js)
+template <int FMODE>
+__device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const float* __restrict__ A,
+                                              float* __restrict__ Rc)
 {
-    A = job_ptr(A, js);
-    Rc = job_ptr(Rc, js);
-    __shared__ uint32_t bt[BT][BT];
-    fill_table(bt);
-    __syncthreads();
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ntiles) return;
     const int nh = n - LB;
     const uint32_t hmask = (1u << nh) - 1u;
-    const uint32_t Ht = tile_of(g, hl, nh, bt);
     const size_t half = (size_t)1 << (n - 1);
     using L = LogOps<float>;
 
@@ -168,8 +157,8 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, flo
     for (uint32_t rest = ~Ht & hmask; rest; rest &= rest - 1) {
         const int j = __ffs(rest) - 1;
         float a[LN], r[LN];
-        load16(A + (size_t)(LB + j) * half + ((size_t)squeeze(Ht, j) << LB), a, true);
-        load16(Rc + ((size_t)(Ht | (1u << j)) << LB), r, false);
+        load16(A + (size_t)(LB + j) * half + ((size_t)squeeze(Ht, j) << LB), a, LD_STREAM);
+        load16(Rc + ((size_t)(Ht | (1u << j)) << LB), r, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + r[l]);
     }
@@ -187,6 +176,98 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, flo
         Rv[l] = m[l] + L::lg(s[l]);
     }
     store16(Rc + ((size_t)Ht << LB), Rv);
+}
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    // every thread of every block of the cluster; release/acquire at cluster
+    // scope orders the tiles written before it against the reads after it
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_blocks()
+{
+    uint32_t r;
+    asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256, 3)
+k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ F,
+               size_t js)
+{
+    A = job_ptr(A, js);
+    F = job_ptr(F, js);
+    __shared__ uint32_t bt[BT][BT];
+    fill_table(bt);
+    __syncthreads();
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ntiles) return;
+    forward_tile<LD_PLAIN>(n, tile_of(g, hl, n - LB, bt), A, F);
+}
+
+__global__ void __launch_bounds__(256, 3)
+k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ Rc,
+                size_t js)
+{
+    A = job_ptr(A, js);
+    Rc = job_ptr(Rc, js);
+    __shared__ uint32_t bt[BT][BT];
+    fill_table(bt);
+    __syncthreads();
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ntiles) return;
+    backward_tile<LD_PLAIN>(n, tile_of(g, hl, n - LB, bt), A, Rc);
+}
+
+// Step 3 of a whole batch group in one persistent launch of thread-block
+// clusters (1 to 8 blocks, by the width of the widest level).  Work item it is F (it even) or R' (it odd) of job it / 2; the
+// clusters take the items in turn (item = cluster id, + clusters, ...).  A
+// cluster runs every popcount level of its item: its blocks' threads split
+// the level's tiles, then meet at a cluster barrier before the next level.
+// The blocks of a cluster are resident together by construction, and no
+// cluster waits for another, so every barrier completes.  Every thread
+// reaches every barrier: the item loop and the level loop are uniform
+// across the cluster.  F and R' tiles written in the launch are read
+// through L2 (another block, on another SM, wrote them).
+__global__ void __launch_bounds__(256, 2)
+k_rows_cluster(int n, int items, const float* __restrict__ A, float* __restrict__ F,
+               float* __restrict__ Rc, size_t js)
+{
+    __shared__ uint32_t bt[BT][BT];
+    fill_table(bt);
+    __syncthreads();
+    const int nh = n - LB;
+    const uint32_t cs = cluster_blocks();
+    const uint32_t cid = blockIdx.x / cs;
+    const uint32_t ncl = gridDim.x / cs;
+    const uint32_t t0 = cluster_rank() * blockDim.x + threadIdx.x;
+    const uint32_t stride = cs * blockDim.x;
+    for (int it = (int)cid; it < items; it += (int)ncl) {
+        const size_t off = (size_t)(it >> 1) * js;
+        const float* Aj = reinterpret_cast<const float*>(reinterpret_cast<const char*>(A) + off);
+        const bool fwd = (it & 1) == 0;
+        float* X = reinterpret_cast<float*>(reinterpret_cast<char*>(fwd ? F : Rc) + off);
+        for (int st = 0; st <= nh; ++st) {
+            const int hl = fwd ? st : nh - st;
+            const uint32_t nt = bt[nh][hl];
+            for (uint32_t g = t0; g < nt; g += stride) {
+                const uint32_t Ht = tile_of(g, hl, nh, bt);
+                if (fwd) forward_tile<LD_L2>(n, Ht, Aj, X);
+                else backward_tile<LD_L2>(n, Ht, Aj, X);
+            }
+            cluster_barrier();
+        }
+    }
 }
 
 namespace {
@@ -233,6 +314,35 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
         if (launches) ++*launches;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_rows_cluster(const Plan& P, const void* A, void* F, void* Rc, cudaStream_t s,
+                                int* launches)
+{
+    // blocks per cluster: one 256-thread block per 256 tiles of the largest
+    // level, at most 8 (the portable cluster size)
+    const int nh = P.n - LB;
+    const uint64_t widest = choose(nh, nh / 2);
+    const unsigned kCluster = (unsigned)std::min<uint64_t>(8, (widest + 255) / 256);
+    const int items = 2 * P.nj;
+    // at most two blocks per SM: 152 * 2 blocks at once
+    const unsigned clusters = (unsigned)std::min(items, 152 * 2 / (int)kCluster);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(clusters * kCluster, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_rows_cluster, P.n, items, (const float*)A, (float*)F,
+                                       (float*)Rc, P.js);
+    if (e == cudaSuccess && launches) ++*launches;
+    return e;
 }
 
 }  // namespace bn

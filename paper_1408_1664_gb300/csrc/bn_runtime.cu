@@ -446,8 +446,8 @@ struct bn_ctx {
     uint64_t reserved = 0;
     // batches
     int flags = 0;
-    // (n, d, prec, binary, jobs) -> schedule (scfg, up13, frows, g13)
-    std::map<std::array<int, 5>, std::array<int, 4>> tuned;
+    // (n, d, prec, binary, jobs) -> schedule (scfg, up13, frows, frc, g13)
+    std::map<std::array<int, 5>, std::array<int, 5>> tuned;
 };
 
 // Jobs of a batch with equal n, d and precision: their arrays lie js bytes
@@ -459,7 +459,6 @@ struct BatchGroup {
     size_t base = 0;           // arena offset of the group's first job
     std::vector<int> members;  // indices into bn_batch::jobs
     bool timed = false;        // schedule chosen by timing (else default or cached)
-    float ms[4][2] = {};       // timings of the alternatives: scores, up-zeta, F/R', Gamma
 };
 
 struct bn_batch {
@@ -476,6 +475,7 @@ struct bn_batch {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t last = nullptr;
     bool ran = false;
+    float ms_default = 0.0f, ms_tuned = 0.0f;   // whole-batch times seen by the autotuner
 };
 
 namespace {
@@ -912,7 +912,9 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
         CK(bn::launch_upzeta(G, reinterpret_cast<const uint32_t*>(at(L.cmasks)), at(L.lbs),
                              at(L.tab), reinterpret_cast<const uint16_t*>(at(L.rk13)), at(L.A), s));
     if (stages & 4u) {
-        if (side && side->s) {
+        if (G.frc) {
+            CK(bn::launch_rows_cluster(G, at(L.A), at(L.F), at(L.Rc), s, nullptr));
+        } else if (side && side->s) {
             CK(cudaEventRecord(side->fork, s));
             CK(cudaStreamWaitEvent(side->s, side->fork, 0));
             CK(bn::launch_backward(G, at(L.A), at(L.Rc), side->s, nullptr));
@@ -940,56 +942,122 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
     return BN_OK;
 }
 
-// Mean device time (ms) of `stages` of group g under plan P: one warm-up run
-// and three timed runs on stream s.
-int time_stages(const bn_batch* b, const BatchGroup& g, const Plan& P, unsigned stages,
-                cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* ms)
+// Every group of the batch on its branch stream (R' beside F), forked from
+// and joined back into stream s: the work of one bn_batch_run.
+int enqueue_batch(const bn_batch* b, cudaStream_t s)
 {
-    BatchGroup t = g;
-    t.P = P;
-    int rc = enqueue_group(b, t, s, stages);
-    if (rc) return rc;
-    CK(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) {
-        rc = enqueue_group(b, t, s, stages);
+    const int nb = (int)b->streams.size();
+    CK(cudaEventRecord(b->fork, s));
+    for (auto st : b->streams) CK(cudaStreamWaitEvent(st, b->fork, 0));
+    for (size_t q = 0; q < b->groups.size(); ++q) {
+        const int rc = enqueue_group(b, b->groups[q], b->streams[q % nb], 31u, &b->sides[q % nb]);
         if (rc) return rc;
     }
-    CK(cudaEventRecord(e1, s));
-    CK(cudaEventSynchronize(e1));
-    CK(cudaEventElapsedTime(ms, e0, e1));
+    for (int q = 0; q < nb; ++q) {
+        CK(cudaEventRecord(b->joins[q], b->streams[q]));
+        CK(cudaStreamWaitEvent(s, b->joins[q], 0));
+    }
+    return BN_OK;
+}
+
+// The whole batch under the groups' current plans, captured from stream s
+// into an executable graph (nullptr on failure).
+cudaGraphExec_t capture_batch(const bn_batch* b, cudaStream_t s, cudaGraph_t* graph)
+{
+    *graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+    const bool cap_ok = enqueue_batch(b, s) == BN_OK;
+    cudaGraph_t gr = nullptr;
+    const bool end_ok = cudaStreamEndCapture(s, &gr) == cudaSuccess;
+    cudaGraphExec_t exec = nullptr;
+    if (cap_ok && end_ok && gr && cudaGraphInstantiate(&exec, gr, 0) == cudaSuccess) {
+        *graph = gr;
+        return exec;
+    }
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    return nullptr;
+}
+
+// Mean device time (ms) of one replay of the batch's graph under the
+// groups' current plans: the graph bn_batch_run would launch, one warm-up
+// replay and three timed ones.
+int time_batch(const bn_batch* b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* ms)
+{
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = capture_batch(b, s, &gr);
+    if (!ex) return BN_ECUDA;
+    cudaError_t e = cudaGraphLaunch(ex, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; e == cudaSuccess && r < 3; ++r) e = cudaGraphLaunch(ex, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return BN_ECUDA;
     *ms /= 3.0f;
     return BN_OK;
 }
 
-// The autotuner: for every stage with alternatives that fit, time each on
-// the group's own data (steps before it computed once with the default
-// schedule) and keep the fastest.  The stages are independent given their
-// inputs, so they are tuned one at a time.
-int tune_group(const bn_batch* b, BatchGroup& g, cudaStream_t s)
+// The autotuner.  The groups of a batch run at the same time, so a kernel
+// that wins alone (by spreading over the whole GPU) can lose in the mix; the
+// objective is therefore the time of the whole batch, on its own data.
+// Starting from the default schedules, each knob in turn -- step 1 score
+// kernel, step 2 tiles, step 3 rows, step 3 cluster kernel, step 4 tiles --
+// is switched to its alternative for three sets of groups where it fits
+// (all, those with n <= 14, those with n > 14); the fastest batch is kept
+// when it beats the current one by more than 1%.
+int tune_batch(bn_batch* b, cudaStream_t s)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
         return BN_ECUDA;
     }
-    int rc = enqueue_group(b, g, s, 31u);
-    struct Knob { int Plan::*flag; bool fits; unsigned stage; };
-    const Knob knobs[4] = {{&Plan::scfg, bn::scores_cfg_fits(g.P), 1u},
-                           {&Plan::up13, bn::tile13_up_fits(g.P), 2u},
-                           {&Plan::frows, bn::rows_levels_fit(g.P), 4u},
-                           {&Plan::g13, bn::tile13_gamma_fits(g.P), 8u}};
-    for (int k = 0; rc == BN_OK && k < 4; ++k) {
-        if (!knobs[k].fits) continue;
-        for (int alt = 0; rc == BN_OK && alt < 2; ++alt) {
-            Plan P = g.P;
-            P.*(knobs[k].flag) = alt;
-            rc = time_stages(b, g, P, knobs[k].stage, s, e0, e1, &g.ms[k][alt]);
+    struct Knob { int Plan::*flag; bool (*fits)(const Plan&); };
+    const Knob knobs[5] = {{&Plan::scfg, bn::scores_cfg_fits}, {&Plan::up13, bn::tile13_up_fits},
+                           {&Plan::frows, bn::rows_levels_fit}, {&Plan::frc, bn::rows_levels_fit},
+                           {&Plan::g13, bn::tile13_gamma_fits}};
+    const bool forced_frc = (b->ctx->flags & BN_CTX_CLUSTER_STEP3) != 0;
+    float best = 0.0f;
+    int rc = time_batch(b, s, e0, e1, &best);
+    b->ms_default = best;
+    for (int k = 0; rc == BN_OK && k < 5; ++k) {
+        if (knobs[k].flag == &Plan::frc && forced_frc) continue;
+        std::vector<Plan> keep;
+        for (auto& g : b->groups) keep.push_back(g.P);
+        std::vector<int> best_sel;                  // groups switched in the best candidate
+        for (int cand = 0; rc == BN_OK && cand < 3; ++cand) {
+            std::vector<int> sel;
+            for (size_t q = 0; q < b->groups.size(); ++q) {
+                const Plan& P = keep[q];
+                const bool in = cand == 0 || (cand == 1 ? P.n <= 14 : P.n > 14);
+                if (in && knobs[k].fits(P)) sel.push_back((int)q);
+            }
+            if (sel.empty()) continue;
+            for (int q : sel) {
+                Plan& P = b->groups[q].P;
+                P.*(knobs[k].flag) = 1 - P.*(knobs[k].flag);
+            }
+            float t = 0.0f;
+            rc = time_batch(b, s, e0, e1, &t);
+            for (int q : sel) b->groups[q].P = keep[q];
+            if (rc == BN_OK && t < 0.99f * best) {
+                best = t;
+                best_sel = sel;
+            }
         }
-        if (rc == BN_OK) g.P.*(knobs[k].flag) = g.ms[k][1] <= g.ms[k][0] ? 1 : 0;
+        for (int q : best_sel) {
+            Plan& P = b->groups[q].P;
+            P.*(knobs[k].flag) = 1 - P.*(knobs[k].flag);
+        }
     }
+    b->ms_tuned = best;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc == BN_OK) g.timed = true;
+    if (rc == BN_OK)
+        for (auto& g : b->groups) g.timed = true;
     return rc;
 }
 
@@ -1081,40 +1149,35 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
              cudaMemcpy(jb + L.Dvals, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(jb + L.alpha, alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
     }
-    // schedules: cached, timed, or the default
-    for (auto& g : b->groups) {
-        if (!ok) break;
-        if (c->flags & BN_CTX_NO_AUTOTUNE) continue;
-        const std::array<int, 5> key{g.P.n, g.P.d, g.P.prec, g.P.allbin, g.P.nj};
-        auto it = c->tuned.find(key);
-        if (it != c->tuned.end()) {
-            g.P.scfg = it->second[0];
-            g.P.up13 = it->second[1];
-            g.P.frows = it->second[2];
-            g.P.g13 = it->second[3];
-            continue;
+    // schedules: the default, forced, cached (when every group's shape is in
+    // the context's cache) or timed
+    for (auto& g : b->groups)
+        if (c->flags & BN_CTX_CLUSTER_STEP3) g.P.frc = bn::rows_levels_fit(g.P);
+    auto key_of = [](const Plan& P) {
+        return std::array<int, 5>{P.n, P.d, P.prec, P.allbin, P.nj};
+    };
+    if (ok && !(c->flags & BN_CTX_NO_AUTOTUNE)) {
+        bool all_cached = true;
+        for (const auto& g : b->groups) all_cached = all_cached && c->tuned.count(key_of(g.P)) > 0;
+        if (all_cached) {
+            for (auto& g : b->groups) {
+                const auto& v = c->tuned[key_of(g.P)];
+                g.P.scfg = v[0];
+                g.P.up13 = v[1];
+                g.P.frows = v[2];
+                g.P.frc = v[3];
+                g.P.g13 = v[4];
+            }
+        } else {
+            ok = tune_batch(b, cap) == BN_OK;
+            for (const auto& g : b->groups)
+                if (ok) c->tuned[key_of(g.P)] = {g.P.scfg, g.P.up13, g.P.frows, g.P.frc, g.P.g13};
         }
-        ok = tune_group(b, g, cap) == BN_OK;
-        if (ok) c->tuned[key] = {g.P.scfg, g.P.up13, g.P.frows, g.P.g13};
     }
     ok = ok && cudaStreamSynchronize(cap) == cudaSuccess;
-    if (ok && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        bool cap_ok = cudaEventRecord(b->fork, cap) == cudaSuccess;
-        for (auto st : b->streams) cap_ok = cap_ok && cudaStreamWaitEvent(st, b->fork, 0) == cudaSuccess;
-        for (size_t q = 0; cap_ok && q < b->groups.size(); ++q)
-            cap_ok = enqueue_group(b, b->groups[q], b->streams[q % nb], 31u,
-                                   &b->sides[q % nb]) == BN_OK;
-        for (int q = 0; cap_ok && q < nb; ++q)
-            cap_ok = cudaEventRecord(b->joins[q], b->streams[q]) == cudaSuccess &&
-                     cudaStreamWaitEvent(cap, b->joins[q], 0) == cudaSuccess;
-        cudaGraph_t gr = nullptr;
-        const bool end_ok = cudaStreamEndCapture(cap, &gr) == cudaSuccess;
-        if (cap_ok && end_ok && gr && cudaGraphInstantiate(&b->exec, gr, 0) == cudaSuccess) {
-            b->graph = gr;
-            rc = BN_OK;
-        } else if (gr) {
-            cudaGraphDestroy(gr);
-        }
+    if (ok) {
+        b->exec = capture_batch(b, cap, &b->graph);
+        if (b->exec) rc = BN_OK;
     }
     cudaGetLastError();
     if (rc) { bn_batch_destroy(b); return rc; }
@@ -1153,12 +1216,12 @@ int bn_batch_describe(bn_batch* b, char* buf, size_t len)
     char line[256];
     for (const auto& g : b->groups) {
         std::snprintf(line, sizeof line,
-                      "n=%d d=%d %s %s jobs=%d scfg=%d up13=%d frows=%d g13=%d %s"
-                      " ms(sc %.3f/%.3f up %.3f/%.3f fr %.3f/%.3f g %.3f/%.3f)\n",
+                      "n=%d d=%d %s %s jobs=%d scfg=%d up13=%d frows=%d frc=%d g13=%d %s"
+                      " batch_ms(default %.3f tuned %.3f)\n",
                       g.P.n, g.P.d, g.P.prec == 0 ? "fp64" : "fp32",
                       g.P.allbin ? "binary" : "general", g.P.nj, g.P.scfg, g.P.up13, g.P.frows,
-                      g.P.g13, g.timed ? "timed" : "default-or-cached", g.ms[0][0], g.ms[0][1],
-                      g.ms[1][0], g.ms[1][1], g.ms[2][0], g.ms[2][1], g.ms[3][0], g.ms[3][1]);
+                      g.P.frc, g.P.g13, g.timed ? "timed" : "default-or-cached", b->ms_default,
+                      b->ms_tuned);
         s += line;
     }
     std::snprintf(buf, len, "%s", s.c_str());

@@ -50,6 +50,47 @@ def test_default_schedule_equals_alone_over_replays(torch_cuda, precision):
                     assert lpd == lpd0
 
 
+def test_cluster_step3_equals_alone(torch_cuda):
+    """Step 3 in the persistent cluster kernel (forced for every FP32 group):
+    the same 16-subset tiles as the per-level row launches, in the same
+    order, so every job equals the job run alone bit for bit -- over two
+    replays, with groups from n = 10 to 18 and more items than clusters."""
+    jobs = _jobs(48, first=100)
+    assert min(ds.n for ds, _ in jobs) <= 11 and max(ds.n for ds, _ in jobs) >= 17
+    with B.Context(0, autotune=False, cluster_step3=True) as ctx:
+        alone = [ctx.edge_posteriors(ds.data, ds.arity, d, precision="fp32") for ds, d in jobs]
+        descs = [B.Job(ds.data, ds.arity, d, precision="fp32") for ds, d in jobs]
+        with B.Batch(ctx.h, descs) as batch:
+            text = batch.describe()
+            assert all(" frc=1 " in line for line in text.strip().splitlines()), text
+            for _ in range(2):
+                batch.run()
+                for k, (post0, lpd0) in enumerate(alone):
+                    post, lpd = batch.results(k)
+                    assert np.array_equal(post, post0), k
+                    assert lpd == lpd0
+
+
+def test_cluster_step3_many_jobs_one_group(torch_cuda):
+    """24 jobs at n = 18 (8-block clusters): 48 work items over at most 38
+    clusters, so some clusters run a second item after the first."""
+    d = 3
+    rng = np.random.default_rng(5)
+    jobs = []
+    for t in range(24):
+        ds = datagen.random_dag_data(18, int(rng.integers(100, 400)), 2, d, 1.0, seed=4000 + t)
+        jobs.append((ds, d))
+    with B.Context(0, autotune=False, cluster_step3=True) as ctx:
+        alone = [ctx.edge_posteriors(ds.data, ds.arity, d, precision="fp32") for ds, d in jobs]
+        with B.Batch(ctx.h, [B.Job(ds.data, ds.arity, d, precision="fp32")
+                             for ds, d in jobs]) as batch:
+            batch.run()
+            for k, (post0, lpd0) in enumerate(alone):
+                post, lpd = batch.results(k)
+                assert np.array_equal(post, post0), k
+                assert lpd == lpd0
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_autotuned_batch_within_tolerance_and_cached(torch_cuda, precision):
     jobs = _jobs(24, first=40)
