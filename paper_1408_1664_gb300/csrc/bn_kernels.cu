@@ -14,6 +14,7 @@
 #include "bn_device.cuh"
 #include "bn_kernels.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace bn {
@@ -60,33 +61,59 @@ __global__ void k_check_data(const uint8_t* __restrict__ data, const uint8_t* __
     }
 }
 
-// T[row*(m+1) + N] = lgamma(alpha_row + N) - lgamma(alpha_row), N = 0..m.
+// T[row*(m+1) + N] = [lgamma(alpha_row + N) - lgamma(alpha_row)] * scale,
+// N = 0..m, rounded to an integer: the fixed-point table (scale = 2^S) the
+// score kernels sum exactly in int64.
+// In a batch group fxj holds each job's (scale, 1/scale) and mj its own m:
+// entries past the job's m stay 0 (no count reaches them).
 __global__ void k_lgamma_table(const double* __restrict__ alpha, int rows, int m,
-                               double* __restrict__ T, size_t js)
+                               long long* __restrict__ T, size_t js, double scale,
+                               const double* __restrict__ fxj, const int* __restrict__ mj)
 {
     alpha = job_ptr(alpha, js);
     T = job_ptr(T, js);
+    if (fxj) scale = job_ptr(fxj, js)[0];
+    const int mown = mj ? *job_ptr(mj, js) : m;
     const int64_t total = (int64_t)rows * (m + 1);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int row = (int)(t / (m + 1));
         const int N = (int)(t % (m + 1));
         const double a = alpha[row];
-        T[t] = N == 0 ? 0.0 : lgamma(a + (double)N) - lgamma(a);
+        T[t] = (N == 0 || N > mown) ? 0ll
+                                    : __double2ll_rn((lgamma(a + (double)N) - lgamma(a)) * scale);
     }
 }
 
-__device__ __forceinline__ int find_row(const double* Dvals, int rows, double D)
+// Bit pattern of the double equal to the integer q >= 1, by integer
+// operations only.
+__device__ __forceinline__ long long double_bits(uint32_t q)
 {
+    const int e = 31 - __clz(q);
+    return ((long long)(1023 + e) << 52) | (long long)(((uint64_t)q << (52 - e)) & ((1ull << 52) - 1));
+}
+
+// Row of the denominator D in the sorted table of denominators.  Positive
+// doubles are ordered like their bit patterns, so the search compares
+// integers: the FP64 pipe, narrow on this GPU, is not used.
+__device__ __forceinline__ int find_row(const double* Dvals, int rows, uint32_t D)
+{
+    const long long key = double_bits(D);
     int lo = 0, hi = rows - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (Dvals[mid] < D) lo = mid + 1; else hi = mid;
+        if (__double_as_longlong(Dvals[mid]) < key) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 
 __device__ __forceinline__ double warp_sum(double x)
+{
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+__device__ __forceinline__ long long warp_sum(long long x)
 {
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
     return x;
@@ -115,6 +142,7 @@ template <> __device__ __forceinline__ float from_fixed<float>(unsigned long lon
         masks = job_ptr(masks, js);                                                       \
         cmasks = job_ptr(cmasks, js);                                                     \
         logB = job_ptr(logB, js);                                                         \
+        if (fxj) tinv = job_ptr(fxj, js)[1];                                              \
     } while (0)
 
 // One warp per family x = i*K + f.  Counts N_jk = popc(AND of bit planes),
@@ -124,9 +152,10 @@ template <> __device__ __forceinline__ float from_fixed<float>(unsigned long lon
 __global__ void __launch_bounds__(256)
 k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__ arity,
          const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
-         const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
+         const long long* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
          int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-         double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
+         double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js, double tinv,
+         const double* __restrict__ fxj)
 {
     BN_JOB_SCORES();
     arity = job_ptr(arity, js);
@@ -144,23 +173,23 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
         int par[32];
         int rad[32];
         int np = 0;
-        double q = 1.0;
+        uint32_t q = 1;                             // at most 65536 cells
         for (uint32_t g = G; g; g &= g - 1) {
             const int p = __ffs(g) - 1;
             par[np] = p;
             rad[np] = arity[p];
-            q *= (double)arity[p];
+            q *= arity[p];
             ++np;
         }
         const int ri = arity[i];
         const int row_q = find_row(Dvals, rows, q);
-        const int row_qr = find_row(Dvals, rows, q * ri);
-        const double* Tq = T + (size_t)row_q * (m + 1);
-        const double* Tqr = T + (size_t)row_qr * (m + 1);
+        const int row_qr = find_row(Dvals, rows, q * (uint32_t)ri);
+        const long long* Tq = T + (size_t)row_q * (m + 1);
+        const long long* Tqr = T + (size_t)row_qr * (m + 1);
         const int64_t qi = (int64_t)q;
         int dig[32];
         for (int t = 0; t < np; ++t) dig[t] = 0;
-        double acc = 0.0;
+        long long acc = 0;
         for (int64_t cfg = 0; cfg < qi; ++cfg) {
             uint32_t Nj = 0;
             for (int xv = 0; xv < ri; ++xv) {
@@ -187,7 +216,7 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
         }
         acc = warp_sum(acc);
         if (lane == 0) {
-            logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+            logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
             masks[x] = G;
             cmasks[x] = cm;
         }
@@ -210,10 +239,11 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
 // The bit planes (n * 2 * W words) stay in L1.
 __global__ void __launch_bounds__(128)
 k_scores_bin(int n, int m, int W, int64_t K, int64_t Kc, const uint64_t* __restrict__ planes,
-             const double* __restrict__ Dvals, int rows, const double* __restrict__ T,
+             const double* __restrict__ Dvals, int rows, const long long* __restrict__ T,
              const double* __restrict__ log_rho, int64_t x_begin, int64_t x_count,
              uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-             double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
+             double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js, double tinv,
+         const double* __restrict__ fxj)
 {
     BN_JOB_SCORES();
     __shared__ uint32_t bt[32][5];                  // C(a, b), b <= 4, for the unrank
@@ -273,10 +303,10 @@ k_scores_bin(int n, int m, int W, int64_t K, int64_t Kc, const uint64_t* __restr
             cnt[2 * j + 1] += (uint32_t)__popcll(E[j] & c1);
         }
     }
-    const double q = (double)(1 << k);
-    const double* Tq = T + (size_t)find_row(Dvals, rows, q) * (m + 1);
-    const double* Tqr = T + (size_t)find_row(Dvals, rows, 2.0 * q) * (m + 1);
-    double acc = 0.0;
+    const uint32_t q = 1u << k;
+    const long long* Tq = T + (size_t)find_row(Dvals, rows, q) * (m + 1);
+    const long long* Tqr = T + (size_t)find_row(Dvals, rows, 2u * q) * (m + 1);
+    long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         acc -= Tq[cnt[2 * j] + cnt[2 * j + 1]];
@@ -289,7 +319,7 @@ k_scores_bin(int n, int m, int W, int64_t K, int64_t Kc, const uint64_t* __restr
         for (int c = 0; c < 32; ++c)
             if (c < cells) debug_counts[c] = cnt[c];
     }
-    logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+    logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
     masks[x] = G;
     cmasks[x] = cm;
 }
@@ -309,9 +339,10 @@ template <int HB>
 __global__ void __launch_bounds__(128)
 k_scores_bin_hi(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
                 const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
-                const double* __restrict__ T, const double* __restrict__ log_rho, int64_t f_begin,
+                const long long* __restrict__ T, const double* __restrict__ log_rho, int64_t f_begin,
                 int64_t f_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-                double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
+                double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js, double tinv,
+         const double* __restrict__ fxj)
 {
     BN_JOB_SCORES();
     constexpr int k = 4 + HB;
@@ -380,10 +411,10 @@ k_scores_bin_hi(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
             cnt[2 * j + 1] += (uint32_t)__popcll(E[j] & c1);
         }
     }
-    const double q = (double)(1 << k);
-    const double* Tq = T + (size_t)find_row(Dvals, rows, q) * (m + 1);
-    const double* Tqr = T + (size_t)find_row(Dvals, rows, 2.0 * q) * (m + 1);
-    double acc = 0.0;
+    const uint32_t q = 1u << k;
+    const long long* Tq = T + (size_t)find_row(Dvals, rows, q) * (m + 1);
+    const long long* Tqr = T + (size_t)find_row(Dvals, rows, 2u * q) * (m + 1);
+    long long acc = 0;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         acc -= Tq[cnt[2 * j] + cnt[2 * j + 1]];
@@ -399,7 +430,7 @@ k_scores_bin_hi(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
     }
     if (h == 0) {
         const int64_t x = (int64_t)i * K + off + (int64_t)(g % Ck);
-        logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+        logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
         masks[x] = G;
         cmasks[x] = cm;
     }
@@ -414,9 +445,10 @@ template <int MP, int MR>
 __global__ void __launch_bounds__(256)
 k_scores_w(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__ arity,
            const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
-           const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
+           const long long* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
            int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-           double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
+           double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js, double tinv,
+         const double* __restrict__ fxj)
 {
     BN_JOB_SCORES();
     arity = job_ptr(arity, js);
@@ -456,12 +488,12 @@ k_scores_w(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__
 #pragma unroll
         for (int v = 0; v < MR; ++v)
             cw[v] = (v < ri && has_word) ? planes[((size_t)i * rmax + v) * W + lane] : 0ull;
-        const double* Tq = T + (size_t)find_row(Dvals, rows, (double)q) * (m + 1);
-        const double* Tqr = T + (size_t)find_row(Dvals, rows, (double)q * ri) * (m + 1);
+        const long long* Tq = T + (size_t)find_row(Dvals, rows, (uint32_t)q) * (m + 1);
+        const long long* Tqr = T + (size_t)find_row(Dvals, rows, (uint32_t)(q * ri)) * (m + 1);
         int dig[MP];
 #pragma unroll
         for (int t = 0; t < MP; ++t) dig[t] = 0;
-        double acc = 0.0;
+        long long acc = 0;
         uint32_t cur = 0, curj = 0;
         int cell = 0;
         for (int cfg = 0; cfg < q; ++cfg) {
@@ -503,7 +535,7 @@ k_scores_w(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__
         if ((q & 31) != 0 && lane < (q & 31)) acc -= Tq[curj];
         acc = warp_sum(acc);
         if (lane == 0) {
-            logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+            logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
             masks[x] = G;
             cmasks[x] = cm;
         }
@@ -521,9 +553,10 @@ template <int MP, int MR>
 __global__ void __launch_bounds__(256)
 k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__ arity,
              const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
-             const double* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
+             const long long* __restrict__ T, const double* __restrict__ log_rho, int64_t x_begin,
              int64_t x_count, uint32_t* __restrict__ masks, uint32_t* __restrict__ cmasks,
-             double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js)
+             double* __restrict__ logB, int64_t* __restrict__ debug_counts, size_t js, double tinv,
+         const double* __restrict__ fxj)
 {
     BN_JOB_SCORES();
     arity = job_ptr(arity, js);
@@ -553,10 +586,10 @@ k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict
             }
         }
         const int ri = arity[i];
-        const double* Tq = T + (size_t)find_row(Dvals, rows, (double)q) * (m + 1);
-        const double* Tqr = T + (size_t)find_row(Dvals, rows, (double)q * ri) * (m + 1);
+        const long long* Tq = T + (size_t)find_row(Dvals, rows, (uint32_t)q) * (m + 1);
+        const long long* Tqr = T + (size_t)find_row(Dvals, rows, (uint32_t)(q * ri)) * (m + 1);
         const uint64_t* cp = planes + (size_t)i * rmax * W;
-        double acc = 0.0;
+        long long acc = 0;
         for (int j0 = 0; j0 < q; j0 += 32) {
             const int j = j0 + lane;
             if (j < q) {
@@ -594,7 +627,7 @@ k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict
         }
         acc = warp_sum(acc);
         if (lane == 0) {
-            logB[x] = acc + (log_rho ? log_rho[k] : 0.0);
+            logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
             masks[x] = G;
             cmasks[x] = cm;
         }
@@ -1187,11 +1220,25 @@ cudaError_t launch_check_data(const uint8_t* data, const uint8_t* arity, int n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T, cudaStream_t s,
-                                int nj, size_t js)
+int fixed_shift(int m, double ess, const double* Dvals, int rows)
+{
+    double L = std::log1p((double)m);
+    for (int r = 0; r < rows; ++r) {
+        const double a = ess / Dvals[r];
+        L = std::max(L, std::max(std::fabs(std::log(a)), std::log(a + (double)m)));
+    }
+    const double B = 2.0 * (double)m * L + 1.0;
+    const int S = 61 - (int)std::ceil(std::log2(B));
+    return std::min(52, std::max(8, S));
+}
+
+cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, int fxs, void* T,
+                                cudaStream_t s, int nj, size_t js, const double* fxj,
+                                const int* mj)
 {
     const int64_t total = (int64_t)rows * (m + 1);
-    k_lgamma_table<<<dim3(grid_for(total, 256), nj), 256, 0, s>>>(alpha, rows, m, T, js);
+    k_lgamma_table<<<dim3(grid_for(total, 256), nj), 256, 0, s>>>(
+        alpha, rows, m, (long long*)T, js, std::ldexp(1.0, fxs), fxj, mj);
     return cudaGetLastError();
 }
 
@@ -1201,10 +1248,13 @@ static uint32_t host_binom(int n, int k);
 // and one k_scores_bin_hi launch per larger family size.  The range is all
 // families or a single one.
 static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, const double* Dvals,
-                                     const double* T, const double* log_rho, int64_t x_begin,
+                                     const void* Tv, const double* log_rho, int64_t x_begin,
                                      int64_t x_count, uint32_t* masks, uint32_t* cmasks,
-                                     double* logB, int64_t* debug_counts, cudaStream_t s)
+                                     double* logB, int64_t* debug_counts, cudaStream_t s,
+                                     const double* fxj)
 {
+    const long long* T = static_cast<const long long*>(Tv);
+    const double tinv = std::ldexp(1.0, -P.fxs);
     int64_t off[10] = {0};
     for (int k = 0; k <= P.d; ++k) off[k + 1] = off[k] + host_binom(P.n - 1, k);
     const int dl = P.d < 4 ? P.d : 4;
@@ -1222,7 +1272,7 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
         const int64_t xn = x_count == 1 ? 1 : (int64_t)P.n * Kc;
         k_scores_bin<<<dim3((unsigned)((xn + 127) / 128), P.nj), 128, 0, s>>>(
             P.n, P.m, P.W, P.K, Kc, planes, Dvals, P.rows, T, log_rho, xb, xn, masks, cmasks, logB,
-            debug_counts, P.js);
+            debug_counts, P.js, tinv, fxj);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1235,7 +1285,7 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
 #define BN_BIN_HI(HB)                                                                             \
     k_scores_bin_hi<HB><<<dim3(grid, P.nj), 128, 0, s>>>(                                      \
         P.n, P.m, P.W, P.K, off[k], Ck, planes, Dvals, P.rows, T, log_rho, fb, fn, masks, cmasks, \
-        logB, debug_counts, P.js)
+        logB, debug_counts, P.js, tinv, fxj)
         switch (k) {
         case 5: BN_BIN_HI(1); break;
         case 6: BN_BIN_HI(2); break;
@@ -1260,44 +1310,47 @@ int scores_launches(const Plan& P)
 }
 
 cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* planes,
-                          const double* Dvals, const double* T, const double* log_rho,
+                          const double* Dvals, const void* Tv, const double* log_rho,
                           int64_t x_begin, int64_t x_count, uint32_t* masks, uint32_t* cmasks,
-                          double* logB, int64_t* debug_counts, cudaStream_t s)
+                          double* logB, int64_t* debug_counts, cudaStream_t s,
+                          const double* fxj)
 {
+    const long long* T = static_cast<const long long*>(Tv);
+    const double tinv = std::ldexp(1.0, -P.fxs);
     const int threads = 256;
     const int64_t warps_wanted = x_count;
     int grid = grid_for(warps_wanted * 32, threads, 152 * 64);
     if (P.allbin && P.d <= 8 && (x_count == 1 || (x_begin == 0 && x_count == (int64_t)P.n * P.K)))
-        return launch_scores_bin(P, planes, Dvals, T, log_rho, x_begin, x_count, masks, cmasks,
-                                 logB, debug_counts, s);
+        return launch_scores_bin(P, planes, Dvals, Tv, log_rho, x_begin, x_count, masks, cmasks,
+                                 logB, debug_counts, s, fxj);
     if (P.scfg && scores_cfg_fits(P) && P.d <= 4 && P.rmax <= 4)
         k_scores_cfg<4, 4><<<dim3(grid, P.nj), threads, 0, s>>>(
             P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals, P.rows, T, log_rho, x_begin, x_count,
-            masks, cmasks, logB, debug_counts, P.js);
+            masks, cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.scfg && scores_cfg_fits(P))
         k_scores_cfg<SC_MP, SC_MR><<<dim3(grid, P.nj), threads, 0, s>>>(
             P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals, P.rows, T, log_rho, x_begin, x_count,
-            masks, cmasks, logB, debug_counts, P.js);
+            masks, cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.W <= 32 && P.d <= 4 && P.rmax <= 2)
         k_scores_w<4, 2><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
-                                                  cmasks, logB, debug_counts, P.js);
+                                                  cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.W <= 32 && P.d <= 4 && P.rmax <= 4)
         k_scores_w<4, 4><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
-                                                  cmasks, logB, debug_counts, P.js);
+                                                  cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.W <= 32 && P.d <= 8 && P.rmax <= 4)
         k_scores_w<8, 4><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
-                                                  cmasks, logB, debug_counts, P.js);
+                                                  cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.d <= SC_MP && P.rmax <= SC_MR)
         k_scores_cfg<SC_MP, SC_MR><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                               P.rows, T, log_rho, x_begin, x_count, masks,
-                                              cmasks, logB, debug_counts, P.js);
+                                              cmasks, logB, debug_counts, P.js, tinv, fxj);
     else
         k_scores<<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                           P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
-                                          logB, debug_counts, P.js);
+                                          logB, debug_counts, P.js, tinv, fxj);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ struct Plan {
     int wb;               // in-warp bits of the F / R' tiles
     int prec;             // 0 = FP64, 1 = FP32
     int allbin = 0;       // every variable has arity 2
+    int fxs = 40;         // fixed-point shift of the lgamma table (fixed_shift)
     // Schedule (set by the planner, changed by the batch autotuner):
     int up13 = 0;         // step 2 by the 13-dimension tiles (n >= 14)
     int g13 = 0;          // step 4 phase 1 by the 13-dimension tiles (n >= 14)
@@ -39,13 +40,24 @@ cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int 
                                int nj = 1, size_t js = 0);
 cudaError_t launch_check_data(const uint8_t* data, const uint8_t* arity, int n, int m,
                               int* err, cudaStream_t s);
-cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, double* T,
-                                cudaStream_t s, int nj = 1, size_t js = 0);
+// The lgamma table T (rows x (m+1) int64) holds lgamma(alpha + N) - lgamma(alpha)
+// in fixed point, scaled by 2^fxs (fixed_shift); the scores sum it exactly.
+// A batch group passes fxj (each job's scale 2^S and 2^-S) and mj (each
+// job's m) at the job stride; fxs then is not used.
+cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, int fxs, void* T,
+                                cudaStream_t s, int nj = 1, size_t js = 0,
+                                const double* fxj = nullptr, const int* mj = nullptr);
+// The fixed-point shift S of the lgamma table: every partial sum of one
+// family's score, at most sum_j |T_q(N_j)| + sum_jk |T_qr(N_jk)| <= 2 m L
+// with L = max |ln(alpha + t)| over the rows (alpha = 1 included) and
+// 0 <= t < m, stays below 2^61 after scaling by 2^S; each term's rounding
+// error is at most 2^-(S+1).
+int fixed_shift(int m, double ess, const double* Dvals, int rows);
 cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* planes,
-                          const double* Dvals, const double* T, const double* log_rho,
+                          const double* Dvals, const void* T, const double* log_rho,
                           int64_t x_begin, int64_t x_count, uint32_t* masks,
                           uint32_t* cmasks, double* logB, int64_t* debug_counts,
-                          cudaStream_t s);
+                          cudaStream_t s, const double* fxj = nullptr);
 // Step 1 has the lane-per-configuration alternative (Plan::scfg): data not
 // all binary, at most 8 parents and arity at most 8.
 bool scores_cfg_fits(const Plan& P);

@@ -160,6 +160,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     if (rows < 0) return BN_ENOMEM;
     P.rows = rows;
     for (int r = 0; r < rows; ++r) tables[rows + r] = j->ess / tables[r];
+    P.fxs = bn::fixed_shift(P.m, j->ess, tables, rows);
     P.b_up = P.n - 1 < 12 ? P.n - 1 : 12;
     P.b_g = P.n - 1 < 13 ? P.n - 1 : 13;
     const int hg = P.n - 1 - P.b_g;
@@ -209,7 +210,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     const uint8_t* ar = base + o_ar;
     const double* Dvals = reinterpret_cast<const double*>(base + o_tab);
     const double* alpha = Dvals + rows;
-    double* lgT = reinterpret_cast<double*>(base + o_lgT);
+    void* lgT = base + o_lgT;                          // int64 fixed-point lgamma table
     uint64_t* planes = reinterpret_cast<uint64_t*>(base + o_pl);
     uint32_t* masks = reinterpret_cast<uint32_t*>(base + o_masks);
     uint32_t* cm = reinterpret_cast<uint32_t*>(base + o_cm);
@@ -217,7 +218,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     double* cmax = reinterpret_cast<double*>(base + o_cmax);
     if (j->data_on_device) CKS(bn::launch_check_data(data_dev, ar, P.n, P.m, err, s));
     CKS(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, planes, s));
-    CKS(bn::launch_lgamma_table(alpha, P.rows, P.m, lgT, s));
+    CKS(bn::launch_lgamma_table(alpha, P.rows, P.m, P.fxs, lgT, s));
     CKS(bn::launch_scores(P, ar, planes, Dvals, lgT,
                           j->log_rho ? reinterpret_cast<const double*>(base + o_lr) : nullptr, 0,
                           (int64_t)P.n * P.K, masks, cm, logB, nullptr, s));

@@ -54,8 +54,8 @@ struct HostJob {
 
 // Byte offsets of every array of a job inside one device allocation.
 struct Layout {
-    size_t data, mj, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB, cmax,
-        lbs, tab, rk13, A, F, Rc, W, Gam, eacc, post, logPD, dbg, total;
+    size_t data, mj, fx, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB,
+        cmax, lbs, tab, rk13, A, F, Rc, W, Gam, eacc, post, logPD, dbg, total;
 };
 
 Layout make_layout(const Plan& P, size_t dbg_cells)
@@ -68,6 +68,7 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     auto take = [&](size_t bytes) { size_t at = o; o += al(std::max<size_t>(bytes, 1)); return at; };
     L.data = take((size_t)P.m * P.n);
     L.mj = take(4);                  // the job's own m (batch groups pad m)
+    L.fx = take(16);                 // the job's lgamma-table scale 2^S and 2^-S (batches)
     L.arity = take(P.n);
     L.log_rho = take((size_t)(P.d + 1) * 8);
     L.Dvals = take((size_t)P.rows * 8);
@@ -161,6 +162,7 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
     hj.Dvals = denominators(hj.arity, P.d);
     if (hj.Dvals.size() > 16384) return BN_EINVAL;
     P.rows = (int)hj.Dvals.size();
+    P.fxs = bn::fixed_shift(P.m, j->ess, hj.Dvals.data(), P.rows);
     P.b_up = std::min(P.n - 1, 12);
     P.b_g = std::min(P.n - 1, 13);
     const int hg = P.n - 1 - P.b_g;
@@ -297,9 +299,9 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     const uint8_t* ar = B.at<uint8_t>(L.arity);
     if (hj.data_on_device) { CK(bn::launch_check_data(data_dev, ar, P.n, P.m, err, s)); ++nl; }
     CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s)); ++nl;
-    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, B.at<double>(L.lgT), s)); ++nl;
+    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, P.fxs, B.at<void>(L.lgT), s)); ++nl;
     CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals),
-                         B.at<double>(L.lgT), hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho),
+                         B.at<void>(L.lgT), hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho),
                          0, (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
                          B.at<double>(L.logB), nullptr, s));
     nl += bn::scores_launches(P);
@@ -749,8 +751,8 @@ int bn_scores(bn_ctx* c, const bn_job_desc* job, uint32_t* parent_mask, double* 
     const uint8_t* ar = B.at<uint8_t>(L.arity);
     if (hj.data_on_device) CK(bn::launch_check_data(data_dev, ar, P.n, P.m, B.at<int>(L.err), s));
     CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s));
-    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, B.at<double>(L.lgT), s));
-    CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals), B.at<double>(L.lgT),
+    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, P.fxs, B.at<void>(L.lgT), s));
+    CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals), B.at<void>(L.lgT),
                          hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho), 0,
                          (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
                          B.at<double>(L.logB), nullptr, s));
@@ -804,9 +806,9 @@ int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask,
     CK(cudaMemcpyAsync(B.at<char>(L.Dvals), hj.Dvals.data(), hj.Dvals.size() * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.at<char>(L.alpha), alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice, s));
     CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s));
-    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, B.at<double>(L.lgT), s));
+    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, P.fxs, B.at<void>(L.lgT), s));
     CK(bn::launch_scores(P, B.at<uint8_t>(L.arity), B.at<uint64_t>(L.planes), B.at<double>(L.Dvals),
-                         B.at<double>(L.lgT), nullptr, (int64_t)i * P.K + f, 1,
+                         B.at<void>(L.lgT), nullptr, (int64_t)i * P.K + f, 1,
                          B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks), B.at<double>(L.logB),
                          B.at<int64_t>(L.dbg), s));
     CK(cudaMemcpyAsync(counts, B.at<char>(L.dbg), (size_t)cells * 8, cudaMemcpyDeviceToHost, s));
@@ -890,15 +892,18 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
                                   G.W, reinterpret_cast<uint64_t*>(at(L.planes)), s,
                                   reinterpret_cast<const int*>(at(L.mj)), G.nj, G.js));
         CK(bn::launch_lgamma_table(reinterpret_cast<const double*>(at(L.alpha)), G.rows, G.m,
-                                   reinterpret_cast<double*>(at(L.lgT)), s, G.nj, G.js));
+                                   G.fxs, at(L.lgT), s, G.nj, G.js,
+                                   reinterpret_cast<const double*>(at(L.fx)),
+                                   reinterpret_cast<const int*>(at(L.mj))));
         CK(bn::launch_scores(G, reinterpret_cast<const uint8_t*>(at(L.arity)),
                              reinterpret_cast<const uint64_t*>(at(L.planes)),
                              reinterpret_cast<const double*>(at(L.Dvals)),
-                             reinterpret_cast<const double*>(at(L.lgT)),
+                             at(L.lgT),
                              reinterpret_cast<const double*>(at(L.log_rho)), 0,
                              (int64_t)G.n * G.K, reinterpret_cast<uint32_t*>(at(L.masks)),
                              reinterpret_cast<uint32_t*>(at(L.cmasks)),
-                             reinterpret_cast<double*>(at(L.logB)), nullptr, s));
+                             reinterpret_cast<double*>(at(L.logB)), nullptr, s,
+                             reinterpret_cast<const double*>(at(L.fx))));
         CK(bn::launch_node_max(G, reinterpret_cast<const double*>(at(L.logB)),
                                reinterpret_cast<double*>(at(L.cmax)), s));
         CK(bn::launch_shift_scores(G, reinterpret_cast<const double*>(at(L.logB)),
@@ -1141,9 +1146,12 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
             dv[r] = hj.Dvals[r];
         }
         const int mj = hj.P.m;
+        // the job's own fixed-point shift, as when it runs alone
+        const double fx[2] = {std::ldexp(1.0, hj.P.fxs), std::ldexp(1.0, -hj.P.fxs)};
         ok = (hj.P.m == 0 || cudaMemcpy(jb + L.data, hj.data, (size_t)hj.P.m * hj.P.n,
                                         cudaMemcpyHostToDevice) == cudaSuccess) &&
              cudaMemcpy(jb + L.mj, &mj, 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(jb + L.fx, fx, 16, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(jb + L.arity, hj.arity.data(), hj.P.n, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(jb + L.log_rho, lr.data(), lr.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(jb + L.Dvals, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
