@@ -58,6 +58,10 @@ def parse():
                     help="the n and d sweep of the paper's experiments (prints one JSON table)")
     ap.add_argument("--subset-n", type=int, default=0,
                     help="use only the first N variables of the workload (profiling)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the 256-job batched workload (prints its JSON object)")
+    ap.add_argument("--batch-reps", type=int, default=5,
+                    help="timed replays of the batch graph")
     ap.add_argument("--degree", type=int, default=0,
                     help="override the workload's in-degree bound d (profiling)")
     return ap.parse_args()
@@ -122,9 +126,12 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def kernel_source_sha() -> str:
+KERNEL_SOURCES = ("bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_device.cuh")
+
+
+def kernel_source_sha(files=KERNEL_SOURCES) -> str:
     h = hashlib.sha1()
-    for f in ("bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_device.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1408_1664_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -132,17 +139,18 @@ def kernel_source_sha() -> str:
 
 def committed_traffic(kernel: str, workload: str, precision: str):
     """dram bytes per launch from a committed ncu summary, only if it was
-    taken on the current kernel source."""
+    taken on the current source of the kernel: each line names the files the
+    kernel is compiled from (src=a+b) and their hash at the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = kernel_source_sha()
     for line in open(path):
         if line.startswith("#") or not line.strip():
             continue
         kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
         if (kv.get("kernel") == kernel and kv.get("workload") == workload
-                and kv.get("precision") == precision and kv.get("src_sha") == sha):
+                and kv.get("precision") == precision and "src" in kv
+                and kv.get("src_sha") == kernel_source_sha(tuple(kv["src"].split("+")))):
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -380,6 +388,37 @@ def run_batched(binding, torch, device: int, jobs_n: int = 256, reps: int = 5) -
     return out
 
 
+def run_batched_only(args) -> None:
+    """The 256-job batch under the default schedule (what the autotuner
+    keeps for this workload): two warm-up replays and --batch-reps timed
+    replays of its graph; used for launch lists."""
+    import torch
+
+    from paper_1408_1664_gb300 import binding
+
+    binding.load(build_if_missing=True)
+    jobs = [datagen.batched_job(j) for j in range(256)]
+    with binding.Context(0, autotune=False) as ctx:
+        batch = binding.Batch(ctx.h, [binding.Job(ds.data, ds.arity, d, precision="fp32")
+                                      for ds, d in jobs])
+        stream = torch.cuda.Stream()
+        for _ in range(2):
+            batch.run(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.batch_reps):
+            batch.run(stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / args.batch_reps
+        groups = len(batch.describe().strip().splitlines())
+        batch.close()
+    print(json.dumps({"batched_default_schedule": {"jobs": 256, "groups": groups,
+                                                   "ms_per_batch": ms,
+                                                   "jobs_per_s": 256 / (ms / 1e3)}}))
+
+
 # ---------------------------------------------------------------- sweep --
 def run_sweep(args) -> None:
     """Time the FP32 path over the configurations of the paper's experiments
@@ -610,6 +649,8 @@ def main():
     args = parse()
     if args.sweep:
         run_sweep(args)
+    elif args.batched_only:
+        run_batched_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
