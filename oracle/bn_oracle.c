@@ -15,15 +15,15 @@
  *      samples, and the BDeu local score  log B_i(G) = log rho(|G|) +
  *      log p(x_i | x_G)  (Eq. 6; the paper leaves p unspecified, Section 2.1,
  *      this oracle reads it as BDeu with equivalent sample size `ess`);
- *   2. A_i(S) = sum_{G subset S, |G|<=d} B_i(G)  (Eq. 7 with q_i = 1) by the
+ *   2. A_i(S) = q_i(S) sum_{G subset S, |G|<=d} B_i(G)  (Eq. 7) by the
  *      truncated upward zeta transform of Definition 1, run serially one
  *      dimension j = 1..n at a time with the guards of Algorithm 2;
  *   3. F(S) = sum_{i in S} A_i(S-{i}) F(S-{i}), F(empty) = 1  (Eq. 9),
  *      lattice level by lattice level (Section 3.1.1);
  *   4. R(S) = sum_{i in S} A_i(V-S) R(S-{i}), R(empty) = 1  (Eq. 10);
- *   5. Gamma_v(G) = sum_{G subset S subset V-{v}} F(S) R(V-{v}-S)  (Eq. 12)
- *      by the truncated downward zeta transform of Definition 2, run serially
- *      with the guards of Algorithm 3;
+ *   5. Gamma_v(G) = sum_{G subset S subset V-{v}} q_v(S) F(S) R(V-{v}-S)
+ *      (Eq. 12) by the truncated downward zeta transform of Definition 2, run
+ *      serially with the guards of Algorithm 3;
  *   6. P(u->v, D) = sum_{G: u in G, |G|<=d} B_v(G) Gamma_v(G)  (Eq. 11);
  *   7. P(u->v | D) = P(u->v, D) / F(V)  (Algorithm 1, last step).
  *
@@ -35,10 +35,16 @@
  * parent configuration of a family is a mixed-radix number with the
  * lowest-numbered parent least significant; cell index = config * r_i + x_i.
  *
+ * A single modular feature f (Eqs. 5-9): B_i carries f_i, P(f, D) = F(V)
+ * computed from those B_i, and P(f | D) = P(f, D) / P(D)
+ * (orc_feature_posterior).
+ *
  * Readings where the paper is silent: BDeu local scores (alpha_jk =
- * ess/(r_i q_i), alpha_j = ess/q_i); q_i = 1; rho_i(G) = exp(log_rho[|G|])
- * (all ones when log_rho is NULL); an in-degree bound d > n-1 is the same as
- * d = n-1.
+ * ess/(r_i q_i), alpha_j = ess/q_i); rho_i(G) = exp(log_rho[|G|] + log_w[i,G])
+ * (log_rho per parent-set size and log_w per family, each zero when NULL);
+ * q_i(S) = exp(log_q[i * n + |S|]), a function of the size of the
+ * predecessor set (all ones when log_q is NULL); an in-degree bound d > n-1
+ * is the same as d = n-1.
  *
  * Loops over independent nodes i and endpoints v, and over the subsets of
  * one lattice level, carry OpenMP pragmas; the arithmetic is unchanged by
@@ -311,6 +317,38 @@ void orc_backward(int n, const double* A, double* R)
     }
 }
 
+int orc_edge_posteriors_ext(int n, int d, int m, const uint8_t* data,
+                            const uint8_t* arity, double ess, const double* log_rho,
+                            const double* log_q, const double* log_w,
+                            double* post, double* log_PD, double* A_out,
+                            double* F_out, double* R_out, double* Gamma_out,
+                            double* logB_out, uint32_t* mask_out);
+
+/* Step 2 for every node: A_i = q_i * (truncated upward zeta transform of B_i
+ * over V), with s(S) = 0 for S containing i (footnote to Section 3.1.2) and
+ * A_i(S) = 0 there.  A is [i * 2^n + S]; logB / masks are [i * K + f]. */
+static int build_A(int n, int d, int64_t K, const uint32_t* masks, const double* logB,
+                   const double* log_q, double* A)
+{
+    const size_t N = (size_t)1 << n;
+    int rc = ORC_OK;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; i++) {
+        double* s = (double*)malloc(N * sizeof(double));
+        double* Ai = A + (size_t)i * N;
+        if (!s) { rc = ORC_ENOMEM; continue; }
+        for (size_t S = 0; S < N; S++) s[S] = -INFINITY;
+        for (int64_t f = 0; f < K; f++) s[masks[(size_t)i * K + f]] = logB[(size_t)i * K + f];
+        if (orc_upzeta(n, d, s, Ai)) rc = ORC_ENOMEM;
+        for (size_t S = 0; S < N; S++) {
+            if (S >> i & 1u) Ai[S] = -INFINITY;
+            else if (log_q) Ai[S] += log_q[(size_t)i * n + popc((uint32_t)S)];   /* Eq. 7 */
+        }
+        free(s);
+    }
+    return rc;
+}
+
 /* Algorithm 1 end to end.  post: n*n; log_PD: log F(V) = log P(D).
  * Optional stage outputs (NULL to skip): A_out [n * 2^n] (A_i(S), zero where
  * i is in S), F_out / R_out [2^n], Gamma_out [n * K] and logB_out / mask_out
@@ -320,6 +358,21 @@ int orc_edge_posteriors(int n, int d, int m, const uint8_t* data,
                         double* post, double* log_PD, double* A_out,
                         double* F_out, double* R_out, double* Gamma_out,
                         double* logB_out, uint32_t* mask_out)
+{
+    return orc_edge_posteriors_ext(n, d, m, data, arity, ess, log_rho, NULL, NULL, post,
+                                   log_PD, A_out, F_out, R_out, Gamma_out, logB_out,
+                                   mask_out);
+}
+
+/* As orc_edge_posteriors, with the order prior q_i(S) by size (log_q, n*n,
+ * row i: log q_i for |S| = 0..n-1) and per-family log weights (log_w, n*K in
+ * canonical family order, added to log B_i(G)); either may be NULL. */
+int orc_edge_posteriors_ext(int n, int d, int m, const uint8_t* data,
+                            const uint8_t* arity, double ess, const double* log_rho,
+                            const double* log_q, const double* log_w,
+                            double* post, double* log_PD, double* A_out,
+                            double* F_out, double* R_out, double* Gamma_out,
+                            double* logB_out, uint32_t* mask_out)
 {
     int rc = validate(n, d, m, data, arity);
     if (rc) return rc;
@@ -336,23 +389,14 @@ int orc_edge_posteriors(int n, int d, int m, const uint8_t* data,
     double* G = (double*)malloc((size_t)n * K * sizeof(double));
     if (!masks || !logB || !A || !F || !R || !G) { rc = ORC_ENOMEM; goto done; }
 
-    /* Step 1: local scores. */
+    /* Step 1: local scores, times the per-family weights. */
     rc = orc_scores(n, d, m, data, arity, ess, log_rho, masks, logB);
     if (rc) goto done;
+    if (log_w)
+        for (int64_t x = 0; x < (int64_t)n * K; x++) logB[x] += log_w[x];
 
-    /* Step 2: A_i = truncated upward zeta transform of B_i over V, with
-     * s(S) = 0 for S containing i (footnote to Section 3.1.2). */
-    #pragma omp parallel for schedule(dynamic, 1)
-    for (int i = 0; i < n; i++) {
-        double* s = (double*)malloc(N * sizeof(double));
-        double* Ai = A + (size_t)i * N;
-        if (!s) { rc = ORC_ENOMEM; continue; }
-        for (size_t S = 0; S < N; S++) s[S] = -INFINITY;
-        for (int64_t f = 0; f < K; f++) s[masks[(size_t)i * K + f]] = logB[(size_t)i * K + f];
-        if (orc_upzeta(n, d, s, Ai)) rc = ORC_ENOMEM;
-        for (size_t S = 0; S < N; S++) if (S >> i & 1u) Ai[S] = -INFINITY;
-        free(s);
-    }
+    /* Step 2. */
+    rc = build_A(n, d, K, masks, logB, log_q, A);
     if (rc) goto done;
 
     /* Steps 3 and 4. */
@@ -369,6 +413,7 @@ int orc_edge_posteriors(int n, int d, int m, const uint8_t* data,
         for (size_t Sx = 0; Sx < N; Sx++) {
             const uint32_t S = (uint32_t)Sx;
             s[S] = (S & bv) ? -INFINITY : F[S] + R[(full & ~bv) & ~S];
+            if (log_q && !(S & bv)) s[S] += log_q[(size_t)v * n + popc(S)];   /* Eq. 12 */
         }
         if (orc_downzeta(n, d, s, t)) rc = ORC_ENOMEM;
         for (int64_t f = 0; f < K; f++) G[(size_t)v * K + f] = t[masks[(size_t)v * K + f]];
@@ -394,5 +439,51 @@ int orc_edge_posteriors(int n, int d, int m, const uint8_t* data,
     if (mask_out) memcpy(mask_out, masks, (size_t)n * K * sizeof(uint32_t));
 done:
     free(masks); free(logB); free(A); free(F); free(R); free(G);
+    return rc;
+}
+
+/* One modular feature f = prod_i f_i(G_i) (Eqs. 5-9): with B^f_i(G) =
+ * B_i(G) f_i(G) (log_f, n*K in canonical family order, log f_i(G); -inf for
+ * f_i(G) = 0), P(f, D) = F^f(V) from the recursion of Eq. 9 over the A^f_i of
+ * Eq. 7, and P(f | D) = F^f(V) / F(V) (the second run with f = 1).  log_q,
+ * log_w and log_rho as in orc_edge_posteriors_ext.  Outputs: *p = P(f | D),
+ * *log_PfD = log P(f, D) (either may be NULL). */
+int orc_feature_posterior(int n, int d, int m, const uint8_t* data, const uint8_t* arity,
+                          double ess, const double* log_rho, const double* log_q,
+                          const double* log_w, const double* log_f, double* p,
+                          double* log_PfD)
+{
+    int rc = validate(n, d, m, data, arity);
+    if (rc) return rc;
+    if (!log_f) return ORC_EINVAL;
+    d = clamp_d(n, d);
+    const size_t N = (size_t)1 << n;
+    const uint32_t full = (uint32_t)(N - 1);
+    const int64_t K = orc_num_families(n, d);
+    uint32_t* masks = (uint32_t*)malloc((size_t)n * K * sizeof(uint32_t));
+    double* logB = (double*)malloc((size_t)n * K * sizeof(double));
+    double* logBf = (double*)malloc((size_t)n * K * sizeof(double));
+    double* A = (double*)malloc((size_t)n * N * sizeof(double));
+    double* F = (double*)malloc(N * sizeof(double));
+    double lpd = 0.0, lpfd = 0.0;
+    if (!masks || !logB || !logBf || !A || !F) { rc = ORC_ENOMEM; goto done; }
+    rc = orc_scores(n, d, m, data, arity, ess, log_rho, masks, logB);
+    if (rc) goto done;
+    for (int64_t x = 0; x < (int64_t)n * K; x++) {
+        if (log_w) logB[x] += log_w[x];
+        logBf[x] = logB[x] + log_f[x];                  /* B_i(G) f_i(G) */
+    }
+    rc = build_A(n, d, K, masks, logB, log_q, A);       /* f = 1: P(D) */
+    if (rc) goto done;
+    orc_forward(n, A, F);
+    lpd = F[full];
+    rc = build_A(n, d, K, masks, logBf, log_q, A);      /* P(f, D) */
+    if (rc) goto done;
+    orc_forward(n, A, F);
+    lpfd = F[full];
+    if (p) *p = exp(lpfd - lpd);
+    if (log_PfD) *log_PfD = lpfd;
+done:
+    free(masks); free(logB); free(logBf); free(A); free(F);
     return rc;
 }

@@ -76,6 +76,13 @@ def lib():
         L.orc_edge_posteriors.argtypes = [C.c_int, C.c_int, C.c_int, _u8p, _u8p, C.c_double,
                                           _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
                                           _f64p, _u32p]
+        L.orc_edge_posteriors_ext.restype = C.c_int
+        L.orc_edge_posteriors_ext.argtypes = [C.c_int, C.c_int, C.c_int, _u8p, _u8p,
+                                              C.c_double, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                              _f64p, _f64p, _f64p, _f64p, _f64p, _u32p]
+        L.orc_feature_posterior.restype = C.c_int
+        L.orc_feature_posterior.argtypes = [C.c_int, C.c_int, C.c_int, _u8p, _u8p, C.c_double,
+                                            _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
     return _lib
 
 
@@ -168,11 +175,21 @@ def backward(n: int, A) -> np.ndarray:
     return R
 
 
+def _f64_or_none(a, size: int):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.shape[0] != size:
+        raise ValueError(f"expected {size} values, got {a.shape[0]}")
+    return a
+
+
 def edge_posteriors(data, arity, d: int, ess: float = 1.0, log_rho=None,
-                    stages: bool = False) -> dict:
+                    stages: bool = False, log_q=None, log_w=None) -> dict:
     """Run Algorithm 1.  Returns {'post': (n, n), 'log_PD': float} and, with
     ``stages``, also 'A' (n, 2^n), 'F', 'R' (2^n), 'Gamma', 'logB', 'masks'
-    (n, K)."""
+    (n, K).  log_q (n, n): log q_i(S) by |S| (Eq. 4, 7, 12); log_w (n, K): per
+    family log weights added to log B (a general rho_i(G))."""
     data, arity = _prep(data, arity)
     n = arity.shape[0]
     K = num_families(n, d)
@@ -185,8 +202,11 @@ def edge_posteriors(data, arity, d: int, ess: float = 1.0, log_rho=None,
         st = dict(A=np.empty((n, N)), F=np.empty(N), R=np.empty(N),
                   Gamma=np.empty((n, K)), logB=np.empty((n, K)),
                   masks=np.empty((n, K), dtype=np.uint32))
-    rc = lib().orc_edge_posteriors(
+    lq = _f64_or_none(log_q, n * n)
+    lw = _f64_or_none(log_w, n * K)
+    rc = lib().orc_edge_posteriors_ext(
         n, d, data.shape[0], _p(data, _u8p), _p(arity, _u8p), ess, _p(lr, _f64p),
+        _p(lq, _f64p), _p(lw, _f64p),
         _p(post, _f64p), _p(lpd, _f64p), _p(st.get("A"), _f64p), _p(st.get("F"), _f64p),
         _p(st.get("R"), _f64p), _p(st.get("Gamma"), _f64p), _p(st.get("logB"), _f64p),
         _p(st.get("masks"), _u32p))
@@ -195,3 +215,24 @@ def edge_posteriors(data, arity, d: int, ess: float = 1.0, log_rho=None,
     out = dict(post=post, log_PD=float(lpd[0]))
     out.update(st)
     return out
+
+
+def feature_posterior(data, arity, d: int, log_f, ess: float = 1.0, log_rho=None,
+                      log_q=None, log_w=None) -> tuple[float, float]:
+    """P(f | D) and log P(f, D) of the modular feature with log f_i(G) =
+    log_f[i, f] (n, K; -inf where f_i(G) = 0), Eqs. 5-9."""
+    data, arity = _prep(data, arity)
+    n = arity.shape[0]
+    K = num_families(n, d)
+    lf = _f64_or_none(log_f, n * K)
+    lq = _f64_or_none(log_q, n * n)
+    lw = _f64_or_none(log_w, n * K)
+    lr = None if log_rho is None else np.ascontiguousarray(log_rho, dtype=np.float64)
+    p = np.zeros(1)
+    lpfd = np.zeros(1)
+    rc = lib().orc_feature_posterior(n, d, data.shape[0], _p(data, _u8p), _p(arity, _u8p), ess,
+                                     _p(lr, _f64p), _p(lq, _f64p), _p(lw, _f64p), _p(lf, _f64p),
+                                     _p(p, _f64p), _p(lpfd, _f64p))
+    if rc:
+        raise ValueError(f"oracle feature_posterior: error {rc}")
+    return float(p[0]), float(lpfd[0])

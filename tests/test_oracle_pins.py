@@ -375,3 +375,124 @@ def test_golden_small_config_regression():
     out = orc.edge_posteriors(ds.data, ds.arity, d)
     assert abs(out["log_PD"] - lpd) < 1e-9
     np.testing.assert_allclose(out["post"], want, atol=1e-12, rtol=0)
+
+
+# ------------------------------------- order prior q, family weights, features --
+
+def brute_force_general(n, masks, logB, log_q=None, log_f=None):
+    """Eq. 5 written out over all n! orders, with the order prior q_i(L_i) of
+    Eq. 4 (log_q[i, |L_i|]) and a modular feature (log_f[i] per family, as
+    logB): returns (log P(f, D), {(u, v): log P(u->v, f=1 elsewhere, D)})."""
+    fam = [dict(zip(masks[i].tolist(), logB[i].tolist())) for i in range(n)]
+    ff = None if log_f is None else [dict(zip(masks[i].tolist(), log_f[i].tolist()))
+                                     for i in range(n)]
+    tot, joint = [], {}
+    for perm in itertools.permutations(range(n)):
+        pre = 0
+        w = 0.0
+        node_terms = {}
+        edge_terms = {}
+        for v in perm:
+            q = 0.0 if log_q is None else log_q[v][bin(pre).count("1")]
+            subs = [G for G in subsets_of(pre) if G in fam[v]]
+            t = q + lse_list([fam[v][G] + (0.0 if ff is None else ff[v][G]) for G in subs])
+            node_terms[v] = t
+            w += t
+            for u in range(n):
+                if pre >> u & 1:
+                    edge_terms[(u, v)] = q + lse_list([fam[v][G] for G in subs if G >> u & 1])
+            pre |= 1 << v
+        tot.append(w)
+        if ff is None:
+            for (u, v), e in edge_terms.items():
+                joint.setdefault((u, v), []).append(w - node_terms[v] + e)
+    return lse_list(tot), {k: lse_list(ws) for k, ws in joint.items()}
+
+
+def _rand_q_w(n, K, rng, zeros=0.0):
+    log_q = rng.normal(0.0, 1.5, size=(n, n))
+    log_w = rng.normal(0.0, 1.0, size=(n, K))
+    if zeros:
+        log_w[rng.random((n, K)) < zeros] = -math.inf
+        log_w[:, 0] = 0.0                                  # keep every node a parent set
+    return log_q, log_w
+
+
+@pytest.mark.parametrize("n,d,arity,seed", [(4, 2, 3, 31), (5, 3, [2, 3, 2, 2, 4], 32),
+                                            (6, 2, 2, 33)])
+def test_order_prior_and_family_weights_match_orders(n, d, arity, seed):
+    """q_i(S) by |S| (Eq. 4, 7, 12) and per-family weights (a general
+    rho_i(G)), some of them zero: Algorithm 1 against the sum over orders."""
+    ds = datagen.random_dag_data(n, 90, arity, min(d, 3), 0.6, seed=seed)
+    masks, logB = orc.scores(ds.data, ds.arity, d)
+    rng = np.random.default_rng(seed)
+    log_q, log_w = _rand_q_w(n, masks.shape[1], rng, zeros=0.25)
+    out = orc.edge_posteriors(ds.data, ds.arity, d, log_q=log_q, log_w=log_w)
+    lpd, joint = brute_force_general(n, masks, logB + log_w, log_q=log_q)
+    assert abs(out["log_PD"] - lpd) < 1e-11 * max(1.0, abs(lpd))
+    want = np.zeros((n, n))
+    for (u, v), lj in joint.items():
+        want[u, v] = math.exp(lj - lpd)
+    np.testing.assert_allclose(out["post"], want, atol=1e-12, rtol=0)
+
+
+def test_constant_order_prior_changes_only_the_normaliser():
+    """q_i(S) = c_i for every S scales every order by prod_i c_i: posteriors
+    unchanged, log P(D) shifted by sum_i log c_i."""
+    ds = datagen.random_dag_data(7, 200, 2, 3, 0.8, seed=34)
+    c = np.linspace(-2.0, 3.0, 7)
+    log_q = np.repeat(c[:, None], 7, axis=1)
+    a = orc.edge_posteriors(ds.data, ds.arity, 3)
+    b = orc.edge_posteriors(ds.data, ds.arity, 3, log_q=log_q)
+    np.testing.assert_allclose(b["post"], a["post"], atol=1e-12, rtol=0)
+    assert abs(b["log_PD"] - a["log_PD"] - c.sum()) < 1e-9
+
+
+@pytest.mark.parametrize("n,d,seed", [(4, 2, 35), (5, 2, 36), (6, 3, 37)])
+def test_feature_posterior_matches_orders(n, d, seed):
+    """A random modular feature (each f_i a random 0/1 pattern over the parent
+    sets, f_i(empty) = 1 so that f has positive probability), with q and
+    weights: P(f | D) = P(f, D) / P(D) against the sum over orders."""
+    ds = datagen.random_dag_data(n, 120, 2, min(d, 3), 0.7, seed=seed)
+    masks, logB = orc.scores(ds.data, ds.arity, d)
+    rng = np.random.default_rng(seed)
+    log_q, log_w = _rand_q_w(n, masks.shape[1], rng)
+    log_f = np.where(rng.random(masks.shape) < 0.4, -math.inf, 0.0)
+    log_f[:, 0] = 0.0
+    p, lpfd = orc.feature_posterior(ds.data, ds.arity, d, log_f, log_q=log_q, log_w=log_w)
+    want_fd, _ = brute_force_general(n, masks, logB + log_w, log_q=log_q, log_f=log_f)
+    want_d, _ = brute_force_general(n, masks, logB + log_w, log_q=log_q)
+    assert abs(lpfd - want_fd) < 1e-11 * max(1.0, abs(want_fd))
+    assert abs(p - math.exp(want_fd - want_d)) < 1e-12
+
+
+def test_edge_feature_equals_forward_backward_edge_posterior():
+    """The feature 'u -> v' (f_v(G) = [u in G], f_i = 1 otherwise) through the
+    single-feature DP (Eqs. 5-9) equals P(u -> v | D) from the
+    forward-backward path (Eqs. 10-12), with q and weights: two algorithms."""
+    n, d = 8, 3
+    ds = datagen.random_dag_data(n, 300, 2, 3, 0.8, seed=38)
+    K = orc.num_families(n, d)
+    rng = np.random.default_rng(38)
+    log_q, log_w = _rand_q_w(n, K, rng)
+    out = orc.edge_posteriors(ds.data, ds.arity, d, log_q=log_q, log_w=log_w)
+    masks, _ = orc.scores(ds.data, ds.arity, d)
+    for (u, v) in [(0, 1), (3, 7), (6, 2), (5, 4)]:
+        log_f = np.zeros((n, K))
+        log_f[v] = np.where((masks[v] >> u) & 1, 0.0, -math.inf)
+        p, _ = orc.feature_posterior(ds.data, ds.arity, d, log_f, log_q=log_q, log_w=log_w)
+        assert abs(p - out["post"][u, v]) < 1e-12
+
+
+def test_trivial_and_impossible_features():
+    """f = 1 gives P = 1 and log P(f, D) = log P(D); f_i = 0 for every parent
+    set of one node gives P = 0."""
+    ds = datagen.random_dag_data(6, 100, 2, 2, 1.0, seed=39)
+    K = orc.num_families(6, 2)
+    p, lpfd = orc.feature_posterior(ds.data, ds.arity, 2, np.zeros((6, K)))
+    assert abs(p - 1.0) < 1e-14
+    assert abs(lpfd - orc.edge_posteriors(ds.data, ds.arity, 2)["log_PD"]) < 1e-12
+    log_f = np.zeros((6, K))
+    log_f[4] = -math.inf
+    p, lpfd = orc.feature_posterior(ds.data, ds.arity, 2, log_f)
+    assert p == 0.0 and lpfd == -math.inf
