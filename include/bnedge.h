@@ -101,7 +101,21 @@ typedef struct bn_job_desc {
                                 size; NULL = all zero                         */
     int32_t data_on_device;  /* nonzero: data is a device pointer             */
     int32_t reserved;
+    const double* log_q;     /* n*n host doubles or NULL: the order prior's
+                                log q_i(S) (Eq. 4, entering A_i in Eq. 7 and
+                                Gamma_v in Eq. 12) as a function of |S|: row
+                                i, column |S| = 0..n-1; NULL = all zero       */
+    const double* log_w;     /* n*K host doubles or NULL: a log weight per
+                                family (i, G), canonical family order, added
+                                to log B_i(G) -- a general rho_i(G) (Eq. 4)
+                                beside the per-size log_rho; NULL = all zero  */
 } bn_job_desc;
+/* log_q and log_w accept -inf (a zero factor; it is held as -1e7 nats,
+ * whose exponential, and that of every sum it enters, is exactly 0); NaN or
+ * +inf give BN_EINVAL.  Batches and
+ * bn_edge_posteriors_static reject a job that sets either (BN_EINVAL).  If
+ * every parent set of some node has weight zero, P(D) = 0 and the
+ * posteriors are undefined. */
 
 typedef struct bn_stats {
     double ms_scores;        /* device time of each stage, CUDA events on the
@@ -142,6 +156,18 @@ int bn_job_footprint(const bn_job_desc* job, uint64_t* bytes);
  * until done. */
 int bn_scores(bn_ctx* ctx, const bn_job_desc* job, uint32_t* parent_mask,
               double* log_B);
+
+/* The posterior of one modular feature f(G) = prod_i f_i(G_i) (Section 2.2,
+ * Eqs. 5-9): P(f, D) = F^f(V) from the forward recursion (Eq. 9) over the
+ * A^f_i of Eq. 7 with B_i(G) f_i(G) in place of B_i(G), and
+ * P(f | D) = P(f, D) / P(D).  log_f: n*K host doubles, log f_i(G) for family
+ * f of node i in canonical order (0 for an indicator that is 1, -inf where
+ * it is 0; any other log weight is allowed).  Outputs: *p = P(f | D) and
+ * *log_PfD = log P(f, D) (natural log; either may be NULL).  Steps 1-3 run
+ * twice (F only, no R', Gamma or edges).  Blocks until done.  BN_EINVAL for
+ * a NULL ctx, job or log_f, an invalid job or a NaN / +inf in log_f. */
+int bn_feature_posterior(bn_ctx* ctx, const bn_job_desc* job, const double* log_f, double* p,
+                         double* log_PfD);
 
 /* Steps 1-5 (Algorithm 1).  post: n*n host doubles; log_PD: host double or
  * NULL.  Blocks until the result is in the host buffers. */

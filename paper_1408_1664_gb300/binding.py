@@ -38,7 +38,8 @@ class bn_ctx_opts(C.Structure):
 class bn_job_desc(C.Structure):
     _fields_ = [("n", C.c_int32), ("d", C.c_int32), ("m", C.c_int32), ("precision", C.c_int32),
                 ("data", C.c_void_p), ("arity", C.c_void_p), ("ess", C.c_double),
-                ("log_rho", C.c_void_p), ("data_on_device", C.c_int32), ("reserved", C.c_int32)]
+                ("log_rho", C.c_void_p), ("data_on_device", C.c_int32), ("reserved", C.c_int32),
+                ("log_q", C.c_void_p), ("log_w", C.c_void_p)]
 
 
 class bn_stats(C.Structure):
@@ -58,7 +59,8 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_edge_posteriors", "bn_edge_posteriors_async", "bn_submit", "bn_poll", "bn_wait",
            "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror", "bn_debug_stage",
            "bn_debug_counts", "bn_edge_posteriors_static", "bn_job_footprint", "bn_batch_create",
-           "bn_batch_run", "bn_batch_results", "bn_batch_describe", "bn_batch_destroy"]
+           "bn_batch_run", "bn_batch_results", "bn_batch_describe", "bn_batch_destroy",
+           "bn_feature_posterior"]
 
 
 def library_path() -> str:
@@ -103,6 +105,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_debug_stage": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
         "bn_debug_counts": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_uint32, P,
                                       C.c_int64]),
+        "bn_feature_posterior": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -169,7 +172,7 @@ class Job:
     """A bn_job_desc plus the arrays it points to (kept alive with it)."""
 
     def __init__(self, data, arity, d: int, ess: float = 1.0, log_rho=None,
-                 precision: str | int = "fp64", m: int | None = None):
+                 precision: str | int = "fp64", m: int | None = None, log_q=None, log_w=None):
         self.arity = np.ascontiguousarray(arity, dtype=np.uint8)
         n = int(self.arity.shape[0])
         on_dev = not isinstance(data, np.ndarray)
@@ -185,9 +188,12 @@ class Job:
         self.log_rho = None if log_rho is None else np.ascontiguousarray(log_rho, np.float64)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.n, self.d, self.m = n, int(d), int(m)
+        self.log_q = None if log_q is None else np.ascontiguousarray(log_q, np.float64).reshape(-1)
+        self.log_w = None if log_w is None else np.ascontiguousarray(log_w, np.float64).reshape(-1)
         self.desc = bn_job_desc(n, int(d), int(m), prec,
                                 _ptr(self.data) if m > 0 else None, _ptr(self.arity),
-                                float(ess), _ptr(self.log_rho), 1 if on_dev else 0, 0)
+                                float(ess), _ptr(self.log_rho), 1 if on_dev else 0, 0,
+                                _ptr(self.log_q), _ptr(self.log_w))
 
 
 def bn_edge_posteriors(ctx: int, job: Job, post: np.ndarray | None = None):
@@ -214,6 +220,19 @@ def bn_edge_posteriors_static(job: Job, post_dev, log_PD_dev=None, stream=None) 
                                           _ptr(stream))
     if rc:
         raise BnError(rc, "bn_edge_posteriors_static")
+
+
+def bn_feature_posterior(ctx: int, job: Job, log_f) -> tuple[float, float]:
+    """P(f | D) and log P(f, D) of the modular feature log_f (n, K)."""
+    lf = np.ascontiguousarray(log_f, dtype=np.float64).reshape(-1)
+    if lf.shape[0] != job.n * bn_num_families(job.n, job.d):
+        raise ValueError("log_f must hold n * K values")
+    p = np.zeros(1)
+    lpfd = np.zeros(1)
+    rc = load().bn_feature_posterior(ctx, C.byref(job.desc), _ptr(lf), _ptr(p), _ptr(lpfd))
+    if rc:
+        raise BnError(rc, "bn_feature_posterior")
+    return float(p[0]), float(lpfd[0])
 
 
 def bn_scores(ctx: int, job: Job):

@@ -913,7 +913,7 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
-           const T* __restrict__ Rc, T* __restrict__ W, size_t js)
+           const T* __restrict__ Rc, T* __restrict__ W, size_t js, const T* __restrict__ lq)
 {
     const int v = blockIdx.z;                       // endpoint: one slice of W each
     F = job_ptr(F, js);
@@ -928,6 +928,7 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
     for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) {
         const uint32_t S = expand((H << b) | t, v);
         vals[t] = F[S] + Rc[S | bv];
+        if (lq) vals[t] += lq[v * n + __popc(S)];   // q_v(S) of Eq. 12
     }
     __syncthreads();
     for (int j = 0; j < b; ++j) {
@@ -1193,6 +1194,43 @@ __global__ void k_edges_fin(int n, int use_z, int qbits, const double* __restric
 }
 
 // ===========================================================================
+// Priors beyond the defaults and single features (Eqs. 4-9).
+// ===========================================================================
+
+// log B_i(G) += log w_i(G): a per-family weight (a general rho_i(G), Eq. 4).
+__global__ void k_add_weights(double* __restrict__ logB, const double* __restrict__ w, int64_t nK)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nK;
+         x += (int64_t)gridDim.x * blockDim.x)
+        logB[x] += w[x];
+}
+
+// A_i(S) += log q_i(S), q_i a function of |S| (Eq. 7): lq[i * n + |S|] in
+// the working precision and log base; A is [i * 2^(n-1) + c], c = S with
+// bit i removed, so |S| = popc(c).
+template <typename T>
+__global__ void k_apply_q(int n, const T* __restrict__ lq, T* __restrict__ A)
+{
+    const int64_t total = (int64_t)n << (n - 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t >> (n - 1));
+        const uint32_t c = (uint32_t)(t & (((int64_t)1 << (n - 1)) - 1));
+        A[t] += lq[i * n + __popc(c)];
+    }
+}
+
+// out = lbs + lf: the shifted scores of B_i(G) f_i(G) (Eq. 6 with a feature).
+template <typename T>
+__global__ void k_add_feature(const T* __restrict__ lbs, const T* __restrict__ lf,
+                              T* __restrict__ out, int64_t nK)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nK;
+         x += (int64_t)gridDim.x * blockDim.x)
+        out[x] = lbs[x] + lf[x];
+}
+
+// ===========================================================================
 // Launchers.
 // ===========================================================================
 static int grid_for(int64_t work, int threads, int cap = 152 * 32)
@@ -1354,6 +1392,37 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
     return cudaGetLastError();
 }
 
+cudaError_t launch_add_weights(const Plan& P, double* logB, const double* w, cudaStream_t s)
+{
+    const int64_t nK = (int64_t)P.n * P.K;
+    k_add_weights<<<grid_for(nK, 256), 256, 0, s>>>(logB, w, nK);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_q(const Plan& P, const void* lq, void* A, cudaStream_t s)
+{
+    const int64_t total = (int64_t)P.n << (P.n - 1);
+    const int grid = grid_for(total, 256, 152 * 16);
+    if (P.prec == 0)
+        k_apply_q<double><<<grid, 256, 0, s>>>(P.n, (const double*)lq, (double*)A);
+    else
+        k_apply_q<float><<<grid, 256, 0, s>>>(P.n, (const float*)lq, (float*)A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_feature(const Plan& P, const void* lbs, const void* lf, void* out,
+                               cudaStream_t s)
+{
+    const int64_t nK = (int64_t)P.n * P.K;
+    if (P.prec == 0)
+        k_add_feature<double><<<grid_for(nK, 256), 256, 0, s>>>(
+            (const double*)lbs, (const double*)lf, (double*)out, nK);
+    else
+        k_add_feature<float><<<grid_for(nK, 256), 256, 0, s>>>(
+            (const float*)lbs, (const float*)lf, (float*)out, nK);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s)
 {
     k_node_max<<<dim3(P.n, P.nj), 256, 0, s>>>(P.K, logB, cmax, P.js);
@@ -1481,20 +1550,20 @@ size_t gamma_p2_smem_bytes(const Plan& P)
 }
 
 cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
-                            void* W, cudaStream_t s)
+                            void* W, cudaStream_t s, const void* lq)
 {
-    if (use_tile13_gamma(P)) return launch_gamma13_p1(P, F, Rc, rk13, W, s);
+    if (use_tile13_gamma(P)) return launch_gamma13_p1(P, F, Rc, rk13, W, s, lq);
     const int h = P.n - 1 - P.b_g;
     const size_t sm1 = gamma_p1_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);
     if (P.prec == 0)
         k_gamma_p1<double><<<grid, 256, sm1, s>>>(P.n, P.d, P.b_g, P.nlow_g,
                                                   (const double*)F, (const double*)Rc,
-                                                  (double*)W, P.js);
+                                                  (double*)W, P.js, (const double*)lq);
     else
         k_gamma_p1<float><<<grid, 256, sm1, s>>>(P.n, P.d, P.b_g, P.nlow_g,
                                                  (const float*)F, (const float*)Rc,
-                                                 (float*)W, P.js);
+                                                 (float*)W, P.js, (const float*)lq);
     return cudaGetLastError();
 }
 

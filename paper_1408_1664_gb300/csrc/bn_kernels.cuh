@@ -21,6 +21,8 @@ struct Plan {
     int prec;             // 0 = FP64, 1 = FP32
     int allbin = 0;       // every variable has arity 2
     int fxs = 40;         // fixed-point shift of the lgamma table (fixed_shift)
+    int hasq = 0;         // an order prior q_i(S) by |S| is given (Eq. 4, 7, 12)
+    int hasw = 0;         // per-family log weights are given (Eq. 4)
     // Schedule (set by the planner, changed by the batch autotuner):
     int up13 = 0;         // step 2 by the 13-dimension tiles (n >= 14)
     int g13 = 0;          // step 4 phase 1 by the 13-dimension tiles (n >= 14)
@@ -63,6 +65,14 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
 bool scores_cfg_fits(const Plan& P);
 // Kernels one launch_scores call over all n * K families starts.
 int scores_launches(const Plan& P);
+// Priors beyond the defaults and single features (Eqs. 4-9):
+// log B += w (n*K doubles, natural log); A_i(S) += lq[i*n + |S|] (lq in the
+// working precision and log base); out = lbs + lf (shifted scores times a
+// feature, working precision).
+cudaError_t launch_add_weights(const Plan& P, double* logB, const double* w, cudaStream_t s);
+cudaError_t launch_apply_q(const Plan& P, const void* lq, void* A, cudaStream_t s);
+cudaError_t launch_add_feature(const Plan& P, const void* lbs, const void* lf, void* out,
+                               cudaStream_t s);
 cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s);
 cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double* cmax,
                                 void* lbs, cudaStream_t s);
@@ -87,8 +97,10 @@ cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t
                             int* launches);
 // Step 4 for every endpoint v in one launch per phase (gridDim.z = n): W
 // holds n slices of 2^(n-1-b_g) * nlow_g values, Gam the n * K outputs.
+// lq (may be null): the order prior's log q_v(S) by |S| (Eq. 12), n*n values
+// in the working precision and log base, added to s_v(S).
 cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
-                            void* W, cudaStream_t s);
+                            void* W, cudaStream_t s, const void* lq = nullptr);
 cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s);
 // Step 5 (three launches); acc: n * (n + 1) scratch words.
 cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
@@ -103,7 +115,8 @@ cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unra
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
                             cudaStream_t s, cudaEvent_t sums_done = nullptr);
 cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
-                              const uint16_t* rank13, void* W, cudaStream_t s);
+                              const uint16_t* rank13, void* W, cudaStream_t s,
+                              const void* lq = nullptr);
 constexpr size_t kRank13Bytes = 2 * 8192 * sizeof(uint16_t);
 size_t upzeta13_smem_bytes(const Plan& P);
 size_t gamma13_smem_bytes(const Plan& P);

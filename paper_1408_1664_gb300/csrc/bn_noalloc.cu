@@ -142,6 +142,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     for (int t = 0; t <= P.d && t < P.n; ++t) cells *= sorted[t];
     if (cells > 65536u) return BN_EINVAL;
     double log_rho[32] = {};
+    if (j->log_q || j->log_w) return BN_EINVAL;        // not in this entry point
     if (j->log_rho)
         for (int k = 0; k <= P.d; ++k) {
             log_rho[k] = j->log_rho[k];

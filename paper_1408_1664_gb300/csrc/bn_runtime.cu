@@ -46,6 +46,8 @@ struct HostJob {
     double ess = 1.0;
     std::vector<uint8_t> arity;
     std::vector<double> log_rho;     // d+1 entries, empty = none
+    std::vector<double> log_q;       // n*n: log q_i(S) by |S| (Eq. 4), empty = none
+    std::vector<double> log_w;       // n*K: per-family log weights, empty = none
     std::vector<double> Dvals;       // sorted distinct denominators q, q*r
     const uint8_t* data = nullptr;   // host or device
     bool data_on_device = false;
@@ -55,10 +57,11 @@ struct HostJob {
 // Byte offsets of every array of a job inside one device allocation.
 struct Layout {
     size_t data, mj, fx, arity, log_rho, Dvals, alpha, lgT, planes, err, masks, cmasks, logB,
-        cmax, lbs, tab, rk13, A, F, Rc, W, Gam, eacc, post, logPD, dbg, total;
+        cmax, lbs, tab, rk13, A, F, Rc, W, Gam, eacc, post, logPD, logq, logw, logf, lbsf, dbg,
+        total;
 };
 
-Layout make_layout(const Plan& P, size_t dbg_cells)
+Layout make_layout(const Plan& P, size_t dbg_cells, bool feature = false)
 {
     const size_t es = P.prec == 0 ? 8 : 4;
     const size_t nK = (size_t)P.n * P.K;
@@ -92,6 +95,10 @@ Layout make_layout(const Plan& P, size_t dbg_cells)
     L.eacc = take((size_t)P.n * (P.n + 1) * 8);
     L.post = take((size_t)P.n * P.n * 8);
     L.logPD = take(8);
+    L.logq = take(P.hasq ? (size_t)P.n * P.n * es : 0);
+    L.logw = take(P.hasw ? nK * 8 : 0);
+    L.logf = take(feature ? nK * es : 0);         // a single feature (bn_feature_posterior)
+    L.lbsf = take(feature ? nK * es : 0);
     L.dbg = take(dbg_cells * 8);
     L.total = o;
     return L;
@@ -119,6 +126,37 @@ std::vector<double> denominators(const std::vector<uint8_t>& arity, int d)
             if ((uint64_t)q * r <= 65536u) D.insert((double)q * r);
     }
     return std::vector<double>(D.begin(), D.end());
+}
+
+// A log weight of zero (-inf) becomes this finite value: every sum and
+// maximum stays finite, its exponential (and that of any sum it enters) is
+// exactly 0, and tiles that span it take the exact scaled path.  It is small
+// enough in magnitude for that path's per-element scales: integers in FP32
+// (log2 units, 1.44e7), 600-nat bands in FP64 (spacing 2e-9 at 1e7).  NaN
+// and +inf are rejected.
+constexpr double kLogZero = -1e7;
+
+int log_weights(const double* src, size_t count, std::vector<double>& dst)
+{
+    dst.assign(src, src + count);
+    for (double& x : dst) {
+        if (std::isnan(x) || x == INFINITY) return BN_EINVAL;
+        if (x < kLogZero) x = kLogZero;
+    }
+    return BN_OK;
+}
+
+// In the working precision and log base (FP32: base 2).
+std::vector<char> working_logs(const std::vector<double>& v, int prec)
+{
+    std::vector<char> out(v.size() * (prec == 0 ? 8 : 4));
+    if (prec == 0) {
+        std::memcpy(out.data(), v.data(), out.size());
+    } else {
+        float* f = reinterpret_cast<float*>(out.data());
+        for (size_t t = 0; t < v.size(); ++t) f[t] = (float)(v[t] * 1.4426950408889634);
+    }
+    return out;
 }
 
 int validate_and_plan(const bn_job_desc* j, HostJob& hj)
@@ -156,6 +194,14 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
             if (j->data[s] >= hj.arity[s % P.n]) return BN_EINVAL;
     }
     P.K = families(P.n, P.d);
+    if (j->log_q) {
+        if (log_weights(j->log_q, (size_t)P.n * P.n, hj.log_q)) return BN_EINVAL;
+        P.hasq = 1;
+    }
+    if (j->log_w) {
+        if (log_weights(j->log_w, (size_t)P.n * P.K, hj.log_w)) return BN_EINVAL;
+        P.hasw = 1;
+    }
     P.W = std::max(1, (P.m + 63) / 64);
     P.rmax = (int)sorted[0];
     P.allbin = sorted[0] == 2 && sorted[P.n - 1] == 2;
@@ -241,6 +287,21 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
                     double* logPD_dev, cudaStream_t s, Events* ev, int* launches,
                     const Side* side = nullptr);
 
+// The order prior q (working precision) and the family weights (FP64) of a
+// job, when given.  Pageable copies: the host vectors may go right after.
+int upload_priors(const HostJob& hj, const Bufs& B, cudaStream_t s)
+{
+    const Plan& P = hj.P;
+    if (P.hasq) {
+        const std::vector<char> q = working_logs(hj.log_q, P.prec);
+        CK(cudaMemcpyAsync(B.at<char>(B.L.logq), q.data(), q.size(), cudaMemcpyHostToDevice, s));
+    }
+    if (P.hasw)
+        CK(cudaMemcpyAsync(B.at<char>(B.L.logw), hj.log_w.data(), hj.log_w.size() * 8,
+                           cudaMemcpyHostToDevice, s));
+    return BN_OK;
+}
+
 // Enqueue steps 1-5 on stream s.  Small host arrays go through `stage`
 // (pinned, >= stage_bytes) when given, else through pageable copies.
 int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_dev,
@@ -284,7 +345,51 @@ int enqueue(const HostJob& hj, const Bufs& B, double* post_dev, double* logPD_de
         CK(cudaMemcpyAsync(B.at<char>(L.Dvals), src + n_ar + n_lr, 2 * n_dv,
                            cudaMemcpyHostToDevice, s));
     }
+    const int rc = upload_priors(hj, B, s);
+    if (rc) return rc;
     return enqueue_kernels(hj, B, data_dev, post_dev, logPD_dev, s, ev, launches, side);
+}
+
+// Step 1 on stream s (inputs on the device): scores, the family weights,
+// the per-node maximum and the shifted scores; the rank tables of the
+// 13-dimension tiles.
+int enqueue_step1(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, cudaStream_t s,
+                  int* nl)
+{
+    const Plan& P = hj.P;
+    const Layout& L = B.L;
+    CK(cudaMemsetAsync(B.at<int>(L.err), 0, 4, s));
+    int* err = B.at<int>(L.err);
+    const uint8_t* ar = B.at<uint8_t>(L.arity);
+    if (hj.data_on_device) { CK(bn::launch_check_data(data_dev, ar, P.n, P.m, err, s)); ++*nl; }
+    CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s)); ++*nl;
+    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, P.fxs, B.at<void>(L.lgT), s)); ++*nl;
+    CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals),
+                         B.at<void>(L.lgT), hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho),
+                         0, (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
+                         B.at<double>(L.logB), nullptr, s));
+    *nl += bn::scores_launches(P);
+    if (P.hasw) { CK(bn::launch_add_weights(P, B.at<double>(L.logB), B.at<double>(L.logw), s)); ++*nl; }
+    CK(bn::launch_node_max(P, B.at<double>(L.logB), B.at<double>(L.cmax), s)); ++*nl;
+    CK(bn::launch_shift_scores(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<void>(L.lbs), s)); ++*nl;
+    if (bn::needs_rank13(P)) {
+        uint16_t* rk = B.at<uint16_t>(L.rk13);
+        CK(bn::launch_rank13_tables(P, rk, rk + 8192, s));
+        ++*nl;
+    }
+    return BN_OK;
+}
+
+// Step 2 from the shifted scores lbs into A, then the order prior q.
+int enqueue_upzeta(const Plan& P, const Bufs& B, const void* lbs, cudaStream_t s, int* nl,
+                   cudaEvent_t sums_done)
+{
+    const Layout& L = B.L;
+    CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), lbs, B.at<void>(L.tab),
+                         B.at<uint16_t>(L.rk13), B.at<void>(L.A), s, sums_done));
+    *nl += bn::use_tile13_up(P) ? 3 : 1;
+    if (P.hasq) { CK(bn::launch_apply_q(P, B.at<void>(L.logq), B.at<void>(L.A), s)); ++*nl; }
+    return BN_OK;
 }
 
 // Enqueue the kernels of steps 1-5 on stream s (inputs already on the device).
@@ -294,29 +399,13 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     const Plan& P = hj.P;
     const Layout& L = B.L;
     int nl = 0;
-    CK(cudaMemsetAsync(B.at<int>(L.err), 0, 4, s));
-    int* err = B.at<int>(L.err);
-    const uint8_t* ar = B.at<uint8_t>(L.arity);
-    if (hj.data_on_device) { CK(bn::launch_check_data(data_dev, ar, P.n, P.m, err, s)); ++nl; }
-    CK(bn::launch_pack_planes(data_dev, P.n, P.m, P.rmax, P.W, B.at<uint64_t>(L.planes), s)); ++nl;
-    CK(bn::launch_lgamma_table(B.at<double>(L.alpha), P.rows, P.m, P.fxs, B.at<void>(L.lgT), s)); ++nl;
-    CK(bn::launch_scores(P, ar, B.at<uint64_t>(L.planes), B.at<double>(L.Dvals),
-                         B.at<void>(L.lgT), hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho),
-                         0, (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
-                         B.at<double>(L.logB), nullptr, s));
-    nl += bn::scores_launches(P);
-    CK(bn::launch_node_max(P, B.at<double>(L.logB), B.at<double>(L.cmax), s)); ++nl;
-    CK(bn::launch_shift_scores(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<void>(L.lbs), s)); ++nl;
-    if (bn::needs_rank13(P)) {
-        uint16_t* rk = B.at<uint16_t>(L.rk13);
-        CK(bn::launch_rank13_tables(P, rk, rk + 8192, s));
-        ++nl;
-    }
+    int rc = enqueue_step1(hj, B, data_dev, s, &nl);
+    if (rc) return rc;
     if (ev) CK(cudaEventRecord(ev->ev[1], s));
-    CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), B.at<void>(L.lbs), B.at<void>(L.tab),
-                         B.at<uint16_t>(L.rk13), B.at<void>(L.A), s,
-                         ev && bn::use_tile13_up(P) ? ev->ev[kEvSums] : nullptr));
-    nl += bn::use_tile13_up(P) ? 3 : 1;
+    rc = enqueue_upzeta(P, B, B.at<void>(L.lbs), s, &nl,
+                        ev && bn::use_tile13_up(P) ? ev->ev[kEvSums] : nullptr);
+    if (rc) return rc;
+    int* err = B.at<int>(L.err);
     if (ev) CK(cudaEventRecord(ev->ev[2], s));
     if (side && side->s) {
         CK(cudaEventRecord(side->fork, s));
@@ -338,7 +427,7 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
         ev->overlap = side && side->s;
     }
     CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
-                           B.at<void>(L.W), s));
+                           B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr));
     if (ev) CK(cudaEventRecord(ev->ev[5], s));
     CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
     if (ev) CK(cudaEventRecord(ev->ev[6], s));
@@ -727,7 +816,7 @@ int bn_scores(bn_ctx* c, const bn_job_desc* job, uint32_t* parent_mask, double* 
     Plan P = hj.P;
     Layout L = make_layout(P, 0);
     const size_t need = L.cmax;   // everything up to and including logB
-    rc = ensure_ws(c, need + al((size_t)P.n * 8));
+    rc = ensure_ws(c, need + al((size_t)P.n * 8) + (P.hasw ? al((size_t)P.n * P.K * 8) : 0));
     if (rc) return rc;
     rc = ensure_pin(&c->pin, &c->pin_bytes, small_bytes(P) + 64);
     if (rc) return rc;
@@ -756,6 +845,12 @@ int bn_scores(bn_ctx* c, const bn_job_desc* job, uint32_t* parent_mask, double* 
                          hj.log_rho.empty() ? nullptr : B.at<double>(L.log_rho), 0,
                          (int64_t)P.n * P.K, B.at<uint32_t>(L.masks), B.at<uint32_t>(L.cmasks),
                          B.at<double>(L.logB), nullptr, s));
+    if (P.hasw) {
+        // the weights sit past logB in the layout: a scratch copy right after it
+        double* w = reinterpret_cast<double*>(c->ws + need + al((size_t)P.n * 8));
+        CK(cudaMemcpyAsync(w, hj.log_w.data(), hj.log_w.size() * 8, cudaMemcpyHostToDevice, s));
+        CK(bn::launch_add_weights(P, B.at<double>(L.logB), w, s));
+    }
     int err = 0;
     CK(cudaMemcpyAsync(parent_mask, B.at<char>(L.masks), (size_t)P.n * P.K * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(log_B, B.at<char>(L.logB), (size_t)P.n * P.K * 8, cudaMemcpyDeviceToHost, s));
@@ -764,6 +859,90 @@ int bn_scores(bn_ctx* c, const bn_job_desc* job, uint32_t* parent_mask, double* 
     c->have_last = false;
     c->tables_sig.clear();
     return err ? BN_EINVAL : BN_OK;
+}
+
+int bn_feature_posterior(bn_ctx* c, const bn_job_desc* job, const double* log_f, double* p,
+                         double* log_PfD)
+{
+    if (!c || !log_f) return BN_EINVAL;
+    HostJob hj;
+    int rc = validate_and_plan(job, hj);
+    if (rc) return rc;
+    const Plan& P = hj.P;
+    std::vector<double> lf;
+    if (log_weights(log_f, (size_t)P.n * P.K, lf)) return BN_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return BN_ECUDA;
+    const Layout L = make_layout(P, 0, true);
+    rc = ensure_ws(c, L.total);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    CK(cudaStreamSynchronize(s));
+    c->have_last = false;
+    c->tables_sig.clear();
+    Bufs B{c->ws, L};
+    // inputs: data, small tables, priors, the feature in the working units
+    const uint8_t* data_dev = B.at<uint8_t>(L.data);
+    if (P.m > 0) {
+        if (hj.data_on_device) data_dev = hj.data;
+        else CK(cudaMemcpyAsync(B.at<uint8_t>(L.data), hj.data, (size_t)P.m * P.n,
+                                cudaMemcpyHostToDevice, s));
+    }
+    std::vector<double> lr(P.d + 1, 0.0);
+    for (size_t t = 0; t < hj.log_rho.size(); ++t) lr[t] = hj.log_rho[t];
+    std::vector<double> alpha(P.rows);
+    for (int r = 0; r < P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
+    CK(cudaMemcpyAsync(B.at<char>(L.arity), hj.arity.data(), P.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.log_rho), lr.data(), lr.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.Dvals), hj.Dvals.data(), hj.Dvals.size() * 8,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.alpha), alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice, s));
+    rc = upload_priors(hj, B, s);
+    if (rc) return rc;
+    const std::vector<char> lfw = working_logs(lf, P.prec);
+    CK(cudaMemcpyAsync(B.at<char>(L.logf), lfw.data(), lfw.size(), cudaMemcpyHostToDevice, s));
+
+    // P(D): steps 1-3 with f = 1 (F only); then P(f, D) from the same
+    // shifted scores plus log f (the shifts c_i cancel in the ratio)
+    const size_t es = P.prec == 0 ? 8 : 4;
+    const size_t full = ((size_t)1 << P.n) - 1;
+    int nl = 0;
+    rc = enqueue_step1(hj, B, data_dev, s, &nl);
+    if (rc) return rc;
+    rc = enqueue_upzeta(P, B, B.at<void>(L.lbs), s, &nl, nullptr);
+    if (rc) return rc;
+    CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
+    double fv[2] = {0.0, 0.0};
+    char raw[2][8];
+    CK(cudaMemcpyAsync(raw[0], B.at<char>(L.F) + full * es, es, cudaMemcpyDeviceToHost, s));
+    CK(bn::launch_add_feature(P, B.at<void>(L.lbs), B.at<void>(L.logf), B.at<void>(L.lbsf), s));
+    rc = enqueue_upzeta(P, B, B.at<void>(L.lbsf), s, &nl, nullptr);
+    if (rc) return rc;
+    CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
+    CK(cudaMemcpyAsync(raw[1], B.at<char>(L.F) + full * es, es, cudaMemcpyDeviceToHost, s));
+    std::vector<double> cmax(P.n);
+    int err = 0;
+    CK(cudaMemcpyAsync(cmax.data(), B.at<char>(L.cmax), (size_t)P.n * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&err, B.at<char>(L.err), 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err) return BN_EINVAL;
+    for (int k = 0; k < 2; ++k) {
+        if (P.prec == 0) {
+            std::memcpy(&fv[k], raw[k], 8);
+        } else {
+            float x;
+            std::memcpy(&x, raw[k], 4);
+            fv[k] = (double)x * 0.69314718055994531;   // base 2 -> natural
+        }
+    }
+    double csum = 0.0;
+    for (double x : cmax) csum += x;
+    // a feature weight of zero is held as kLogZero: a P(f, D) that far below
+    // P(D) is an exact zero (a real feature's ratio is many orders of
+    // magnitude closer)
+    const bool zero = fv[1] - fv[0] < 0.5 * kLogZero;
+    if (p) *p = zero ? 0.0 : std::exp(fv[1] - fv[0]);
+    if (log_PfD) *log_PfD = zero ? -INFINITY : fv[1] + csum;
+    return BN_OK;
 }
 
 int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask, int64_t* counts,
@@ -1081,6 +1260,7 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
     for (int k = 0; k < count; ++k) {
         HostJob& hj = b->jobs[k];
         int rc = jobs[k].data_on_device ? BN_EINVAL : validate_and_plan(&jobs[k], hj);
+        if (!rc && (hj.P.hasq || hj.P.hasw)) rc = BN_EINVAL;   // not in the batch layout
         if (rc) { delete b; return rc; }
         const Plan& P = hj.P;
         hj.data_copy.assign(jobs[k].data ? jobs[k].data : (const uint8_t*)"",

@@ -725,7 +725,12 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
         using Wn = Window<T>;
         const T M = ord_dec(*tmax) + T(TB);
         const T span = M - A1[0];
-        const int npass = span < Wn::win ? 1 : (int)ceil(span / Wn::win);
+        // spans past max_pass windows (a zero weight held as -1e7 nats gives an
+        // empty-set column far below the rest) and NaN go to the exact path
+        // without converting the span to an integer
+        const int npass = span < Wn::win ? 1
+                          : span < T(Wn::max_pass) * Wn::win ? (int)ceil(span / Wn::win)
+                                                             : Wn::max_pass + 1;
         if (npass == 1) {                        // one window holds the whole tile
             const T sp = M - Wn::top;
             T x[TR];
@@ -810,7 +815,7 @@ template <typename T>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 3 : 1)
 k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W,
-             size_t js)
+             size_t js, const T* __restrict__ lq)
 {
     const int v = blockIdx.z;                       // endpoint: one slice of W each
     F = job_ptr(F, js);
@@ -828,7 +833,9 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     using O = typename OrdInt<T>::type;
     __shared__ O tmax_s;
     __shared__ T sfull_s;
+    __shared__ T lq_s[32];                          // q_v by |S| (Eq. 12), when given
     if (t == 0) tmax_s = ord_enc(Lg::ninf());
+    if (lq && t < n) lq_s[t] = lq[v * n + t];
     __syncthreads();
     T x[TR];
     T mx = Lg::ninf();
@@ -837,6 +844,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         const uint32_t el = el1(r, t);
         const uint32_t S = expand((H << TB) | el, v);
         x[r] = F[S] + Rc[S | bv];
+        if (lq) x[r] += lq_s[__popc(S)];
         mx = x[r] > mx ? x[r] : mx;
     }
     for (int o = 16; o; o >>= 1) {
@@ -992,17 +1000,19 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
 }
 
 cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
-                              const uint16_t* rank13, void* W, cudaStream_t s)
+                              const uint16_t* rank13, void* W, cudaStream_t s, const void* lq)
 {
     const int h = P.n - 1 - TB;
     const size_t sm = gamma13_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);
     if (P.prec == 0)
         k_gamma13_p1<double><<<grid, TT, sm, s>>>(P.n, P.d, P.nlow_g, (const double*)F,
-                                                   (const double*)Rc, rank13, (double*)W, P.js);
+                                                   (const double*)Rc, rank13, (double*)W, P.js,
+                                                   (const double*)lq);
     else
         k_gamma13_p1<float><<<grid, TT, sm, s>>>(P.n, P.d, P.nlow_g, (const float*)F,
-                                                  (const float*)Rc, rank13, (float*)W, P.js);
+                                                  (const float*)Rc, rank13, (float*)W, P.js,
+                                                  (const float*)lq);
     return cudaGetLastError();
 }
 

@@ -56,11 +56,12 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bn_ctx_destroy(None) == B.BN_EINVAL
     assert lib.bn_edge_posteriors(None, None, None, None) == B.BN_EINVAL
     assert lib.bn_job_stats(None, 0, None) == B.BN_EINVAL
+    assert lib.bn_feature_posterior(None, None, None, None, None) == B.BN_EINVAL
 
 
 def test_structure_layouts_match_header(lib):
-    # 4 int32 + 2 pointers + double + pointer + 2 int32 on LP64
-    assert ctypes.sizeof(B.bn_job_desc) == 16 + 16 + 8 + 8 + 8
+    # 4 int32 + 2 pointers + double + pointer + 2 int32 + 2 pointers on LP64
+    assert ctypes.sizeof(B.bn_job_desc) == 16 + 16 + 8 + 8 + 8 + 16
     assert ctypes.sizeof(B.bn_ctx_opts) == 4 + 4 + 8 + 4 + 4
     assert ctypes.sizeof(B.bn_stats) == 10 * 8 + 8 + 8
 
@@ -76,16 +77,18 @@ def test_structure_sizes_match_a_c_compiler(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "bnedge.h"\n'
-        "int main(void) { printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(bn_job_desc), "
+        "int main(void) { printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(bn_job_desc), "
         "sizeof(bn_ctx_opts), sizeof(bn_stats), offsetof(bn_stats, kernels), "
-        "offsetof(bn_stats, ms_upzeta_sums)); return 0; }\n")
+        "offsetof(bn_stats, ms_upzeta_sums), offsetof(bn_job_desc, log_q), "
+        "offsetof(bn_job_desc, log_w)); return 0; }\n")
     exe = tmp_path / "sz"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     assert got == [ctypes.sizeof(B.bn_job_desc), ctypes.sizeof(B.bn_ctx_opts),
                    ctypes.sizeof(B.bn_stats), B.bn_stats.kernels.offset,
-                   B.bn_stats.ms_upzeta_sums.offset]
+                   B.bn_stats.ms_upzeta_sums.offset, B.bn_job_desc.log_q.offset,
+                   B.bn_job_desc.log_w.offset]
 
 
 def test_product_does_not_import_oracle():
