@@ -419,6 +419,45 @@ def run_batched_only(args) -> None:
                                                    "jobs_per_s": 256 / (ms / 1e3)}}))
 
 
+def run_priors_features(binding, ctx, ds, d: int, prec: str, reps: int = 3) -> dict:
+    """The same job with an order prior q_i(|S|) and per-family weights
+    (Eq. 4, 7, 12; seeded normal log values, a quarter of the weights zero,
+    the empty parent set kept), and one edge feature (0 -> 1) through the
+    single-feature DP (Eqs. 5-9: steps 1-3 twice), both on the job's
+    precision.  Device time of the prior run from the library's CUDA events;
+    the feature call blocks, so it is timed on the host."""
+    import math
+
+    n = ds.n
+    K = binding.bn_num_families(n, d)
+    rng = np.random.default_rng(77)
+    log_q = rng.normal(0.0, 1.5, size=(n, n))
+    log_w = rng.normal(0.0, 1.0, size=(n, K))
+    log_w[rng.random((n, K)) < 0.25] = -math.inf
+    log_w[:, 0] = 0.0
+    job = binding.Job(ds.data, ds.arity, d, precision=prec, log_q=log_q, log_w=log_w)
+    binding.bn_edge_posteriors(ctx.h, job)
+    ms = []
+    for _ in range(reps):
+        binding.bn_edge_posteriors(ctx.h, job)
+        ms.append(ctx.stats()["ms_total"])
+    masks, _ = binding.bn_scores(ctx.h, binding.Job(ds.data, ds.arity, d))
+    log_f = np.zeros((n, K))
+    log_f[1] = np.where((masks[1] >> 0) & 1, 0.0, -math.inf)
+    plain = binding.Job(ds.data, ds.arity, d, precision=prec)
+    post, _ = binding.bn_edge_posteriors(ctx.h, plain)
+    p, _ = binding.bn_feature_posterior(ctx.h, plain, log_f)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        p, _ = binding.bn_feature_posterior(ctx.h, plain, log_f)
+    feat_ms = (time.perf_counter() - t0) / reps * 1e3
+    cells = n * 2 ** n
+    return {"edge_posteriors_with_prior_and_weights": {
+                "ms": statistics.median(ms), "cells_per_s": cells / (statistics.median(ms) / 1e3)},
+            "feature_posterior_edge_0_1": {
+                "ms_host": feat_ms, "p": p, "abs_diff_vs_edge_path": abs(p - float(post[0, 1]))}}
+
+
 # ---------------------------------------------------------------- sweep --
 def run_sweep(args) -> None:
     """Time the FP32 path over the configurations of the paper's experiments
@@ -611,6 +650,7 @@ def run_ours(args):
     if rank == 0 and not args.no_serve:
         extra["serving"] = run_serving(binding, local, args.serve_seconds)
         extra["batched"] = run_batched(binding, torch, local)
+        extra["priors_and_features"] = run_priors_features(binding, ctx, ds, d, prec)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -811,7 +811,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 // (bit v removed); s_v(S) = F(S) + R'(S + {v}); keeps the outputs with at
 // most d low elements in row H of W.
 // ===========================================================================
-template <typename T>
+template <typename T, bool Q>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 3 : 1)
 k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W,
@@ -833,9 +833,9 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     using O = typename OrdInt<T>::type;
     __shared__ O tmax_s;
     __shared__ T sfull_s;
-    __shared__ T lq_s[32];                          // q_v by |S| (Eq. 12), when given
+    __shared__ T lq_s[Q ? 32 : 1];                  // q_v by |S| (Eq. 12), when given
     if (t == 0) tmax_s = ord_enc(Lg::ninf());
-    if (lq && t < n) lq_s[t] = lq[v * n + t];
+    if (Q && t < n) lq_s[t] = lq[v * n + t];
     __syncthreads();
     T x[TR];
     T mx = Lg::ninf();
@@ -844,7 +844,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         const uint32_t el = el1(r, t);
         const uint32_t S = expand((H << TB) | el, v);
         x[r] = F[S] + Rc[S | bv];
-        if (lq) x[r] += lq_s[__popc(S)];
+        if (Q) x[r] += lq_s[__popc(S)];
         mx = x[r] > mx ? x[r] : mx;
     }
     for (int o = 16; o; o >>= 1) {
@@ -1005,14 +1005,26 @@ cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
     const int h = P.n - 1 - TB;
     const size_t sm = gamma13_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);
-    if (P.prec == 0)
-        k_gamma13_p1<double><<<grid, TT, sm, s>>>(P.n, P.d, P.nlow_g, (const double*)F,
-                                                   (const double*)Rc, rank13, (double*)W, P.js,
-                                                   (const double*)lq);
-    else
-        k_gamma13_p1<float><<<grid, TT, sm, s>>>(P.n, P.d, P.nlow_g, (const float*)F,
-                                                  (const float*)Rc, rank13, (float*)W, P.js,
-                                                  (const float*)lq);
+    // the order prior is a separate instance: the plain kernel has no trace of it
+    if (P.prec == 0) {
+        if (lq)
+            k_gamma13_p1<double, true><<<grid, TT, sm, s>>>(
+                P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
+                (const double*)lq);
+        else
+            k_gamma13_p1<double, false><<<grid, TT, sm, s>>>(
+                P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
+                nullptr);
+    } else {
+        if (lq)
+            k_gamma13_p1<float, true><<<grid, TT, sm, s>>>(
+                P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
+                (const float*)lq);
+        else
+            k_gamma13_p1<float, false><<<grid, TT, sm, s>>>(
+                P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
+                nullptr);
+    }
     return cudaGetLastError();
 }
 
@@ -1028,8 +1040,10 @@ cudaError_t set_tile13_attributes()
     SETA(k_upzeta13_colw<float>)
     SETA(k_upzeta13<double>)
     SETA(k_upzeta13<float>)
-    SETA(k_gamma13_p1<double>)
-    SETA(k_gamma13_p1<float>)
+    SETA((k_gamma13_p1<double, false>))
+    SETA((k_gamma13_p1<float, false>))
+    SETA((k_gamma13_p1<double, true>))
+    SETA((k_gamma13_p1<float, true>))
 #undef SETA
     return cudaSuccess;
 }
