@@ -1550,9 +1550,9 @@ size_t gamma_p2_smem_bytes(const Plan& P)
 }
 
 cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
-                            void* W, cudaStream_t s, const void* lq)
+                            void* W, cudaStream_t s, const void* lq, const void* A)
 {
-    if (use_tile13_gamma(P)) return launch_gamma13_p1(P, F, Rc, rk13, W, s, lq);
+    if (use_tile13_gamma(P)) return launch_gamma13_p1(P, F, Rc, rk13, W, s, lq, A);
     const int h = P.n - 1 - P.b_g;
     const size_t sm1 = gamma_p1_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);

@@ -98,9 +98,11 @@ cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t
 // Step 4 for every endpoint v in one launch per phase (gridDim.z = n): W
 // holds n slices of 2^(n-1-b_g) * nlow_g values, Gam the n * K outputs.
 // lq (may be null): the order prior's log q_v(S) by |S| (Eq. 12), n*n values
-// in the working precision and log base, added to s_v(S).
+// in the working precision and log base, added to s_v(S).  A (may be null):
+// the step-2 output, which gives the 13-dimension tiles their relevance cut.
 cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
-                            void* W, cudaStream_t s, const void* lq = nullptr);
+                            void* W, cudaStream_t s, const void* lq = nullptr,
+                            const void* A = nullptr);
 cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s);
 // Step 5 (three launches); acc: n * (n + 1) scratch words.
 cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
@@ -116,7 +118,7 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
                             cudaStream_t s, cudaEvent_t sums_done = nullptr);
 cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
                               const uint16_t* rank13, void* W, cudaStream_t s,
-                              const void* lq = nullptr);
+                              const void* lq = nullptr, const void* A = nullptr);
 constexpr size_t kRank13Bytes = 2 * 8192 * sizeof(uint16_t);
 size_t upzeta13_smem_bytes(const Plan& P);
 size_t gamma13_smem_bytes(const Plan& P);

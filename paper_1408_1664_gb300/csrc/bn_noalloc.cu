@@ -230,7 +230,7 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
     CKS(bn::launch_upzeta(P, cm, base + o_lbs, base + o_reo, rk13, base + o_A, s));
     CKS(bn::launch_forward(P, base + o_A, base + o_F, s, nullptr));
     CKS(bn::launch_backward(P, base + o_A, base + o_Rc, s, nullptr));
-    CKS(bn::launch_gamma_p1(P, base + o_F, base + o_Rc, rk13, base + o_W, s));
+    CKS(bn::launch_gamma_p1(P, base + o_F, base + o_Rc, rk13, base + o_W, s, nullptr, base + o_A));
     CKS(bn::launch_gamma_p2(P, base + o_W, base + o_G, s));
     CKS(bn::launch_edges(P, logB, cmax, masks, base + o_G, base + o_F, err,
                          reinterpret_cast<unsigned long long*>(base + o_ea), post_dev,

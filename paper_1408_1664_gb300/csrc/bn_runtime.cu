@@ -427,7 +427,8 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
         ev->overlap = side && side->s;
     }
     CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
-                           B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr));
+                           B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr,
+                           B.at<void>(L.A)));
     if (ev) CK(cudaEventRecord(ev->ev[5], s));
     CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
     if (ev) CK(cudaEventRecord(ev->ev[6], s));
@@ -1112,7 +1113,7 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
     }
     if (stages & 8u) {
         CK(bn::launch_gamma_p1(G, at(L.F), at(L.Rc), reinterpret_cast<const uint16_t*>(at(L.rk13)),
-                               at(L.W), s));
+                               at(L.W), s, nullptr, at(L.A)));
         CK(bn::launch_gamma_p2(G, at(L.W), at(L.Gam), s));
     }
     if (stages & 16u)

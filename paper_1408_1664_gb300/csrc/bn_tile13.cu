@@ -25,6 +25,8 @@
 #include "bn_device.cuh"
 #include "bn_kernels.cuh"
 
+#include <cmath>
+
 namespace bn {
 namespace {
 
@@ -225,12 +227,13 @@ __device__ __forceinline__ void bfly_plain(T (&x)[TR], int k0, int nk)
 // output left over has scaled value below 2^lo in pass p, hence below 2^top
 // in pass p + 1, so no term of it overflows there (2^128; e^709).
 template <typename T> struct Window;
+// gap: how far below a relevance cut an output is held (64 bits; 45 nats).
 template <> struct Window<float> {                 // bits
-    static constexpr float top = 126.0f, lo = -80.0f, win = 206.0f;
+    static constexpr float top = 126.0f, lo = -80.0f, win = 206.0f, gap = 64.0f;
     static constexpr int max_pass = 2;     // a third pass costs more than the exact path
 };
 template <> struct Window<double> {                // nats
-    static constexpr double top = 700.0, lo = -600.0, win = 1300.0;
+    static constexpr double top = 700.0, lo = -600.0, win = 1300.0, gap = 45.0;
     static constexpr int max_pass = 3;
 };
 
@@ -811,11 +814,23 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 // (bit v removed); s_v(S) = F(S) + R'(S + {v}); keeps the outputs with at
 // most d low elements in row H of W.
 // ===========================================================================
+//
+// Relevance cut (when Aup is given).  Every output W[H][g] reaches a
+// posterior only through B_v(G) Gamma_v(G) / F(V) with G inside the tile's
+// full set S_H = H + all 13 low bits, and B_v(G) <= A_v(S_H).  An output
+// below L = F(V) - margin - A_v(S_H) therefore moves no posterior by more than
+// 2^-margin, and the K * 2^h outputs of v together by at most
+// K 2^h 2^-margin; the launcher takes margin = 64 + log2(K 2^h) bits, so the
+// total is below 2^-64.  A tile whose upper bound M is below L writes every
+// output as L - gap (no butterflies); a tile within one window of
+// max(L, s(full)) takes the single-scale pass, its outputs held at >= L - gap.
+// Outputs at or above L are exact as before.  The written value, like the
+// true one, is below 2^L: the error of such an output is within the bound.
 template <typename T, bool Q>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 3 : 1)
 k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W,
-             size_t js, const T* __restrict__ lq)
+             size_t js, const T* __restrict__ lq, const T* __restrict__ Aup, T margin)
 {
     const int v = blockIdx.z;                       // endpoint: one slice of W each
     F = job_ptr(F, js);
@@ -860,7 +875,21 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         // included: it lies between s(full) and M, so a tile that spans
         // less than one window resolves in one single-scale pass (Window)
         const T M = ord_dec(tmax_s) + T(TB);
-        if (M - sfull_s < Window<T>::win) {
+        T L = Lg::ninf();                           // relevance cut (see above)
+        if (Aup) {
+            const T at = job_ptr(Aup, js)[((size_t)v << (n - 1)) + (((size_t)H << TB) | (TN - 1))];
+            L = F[((size_t)1 << n) - 1] - margin - at;
+        }
+        const T floorv = L - Window<T>::gap;
+        if (M < L) {                                // nothing in the tile matters
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const uint32_t el = el3(r, t);
+                if (__popc(el) <= d) row[rank13[el]] = floorv;
+            }
+            return;
+        }
+        if (M - (L > sfull_s ? L : sfull_s) < Window<T>::win) {
             const T sp = M - Window<T>::top;
 #pragma unroll
             for (int r = 0; r < TR; ++r) x[r] = Lg::ex(x[r] - sp);
@@ -876,7 +905,8 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
                 const uint32_t el = el3(r, t);
-                if (__popc(el) <= d) row[rank13[el]] = sp + Lg::lg(x[r]);
+                const T o = sp + Lg::lg(x[r]);
+                if (__popc(el) <= d) row[rank13[el]] = o > floorv ? o : floorv;
             }
             return;
         }
@@ -1000,30 +1030,34 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
 }
 
 cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
-                              const uint16_t* rank13, void* W, cudaStream_t s, const void* lq)
+                              const uint16_t* rank13, void* W, cudaStream_t s, const void* lq,
+                              const void* A)
 {
     const int h = P.n - 1 - TB;
     const size_t sm = gamma13_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);
+    // relevance margin: 64 bits + log2(K 2^h), in bits (FP32) or nats (FP64)
+    const double mbits = 64.0 + std::ceil(std::log2((double)P.K)) + h;
+    const double margin = P.prec == 0 ? mbits * 0.69314718055994531 : mbits;
     // the order prior is a separate instance: the plain kernel has no trace of it
     if (P.prec == 0) {
         if (lq)
             k_gamma13_p1<double, true><<<grid, TT, sm, s>>>(
                 P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
-                (const double*)lq);
+                (const double*)lq, (const double*)A, margin);
         else
             k_gamma13_p1<double, false><<<grid, TT, sm, s>>>(
                 P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
-                nullptr);
+                nullptr, (const double*)A, margin);
     } else {
         if (lq)
             k_gamma13_p1<float, true><<<grid, TT, sm, s>>>(
                 P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
-                (const float*)lq);
+                (const float*)lq, (const float*)A, (float)margin);
         else
             k_gamma13_p1<float, false><<<grid, TT, sm, s>>>(
                 P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
-                nullptr);
+                nullptr, (const float*)A, (float)margin);
     }
     return cudaGetLastError();
 }
