@@ -161,8 +161,10 @@ def stage_table(n: int, d: int, es: int) -> dict:
     from math import comb
     N = 2 ** n
     A_bytes = n * N / 2 * es                      # A: n 2^(n-1) values, written once
-    nh = (n - 4 + 1) if (es == 4 and n >= 5) else (n - min(n, 5) + 1)   # F / R' launches (one per level)
-    rows = es == 4 and n >= 5                     # FP32: one thread per 16-subset tile
+    # F / R' launches, one per level: row tiles of 16 subsets (FP32, n >= 5) or
+    # 8 subsets (FP64, n >= 4), else warp tiles of 32 subsets
+    rows = (es == 4 and n >= 5) or (es == 8 and n >= 4)
+    nh = (n - (4 if es == 4 else 3) + 1) if rows else (n - min(n, 5) + 1)
     fwd, bwd = ("k_forward_rows", "k_backward_rows") if rows else ("k_forward_level",
                                                                    "k_backward_level")
     tab = {

@@ -1493,7 +1493,7 @@ static int tiles_per_warp(uint32_t ntiles)
 
 cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches)
 {
-    if (use_rows_levels(P)) return launch_forward_rows(P, A, F, s, launches);
+    if (use_rows_levels(P) || rows64_fit(P)) return launch_forward_rows(P, A, F, s, launches);
     const int nh = P.n - P.wb;
     for (int hl = 0; hl <= nh; ++hl) {
         const uint32_t nt = host_binom(nh, hl);
@@ -1515,7 +1515,7 @@ cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s
 
 cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t s, int* launches)
 {
-    if (use_rows_levels(P)) return launch_backward_rows(P, A, Rc, s, launches);
+    if (use_rows_levels(P) || rows64_fit(P)) return launch_backward_rows(P, A, Rc, s, launches);
     const int nh = P.n - P.wb;
     for (int hl = nh; hl >= 0; --hl) {
         const uint32_t nt = host_binom(nh, hl);

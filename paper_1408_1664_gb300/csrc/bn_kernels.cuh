@@ -85,6 +85,7 @@ cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs
                           const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done = nullptr);
 // Step 3 in FP32 with one thread per 16-subset tile (bn_levels.cu).
 bool rows_levels_fit(const Plan& P);      // FP32 and 5 <= n < 32
+bool rows64_fit(const Plan& P);           // FP64 and 4 <= n < 31: 8-subset row tiles
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
 // F and R' of every job of a batch group in one persistent launch of
 // thread-block clusters (FP32, rows_levels_fit); one launch.

@@ -1,21 +1,23 @@
-// bn_levels.cu -- F (Eq. 9) and R' (Eq. 10) over the subset lattice in FP32,
-// one thread per tile of 16 subsets.
+// bn_levels.cu -- F (Eq. 9) and R' (Eq. 10) over the subset lattice, one
+// thread per tile of 2^B subsets: 16 in FP32 (base-2 logs), 8 in FP64
+// (natural logs; a row of 8 doubles is 64 bytes, like 16 floats).
 //
-// A tile is the 16 subsets S = (Ht << 4) | l that share their high bits Ht
-// (l = the 4 low bits).  Tiles are launched one popcount level of Ht at a
+// A tile is the 2^B subsets S = (Ht << B) | l that share their high bits Ht
+// (l = the B low bits).  Tiles are launched one popcount level of Ht at a
 // time (the sub-cube order of Section 3.2.2): every term that leaves the
 // tile reads a tile of the previous level.  A thread
-//   * adds the terms across tiles, one row of 16 values of A_i and one row of
+//   * adds the terms across tiles, one row of 2^B values of A_i and one row of
 //     F (or R') per high bit, read as four 128-bit loads each;
 //   * resolves the terms inside the tile in registers, in popcount order of l;
-//   * writes its row of 16 values.
+//   * writes its row of 2^B values.
 // Every thread of a launch has the same number of terms (same |Ht|), so warps
-// do not diverge, and the index arithmetic is shared by the 16 subsets.
+// do not diverge, and the index arithmetic is shared by the 2^B subsets.
 //
-// Log-sum-exp is kept lazily: (m, s) stands for m + log2(s) with m the first
-// term and s rescaled only when a term exceeds m by more than 2^64, so a term
-// costs one exponential.  s stays below 2^64 * 32 and every value entering is
-// finite (A and F are logs of positive sums).
+// Log-sum-exp is kept lazily: (m, s) stands for m + lg(s) with m the first
+// term and s rescaled only when a term exceeds m by more than 2^64 (FP32) or
+// e^40 (FP64), so a term costs one exponential.  s stays below that factor
+// times 32, and every value entering is finite (A and F are logs of
+// positive sums; a zero weight is a finite soft zero).
 #include <algorithm>
 
 #include "bn_device.cuh"
@@ -24,9 +26,9 @@
 namespace bn {
 namespace {
 
-constexpr int LB = 4;             // low bits of a tile
-constexpr int LN = 1 << LB;       // subsets per tile
-constexpr int BT = 28;            // binomial table rows (n - LB < 28)
+constexpr int LB = 4;             // low bits of an FP32 tile
+constexpr int LB64 = 3;           // low bits of an FP64 tile
+constexpr int BT = 28;            // binomial table rows (n - B < 28)
 
 __device__ const BinomTable g_binom_lanes = make_binom_table();
 
@@ -39,7 +41,16 @@ __device__ __forceinline__ void lazy_add(float& m, float& s, float x)
     m = big ? x : m;
 }
 
-// x with bit i (i < LB) removed: an index among the 8 four-bit patterns
+__device__ __forceinline__ void lazy_add(double& m, double& s, double x)
+{
+    const double dd = x - m;                      // +inf while the accumulator is empty
+    const bool big = dd > 40.0;
+    const double e = exp(big ? -dd : dd);
+    s = big ? fma(s, e, 1.0) : s + e;
+    m = big ? x : m;
+}
+
+// x with bit i (i < B) removed: an index among the 2^(B-1) B-bit patterns
 // without bit i.
 __host__ __device__ constexpr int squeeze4(int x, int i)
 {
@@ -50,11 +61,13 @@ __host__ __device__ constexpr int squeeze4(int x, int i)
 // L2 only: values another block of the same launch wrote).
 enum { LD_PLAIN = 0, LD_STREAM = 1, LD_L2 = 2 };
 
-__device__ __forceinline__ void load16(const float* p, float (&v)[LN], int mode)
+// A row of N values, 128-bit loads (N * sizeof(T) is a multiple of 16).
+template <int N>
+__device__ __forceinline__ void load_row(const float* p, float (&v)[N], int mode)
 {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int k = 0; k < LN / 4; ++k) {
+    for (int k = 0; k < N / 4; ++k) {
         const float4 x = mode == LD_STREAM ? __ldcs(q + k) : mode == LD_L2 ? __ldcg(q + k) : q[k];
         v[4 * k] = x.x;
         v[4 * k + 1] = x.y;
@@ -63,24 +76,32 @@ __device__ __forceinline__ void load16(const float* p, float (&v)[LN], int mode)
     }
 }
 
-__device__ __forceinline__ void load8(const float* p, float (&v)[8])
+template <int N>
+__device__ __forceinline__ void load_row(const double* p, double (&v)[N], int mode)
 {
-    const float4* q = reinterpret_cast<const float4*>(p);
+    const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float4 x = __ldcs(q + k);
-        v[4 * k] = x.x;
-        v[4 * k + 1] = x.y;
-        v[4 * k + 2] = x.z;
-        v[4 * k + 3] = x.w;
+    for (int k = 0; k < N / 2; ++k) {
+        const double2 x = mode == LD_STREAM ? __ldcs(q + k) : mode == LD_L2 ? __ldcg(q + k) : q[k];
+        v[2 * k] = x.x;
+        v[2 * k + 1] = x.y;
     }
 }
 
-__device__ __forceinline__ void store16(float* p, const float (&v)[LN])
+template <int N>
+__device__ __forceinline__ void store_row(float* p, const float (&v)[N])
 {
     float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
-    for (int k = 0; k < LN / 4; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    for (int k = 0; k < N / 4; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+
+template <int N>
+__device__ __forceinline__ void store_row(double* p, const double (&v)[N])
+{
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) q[k] = make_double2(v[2 * k], v[2 * k + 1]);
 }
 
 // Tile g of the level: the g-th hl-element subset of nh bits in colex order.
@@ -102,80 +123,82 @@ __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
     for (int x = threadIdx.x; x < BT * BT; x += blockDim.x) bt[x / BT][x % BT] = g_binom_lanes.v[x / BT][x % BT];
 }
 
-// The 16 values of F in tile Ht (its level's tiles of F already written):
+// The 2^B values of F in tile Ht (its level's tiles of F already written):
 //   F(S) = sum_{i in S} A_i(S - {i}) F(S - {i}),  F(empty) = 1
-template <int FMODE>
-__device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const float* __restrict__ A,
-                                             float* __restrict__ F)
+template <typename T, int FMODE, int B>
+__device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __restrict__ A,
+                                             T* __restrict__ F)
 {
+    constexpr int LN = 1 << B;
     const size_t half = (size_t)1 << (n - 1);
-    using L = LogOps<float>;
+    using L = LogOps<T>;
 
-    float m[LN], s[LN];
+    T m[LN], s[LN];
 #pragma unroll
-    for (int l = 0; l < LN; ++l) { m[l] = L::ninf(); s[l] = 0.0f; }
-    // terms across tiles: i = LB + j for the set bits j of Ht
+    for (int l = 0; l < LN; ++l) { m[l] = L::ninf(); s[l] = T(0); }
+    // terms across tiles: i = B + j for the set bits j of Ht
     for (uint32_t rest = Ht; rest; rest &= rest - 1) {
         const int j = __ffs(rest) - 1;
         const uint32_t Hm = Ht & ~(1u << j);
-        float a[LN], f[LN];
-        load16(A + (size_t)(LB + j) * half + ((size_t)squeeze(Hm, j) << LB), a, LD_STREAM);
-        load16(F + ((size_t)Hm << LB), f, FMODE);
+        T a[LN], f[LN];
+        load_row(A + (size_t)(B + j) * half + ((size_t)squeeze(Hm, j) << B), a, LD_STREAM);
+        load_row(F + ((size_t)Hm << B), f, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + f[l]);
     }
-    // terms inside the tile: A_i(S - {i}) for i < LB, 8 values per i
-    float ai[LB][8];
+    // terms inside the tile: A_i(S - {i}) for i < B, 2^(B-1) values per i
+    T ai[B][LN / 2];
 #pragma unroll
-    for (int i = 0; i < LB; ++i) load8(A + (size_t)i * half + ((size_t)Ht << (LB - 1)), ai[i]);
-    float Fv[LN];
-    Fv[0] = Ht == 0u ? 0.0f : m[0] + L::lg(s[0]);
+    for (int i = 0; i < B; ++i) load_row(A + (size_t)i * half + ((size_t)Ht << (B - 1)), ai[i], LD_STREAM);
+    T Fv[LN];
+    Fv[0] = Ht == 0u ? T(0) : m[0] + L::lg(s[0]);
 #pragma unroll
     for (int l = 1; l < LN; ++l) {
 #pragma unroll
-        for (int i = 0; i < LB; ++i)
+        for (int i = 0; i < B; ++i)
             if (l >> i & 1) lazy_add(m[l], s[l], ai[i][squeeze4(l ^ (1 << i), i)] + Fv[l ^ (1 << i)]);
         Fv[l] = m[l] + L::lg(s[l]);
     }
-    store16(F + ((size_t)Ht << LB), Fv);
+    store_row(F + ((size_t)Ht << B), Fv);
 }
 
-// The 16 values of R' in tile Ht (the tiles of the level above written):
+// The 2^B values of R' in tile Ht (the tiles of the level above written):
 //   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),  R'(V) = 1
-template <int FMODE>
-__device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const float* __restrict__ A,
-                                              float* __restrict__ Rc)
+template <typename T, int FMODE, int B>
+__device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const T* __restrict__ A,
+                                              T* __restrict__ Rc)
 {
-    const int nh = n - LB;
+    constexpr int LN = 1 << B;
+    const int nh = n - B;
     const uint32_t hmask = (1u << nh) - 1u;
     const size_t half = (size_t)1 << (n - 1);
-    using L = LogOps<float>;
+    using L = LogOps<T>;
 
-    float m[LN], s[LN];
+    T m[LN], s[LN];
 #pragma unroll
-    for (int l = 0; l < LN; ++l) { m[l] = L::ninf(); s[l] = 0.0f; }
+    for (int l = 0; l < LN; ++l) { m[l] = L::ninf(); s[l] = T(0); }
     for (uint32_t rest = ~Ht & hmask; rest; rest &= rest - 1) {
         const int j = __ffs(rest) - 1;
-        float a[LN], r[LN];
-        load16(A + (size_t)(LB + j) * half + ((size_t)squeeze(Ht, j) << LB), a, LD_STREAM);
-        load16(Rc + ((size_t)(Ht | (1u << j)) << LB), r, FMODE);
+        T a[LN], r[LN];
+        load_row(A + (size_t)(B + j) * half + ((size_t)squeeze(Ht, j) << B), a, LD_STREAM);
+        load_row(Rc + ((size_t)(Ht | (1u << j)) << B), r, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + r[l]);
     }
-    // A_i(T) for i < LB not in T, 8 values per i
-    float ai[LB][8];
+    // A_i(T) for i < B not in T, 2^(B-1) values per i
+    T ai[B][LN / 2];
 #pragma unroll
-    for (int i = 0; i < LB; ++i) load8(A + (size_t)i * half + ((size_t)Ht << (LB - 1)), ai[i]);
-    float Rv[LN];
-    Rv[LN - 1] = Ht == hmask ? 0.0f : m[LN - 1] + L::lg(s[LN - 1]);
+    for (int i = 0; i < B; ++i) load_row(A + (size_t)i * half + ((size_t)Ht << (B - 1)), ai[i], LD_STREAM);
+    T Rv[LN];
+    Rv[LN - 1] = Ht == hmask ? T(0) : m[LN - 1] + L::lg(s[LN - 1]);
 #pragma unroll
     for (int l = LN - 2; l >= 0; --l) {
 #pragma unroll
-        for (int i = 0; i < LB; ++i)
+        for (int i = 0; i < B; ++i)
             if (!(l >> i & 1)) lazy_add(m[l], s[l], ai[i][squeeze4(l, i)] + Rv[l | (1 << i)]);
         Rv[l] = m[l] + L::lg(s[l]);
     }
-    store16(Rc + ((size_t)Ht << LB), Rv);
+    store_row(Rc + ((size_t)Ht << B), Rv);
 }
 
 __device__ __forceinline__ void cluster_barrier()
@@ -201,10 +224,14 @@ __device__ __forceinline__ uint32_t cluster_blocks()
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 3)
-k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ F,
+// FP32: 16-subset tiles at three blocks per SM (80 registers); FP64:
+// 8-subset tiles at two.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ F,
                size_t js)
 {
+    constexpr int B = sizeof(T) == 4 ? LB : LB64;
     A = job_ptr(A, js);
     F = job_ptr(F, js);
     __shared__ uint32_t bt[BT][BT];
@@ -212,13 +239,15 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, floa
     __syncthreads();
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ntiles) return;
-    forward_tile<LD_PLAIN>(n, tile_of(g, hl, n - LB, bt), A, F);
+    forward_tile<T, LD_PLAIN, B>(n, tile_of(g, hl, n - B, bt), A, F);
 }
 
-__global__ void __launch_bounds__(256, 3)
-k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, float* __restrict__ Rc,
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ Rc,
                 size_t js)
 {
+    constexpr int B = sizeof(T) == 4 ? LB : LB64;
     A = job_ptr(A, js);
     Rc = job_ptr(Rc, js);
     __shared__ uint32_t bt[BT][BT];
@@ -226,7 +255,7 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const float* __restrict__ A, flo
     __syncthreads();
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ntiles) return;
-    backward_tile<LD_PLAIN>(n, tile_of(g, hl, n - LB, bt), A, Rc);
+    backward_tile<T, LD_PLAIN, B>(n, tile_of(g, hl, n - B, bt), A, Rc);
 }
 
 // Step 3 of a whole batch group in one persistent launch of thread-block
@@ -262,8 +291,8 @@ k_rows_cluster(int n, int items, const float* __restrict__ A, float* __restrict_
             const uint32_t nt = bt[nh][hl];
             for (uint32_t g = t0; g < nt; g += stride) {
                 const uint32_t Ht = tile_of(g, hl, nh, bt);
-                if (fwd) forward_tile<LD_L2>(n, Ht, Aj, X);
-                else backward_tile<LD_L2>(n, Ht, Aj, X);
+                if (fwd) forward_tile<float, LD_L2, LB>(n, Ht, Aj, X);
+                else backward_tile<float, LD_L2, LB>(n, Ht, Aj, X);
             }
             cluster_barrier();
         }
@@ -287,13 +316,23 @@ bool rows_levels_fit(const Plan& P)
     return P.prec != 0 && P.n >= LB + 1 && P.n - LB < BT;
 }
 
+bool rows64_fit(const Plan& P)
+{
+    return P.prec == 0 && P.n >= LB64 + 1 && P.n - LB64 < BT;
+}
+
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches)
 {
-    const int nh = P.n - LB;
+    const int nh = P.n - (P.prec == 0 ? LB64 : LB);
     for (int hl = 0; hl <= nh; ++hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        k_forward_rows<<<dim3((nt + 255) / 256, P.nj), 256, 0, s>>>(P.n, hl, nt, (const float*)A,
-                                                                   (float*)F, P.js);
+        const dim3 grid((nt + 255) / 256, P.nj);
+        if (P.prec == 0)
+            k_forward_rows<double><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A, (double*)F,
+                                                        P.js);
+        else
+            k_forward_rows<float><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A, (float*)F,
+                                                       P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
@@ -304,11 +343,16 @@ cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStrea
 cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStream_t s,
                                  int* launches)
 {
-    const int nh = P.n - LB;
+    const int nh = P.n - (P.prec == 0 ? LB64 : LB);
     for (int hl = nh; hl >= 0; --hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        k_backward_rows<<<dim3((nt + 255) / 256, P.nj), 256, 0, s>>>(P.n, hl, nt, (const float*)A,
-                                                                    (float*)Rc, P.js);
+        const dim3 grid((nt + 255) / 256, P.nj);
+        if (P.prec == 0)
+            k_backward_rows<double><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A,
+                                                         (double*)Rc, P.js);
+        else
+            k_backward_rows<float><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+                                                        (float*)Rc, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
