@@ -436,6 +436,106 @@ k_scores_bin_hi(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
     }
 }
 
+// Scores of the families with exactly KP parents (5 <= KP <= 8), binary
+// data, from a histogram of the samples' cells: one warp per family.  A lane
+// takes runs of 16 samples; for each valid sample it forms the cell key
+// (parent t's value in bit t, the child's value in bit KP) from the bit
+// planes with shifts and masks, and adds 1 to the warp's histogram of
+// 2^(KP+1) cells in shared memory.  The BDeu terms follow configuration by
+// configuration (cell = 2 * configuration + child value, the canonical
+// order) in 64-bit fixed point, so the sum equals the per-cell kernels' bit
+// for bit.  The work is O(m) per family instead of O(2^KP m / 64) popcs:
+// the better choice once 2^KP cells outnumber the words.
+template <int KP>
+__global__ void __launch_bounds__(256)
+k_scores_bin_hist(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
+                  const uint64_t* __restrict__ planes, const double* __restrict__ Dvals, int rows,
+                  const long long* __restrict__ T, const double* __restrict__ log_rho,
+                  int64_t f_begin, int64_t f_count, uint32_t* __restrict__ masks,
+                  uint32_t* __restrict__ cmasks, double* __restrict__ logB,
+                  int64_t* __restrict__ debug_counts, size_t js, double tinv,
+                  const double* __restrict__ fxj)
+{
+    BN_JOB_SCORES();
+    constexpr int NCFG = 1 << KP;
+    __shared__ uint32_t hist[8][2 * NCFG];
+    __shared__ uint32_t bt[32][KP + 1];
+    for (int e = threadIdx.x; e < 32 * (KP + 1); e += blockDim.x)
+        bt[e / (KP + 1)][e % (KP + 1)] = binom(e / (KP + 1), e % (KP + 1));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* hw = hist[warp];
+    for (int c = lane; c < 2 * NCFG; c += 32) hw[c] = 0u;
+    __syncthreads();
+    const long long* Tq = T + (size_t)find_row(Dvals, rows, (uint32_t)NCFG) * (m + 1);
+    const long long* Tqr = T + (size_t)find_row(Dvals, rows, 2u * NCFG) * (m + 1);
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    for (int64_t fi = (int64_t)blockIdx.x * 8 + warp; fi < f_count; fi += nwarps) {
+        const int64_t g = f_begin + fi;
+        const int i = (int)(g / Ck);
+        uint32_t r = (uint32_t)(g % Ck);
+        const uint32_t rank = r;
+        uint32_t cm = 0;                            // colex unrank of r among KP-subsets
+        {
+            int c = n - 2;
+            for (int t = KP; t >= 1; --t) {
+                while (bt[c][t] > r) --c;
+                cm |= 1u << c;
+                r -= bt[c][t];
+                --c;
+            }
+        }
+        const uint32_t G = expand(cm, i);
+        const uint64_t* pr[KP];                     // the value-1 plane of each parent
+        {
+            uint32_t gg = G;
+#pragma unroll
+            for (int t = 0; t < KP; ++t) {
+                pr[t] = planes + ((size_t)(__ffs(gg) - 1) * 2 + 1) * W;
+                gg &= gg - 1;
+            }
+        }
+        const uint64_t* c0 = planes + (size_t)i * 2 * W;
+        const uint64_t* c1 = c0 + W;
+        for (int ch = lane; ch < 4 * W; ch += 32) {
+            const int w = ch >> 2, sh = (ch & 3) * 16;
+            const uint64_t x1w = c1[w];
+            uint32_t valid = (uint32_t)((c0[w] | x1w) >> sh) & 0xFFFFu;
+            const uint32_t x1 = (uint32_t)(x1w >> sh);
+            uint32_t pb[KP];
+#pragma unroll
+            for (int t = 0; t < KP; ++t) pb[t] = (uint32_t)(pr[t][w] >> sh);
+            while (valid) {
+                const int b = __ffs(valid) - 1;
+                valid &= valid - 1;
+                uint32_t key = (x1 >> b & 1u) << KP;
+#pragma unroll
+                for (int t = 0; t < KP; ++t) key |= (pb[t] >> b & 1u) << t;
+                atomicAdd(&hw[key], 1u);
+            }
+        }
+        __syncwarp();
+        long long acc = 0;
+        for (int j = lane; j < NCFG; j += 32) {
+            const uint32_t N0 = hw[j], N1 = hw[j | NCFG];
+            acc += Tqr[N0] + Tqr[N1] - Tq[N0 + N1];
+            if (debug_counts) {
+                debug_counts[2 * j] = N0;
+                debug_counts[2 * j + 1] = N1;
+            }
+            hw[j] = 0u;
+            hw[j | NCFG] = 0u;
+        }
+        __syncwarp();
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const int64_t x = (int64_t)i * K + off + rank;
+            logB[x] = (double)acc * tinv + (log_rho ? log_rho[KP] : 0.0);
+            masks[x] = G;
+            cmasks[x] = cm;
+        }
+    }
+}
+
 // Scores with one warp per family and one lane per 64-sample word (m <= 2048):
 // every lane keeps its word of each parent plane and child plane in
 // registers, so a cell costs an AND chain, a popc and one warp reduction.
@@ -1283,8 +1383,10 @@ cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, int fxs, v
 static uint32_t host_binom(int n, int k);
 
 // Binary data, d <= 8: k_scores_bin for the families of at most 4 parents
-// and one k_scores_bin_hi launch per larger family size.  The range is all
-// families or a single one.
+// and one launch per larger family size: k_scores_bin_hi (per-cell popc)
+// below kHistFrom parents, k_scores_bin_hist (per-sample histogram) from
+// there.  The range is all families or a single one.
+static constexpr int kHistFrom = 7;
 static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, const double* Dvals,
                                      const void* Tv, const double* log_rho, int64_t x_begin,
                                      int64_t x_count, uint32_t* masks, uint32_t* cmasks,
@@ -1318,6 +1420,23 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
         const int64_t Ck = host_binom(P.n - 1, k);
         const int64_t fb = x_count == 1 ? i1 * Ck + (f1 - off[k]) : 0;
         const int64_t fn = x_count == 1 ? 1 : (int64_t)P.n * Ck;
+        if (k >= kHistFrom) {                       // histogram of the samples' cells
+            const unsigned grid = (unsigned)std::min<int64_t>((fn + 7) / 8, 152 * 32);
+#define BN_BIN_HIST(KP)                                                                           \
+    k_scores_bin_hist<KP><<<dim3(grid, P.nj), 256, 0, s>>>(                                    \
+        P.n, P.m, P.W, P.K, off[k], Ck, planes, Dvals, P.rows, T, log_rho, fb, fn, masks, cmasks, \
+        logB, debug_counts, P.js, tinv, fxj)
+            switch (k) {
+            case 5: BN_BIN_HIST(5); break;
+            case 6: BN_BIN_HIST(6); break;
+            case 7: BN_BIN_HIST(7); break;
+            default: BN_BIN_HIST(8); break;
+            }
+#undef BN_BIN_HIST
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         const int64_t threads = fn << (k - 4);
         const unsigned grid = (unsigned)((threads + 127) / 128);
 #define BN_BIN_HI(HB)                                                                             \
