@@ -597,6 +597,82 @@ __device__ __forceinline__ void lse_lazy(T& m, T& s, T x)
 // Columns with d low elements are copies, those with d - 1 take the 1 + |H|
 // rows of at most one high element, the others every row of size at most
 // d - |G_L|.
+// Column sums by butterflies over the h high dimensions (FP32): one block per
+// node i and run of CPB consecutive low columns c.  The 2^h values
+// B_i(G_H + G_L) of each column (zero where |G_H| > d - |G_L|) are gathered
+// from the reordered table, the truncated upward zeta over the subsets of
+// every H follows in shared memory with a log-sum-exp per step (h * 2^(h-1)
+// per column, against sum_H C(|H|, <= d - |G_L|) terms summed directly: the
+// better order once d is large), and each C_H(G_L) goes to slot c of tile
+// (i, H), the CPB columns of a run side by side (32-byte writes).
+template <int CPB>
+__global__ void __launch_bounds__(256)
+k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* __restrict__ A,
+                size_t js)
+{
+    tab = job_ptr(tab, js);
+    A = job_ptr(A, js);
+    using Lg = LogOps<float>;
+    __shared__ SBinom sb;
+    __shared__ uint32_t off13[16];
+    __shared__ uint32_t rowoff_k[32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* v = reinterpret_cast<float*>(smem_raw);  // [H][column of the run]
+    const int h = n - 1 - TB;
+    const uint32_t H2 = 1u << h;
+    fill_sbinom(sb);
+    if (threadIdx.x < 16) {
+        uint32_t o = 0;
+        for (int k = 0; k < (int)threadIdx.x && k <= TB; ++k) o += binom(TB, k);
+        off13[threadIdx.x] = o;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t o = 0;
+        for (int k = 0; k < (int)threadIdx.x && k <= min(d, h); ++k)
+            o += binom(h, k) * off13[min(d - k, TB) + 1];
+        rowoff_k[threadIdx.x] = o;
+    }
+    __syncthreads();
+    const uint32_t ncol = num_small_subsets(TB, d);
+    const uint32_t nrun = (ncol + CPB - 1) / CPB;
+    const int i = (int)(blockIdx.x / nrun);
+    const uint32_t c0 = (blockIdx.x % nrun) * CPB;
+    const float* tb = tab + (size_t)i * K;
+    for (uint32_t e = threadIdx.x; e < H2 * CPB; e += blockDim.x) {
+        const uint32_t H = e / CPB, c = c0 + e % CPB;
+        float val = Lg::ninf();
+        if (c < ncol) {
+            int kl = 0;
+            while (off13[kl + 1] <= c) ++kl;
+            const int kh = __popc(H);
+            if (kh <= d - kl) {
+                uint32_t r = 0;                     // colex rank of H among kh-subsets
+                int t = 1;
+                for (uint32_t x = H; x; x &= x - 1, ++t) r += sb_binom(sb, __ffs(x) - 1, t);
+                val = tb[rowoff_k[kh] + r * off13[min(d - kh, TB) + 1] + c];
+            }
+        }
+        v[e] = val;
+    }
+    __syncthreads();
+    for (int j = 0; j < h; ++j) {
+        const uint32_t jm = (1u << j) - 1u;
+        for (uint32_t e = threadIdx.x; e < (H2 >> 1) * CPB; e += blockDim.x) {
+            const uint32_t p = e / CPB, cc = e % CPB;
+            const uint32_t lo = ((p & ~jm) << 1) | (p & jm);
+            const uint32_t hi = lo | (1u << j);
+            v[hi * CPB + cc] = Lg::lse(v[hi * CPB + cc], v[lo * CPB + cc]);
+        }
+        __syncthreads();
+    }
+    float* Ai = A + ((size_t)i << (n - 1));
+    for (uint32_t e = threadIdx.x; e < H2 * CPB; e += blockDim.x) {
+        const uint32_t H = e / CPB, c = c0 + e % CPB;
+        if (c < ncol) Ai[((size_t)H << TB) + c] = v[e];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A, size_t js)
@@ -947,6 +1023,25 @@ __global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restr
 // ===========================================================================
 // Launchers.
 // ===========================================================================
+// FP32 column sums by butterflies over the h high dimensions when they take
+// at most two thirds of the steps of the direct sums and a column run fits 64 KB of
+// shared memory (h <= 13): the high in-degree bounds (d >= 6 at n = 25).
+bool use_colb(const Plan& P)
+{
+    const int h = P.n - 1 - TB;
+    if (P.prec == 0 || h > 13) return false;
+    double direct = 0.0, ncol = 0.0;
+    for (int kl = 0; kl <= P.d && kl <= TB; ++kl) {
+        ncol += (double)binom_host(TB, kl);
+        double rows = 0.0;
+        for (int kh = 0; kh <= P.d - kl && kh <= h; ++kh)
+            rows += (double)binom_host(h, kh) * std::ldexp(1.0, h - kh);
+        direct += (double)binom_host(TB, kl) * rows;
+    }
+    const double bfly = ncol * h * std::ldexp(1.0, h - 1);
+    return direct >= 1.5 * bfly;
+}
+
 size_t upzeta13_cols_smem_bytes(const Plan& P)
 {
     const size_t es = P.prec == 0 ? 8 : 4;
@@ -1000,7 +1095,22 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
     const size_t sc = upzeta13_cols_smem_bytes(P), sm = upzeta13_smem_bytes(P);
     uint64_t nrow = 0;
     for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
-    if (nrow * 4 * 8 <= 160 * 1024) {                 // warp per tile, 8 tiles per block
+    if (use_colb(P)) {                                // butterflies over the high dims
+        const int cpb = h <= 11 ? 8 : (h == 12 ? 4 : 2);
+        uint64_t ncol = 0;
+        for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
+        const unsigned nblk = (unsigned)((uint64_t)P.n * ((ncol + cpb - 1) / cpb));
+        const size_t smb = ((size_t)cpb << h) * 4;
+        if (cpb == 8)
+            k_upzeta13_colb<8><<<dim3(nblk, P.nj), 256, smb, s>>>(P.n, P.d, P.K,
+                                                                  (const float*)tab, (float*)A, P.js);
+        else if (cpb == 4)
+            k_upzeta13_colb<4><<<dim3(nblk, P.nj), 256, smb, s>>>(P.n, P.d, P.K,
+                                                                  (const float*)tab, (float*)A, P.js);
+        else
+            k_upzeta13_colb<2><<<dim3(nblk, P.nj), 256, smb, s>>>(P.n, P.d, P.K,
+                                                                  (const float*)tab, (float*)A, P.js);
+    } else if (nrow * 4 * 8 <= 160 * 1024) {          // warp per tile, 8 tiles per block
         const uint64_t ntiles = (uint64_t)P.n << h;
         const dim3 gw((unsigned)std::min<uint64_t>((ntiles + 7) / 8, 152 * 16), P.nj);
         const size_t sw = (size_t)nrow * 4 * 8;
@@ -1072,6 +1182,9 @@ cudaError_t set_tile13_attributes()
     SETA(k_upzeta13_cols<float>)
     SETA(k_upzeta13_colw<double>)
     SETA(k_upzeta13_colw<float>)
+    SETA(k_upzeta13_colb<8>)
+    SETA(k_upzeta13_colb<4>)
+    SETA(k_upzeta13_colb<2>)
     SETA(k_upzeta13<double>)
     SETA(k_upzeta13<float>)
     SETA((k_gamma13_p1<double, false>))
