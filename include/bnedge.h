@@ -286,9 +286,9 @@ enum {
 /* Copies a stage array of the last job into host memory.  DP arrays are
  * doubles (natural log) for BN_FP64 and floats (log2) for BN_FP32_SHIFTED;
  * `bytes` must equal the stage size.  BN_EINVAL otherwise.  For n >= 14 a
- * Gamma_v(G) whose B_v(G) Gamma_v(G) lies more than 64 + log2(K 2^(n-14))
- * bits below F(V) may hold a smaller floor value (it moves no posterior by
- * more than 2^-64 in all). */
+ * Gamma_v(G) whose B_v(G) Gamma_v(G) lies more than 64 (FP64) or 24 (FP32)
+ * + log2(K 2^(n-14)) bits below F(V) may hold a floor value instead (it moves
+ * no posterior by more than 2^-64, resp. 2^-24, in all). */
 int bn_debug_stage(bn_ctx* ctx, int32_t stage, void* host_out, size_t bytes);
 /* Contingency counts of one family computed by the device counting routine:
  * counts[config*r_i + x_i], q*r_i int64 values on the host. */

@@ -896,8 +896,9 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 // full set S_H = H + all 13 low bits, and B_v(G) <= A_v(S_H).  An output
 // below L = F(V) - margin - A_v(S_H) therefore moves no posterior by more than
 // 2^-margin, and the K * 2^h outputs of v together by at most
-// K 2^h 2^-margin; the launcher takes margin = 64 + log2(K 2^h) bits, so the
-// total is below 2^-64.  A tile whose upper bound M is below L writes every
+// K 2^h 2^-margin; the launcher takes margin = 64 + log2(K 2^h) bits in FP64
+// and 24 + log2(K 2^h) in FP32, so the total is below 2^-64 (resp. 2^-24,
+// against the FP32 tolerance of 1e-4).  A tile whose upper bound M is below L writes every
 // output as L - gap (no butterflies); a tile within one window of
 // max(L, s(full)) takes the single-scale pass, its outputs held at >= L - gap.
 // Outputs at or above L are exact as before.  The written value, like the
@@ -1146,8 +1147,9 @@ cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
     const int h = P.n - 1 - TB;
     const size_t sm = gamma13_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);
-    // relevance margin: 64 bits + log2(K 2^h), in bits (FP32) or nats (FP64)
-    const double mbits = 64.0 + std::ceil(std::log2((double)P.K)) + h;
+    // relevance margin: 64 (FP64) or 24 (FP32: its tolerance is 1e-4) bits +
+    // log2(K 2^h), in bits (FP32) or nats (FP64)
+    const double mbits = (P.prec == 0 ? 64.0 : 24.0) + std::ceil(std::log2((double)P.K)) + h;
     const double margin = P.prec == 0 ? mbits * 0.69314718055994531 : mbits;
     // the order prior is a separate instance: the plain kernel has no trace of it
     if (P.prec == 0) {
