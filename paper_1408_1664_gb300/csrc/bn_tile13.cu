@@ -327,13 +327,14 @@ __device__ __forceinline__ void sum_pass(T (&v)[TR], T (&sc)[TR], T* A1, T* A0, 
 {
     using Lg = LogOps<T>;
     T* E = A1;
+    const int pt = __popc(t);             // |el3(r, t)| = |r| + |t| (disjoint bits)
 #pragma unroll
     for (int r = 0; r < TR; ++r) sc[r] = scale_of(v[r]);
     ld3(A1, v, t);                        // inputs
     st3(E, sc, t);                        // scales, read again in layouts 2 and 1
 #pragma unroll
     for (int r = 0; r < TR; ++r)
-        v[r] = (!UP || __popc(el3(r, t)) <= d) ? Lg::ex(v[r] - scale_base(sc[r])) : T(0);
+        v[r] = (!UP || __popc(r) + pt <= d) ? Lg::ex(v[r] - scale_base(sc[r])) : T(0);
     sum_bfly<UP>(v, sc, 0, 3);
     __syncthreads();
     st3(A0, v, t);
@@ -775,10 +776,10 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     const uint32_t H = blockIdx.x & ((1u << h) - 1u);
     T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
 
+    // |el1(r, t)| = |r| + |t| (disjoint bits): the slots with more than d
+    // elements are no column (no input)
+    const int pt = __popc(t);
     if (t == 0) *tmax = ord_enc(Lg::ninf());
-#pragma unroll
-    for (int r = 0; r < TR; ++r)                 // no term: zero (slots that are no column)
-        if (__popc(el1(r, t)) > d) A0[swz(el1(r, t))] = Lg::ninf();
     T tm = Lg::ninf();
     for (uint32_t c = t; c < ncol; c += TT) {
         const T v = out[c];
@@ -816,7 +817,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
             ld1(A1, x, t);
 #pragma unroll
             for (int r = 0; r < TR; ++r)
-                x[r] = (__popc(el1(r, t)) <= d) ? Lg::ex(x[r] - sp) : T(0);
+                x[r] = (__popc(r) + pt <= d) ? Lg::ex(x[r] - sp) : T(0);
             bfly_plain<true>(x, 0, 5);
             st1(A0, x, t);
             __syncthreads();
@@ -840,7 +841,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
                 ld1(A1, x, t);
 #pragma unroll
                 for (int r = 0; r < TR; ++r)
-                    x[r] = (__popc(el1(r, t)) <= d) ? Lg::ex(x[r] - sp) : T(0);
+                    x[r] = (__popc(r) + pt <= d) ? Lg::ex(x[r] - sp) : T(0);
                 bfly_plain<true>(x, 0, 5);
                 st1(A0, x, t);
                 __syncthreads();
@@ -866,6 +867,10 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     }
 
     // --- max-plus pass: layouts 1, 2, 3 ------------------------------------
+#pragma unroll
+    for (int r = 0; r < TR; ++r)                 // no term: zero (slots that are no column)
+        if (__popc(r) + pt > d) A0[swz(el1(r, t))] = Lg::ninf();
+    __syncthreads();
     T v[TR];
     ld1(A0, v, t);
     bfly_max<true>(v, 0, 5);
