@@ -93,6 +93,53 @@ __device__ __forceinline__ uint32_t squeeze(uint32_t S, int i)
     return (S & low) | ((S >> 1) & ~low);
 }
 
+// ---------------------------------------------------------------------------
+// Rows of A in level order inside each tile (use_tlo).  With the FP32
+// schedule of 13-dimension up-zeta tiles and step-3 row kernels, A_i(S')
+// (S' over the n - 1 other variables) is held in rows of 2^lw values
+// (lw = 3 for i < 4, else 4: the row widths step 3 reads), S' = (R << lw) | l,
+// and the 2^rb rows of one up-zeta tile (rb = 13 - lw, R = (H << rb) | r)
+// are ordered by |r|, then colexicographically: row R sits at
+// (H << rb) | place_rb(r).  A popcount level of step 3 then reads one
+// contiguous run of rows from each tile block, not rows scattered over it;
+// every up-zeta tile still writes its own block only, and the empty and
+// full in-tile sets keep their places (first and last).
+// ---------------------------------------------------------------------------
+struct PlaceTable {
+    uint16_t p9[512];
+    uint16_t p10[1024];
+};
+
+constexpr PlaceTable make_place_table()
+{
+    const BinomTable b = make_binom_table();
+    PlaceTable t{};
+    for (int rb = 9; rb <= 10; ++rb)
+        for (uint32_t r = 0; r < (1u << rb); ++r) {
+            int k = 0;
+            uint32_t colex = 0;
+            for (int x = 0; x < rb; ++x)
+                if (r >> x & 1u) {
+                    ++k;
+                    colex += b.v[x][k];                 // C(element, its index)
+                }
+            uint32_t start = 0;                         // rows with fewer elements
+            for (int q = 0; q < k; ++q) start += b.v[rb][q];
+            if (rb == 9) t.p9[r] = (uint16_t)(start + colex);
+            else t.p10[r] = (uint16_t)(start + colex);
+        }
+    return t;
+}
+
+__device__ const PlaceTable g_place = make_place_table();
+
+// Place of row R (rb = 9 or 10 in-tile bits) in the tile-level order.
+__device__ __forceinline__ uint32_t tlo_row(uint32_t R, int rb)
+{
+    const uint32_t m = (1u << rb) - 1u;
+    return (R & ~m) | (rb == 9 ? g_place.p9[R & m] : g_place.p10[R & m]);
+}
+
 // Insert a zero bit at position i.
 __device__ __forceinline__ uint32_t expand(uint32_t c, int i)
 {

@@ -1309,14 +1309,25 @@ __global__ void k_add_weights(double* __restrict__ logB, const double* __restric
 // the working precision and log base; A is [i * 2^(n-1) + c], c = S with
 // bit i removed, so |S| = popc(c).
 template <typename T>
-__global__ void k_apply_q(int n, const T* __restrict__ lq, T* __restrict__ A)
+__global__ void k_apply_q(int n, const T* __restrict__ lq, T* __restrict__ A, int tlo)
 {
     const int64_t total = (int64_t)n << (n - 1);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t >> (n - 1));
         const uint32_t c = (uint32_t)(t & (((int64_t)1 << (n - 1)) - 1));
-        A[t] += lq[i * n + __popc(c)];
+        int size = __popc(c);
+        if (tlo) {
+            // in tile-level order the in-tile row part of c is a place p:
+            // its size is the number of row sizes whose places end at or
+            // before p (places of size k start at sum_{q<k} C(rb, q))
+            const int lw = i < 4 ? 3 : 4, rb = 13 - lw;
+            const uint32_t p = (c >> lw) & ((1u << rb) - 1u);
+            int k = 0;
+            for (uint32_t end = 1; end <= p; end += binom(rb, k)) ++k;
+            size = __popc(c >> 13) + k + __popc(c & ((1u << lw) - 1u));
+        }
+        A[t] += lq[i * n + size];
     }
 }
 
@@ -1523,9 +1534,10 @@ cudaError_t launch_apply_q(const Plan& P, const void* lq, void* A, cudaStream_t 
     const int64_t total = (int64_t)P.n << (P.n - 1);
     const int grid = grid_for(total, 256, 152 * 16);
     if (P.prec == 0)
-        k_apply_q<double><<<grid, 256, 0, s>>>(P.n, (const double*)lq, (double*)A);
+        k_apply_q<double><<<grid, 256, 0, s>>>(P.n, (const double*)lq, (double*)A, 0);
     else
-        k_apply_q<float><<<grid, 256, 0, s>>>(P.n, (const float*)lq, (float*)A);
+        k_apply_q<float><<<grid, 256, 0, s>>>(P.n, (const float*)lq, (float*)A,
+                                              use_tlo(P) ? 1 : 0);
     return cudaGetLastError();
 }
 

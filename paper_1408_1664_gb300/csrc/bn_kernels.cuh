@@ -133,6 +133,9 @@ inline bool use_tile13_up(const Plan& P) { return P.up13 != 0; }
 inline bool use_tile13_gamma(const Plan& P) { return P.g13 != 0; }
 inline bool use_rows_levels(const Plan& P) { return P.frows != 0; }
 inline bool needs_rank13(const Plan& P) { return P.up13 || P.g13; }
+// A in tile-level row order (see bn_device.cuh): FP32 with the 13-dimension
+// up-zeta tiles and the step-3 row kernels (not the cluster kernel).
+inline bool use_tlo(const Plan& P) { return P.prec != 0 && P.up13 && P.frows && !P.frc; }
 // The default schedule: every specialised kernel that fits.
 inline void default_schedule(Plan& P)
 {

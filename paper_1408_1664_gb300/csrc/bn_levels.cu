@@ -123,9 +123,14 @@ __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
     for (int x = threadIdx.x; x < BT * BT; x += blockDim.x) bt[x / BT][x % BT] = g_binom_lanes.v[x / BT][x % BT];
 }
 
+// TLO (B = 4): the rows of A in tile-level order (see bn_device.cuh): a
+// term across tiles reads row tlo_row(R, 9) of A_{B+j} (rows of 16 values,
+// nine in-tile row bits); the in-tile rows of A_i (i < B: rows of 8 values,
+// ten in-tile row bits) sit at tlo_row(Ht, 10).
+//
 // The 2^B values of F in tile Ht (its level's tiles of F already written):
 //   F(S) = sum_{i in S} A_i(S - {i}) F(S - {i}),  F(empty) = 1
-template <typename T, int FMODE, int B>
+template <typename T, int FMODE, int B, bool TLO = false>
 __device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __restrict__ A,
                                              T* __restrict__ F)
 {
@@ -141,7 +146,8 @@ __device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __rest
         const int j = __ffs(rest) - 1;
         const uint32_t Hm = Ht & ~(1u << j);
         T a[LN], f[LN];
-        load_row(A + (size_t)(B + j) * half + ((size_t)squeeze(Hm, j) << B), a, LD_STREAM);
+        const uint32_t row = TLO ? tlo_row(squeeze(Hm, j), 9) : squeeze(Hm, j);
+        load_row(A + (size_t)(B + j) * half + ((size_t)row << B), a, LD_STREAM);
         load_row(F + ((size_t)Hm << B), f, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + f[l]);
@@ -149,7 +155,9 @@ __device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __rest
     // terms inside the tile: A_i(S - {i}) for i < B, 2^(B-1) values per i
     T ai[B][LN / 2];
 #pragma unroll
-    for (int i = 0; i < B; ++i) load_row(A + (size_t)i * half + ((size_t)Ht << (B - 1)), ai[i], LD_STREAM);
+    for (int i = 0; i < B; ++i)
+        load_row(A + (size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)), ai[i],
+                 LD_STREAM);
     T Fv[LN];
     Fv[0] = Ht == 0u ? T(0) : m[0] + L::lg(s[0]);
 #pragma unroll
@@ -164,7 +172,7 @@ __device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __rest
 
 // The 2^B values of R' in tile Ht (the tiles of the level above written):
 //   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),  R'(V) = 1
-template <typename T, int FMODE, int B>
+template <typename T, int FMODE, int B, bool TLO = false>
 __device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const T* __restrict__ A,
                                               T* __restrict__ Rc)
 {
@@ -180,7 +188,8 @@ __device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const T* __res
     for (uint32_t rest = ~Ht & hmask; rest; rest &= rest - 1) {
         const int j = __ffs(rest) - 1;
         T a[LN], r[LN];
-        load_row(A + (size_t)(B + j) * half + ((size_t)squeeze(Ht, j) << B), a, LD_STREAM);
+        const uint32_t row = TLO ? tlo_row(squeeze(Ht, j), 9) : squeeze(Ht, j);
+        load_row(A + (size_t)(B + j) * half + ((size_t)row << B), a, LD_STREAM);
         load_row(Rc + ((size_t)(Ht | (1u << j)) << B), r, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + r[l]);
@@ -188,7 +197,9 @@ __device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const T* __res
     // A_i(T) for i < B not in T, 2^(B-1) values per i
     T ai[B][LN / 2];
 #pragma unroll
-    for (int i = 0; i < B; ++i) load_row(A + (size_t)i * half + ((size_t)Ht << (B - 1)), ai[i], LD_STREAM);
+    for (int i = 0; i < B; ++i)
+        load_row(A + (size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)), ai[i],
+                 LD_STREAM);
     T Rv[LN];
     Rv[LN - 1] = Ht == hmask ? T(0) : m[LN - 1] + L::lg(s[LN - 1]);
 #pragma unroll
@@ -226,7 +237,7 @@ __device__ __forceinline__ uint32_t cluster_blocks()
 
 // FP32: 16-subset tiles at three blocks per SM (80 registers); FP64:
 // 8-subset tiles at two.
-template <typename T>
+template <typename T, bool TLO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ F,
                size_t js)
@@ -239,10 +250,10 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __res
     __syncthreads();
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ntiles) return;
-    forward_tile<T, LD_PLAIN, B>(n, tile_of(g, hl, n - B, bt), A, F);
+    forward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, F);
 }
 
-template <typename T>
+template <typename T, bool TLO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ Rc,
                 size_t js)
@@ -255,7 +266,7 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __re
     __syncthreads();
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ntiles) return;
-    backward_tile<T, LD_PLAIN, B>(n, tile_of(g, hl, n - B, bt), A, Rc);
+    backward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, Rc);
 }
 
 // Step 3 of a whole batch group in one persistent launch of thread-block
@@ -328,11 +339,14 @@ cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStrea
         const uint32_t nt = (uint32_t)choose(nh, hl);
         const dim3 grid((nt + 255) / 256, P.nj);
         if (P.prec == 0)
-            k_forward_rows<double><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A, (double*)F,
-                                                        P.js);
+            k_forward_rows<double, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A,
+                                                               (double*)F, P.js);
+        else if (use_tlo(P))
+            k_forward_rows<float, true><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+                                                             (float*)F, P.js);
         else
-            k_forward_rows<float><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A, (float*)F,
-                                                       P.js);
+            k_forward_rows<float, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+                                                              (float*)F, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
@@ -348,11 +362,14 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
         const uint32_t nt = (uint32_t)choose(nh, hl);
         const dim3 grid((nt + 255) / 256, P.nj);
         if (P.prec == 0)
-            k_backward_rows<double><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A,
-                                                         (double*)Rc, P.js);
+            k_backward_rows<double, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A,
+                                                                (double*)Rc, P.js);
+        else if (use_tlo(P))
+            k_backward_rows<float, true><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+                                                              (float*)Rc, P.js);
         else
-            k_backward_rows<float><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
-                                                        (float*)Rc, P.js);
+            k_backward_rows<float, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+                                                               (float*)Rc, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;

@@ -2,6 +2,7 @@
 // validation, job planning, the device workspace, the launch sequence of
 // Algorithm 1, and the serving queue (bn_submit / bn_poll / bn_wait).
 #include "bnedge.h"
+#include "bn_device.cuh"
 #include "bn_kernels.cuh"
 
 #include <algorithm>
@@ -998,6 +999,24 @@ int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask,
     return BN_OK;
 }
 
+// A_i read back from tile-level row order (bn_device.cuh) into plain order:
+// row R of A_i (rows of 2^lw values, rb = 13 - lw in-tile row bits) sits at
+// (R with its low rb bits replaced by their place).
+static void tlo_to_plain(int n, const float* raw, float* out)
+{
+    static constexpr bn::PlaceTable pt = bn::make_place_table();
+    const size_t half = (size_t)1 << (n - 1);
+    for (int i = 0; i < n; ++i) {
+        const int lw = i < 4 ? 3 : 4, rb = 13 - lw;
+        const uint32_t m = (1u << rb) - 1u;
+        for (uint32_t R = 0; R < (uint32_t)(half >> lw); ++R) {
+            const uint32_t at = (R & ~m) | (rb == 9 ? pt.p9[R & m] : pt.p10[R & m]);
+            std::memcpy(out + i * half + ((size_t)R << lw), raw + i * half + ((size_t)at << lw),
+                        sizeof(float) << lw);
+        }
+    }
+}
+
 int bn_debug_stage(bn_ctx* c, int32_t stage, void* host_out, size_t bytes)
 {
     if (!c || !host_out || !c->have_last) return BN_EINVAL;
@@ -1018,6 +1037,12 @@ int bn_debug_stage(bn_ctx* c, int32_t stage, void* host_out, size_t bytes)
     }
     if (bytes != want) return BN_EINVAL;
     CK(cudaStreamSynchronize(c->stream));
+    if (stage == BN_STAGE_A && bn::use_tlo(P)) {
+        std::vector<float> raw(want / sizeof(float));
+        CK(cudaMemcpy(raw.data(), c->ws + off, want, cudaMemcpyDeviceToHost));
+        tlo_to_plain(P.n, raw.data(), static_cast<float*>(host_out));
+        return BN_OK;
+    }
     CK(cudaMemcpy(host_out, c->ws + off, want, cudaMemcpyDeviceToHost));
     return BN_OK;
 }

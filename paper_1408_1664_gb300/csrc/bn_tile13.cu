@@ -757,7 +757,10 @@ k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
 // sums of part 1 are placed at their low patterns (every other slot holds
 // zero) and the truncated upward zeta over the 13 low bits follows.
 // ===========================================================================
-template <typename T>
+//
+// TLO: the rows of A in tile-level order (see bn_device.cuh): output element
+// e of the tile goes to row place(e >> lw) of the tile's block.
+template <typename T, bool TLO>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ A, size_t js)
 {
@@ -775,6 +778,14 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     const int i = (int)(blockIdx.x >> h);
     const uint32_t H = blockIdx.x & ((1u << h) - 1u);
     T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
+    // place of element e in the tile's block
+    const int lw = i < 4 ? 3 : 4;                // row width of A_i in step 3
+    const uint32_t lmask = (1u << lw) - 1u;
+    auto opos = [&](uint32_t e) -> uint32_t {
+        if (!TLO) return e;
+        const uint32_t r = e >> lw;
+        return ((lw == 4 ? g_place.p9[r] : g_place.p10[r]) << lw) | (e & lmask);
+    };
 
     // |el1(r, t)| = |r| + |t| (disjoint bits): the slots with more than d
     // elements are no column (no input)
@@ -829,11 +840,26 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
             bfly_plain<true>(x, 0, 3);
 #pragma unroll
             for (int r = 0; r < TR; ++r) x[r] = sp + Lg::lg(x[r]);
-            st_out3(out, x, t);
+            if constexpr (TLO) {
+                // a run of 8 consecutive elements stays inside one row (lw >= 3)
+#pragma unroll
+                for (int q = 0; q < TR / 8; ++q) {
+                    float4* p = reinterpret_cast<float4*>(out + opos(el3(8 * q, t)));
+                    p[0] = make_float4(x[8 * q], x[8 * q + 1], x[8 * q + 2], x[8 * q + 3]);
+                    p[1] = make_float4(x[8 * q + 4], x[8 * q + 5], x[8 * q + 6], x[8 * q + 7]);
+                }
+            } else {
+                st_out3(out, x, t);
+            }
             return;
         }
         if (npass <= Wn::max_pass) {
             uint32_t done = 0u;                  // bit r: output el3(r, t) written
+            // registers 8q..8q+7 (layout 3) are 8 consecutive elements of one
+            // row: their places start at run3[q]
+            uint32_t run3[TR / 8];
+#pragma unroll
+            for (int q = 0; q < TR / 8; ++q) run3[q] = opos(el3(8 * q, t));
             T sp = M - Wn::top;
             for (int p = 0; p < npass; ++p, sp -= Wn::win) {
                 const bool last = p + 1 == npass;
@@ -855,7 +881,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
                 for (int r = 0; r < TR; ++r) {
                     const T lx = Lg::lg(x[r]);
                     if (!(done >> r & 1u) && (last || lx >= Wn::lo)) {
-                        out[el3(r, t)] = sp + lx;
+                        out[run3[r >> 3] + (r & 7)] = sp + lx;
                         done |= 1u << r;
                     }
                 }
@@ -887,7 +913,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     T sc[TR];
     sum_pass<true>(v, sc, A1, A0, t, d);
 #pragma unroll
-    for (int r = 0; r < TR; ++r) out[el1(r, t)] = scaled_log(v[r], sc[r]);
+    for (int r = 0; r < TR; ++r) out[opos(el1(r, t))] = scaled_log(v[r], sc[r]);
 }
 
 // ===========================================================================
@@ -1139,9 +1165,11 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         if (e != cudaSuccess) return e;
     }
     if (P.prec == 0)
-        k_upzeta13<double><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A, P.js);
+        k_upzeta13<double, false><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A, P.js);
+    else if (use_tlo(P))
+        k_upzeta13<float, true><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A, P.js);
     else
-        k_upzeta13<float><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A, P.js);
+        k_upzeta13<float, false><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A, P.js);
     return cudaGetLastError();
 }
 
@@ -1192,8 +1220,9 @@ cudaError_t set_tile13_attributes()
     SETA(k_upzeta13_colb<8>)
     SETA(k_upzeta13_colb<4>)
     SETA(k_upzeta13_colb<2>)
-    SETA(k_upzeta13<double>)
-    SETA(k_upzeta13<float>)
+    SETA((k_upzeta13<double, false>))
+    SETA((k_upzeta13<float, false>))
+    SETA((k_upzeta13<float, true>))
     SETA((k_gamma13_p1<double, false>))
     SETA((k_gamma13_p1<float, false>))
     SETA((k_gamma13_p1<double, true>))
