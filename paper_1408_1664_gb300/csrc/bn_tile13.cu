@@ -202,13 +202,38 @@ __device__ __forceinline__ void lse_online(T& m, T& s, T x)
     m = mn;
 }
 
-// Sum butterflies without bands (every value in one common scale).
+// a0 += b0 and a1 += b1 in one packed FP32 instruction (each lane rounds
+// like a scalar add).
+__device__ __forceinline__ void add_f32x2(float& a0, float& a1, float b0, float b1)
+{
+    unsigned long long ra, rb;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b0), "f"(b1));
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(ra) : "l"(rb));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(ra));
+}
+
+// Sum butterflies without bands (every value in one common scale).  In FP32
+// a butterfly over register bit k >= 1 pairs registers r, r + 1 with s, s + 1:
+// packed adds.
 template <bool UP, typename T>
 __device__ __forceinline__ void bfly_plain(T (&x)[TR], int k0, int nk)
 {
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         if (k < k0 || k >= k0 + nk) continue;
+        if constexpr (sizeof(T) == 4) {
+            if (k >= 1) {
+#pragma unroll
+                for (int r = 0; r < TR; r += 2) {
+                    if (r & (1 << k)) continue;
+                    const int s = r | (1 << k);
+                    if (UP) add_f32x2(x[s], x[s + 1], x[r], x[r + 1]);
+                    else add_f32x2(x[r], x[r + 1], x[s], x[s + 1]);
+                }
+                continue;
+            }
+        }
 #pragma unroll
         for (int r = 0; r < TR; ++r) {
             if (r & (1 << k)) continue;
