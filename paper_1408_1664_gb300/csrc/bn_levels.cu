@@ -332,20 +332,30 @@ bool rows64_fit(const Plan& P)
     return P.prec == 0 && P.n >= LB64 + 1 && P.n - LB64 < BT;
 }
 
+// Threads per block for a level of nt tiles: 256, or fewer for the small
+// levels, so that a level's blocks spread over all SMs (two per SM at least).
+static unsigned level_block(uint32_t nt)
+{
+    for (unsigned b = 256; b > 64; b >>= 1)
+        if ((uint64_t)nt >= (uint64_t)b * 2 * 152) return b;
+    return 64;
+}
+
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches)
 {
     const int nh = P.n - (P.prec == 0 ? LB64 : LB);
     for (int hl = 0; hl <= nh; ++hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        const dim3 grid((nt + 255) / 256, P.nj);
+        const unsigned tb = level_block(nt);
+        const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
-            k_forward_rows<double, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A,
+            k_forward_rows<double, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const double*)A,
                                                                (double*)F, P.js);
         else if (use_tlo(P))
-            k_forward_rows<float, true><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+            k_forward_rows<float, true><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
                                                              (float*)F, P.js);
         else
-            k_forward_rows<float, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+            k_forward_rows<float, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
                                                               (float*)F, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -360,15 +370,16 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
     const int nh = P.n - (P.prec == 0 ? LB64 : LB);
     for (int hl = nh; hl >= 0; --hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        const dim3 grid((nt + 255) / 256, P.nj);
+        const unsigned tb = level_block(nt);
+        const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
-            k_backward_rows<double, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const double*)A,
+            k_backward_rows<double, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const double*)A,
                                                                 (double*)Rc, P.js);
         else if (use_tlo(P))
-            k_backward_rows<float, true><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+            k_backward_rows<float, true><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
                                                               (float*)Rc, P.js);
         else
-            k_backward_rows<float, false><<<grid, 256, 0, s>>>(P.n, hl, nt, (const float*)A,
+            k_backward_rows<float, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
                                                                (float*)Rc, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
