@@ -999,20 +999,25 @@ int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask,
     return BN_OK;
 }
 
-// A_i read back from tile-level row order (bn_device.cuh) into plain order:
-// row R of A_i (rows of 2^lw values, rb = 13 - lw in-tile row bits) sits at
-// (R with its low rb bits replaced by their place).
-static void tlo_to_plain(int n, const float* raw, float* out)
+// A_i read back from tile-level row order (bn_device.cuh) into plain order,
+// in place: the order permutes the rows inside each 2^13-value tile block
+// only (row (H << rb) | r of A_i at (H << rb) | place(r), rows of 2^lw
+// values, rb = 13 - lw), so one block at a time goes through a 32 KB copy.
+static void tlo_to_plain(int n, float* a)
 {
     static constexpr bn::PlaceTable pt = bn::make_place_table();
     const size_t half = (size_t)1 << (n - 1);
+    std::vector<float> blk(8192);
     for (int i = 0; i < n; ++i) {
         const int lw = i < 4 ? 3 : 4, rb = 13 - lw;
-        const uint32_t m = (1u << rb) - 1u;
-        for (uint32_t R = 0; R < (uint32_t)(half >> lw); ++R) {
-            const uint32_t at = (R & ~m) | (rb == 9 ? pt.p9[R & m] : pt.p10[R & m]);
-            std::memcpy(out + i * half + ((size_t)R << lw), raw + i * half + ((size_t)at << lw),
-                        sizeof(float) << lw);
+        for (size_t b = 0; b < half; b += 8192) {
+            float* base = a + i * half + b;
+            std::memcpy(blk.data(), base, sizeof(float) * 8192);
+            for (uint32_t r = 0; r < (1u << rb); ++r) {
+                const uint32_t at = rb == 9 ? pt.p9[r] : pt.p10[r];
+                std::memcpy(base + ((size_t)r << lw), blk.data() + ((size_t)at << lw),
+                            sizeof(float) << lw);
+            }
         }
     }
 }
@@ -1037,13 +1042,8 @@ int bn_debug_stage(bn_ctx* c, int32_t stage, void* host_out, size_t bytes)
     }
     if (bytes != want) return BN_EINVAL;
     CK(cudaStreamSynchronize(c->stream));
-    if (stage == BN_STAGE_A && bn::use_tlo(P)) {
-        std::vector<float> raw(want / sizeof(float));
-        CK(cudaMemcpy(raw.data(), c->ws + off, want, cudaMemcpyDeviceToHost));
-        tlo_to_plain(P.n, raw.data(), static_cast<float*>(host_out));
-        return BN_OK;
-    }
     CK(cudaMemcpy(host_out, c->ws + off, want, cudaMemcpyDeviceToHost));
+    if (stage == BN_STAGE_A && bn::use_tlo(P)) tlo_to_plain(P.n, static_cast<float*>(host_out));
     return BN_OK;
 }
 
