@@ -51,6 +51,9 @@
 extern "C" {
 #endif
 
+/* Every int-returning function returns BN_OK or one of these codes; no C++
+ * exception crosses this interface (a failed host allocation inside the
+ * library returns BN_ENOMEM). */
 enum {
     BN_OK = 0,
     BN_EINVAL = -1,          /* invalid argument or input data               */

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <new>
 
 static __device__ __align__(256) unsigned char g_bn_static_scratch[BN_STATIC_SCRATCH_BYTES];
 
@@ -112,11 +113,23 @@ int denominators(const uint8_t* arity, int n, int d, double* D)
     return nd;
 }
 
+// No C++ exception leaves the library (a lock can throw): BN_EINVAL.
+int exception_code() noexcept
+{
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        return BN_ENOMEM;
+    } catch (...) {
+        return BN_EINVAL;
+    }
+}
+
 }  // namespace
 
 extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                                          double* log_PD_dev, void* stream)
-{
+try {
     if (!j || !post_dev) return BN_EINVAL;
     if (j->n < 1 || j->n > 31 || j->d < 0 || j->m < 0 || !j->arity) return BN_EINVAL;
     if (j->m > 0 && !j->data) return BN_EINVAL;
@@ -237,4 +250,6 @@ extern "C" int bn_edge_posteriors_static(const bn_job_desc* j, double* post_dev,
                          log_PD_dev, s));
 #undef CKS
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }

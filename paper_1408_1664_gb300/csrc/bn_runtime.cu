@@ -6,6 +6,8 @@
 #include "bn_kernels.cuh"
 
 #include <algorithm>
+#include <new>
+#include <stdexcept>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -670,6 +672,21 @@ void pump(bn_ctx* c);
 
 }  // namespace
 
+// No C++ exception leaves the library: an entry point that catches one
+// returns BN_ENOMEM for a failed host allocation and BN_EINVAL otherwise.
+static int exception_code() noexcept
+{
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        return BN_ENOMEM;
+    } catch (const std::length_error&) {
+        return BN_ENOMEM;
+    } catch (...) {
+        return BN_EINVAL;
+    }
+}
+
 extern "C" {
 
 const char* bn_strerror(int code)
@@ -691,17 +708,19 @@ const char* bn_strerror(int code)
 int64_t bn_num_families(int32_t n, int32_t d) { return families(n, d); }
 
 int bn_job_footprint(const bn_job_desc* job, uint64_t* bytes)
-{
+try {
     if (!bytes) return BN_EINVAL;
     HostJob hj;
     const int rc = validate_and_plan(job, hj);
     if (rc) return rc;
     *bytes = make_layout(hj.P, 0).total;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_ctx_create(bn_ctx** out, const bn_ctx_opts* o)
-{
+try {
     if (!out) return BN_EINVAL;
     *out = nullptr;
     bn_ctx_opts opts{};
@@ -747,10 +766,12 @@ int bn_ctx_create(bn_ctx** out, const bn_ctx_opts* o)
     }
     *out = c;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_ctx_destroy(bn_ctx* c)
-{
+try {
     if (!c) return BN_EINVAL;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
@@ -769,11 +790,13 @@ int bn_ctx_destroy(bn_ctx* c)
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_edge_posteriors_async(bn_ctx* c, const bn_job_desc* job, double* post_dev,
                              double* log_PD_dev, void* stream)
-{
+try {
     if (!c || !post_dev) return BN_EINVAL;
     HostJob hj;
     int rc = validate_and_plan(job, hj);
@@ -781,10 +804,12 @@ int bn_edge_posteriors_async(bn_ctx* c, const bn_job_desc* job, double* post_dev
     if (cudaSetDevice(c->device) != cudaSuccess) return BN_ECUDA;
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     return run_direct(c, job, hj, post_dev, log_PD_dev, s);
+} catch (...) {
+    return exception_code();
 }
 
 int bn_edge_posteriors(bn_ctx* c, const bn_job_desc* job, double* post, double* log_PD)
-{
+try {
     if (!c || !post) return BN_EINVAL;
     HostJob hj;
     int rc = validate_and_plan(job, hj);
@@ -805,10 +830,12 @@ int bn_edge_posteriors(bn_ctx* c, const bn_job_desc* job, double* post, double* 
     Events& ev = c->ring[(c->ring_pos + bn_ctx::kRing - 1) % bn_ctx::kRing];
     fill_stats(P, ev, c->last_launches, &c->last_stats);
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_scores(bn_ctx* c, const bn_job_desc* job, uint32_t* parent_mask, double* log_B)
-{
+try {
     if (!c || !parent_mask || !log_B) return BN_EINVAL;
     HostJob hj;
     int rc = validate_and_plan(job, hj);
@@ -861,11 +888,13 @@ int bn_scores(bn_ctx* c, const bn_job_desc* job, uint32_t* parent_mask, double* 
     c->have_last = false;
     c->tables_sig.clear();
     return err ? BN_EINVAL : BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_feature_posterior(bn_ctx* c, const bn_job_desc* job, const double* log_f, double* p,
                          double* log_PfD)
-{
+try {
     if (!c || !log_f) return BN_EINVAL;
     HostJob hj;
     int rc = validate_and_plan(job, hj);
@@ -945,11 +974,13 @@ int bn_feature_posterior(bn_ctx* c, const bn_job_desc* job, const double* log_f,
     if (p) *p = zero ? 0.0 : std::exp(fv[1] - fv[0]);
     if (log_PfD) *log_PfD = zero ? -INFINITY : fv[1] + csum;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask, int64_t* counts,
                     int64_t cells)
-{
+try {
     if (!c || !counts) return BN_EINVAL;
     HostJob hj;
     int rc = validate_and_plan(job, hj);
@@ -997,6 +1028,8 @@ int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask,
     c->have_last = false;
     c->tables_sig.clear();
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 // A_i read back from tile-level row order (bn_device.cuh) into plain order,
@@ -1023,7 +1056,7 @@ static void tlo_to_plain(int n, float* a)
 }
 
 int bn_debug_stage(bn_ctx* c, int32_t stage, void* host_out, size_t bytes)
-{
+try {
     if (!c || !host_out || !c->have_last) return BN_EINVAL;
     const Plan& P = c->last;
     const Layout& L = c->last_layout;
@@ -1045,10 +1078,12 @@ int bn_debug_stage(bn_ctx* c, int32_t stage, void* host_out, size_t bytes)
     CK(cudaMemcpy(host_out, c->ws + off, want, cudaMemcpyDeviceToHost));
     if (stage == BN_STAGE_A && bn::use_tlo(P)) tlo_to_plain(P.n, static_cast<float*>(host_out));
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_job_stats(bn_ctx* c, uint64_t id, bn_stats* st)
-{
+try {
     if (!c || !st) return BN_EINVAL;
     if (id == 0) {
         *st = c->last_stats;
@@ -1059,10 +1094,12 @@ int bn_job_stats(bn_ctx* c, uint64_t id, bn_stats* st)
     if (it == c->jobs.end()) return BN_ENOTFOUND;
     *st = it->second.stats;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_stats_history(bn_ctx* c, bn_stats* out, int32_t max, int32_t* count)
-{
+try {
     if (!c || !out || !count || max < 0) return BN_EINVAL;
     const int k = std::min<int>(max, c->ring_count);
     for (int t = 0; t < k; ++t) {
@@ -1073,6 +1110,8 @@ int bn_stats_history(bn_ctx* c, bn_stats* out, int32_t max, int32_t* count)
     }
     *count = k;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 // ---------------------------------------------------------------- batches --
@@ -1274,7 +1313,7 @@ int tune_batch(bn_batch* b, cudaStream_t s)
 }  // namespace
 
 int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch** out)
-{
+try {
     if (!c || !jobs || !out || count < 1) return BN_EINVAL;
     *out = nullptr;
     bn_batch* b = new bn_batch();
@@ -1397,20 +1436,24 @@ int bn_batch_create(bn_ctx* c, const bn_job_desc* jobs, int32_t count, bn_batch*
     if (rc) { bn_batch_destroy(b); return rc; }
     *out = b;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_batch_run(bn_batch* b, void* stream)
-{
+try {
     if (!b || !b->exec) return BN_EINVAL;
     cudaSetDevice(b->ctx->device);
     b->last = stream ? (cudaStream_t)stream : b->ctx->stream;
     CK(cudaGraphLaunch(b->exec, b->last));
     b->ran = true;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_batch_results(bn_batch* b, int32_t k, double* post, double* log_PD)
-{
+try {
     if (!b || !post || k < 0 || k >= (int32_t)b->jobs.size() || !b->ran) return BN_EINVAL;
     const Plan& P = b->jobs[k].P;
     const BatchGroup& g = b->groups[b->group_of[k]];
@@ -1421,10 +1464,12 @@ int bn_batch_results(bn_batch* b, int32_t k, double* post, double* log_PD)
     int err = 0;
     CK(cudaMemcpy(&err, jb + g.L.err, 4, cudaMemcpyDeviceToHost));
     return err ? BN_EINVAL : BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_batch_describe(bn_batch* b, char* buf, size_t len)
-{
+try {
     if (!b || !buf || len == 0) return BN_EINVAL;
     std::string s;
     char line[256];
@@ -1440,10 +1485,12 @@ int bn_batch_describe(bn_batch* b, char* buf, size_t len)
     }
     std::snprintf(buf, len, "%s", s.c_str());
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_batch_destroy(bn_batch* b)
-{
+try {
     if (!b) return BN_EINVAL;
     cudaSetDevice(b->ctx->device);
     if (b->ran) cudaStreamSynchronize(b->last);
@@ -1456,12 +1503,14 @@ int bn_batch_destroy(bn_batch* b)
     if (b->arena) cudaFree(b->arena);
     delete b;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 // ---------------------------------------------------------------- serving --
 
 int bn_submit(bn_ctx* c, const bn_job_desc* job, uint64_t* id)
-{
+try {
     if (!c || !id || !job) return BN_EINVAL;
     if (job->data_on_device) return BN_EINVAL;   // served jobs copy host inputs
     ServedJob sj;
@@ -1480,10 +1529,12 @@ int bn_submit(bn_ctx* c, const bn_job_desc* job, uint64_t* id)
     *id = jid;
     pump(c);
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_poll(bn_ctx* c, uint64_t id, double* post, double* log_PD)
-{
+try {
     if (!c) return BN_EINVAL;
     std::lock_guard<std::mutex> g(c->mu);
     pump(c);
@@ -1499,10 +1550,12 @@ int bn_poll(bn_ctx* c, uint64_t id, double* post, double* log_PD)
     c->last_stats = sj.stats;
     c->jobs.erase(it);
     return rc;
+} catch (...) {
+    return exception_code();
 }
 
 int bn_wait(bn_ctx* c, uint64_t id, double timeout_s, double* post, double* log_PD)
-{
+try {
     if (!c) return BN_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -1512,10 +1565,12 @@ int bn_wait(bn_ctx* c, uint64_t id, double timeout_s, double* post, double* log_
         if (el >= timeout_s) return BN_ETIMEOUT;
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
+} catch (...) {
+    return exception_code();
 }
 
 int bn_cancel(bn_ctx* c, uint64_t id)
-{
+try {
     if (!c) return BN_EINVAL;
     std::lock_guard<std::mutex> g(c->mu);
     auto it = c->jobs.find(id);
@@ -1525,6 +1580,8 @@ int bn_cancel(bn_ctx* c, uint64_t id)
     it->second.state = Q_DONE;
     it->second.rc = BN_ECANCELED;
     return BN_OK;
+} catch (...) {
+    return exception_code();
 }
 
 }  // extern "C"
