@@ -34,7 +34,8 @@
  *     1 <= arity[i] <= 255, at most 65536 cells (q*r_i) per family.
  *
  * Errors: every function returns BN_OK (0) or a negative BN_E* code and never
- * throws or aborts.  bn_strerror() names a code.  On error the output
+ * throws or aborts (a failed host allocation inside the library returns
+ * BN_ENOMEM).  bn_strerror() names a code.  On error the output
  * buffers are left unspecified.
  *
  * Ownership: the caller owns every buffer it passes.  The context owns all
@@ -51,9 +52,6 @@
 extern "C" {
 #endif
 
-/* Every int-returning function returns BN_OK or one of these codes; no C++
- * exception crosses this interface (a failed host allocation inside the
- * library returns BN_ENOMEM). */
 enum {
     BN_OK = 0,
     BN_EINVAL = -1,          /* invalid argument or input data               */
