@@ -185,26 +185,35 @@ int bn_edge_posteriors_async(bn_ctx* ctx, const bn_job_desc* job,
                              double* post_dev, double* log_PD_dev,
                              void* stream);
 
-/* No-allocation variant of bn_edge_posteriors_async (the paper has no
- * counterpart; this serves callers that must not allocate device memory:
- * code running inside a CUDA graph capture, where cudaMalloc is not allowed;
- * applications that own and partition all GPU memory themselves; loops that
- * cannot afford the device-wide synchronisation of cudaFree).
+/* No-allocation variant of bn_edge_posteriors_async.  The paper has no
+ * counterpart.  It serves callers that cannot let a library allocate device
+ * memory: host applications that own and partition all GPU memory
+ * themselves (a library may not take memory behind their back), and
+ * latency-sensitive loops that cannot pay for cudaMalloc or for the
+ * device-wide synchronisation of cudaFree.
  *
  * Needs no context.  Every intermediate array lives in one file-scope device
  * array of BN_STATIC_SCRATCH_BYTES (64 MiB) that every GPU loading this
  * library holds until the process exits.  Jobs whose arrays do not fit it
  * (roughly n > 19 on the FP64 path, n > 20 on the FP32 path) are rejected
- * with BN_ENOMEM before any GPU work.  Runs on the current device, enqueued
+ * with BN_ENOMEM before any GPU work; so are jobs whose arities give more
+ * than 1024 distinct lgamma-table denominators or more than 1024 distinct
+ * (product of parent arities, number of parents) pairs (two fixed host
+ * tables; only jobs with many distinct arities come near them).  log_q and
+ * log_w are not accepted (BN_EINVAL).  Runs on the current device, enqueued
  * on `stream` (a cudaStream_t, NULL = the legacy default stream).  The first
- * call on a device looks up the array's device address for that device; make
- * that first call before any stream capture begins.  job->data may be host
- * or device memory (host data and the small tables are copied with
- * cudaMemcpyAsync from pageable memory); post_dev (n*n doubles) and
- * log_PD_dev (one double, or NULL) are device memory owned by the caller.
- * All calls on a device share the array and it keeps the previous call's
- * contents: calls whose GPU work may overlap (different streams without
- * ordering) race and give undefined results. */
+ * call on a device looks up the array's device address for that device (a
+ * one-time set-up; make that first call before any stream capture begins).
+ * job->data may be host or device memory (host data and the small tables are
+ * copied with cudaMemcpyAsync from pageable memory, which has consumed the
+ * host bytes when the call returns); post_dev (n*n doubles) and log_PD_dev
+ * (one double, or NULL) are device memory owned by the caller.  Host data is
+ * checked on the host (BN_EINVAL).  Device data is checked only on the GPU:
+ * since the call never synchronises, a value not below its arity makes every
+ * posterior and log P(D) NaN instead of returning an error code.  All calls
+ * on a device share the array and it keeps the previous call's contents:
+ * calls whose GPU work may overlap (different streams without ordering) race
+ * and give undefined results. */
 #define BN_STATIC_SCRATCH_BYTES (64u << 20)
 int bn_edge_posteriors_static(const bn_job_desc* job, double* post_dev,
                               double* log_PD_dev, void* stream);
@@ -273,7 +282,11 @@ int bn_stats_history(bn_ctx* ctx, bn_stats* out, int32_t max, int32_t* count);
 
 const char* bn_strerror(int code);
 
-/* ---- test hooks: stage dumps of the last bn_edge_posteriors call ------- */
+/* ---- test hooks: stage dumps of the last bn_edge_posteriors call ------- *
+ * Declared and exported only in the testing build of the library (compiled
+ * with BN_TESTING defined: _build/libbnedge_testing.so); the release build
+ * (_build/libbnedge.so) has neither function. */
+#ifdef BN_TESTING
 enum {
     BN_STAGE_LOGB = 1,   /* n*K doubles, natural log, unshifted               */
     BN_STAGE_MASKS = 2,  /* n*K uint32 parent masks                           */
@@ -295,6 +308,7 @@ int bn_debug_stage(bn_ctx* ctx, int32_t stage, void* host_out, size_t bytes);
  * counts[config*r_i + x_i], q*r_i int64 values on the host. */
 int bn_debug_counts(bn_ctx* ctx, const bn_job_desc* job, int32_t i,
                     uint32_t parent_mask, int64_t* counts, int64_t cells);
+#endif /* BN_TESTING */
 
 #ifdef __cplusplus
 }

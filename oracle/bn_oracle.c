@@ -189,7 +189,7 @@ double orc_family_score(int n, int m, const uint8_t* data, const uint8_t* arity,
 
 static int validate(int n, int d, int m, const uint8_t* data, const uint8_t* arity)
 {
-    if (n < 1 || n > 30 || d < 0 || m < 0 || !arity) return ORC_EINVAL;
+    if (n < 1 || n > 31 || d < 0 || m < 0 || !arity) return ORC_EINVAL;
     if (m > 0 && !data) return ORC_EINVAL;
     for (int i = 0; i < n; i++) if (arity[i] < 1) return ORC_EINVAL;
     for (size_t s = 0; s < (size_t)m * n; s++)

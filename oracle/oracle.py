@@ -188,8 +188,9 @@ def edge_posteriors(data, arity, d: int, ess: float = 1.0, log_rho=None,
                     stages: bool = False, log_q=None, log_w=None) -> dict:
     """Run Algorithm 1.  Returns {'post': (n, n), 'log_PD': float} and, with
     ``stages``, also 'A' (n, 2^n), 'F', 'R' (2^n), 'Gamma', 'logB', 'masks'
-    (n, K).  log_q (n, n): log q_i(S) by |S| (Eq. 4, 7, 12); log_w (n, K): per
-    family log weights added to log B (a general rho_i(G))."""
+    (n, K); ``stages`` may also name a subset of these, e.g. ("F", "R").
+    log_q (n, n): log q_i(S) by |S| (Eq. 4, 7, 12); log_w (n, K): per family
+    log weights added to log B (a general rho_i(G))."""
     data, arity = _prep(data, arity)
     n = arity.shape[0]
     K = num_families(n, d)
@@ -199,9 +200,11 @@ def edge_posteriors(data, arity, d: int, ess: float = 1.0, log_rho=None,
     lr = None if log_rho is None else np.ascontiguousarray(log_rho, dtype=np.float64)
     st = {}
     if stages:
-        st = dict(A=np.empty((n, N)), F=np.empty(N), R=np.empty(N),
-                  Gamma=np.empty((n, K)), logB=np.empty((n, K)),
-                  masks=np.empty((n, K), dtype=np.uint32))
+        make = dict(A=lambda: np.empty((n, N)), F=lambda: np.empty(N), R=lambda: np.empty(N),
+                    Gamma=lambda: np.empty((n, K)), logB=lambda: np.empty((n, K)),
+                    masks=lambda: np.empty((n, K), dtype=np.uint32))
+        names = make if stages is True else stages
+        st = {k: make[k]() for k in names}
     lq = _f64_or_none(log_q, n * n)
     lw = _f64_or_none(log_w, n * K)
     rc = lib().orc_edge_posteriors_ext(

@@ -57,14 +57,24 @@ class bn_stats(C.Structure):
 _lib = None
 EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_edge_posteriors", "bn_edge_posteriors_async", "bn_submit", "bn_poll", "bn_wait",
-           "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror", "bn_debug_stage",
-           "bn_debug_counts", "bn_edge_posteriors_static", "bn_job_footprint", "bn_batch_create",
+           "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror",
+           "bn_edge_posteriors_static", "bn_job_footprint", "bn_batch_create",
            "bn_batch_run", "bn_batch_results", "bn_batch_describe", "bn_batch_destroy",
            "bn_feature_posterior"]
 
 
+# Test hooks: exported only by the testing build (BN_TESTING).
+TEST_EXPORTS = ["bn_debug_stage", "bn_debug_counts"]
+
+
+def testing_build() -> bool:
+    """The testing build of the library (with the BN_TESTING hooks) is loaded
+    when the environment sets BN_TESTING=1; the test suite does."""
+    return os.environ.get("BN_TESTING") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_TESTING if testing_build() else _build.LIB
 
 
 def load(build_if_missing: bool = False) -> C.CDLL:
@@ -72,9 +82,9 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = library_path()
     if build_if_missing:
-        path = _build.build()
+        _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} is missing "
                            "(run __graft_entry__.build()); there is no CPU fallback")
@@ -108,6 +118,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_feature_posterior": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
     }
     for name, (res, args) in sig.items():
+        if name in TEST_EXPORTS and not hasattr(L, name):
+            continue                                   # release build
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args

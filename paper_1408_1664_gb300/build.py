@@ -1,7 +1,12 @@
-"""Build the CUDA library ``_build/libbnedge.so`` for sm_103a with nvcc.
+"""Build the CUDA library for sm_103a with nvcc.
 
-The translation units compile in parallel and link into one shared library
-with a plain C ABI (``include/bnedge.h``).  No torch headers are involved.
+The translation units compile in parallel and link into two shared libraries
+with a plain C ABI (``include/bnedge.h``): ``_build/libbnedge.so`` (the
+release build) and ``_build/libbnedge_testing.so``, the same objects plus the
+test hooks of the header's BN_TESTING section (the runtime unit compiled a
+second time with BN_TESTING defined).  ``_build/libbnpeaks.so`` holds the
+arithmetic-rate probes the benchmark uses for its ALU rooflines.  No torch
+headers are involved.
 """
 from __future__ import annotations
 
@@ -16,7 +21,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUTDIR, "libbnedge.so")
+LIB_TESTING = os.path.join(OUTDIR, "libbnedge_testing.so")
+LIB_PEAKS = os.path.join(OUTDIR, "libbnpeaks.so")
 SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_runtime.cu", "bn_noalloc.cu"]
+PEAKS_SOURCE = "bn_peaks.cu"
+# (source, object, extra flags) of the second compile of the runtime unit
+TESTING_UNIT = ("bn_runtime.cu", "bn_runtime_testing.o", ["-DBN_TESTING"])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,9 +44,10 @@ def _inputs():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    libs = (LIB, LIB_TESTING, LIB_PEAKS)
+    if not all(os.path.exists(x) for x in libs):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(x) for x in libs)
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
@@ -48,9 +59,10 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"] + (extra or [])
 
-    def one(src):
-        obj = os.path.join(OUTDIR, src.replace(".cu", ".o"))
-        cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags
+    def one(unit):
+        src, obj, more = unit
+        obj = os.path.join(OUTDIR, obj)
+        cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags + more
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -58,14 +70,19 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
             print(r.stdout, r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(one, SOURCES))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    units = ([(src, src.replace(".cu", ".o"), []) for src in SOURCES] + [TESTING_UNIT]
+             + [(PEAKS_SOURCE, PEAKS_SOURCE.replace(".cu", ".o"), [])])
+    with cf.ThreadPoolExecutor(len(units)) as ex:
+        objs = list(ex.map(one, units))
+    release = objs[:len(SOURCES)]
+    testing = [o for o in release if not o.endswith("bn_runtime.o")] + [objs[-2]]
+    for out, parts in ((LIB, release), (LIB_TESTING, testing), (LIB_PEAKS, [objs[-1]])):
+        tmp = out + ".tmp"
+        cmd = [nvcc(), "-shared", "-o", tmp] + parts + ARCH + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
     return LIB
 
 

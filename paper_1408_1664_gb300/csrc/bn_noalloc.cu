@@ -2,10 +2,11 @@
 // with every intermediate array in one fixed device array, for callers that
 // must not allocate device memory.
 //
-// Who needs it: code that runs inside a CUDA graph capture (cudaMalloc is not
-// allowed there), code embedded in a host application that owns and
-// partitions all GPU memory itself, and latency-sensitive loops that cannot
-// afford cudaMalloc / cudaFree (cudaFree synchronises the whole device).
+// Who needs it: code embedded in a host application that owns and partitions
+// all GPU memory itself (a game engine, a database, a runtime with its own
+// device allocator), where a library may not take memory behind the
+// application's back; and latency-sensitive loops that cannot afford
+// cudaMalloc / cudaFree (cudaFree synchronises the whole device).
 //
 // The scratch is the file-scope array below (BN_STATIC_SCRATCH_BYTES).  Every
 // GPU that loads this library holds it until the process exits.  All calls
@@ -17,7 +18,13 @@
 // No cudaMalloc, cudaMallocAsync, cudaMallocHost, cudaFree or other
 // allocating routine is called, and no host heap memory is used: the small
 // host tables live on the stack and are copied with cudaMemcpyAsync from
-// pageable memory (the copy consumes the source before returning).
+// pageable memory.  For a pageable source the runtime has consumed the host
+// bytes when cudaMemcpyAsync returns, so the stack frame may end right after.
+// Besides the size of the array, two fixed host tables bound a job: at most
+// kMaxStates distinct (product of arities, number of parents) pairs and
+// kMaxRows distinct lgamma-table denominators (both 1024; only jobs with many
+// distinct arities come near them).  Either limit gives BN_ENOMEM, like the
+// size limit, before any GPU work.
 #include "bnedge.h"
 #include "bn_kernels.cuh"
 

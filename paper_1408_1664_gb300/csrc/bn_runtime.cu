@@ -978,6 +978,9 @@ try {
     return exception_code();
 }
 
+#ifdef BN_TESTING
+// Test hooks (stage dumps and device counts), compiled only into the testing
+// build of the library.
 int bn_debug_counts(bn_ctx* c, const bn_job_desc* job, int32_t i, uint32_t mask, int64_t* counts,
                     int64_t cells)
 try {
@@ -1081,6 +1084,7 @@ try {
 } catch (...) {
     return exception_code();
 }
+#endif  // BN_TESTING
 
 int bn_job_stats(bn_ctx* c, uint64_t id, bn_stats* st)
 try {

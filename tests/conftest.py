@@ -9,3 +9,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running case")
+
+
+# The tests load the testing build of the library (libbnedge_testing.so), which
+# adds the stage-dump and count hooks of the header's BN_TESTING section.
+os.environ.setdefault("BN_TESTING", "1")

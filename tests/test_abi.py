@@ -38,6 +38,22 @@ def test_library_exports_every_declared_function(lib):
     assert set(B.EXPORTS) <= set(names)
 
 
+def test_test_hooks_only_in_the_testing_build(lib):
+    """bn_debug_stage / bn_debug_counts sit in the header's BN_TESTING
+    section; the release library does not export them, the testing one does."""
+    txt = open(os.path.join(ROOT, "include", "bnedge.h")).read()
+    guarded = txt[txt.index("#ifdef BN_TESTING"):txt.index("#endif /* BN_TESTING */")]
+    for name in B.TEST_EXPORTS:
+        assert name + "(" in guarded
+        assert name + "(" not in txt.replace(guarded, "")
+    release = ctypes.CDLL(Bld.LIB)
+    testing = ctypes.CDLL(Bld.LIB_TESTING)
+    for name in B.TEST_EXPORTS:
+        assert not hasattr(release, name) and hasattr(testing, name)
+    for name in B.EXPORTS:
+        assert hasattr(release, name) and hasattr(testing, name)
+
+
 def test_num_families_matches_oracle(lib):
     for n in range(1, 32):
         for d in range(0, 6):

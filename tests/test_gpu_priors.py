@@ -67,15 +67,18 @@ def test_scores_include_family_weights(ctx):
 
 
 def test_prior_served_equals_direct(ctx):
-    """The served path uploads the priors like the direct one: identical bits."""
+    """The served path uploads the priors like the direct one: identical bits,
+    and both within the FP32 tolerance of the oracle."""
     ds = datagen.random_dag_data(13, 300, 2, 3, 1.0, seed=611)
     log_q, log_w = _priors(13, orc.num_families(13, 3), 12)
+    ref = orc.edge_posteriors(ds.data, ds.arity, 3, log_q=log_q, log_w=log_w)
     job = B.Job(ds.data, ds.arity, 3, precision="fp32", log_q=log_q, log_w=log_w)
     post0, lpd0 = B.bn_edge_posteriors(ctx.h, job)
     jid = B.bn_submit(ctx.h, job)
     rc, post1, lpd1 = B.bn_wait(ctx.h, jid, 13)
     assert rc == 0
     assert np.array_equal(post0, post1) and lpd0 == lpd1
+    np.testing.assert_allclose(post1, ref["post"], atol=TOL["fp32"], rtol=0)
 
 
 def _random_feature(masks, seed, p_zero=0.4):

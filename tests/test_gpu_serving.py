@@ -4,13 +4,15 @@ Jobs of different sizes submitted together run concurrently on the
 context's slots (separate streams); each result must equal the same job run
 alone through bn_edge_posteriors.  Every reduction of the library has a fixed
 order, so "equal" is bit-for-bit here, which is tighter than the stated
-tolerances (1e-9 FP64, 1e-4 FP32).
+tolerances (1e-9 FP64, 1e-4 FP32).  Each served result is also compared with
+the CPU FP64 oracle within those tolerances.
 """
 import time
 
 import numpy as np
 import pytest
 
+from oracle import oracle as orc
 from paper_1408_1664_gb300 import binding as B
 from paper_1408_1664_gb300 import datagen
 
@@ -38,15 +40,18 @@ def _mix():
 
 def test_results_equal_alone_and_in_the_mix(torch_cuda):
     jobs = _mix()
+    refs = [orc.edge_posteriors(ds.data, ds.arity, d) for ds, d, _ in jobs]
     with B.Context(0, slots=4) as ctx:
         alone = [ctx.edge_posteriors(ds.data, ds.arity, d, precision=p) for ds, d, p in jobs]
         descs = [B.Job(ds.data, ds.arity, d, precision=p) for ds, d, p in jobs]
         ids = [B.bn_submit(ctx.h, j) for j in descs]
-        for (ds, d, p), jid, (post0, lpd0) in zip(jobs, ids, alone):
+        for (ds, d, p), jid, (post0, lpd0), ref in zip(jobs, ids, alone, refs):
             rc, post, lpd = B.bn_wait(ctx.h, jid, ds.n, timeout_s=60.0)
             assert rc == B.BN_OK, B.bn_strerror(rc)
             assert np.array_equal(post, post0), (ds.n, p)
             assert lpd == lpd0
+            tol = 1e-9 if p == "fp64" else 1e-4
+            np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
             st = B.bn_job_stats(ctx.h, 0)
             assert st["kernels"] > 0 and st["ms_total"] > 0
 

@@ -1,9 +1,10 @@
 """The no-allocation entry point, bn_edge_posteriors_static.
 
-It exists for callers that cannot allocate device memory (inside a CUDA
-graph capture, inside applications that manage all GPU memory themselves, or
-in loops that cannot pay for cudaMalloc / cudaFree).  It keeps every
-intermediate array in one fixed device array inside the library.  These
+It exists for callers that cannot let a library allocate device memory:
+host applications that own and partition all GPU memory themselves, and
+loops that cannot pay for cudaMalloc or for the device-wide synchronisation
+of cudaFree.  It keeps every intermediate array in one fixed device array
+inside the library.  These
 checks call it through the C ABI, twice in a row on different jobs (the
 fixed array keeps the previous call's contents), and compare each result
 with bn_edge_posteriors on the same job within the tolerances used for the
@@ -56,6 +57,21 @@ def test_static_matches_existing_entry_point_two_calls(torch_cuda):
     # and once more on the first job after the second has overwritten the scratch
     again, _ = _static(torch, job1, small.n, stream)
     np.testing.assert_allclose(again, want1, atol=1e-9, rtol=0)
+
+
+def test_static_with_per_size_prior(torch_cuda):
+    """A per-size structure prior (log_rho) travels to the device in its own
+    small table of the fixed array: same result as the existing entry point."""
+    torch = torch_cuda
+    ds = datagen.random_dag_data(11, 300, 2, 3, 1.0, seed=91)
+    rho = [0.0, -0.7, -1.9, -3.3]
+    stream = torch.cuda.Stream()
+    with B.Context(0) as ctx:
+        want, lpd = ctx.edge_posteriors(ds.data, ds.arity, 3, log_rho=rho, precision="fp64")
+    got, g = _static(torch, B.Job(ds.data, ds.arity, 3, precision="fp64", log_rho=rho),
+                     ds.n, stream)
+    np.testing.assert_allclose(got, want, atol=1e-9, rtol=0)
+    assert abs(g - lpd) <= 1e-9 * abs(lpd)
 
 
 def test_static_rejects_jobs_beyond_the_scratch(torch_cuda):
