@@ -45,6 +45,109 @@ __device__ __forceinline__ P* job_ptr(P* p, size_t js)
     return reinterpret_cast<P*>(reinterpret_cast<B*>(p) + (size_t)blockIdx.y * js);
 }
 
+// ---------------------------------------------------------------------------
+// Per-level bases of F and R' in FP32 (the per-level max shift of the FP32
+// form).  F(S) grows by about a factor |S| and an A term per lattice level, so
+// in log2 units the forward and backward sums of a large job reach thousands
+// (about -4600 at n = 29), where one FP32 rounding unit is 2^-11: rounded
+// level after level that costs up to 1e-4 in a posterior.  The step-3 row
+// kernels therefore store every value relative to an integer base of its
+// tile level k = |S >> kLevelShift| (the level of the launch that writes it):
+//   F_s(S) = F(S) - bF[k],   bF[0] = 0,  bF[k] = bF[k-1] + dF[k-1],
+//   R_s(T) = R'(T) - bR[k],  bR[nh] = 0, bR[k] = bR[k+1] + dR[k+1],
+// where d[k] = floor of the largest stored value of level k (nh = n - 4), so
+// that the largest values of every level stay within a few dozen units of
+// zero.  The kLevelWords ints right after the 2^n values of F (and of R')
+// hold d[k] per level and, in word kLevelMode, the tile shift the bases
+// refer to (0: no bases, every b = 0; kernels other than the FP32 row kernels
+// write 0).  The bases are exact small integers, so adding them back (the
+// down-zeta input F(S) + R'(S + {v}), log P(D)) loses nothing.
+// ---------------------------------------------------------------------------
+constexpr int kLevelWords = 32;
+constexpr int kLevelMode = 31;
+constexpr int kLevelShift = 4;
+constexpr int kLevelUnset = -2147483647 - 1;
+
+__host__ __device__ __forceinline__ double level_delta(const int* lw, int k)
+{
+    return lw[k] == kLevelUnset ? 0.0 : (double)lw[k];
+}
+// bF[k] (forward) and bR[k] (backward) from the level words; 0 without bases.
+__host__ __device__ __forceinline__ double level_base_fwd(const int* lw, int k)
+{
+    if (lw[kLevelMode] != kLevelShift) return 0.0;
+    double b = 0.0;
+    for (int j = 0; j < k; ++j) b += level_delta(lw, j);
+    return b;
+}
+__host__ __device__ __forceinline__ double level_base_bwd(const int* lw, int k, int nh)
+{
+    if (lw[kLevelMode] != kLevelShift) return 0.0;
+    double b = 0.0;
+    for (int j = nh; j > k; --j) b += level_delta(lw, j);
+    return b;
+}
+// The level words after an FP32 array of 2^n values.
+__host__ __device__ __forceinline__ const int* level_words(const float* X, int n)
+{
+    return reinterpret_cast<const int*>(X + ((size_t)1 << n));
+}
+__host__ __device__ __forceinline__ int* level_words(float* X, int n)
+{
+    return reinterpret_cast<int*>(X + ((size_t)1 << n));
+}
+// floor(x) as an int for the level words (kLevelUnset for -inf or below).
+__device__ __forceinline__ int level_floor(float x)
+{
+    return x > -2.0e9f ? (int)floorf(x) : kLevelUnset;
+}
+
+// FP32 down-zeta input for endpoint v: s_v(S) = F_s(S) + R_s(S + {v}) +
+// off[|S >> *sh|] equals F(S) + R'(S + {v}) - Z, with the integer
+// Z = bF[nh] + floor(F_s(V)), so that log P(D) - Z = *fvrel lies in [0, 1)
+// (in the shifted log2 units of the FP32 path).  Without bases *sh = 31 and
+// off[0] = -Z.  Called by all 32 lanes of one warp; writes off[0..nh].
+__device__ __forceinline__ void gamma_offsets(int n, int v, const float* F, const float* Rc,
+                                              float* off, int* sh, float* fvrel)
+{
+    const int lane = threadIdx.x & 31;
+    const int* lf = level_words(F, n);
+    const int* lr = level_words(Rc, n);
+    const bool bases = lf[kLevelMode] == kLevelShift && lr[kLevelMode] == kLevelShift;
+    const float fs = F[((size_t)1 << n) - 1];
+    const double z0 = floor((double)fs);
+    if (lane == 0) *fvrel = (float)((double)fs - z0);
+    if (!bases) {
+        if (lane == 0) {
+            off[0] = (float)(-z0);
+            *sh = 31;
+        }
+        return;
+    }
+    const int nh = n - kLevelShift;
+    // bF[a] = sum_{j < a} dF[j]: exclusive prefix sum over the lanes
+    const double x = lane < nh ? level_delta(lf, lane) : 0.0;
+    double incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const double bF = incl - x;
+    // bR[k] = sum_{k < j <= nh} dR[j]: exclusive suffix sum
+    const double r = (lane >= 1 && lane <= nh) ? level_delta(lr, lane) : 0.0;
+    double suf = r;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, suf, o);
+        if (lane + o < 32) suf += y;
+    }
+    const double bR = suf - r;
+    const double Z = __shfl_sync(0xffffffffu, bF, nh) + z0;
+    // |(S + {v}) >> 4| = |S >> 4| + [v >= 4]
+    const double bRv = __shfl_sync(0xffffffffu, bR, min(lane + (v >= kLevelShift ? 1 : 0), nh));
+    if (lane <= nh) off[lane] = (float)(bF + bRv - Z);
+    if (lane == 0) *sh = kLevelShift;
+}
+
 // Number of subsets of an nb-element set with at most d elements.
 __device__ __forceinline__ uint32_t num_small_subsets(int nb, int d)
 {

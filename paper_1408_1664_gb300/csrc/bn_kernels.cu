@@ -889,6 +889,9 @@ k_forward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __rest
     A = job_ptr(A, js);
     F = job_ptr(F, js);
     using L = LogOps<T>;
+    // FP32: these tiles keep no per-level bases (bn_device.cuh)
+    if (sizeof(T) == 4 && hl == 0 && blockIdx.x == 0 && threadIdx.x == 0)
+        level_words(reinterpret_cast<float*>(F), n)[kLevelMode] = 0;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t first = warp * (uint32_t)tpw;
@@ -947,6 +950,8 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
     A = job_ptr(A, js);
     Rc = job_ptr(Rc, js);
     using L = LogOps<T>;
+    if (sizeof(T) == 4 && hl == n - wb && blockIdx.x == 0 && threadIdx.x == 0)
+        level_words(reinterpret_cast<float*>(Rc), n)[kLevelMode] = 0;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t first = warp * (uint32_t)tpw;
@@ -1025,10 +1030,22 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
     const uint32_t tileN = 1u << b;
     const uint32_t H = blockIdx.x;
     const uint32_t bv = 1u << v;
+    constexpr bool kBases = sizeof(T) == 4;         // FP32: per-level bases of F and R'
+    __shared__ float off_s[kBases ? 32 : 1];
+    __shared__ int sh_s;
+    __shared__ float fvrel_s;
     for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) {
         const uint32_t S = expand((H << b) | t, v);
         vals[t] = F[S] + Rc[S | bv];
         if (lq) vals[t] += lq[v * n + __popc(S)];   // q_v(S) of Eq. 12
+    }
+    if constexpr (kBases) {
+        if (threadIdx.x < 32)
+            gamma_offsets(n, v, reinterpret_cast<const float*>(F),
+                          reinterpret_cast<const float*>(Rc), off_s, &sh_s, &fvrel_s);
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x)
+            vals[t] += off_s[__popc(expand((H << b) | t, v) >> sh_s)];
     }
     __syncthreads();
     for (int j = 0; j < b; ++j) {
@@ -1244,7 +1261,10 @@ k_edges_acc(int n, int64_t K, int qbits, const double* __restrict__ logB,
     if (tid == 0) Nz = 0ull;
     __syncthreads();
     const uint32_t full = (1u << n) - 1u;
-    const double lnFV = L::to_ln((double)F[full]);
+    // FP32: Gamma is relative to the integer Z = floor of log P(D) in the
+    // level-based units (see gamma_offsets), so P(D) enters as F(V) - Z
+    const double fv = (double)F[full];
+    const double lnFV = L::to_ln(sizeof(T) == 4 ? fv - floor(fv) : fv);
     const double qscale = ldexp(1.0, qbits);
     const double cv = cmax[v];
     unsigned long long z = 0ull;
@@ -1289,7 +1309,10 @@ __global__ void k_edges_fin(int n, int use_z, int qbits, const double* __restric
     if (threadIdx.x == 0 && log_PD) {
         double c = 0.0;
         for (int i = 0; i < n; ++i) c += cmax[i];
-        *log_PD = bad ? NAN : LogOps<T>::to_ln((double)F[(1u << n) - 1u]) + c;
+        double fv = (double)F[(1u << n) - 1u];
+        if (sizeof(T) == 4)                       // FP32: add the level base of F(V)
+            fv += level_base_fwd(level_words(reinterpret_cast<const float*>(F), n), n - kLevelShift);
+        *log_PD = bad ? NAN : LogOps<T>::to_ln(fv) + c;
     }
 }
 

@@ -130,9 +130,13 @@ __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
 //
 // The 2^B values of F in tile Ht (its level's tiles of F already written):
 //   F(S) = sum_{i in S} A_i(S - {i}) F(S - {i}),  F(empty) = 1
+//
+// rebase: the previous level's stored values are relative to a base larger by
+// this much than this level's (the FP32 per-level bases, bn_device.cuh; 0
+// otherwise).  Returns the largest value written.
 template <typename T, int FMODE, int B, bool TLO = false>
-__device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __restrict__ A,
-                                             T* __restrict__ F)
+__device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restrict__ A,
+                                          T* __restrict__ F, T rebase = T(0))
 {
     constexpr int LN = 1 << B;
     const size_t half = (size_t)1 << (n - 1);
@@ -152,6 +156,10 @@ __device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __rest
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + f[l]);
     }
+    // (m, s) stands for m + lg(s): moving the cross-tile sums to this level's
+    // base moves m
+#pragma unroll
+    for (int l = 0; l < LN; ++l) m[l] -= rebase;
     // terms inside the tile: A_i(S - {i}) for i < B, 2^(B-1) values per i
     T ai[B][LN / 2];
 #pragma unroll
@@ -168,13 +176,17 @@ __device__ __forceinline__ void forward_tile(int n, uint32_t Ht, const T* __rest
         Fv[l] = m[l] + L::lg(s[l]);
     }
     store_row(F + ((size_t)Ht << B), Fv);
+    T mx = Fv[0];
+#pragma unroll
+    for (int l = 1; l < LN; ++l) mx = Fv[l] > mx ? Fv[l] : mx;
+    return mx;
 }
 
 // The 2^B values of R' in tile Ht (the tiles of the level above written):
 //   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),  R'(V) = 1
 template <typename T, int FMODE, int B, bool TLO = false>
-__device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const T* __restrict__ A,
-                                              T* __restrict__ Rc)
+__device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restrict__ A,
+                                           T* __restrict__ Rc, T rebase = T(0))
 {
     constexpr int LN = 1 << B;
     const int nh = n - B;
@@ -194,6 +206,8 @@ __device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const T* __res
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + r[l]);
     }
+#pragma unroll
+    for (int l = 0; l < LN; ++l) m[l] -= rebase;
     // A_i(T) for i < B not in T, 2^(B-1) values per i
     T ai[B][LN / 2];
 #pragma unroll
@@ -210,6 +224,31 @@ __device__ __forceinline__ void backward_tile(int n, uint32_t Ht, const T* __res
         Rv[l] = m[l] + L::lg(s[l]);
     }
     store_row(Rc + ((size_t)Ht << B), Rv);
+    T mx = Rv[0];
+#pragma unroll
+    for (int l = 1; l < LN; ++l) mx = Rv[l] > mx ? Rv[l] : mx;
+    return mx;
+}
+
+// The largest value a block wrote for its level, floored, into the level's
+// word (one atomic per block; every thread of the block calls this).
+__device__ __forceinline__ void block_level_max(int* word, float mx)
+{
+    __shared__ int wm[8];
+    int v = __reduce_max_sync(0xffffffffu, level_floor(mx));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = max(v, wm[w]);
+        if (v != kLevelUnset) atomicMax(word, v);
+    }
+}
+// The first level of a sweep (one tile, one thread) starts the level words.
+__device__ __forceinline__ void level_words_start(int* lw, int level, float mx)
+{
+    for (int k = 0; k < kLevelMode; ++k) lw[k] = kLevelUnset;
+    lw[kLevelMode] = kLevelShift;
+    lw[level] = level_floor(mx);
 }
 
 __device__ __forceinline__ void cluster_barrier()
@@ -237,20 +276,37 @@ __device__ __forceinline__ uint32_t cluster_blocks()
 
 // FP32: 16-subset tiles at three blocks per SM (80 registers); FP64:
 // 8-subset tiles at two.
+//
+// FP32 keeps the per-level bases (bn_device.cuh): level hl reads the
+// previous level's word (its values' base minus this level's base), and
+// every block adds its largest written value to the level's word.
 template <typename T, bool TLO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ F,
                size_t js)
 {
     constexpr int B = sizeof(T) == 4 ? LB : LB64;
+    constexpr bool kBases = sizeof(T) == 4;
     A = job_ptr(A, js);
     F = job_ptr(F, js);
     __shared__ uint32_t bt[BT][BT];
     fill_table(bt);
     __syncthreads();
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ntiles) return;
-    forward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, F);
+    if constexpr (kBases) {
+        int* lw = level_words(reinterpret_cast<float*>(F), n);
+        const T rebase = hl > 0 ? (T)level_delta(lw, hl - 1) : T(0);
+        T mx = LogOps<T>::ninf();
+        if (g < ntiles) mx = forward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, F, rebase);
+        if (hl == 0) {
+            if (g == 0) level_words_start(lw, 0, mx);
+        } else {
+            block_level_max(lw + hl, mx);
+        }
+    } else {
+        if (g >= ntiles) return;
+        forward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, F);
+    }
 }
 
 template <typename T, bool TLO>
@@ -259,14 +315,28 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __re
                 size_t js)
 {
     constexpr int B = sizeof(T) == 4 ? LB : LB64;
+    constexpr bool kBases = sizeof(T) == 4;
     A = job_ptr(A, js);
     Rc = job_ptr(Rc, js);
     __shared__ uint32_t bt[BT][BT];
     fill_table(bt);
     __syncthreads();
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ntiles) return;
-    backward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, Rc);
+    if constexpr (kBases) {
+        const int nh = n - B;
+        int* lw = level_words(reinterpret_cast<float*>(Rc), n);
+        const T rebase = hl < nh ? (T)level_delta(lw, hl + 1) : T(0);
+        T mx = LogOps<T>::ninf();
+        if (g < ntiles) mx = backward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, nh, bt), A, Rc, rebase);
+        if (hl == nh) {
+            if (g == 0) level_words_start(lw, nh, mx);
+        } else {
+            block_level_max(lw + hl, mx);
+        }
+    } else {
+        if (g >= ntiles) return;
+        backward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, Rc);
+    }
 }
 
 // Step 3 of a whole batch group in one persistent launch of thread-block
@@ -297,13 +367,24 @@ k_rows_cluster(int n, int items, const float* __restrict__ A, float* __restrict_
         const float* Aj = reinterpret_cast<const float*>(reinterpret_cast<const char*>(A) + off);
         const bool fwd = (it & 1) == 0;
         float* X = reinterpret_cast<float*>(reinterpret_cast<char*>(fwd ? F : Rc) + off);
+        // the per-level bases of the level kernels, with the level words
+        // read after the cluster barrier that ends the level before
+        int* lw = level_words(X, n);
         for (int st = 0; st <= nh; ++st) {
             const int hl = fwd ? st : nh - st;
             const uint32_t nt = bt[nh][hl];
+            const float rebase = st == 0 ? 0.f : (float)level_delta(lw, fwd ? hl - 1 : hl + 1);
+            float mx = LogOps<float>::ninf();
             for (uint32_t g = t0; g < nt; g += stride) {
                 const uint32_t Ht = tile_of(g, hl, nh, bt);
-                if (fwd) forward_tile<float, LD_L2, LB>(n, Ht, Aj, X);
-                else backward_tile<float, LD_L2, LB>(n, Ht, Aj, X);
+                const float m1 = fwd ? forward_tile<float, LD_L2, LB>(n, Ht, Aj, X, rebase)
+                                     : backward_tile<float, LD_L2, LB>(n, Ht, Aj, X, rebase);
+                mx = m1 > mx ? m1 : mx;
+            }
+            if (st == 0) {
+                if (t0 == 0) level_words_start(lw, hl, mx);   // the level's one tile
+            } else {
+                block_level_max(lw + hl, mx);
             }
             cluster_barrier();
         }

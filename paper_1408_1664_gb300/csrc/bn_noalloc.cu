@@ -26,6 +26,7 @@
 // distinct arities come near them).  Either limit gives BN_ENOMEM, like the
 // size limit, before any GPU work.
 #include "bnedge.h"
+#include "bn_device.cuh"
 #include "bn_kernels.cuh"
 
 #include <cmath>
@@ -205,8 +206,9 @@ try {
                  o_cmax = take((size_t)P.n * 8), o_lbs = take(nK * es),
                  o_reo = take(bn::use_tile13_up(P) ? nK * es : 0),
                  o_rk = take(bn::needs_rank13(P) ? bn::kRank13Bytes : 0),
-                 o_A = take(((size_t)P.n << (P.n - 1)) * es), o_F = take(((size_t)1 << P.n) * es),
-                 o_Rc = take(((size_t)1 << P.n) * es),
+                 o_A = take(((size_t)P.n << (P.n - 1)) * es),
+                 o_F = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4),
+                 o_Rc = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4),
                  o_W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es),
                  o_ea = take((size_t)P.n * (P.n + 1) * 8);
     if (o > (size_t)BN_STATIC_SCRATCH_BYTES) return BN_ENOMEM;   // job too large

@@ -91,8 +91,9 @@ Layout make_layout(const Plan& P, size_t dbg_cells, bool feature = false)
     L.tab = take(bn::tile13_up_fits(P) ? nK * es : 0);
     L.rk13 = take(bn::tile13_gamma_fits(P) ? bn::kRank13Bytes : 0);
     L.A = take(((size_t)P.n << (P.n - 1)) * es);
-    L.F = take(((size_t)1 << P.n) * es);
-    L.Rc = take(((size_t)1 << P.n) * es);
+    // F and R' are each followed by the per-level words of the FP32 bases
+    L.F = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4);
+    L.Rc = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4);
     L.W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es);   // one slice per endpoint
     L.Gam = take(nK * es);
     L.eacc = take((size_t)P.n * (P.n + 1) * 8);
@@ -944,12 +945,19 @@ try {
     CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
     double fv[2] = {0.0, 0.0};
     char raw[2][8];
+    int lw[2][bn::kLevelWords];                  // FP32: the level words of each run's F
     CK(cudaMemcpyAsync(raw[0], B.at<char>(L.F) + full * es, es, cudaMemcpyDeviceToHost, s));
+    if (P.prec != 0)
+        CK(cudaMemcpyAsync(lw[0], B.at<char>(L.F) + (full + 1) * es, sizeof(lw[0]),
+                           cudaMemcpyDeviceToHost, s));
     CK(bn::launch_add_feature(P, B.at<void>(L.lbs), B.at<void>(L.logf), B.at<void>(L.lbsf), s));
     rc = enqueue_upzeta(P, B, B.at<void>(L.lbsf), s, &nl, nullptr);
     if (rc) return rc;
     CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
     CK(cudaMemcpyAsync(raw[1], B.at<char>(L.F) + full * es, es, cudaMemcpyDeviceToHost, s));
+    if (P.prec != 0)
+        CK(cudaMemcpyAsync(lw[1], B.at<char>(L.F) + (full + 1) * es, sizeof(lw[1]),
+                           cudaMemcpyDeviceToHost, s));
     std::vector<double> cmax(P.n);
     int err = 0;
     CK(cudaMemcpyAsync(cmax.data(), B.at<char>(L.cmax), (size_t)P.n * 8, cudaMemcpyDeviceToHost, s));
@@ -962,7 +970,8 @@ try {
         } else {
             float x;
             std::memcpy(&x, raw[k], 4);
-            fv[k] = (double)x * 0.69314718055994531;   // base 2 -> natural
+            const double b = bn::level_base_fwd(lw[k], P.n - bn::kLevelShift);
+            fv[k] = ((double)x + b) * 0.69314718055994531;   // base 2 -> natural
         }
     }
     double csum = 0.0;
@@ -1058,6 +1067,33 @@ static void tlo_to_plain(int n, float* a)
     }
 }
 
+// FP32 F and R' are stored relative to per-level integer bases and Gamma
+// relative to the integer Z (bn_device.cuh); the dumps add them back.
+static void undo_level_bases(bn_ctx* c, const Plan& P, const Layout& L, int stage, float* out)
+{
+    const size_t N = (size_t)1 << P.n;
+    int lf[bn::kLevelWords], lr[bn::kLevelWords];
+    float fs = 0.f;
+    if (cudaMemcpy(lf, c->ws + L.F + N * 4, sizeof(lf), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(lr, c->ws + L.Rc + N * 4, sizeof(lr), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&fs, c->ws + L.F + (N - 1) * 4, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        throw std::runtime_error("level words");
+    const int nh = P.n - bn::kLevelShift;
+    const bool fb = lf[bn::kLevelMode] == bn::kLevelShift, rb = lr[bn::kLevelMode] == bn::kLevelShift;
+    if (stage == BN_STAGE_GAMMA) {
+        const double Z = (fb ? bn::level_base_fwd(lf, nh) : 0.0) + std::floor((double)fs);
+        for (size_t x = 0; x < (size_t)P.n * P.K; ++x) out[x] = (float)((double)out[x] + Z);
+        return;
+    }
+    const int* lw = stage == BN_STAGE_F ? lf : lr;
+    if (!(stage == BN_STAGE_F ? fb : rb)) return;
+    double base[32];
+    for (int k = 0; k <= nh; ++k)
+        base[k] = stage == BN_STAGE_F ? bn::level_base_fwd(lw, k) : bn::level_base_bwd(lw, k, nh);
+    for (size_t S = 0; S < N; ++S)
+        out[S] = (float)((double)out[S] + base[__builtin_popcount((uint32_t)(S >> bn::kLevelShift))]);
+}
+
 int bn_debug_stage(bn_ctx* c, int32_t stage, void* host_out, size_t bytes)
 try {
     if (!c || !host_out || !c->have_last) return BN_EINVAL;
@@ -1080,6 +1116,8 @@ try {
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaMemcpy(host_out, c->ws + off, want, cudaMemcpyDeviceToHost));
     if (stage == BN_STAGE_A && bn::use_tlo(P)) tlo_to_plain(P.n, static_cast<float*>(host_out));
+    if (P.prec != 0 && (stage == BN_STAGE_F || stage == BN_STAGE_RC || stage == BN_STAGE_GAMMA))
+        undo_level_bases(c, P, L, stage, static_cast<float*>(host_out));
     return BN_OK;
 } catch (...) {
     return exception_code();

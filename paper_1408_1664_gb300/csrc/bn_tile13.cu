@@ -979,19 +979,32 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     const uint32_t bv = 1u << v;
 
     using O = typename OrdInt<T>::type;
+    constexpr bool kBases = sizeof(T) == 4;         // FP32: per-level bases of F and R'
     __shared__ O tmax_s;
     __shared__ T sfull_s;
     __shared__ T lq_s[Q ? 32 : 1];                  // q_v by |S| (Eq. 12), when given
+    __shared__ float off_s[kBases ? 32 : 1];        // F + R' - Z by level (bn_device.cuh)
+    __shared__ int sh_s;
+    __shared__ float fvrel_s;
     if (t == 0) tmax_s = ord_enc(Lg::ninf());
     if (Q && t < n) lq_s[t] = lq[v * n + t];
-    __syncthreads();
     T x[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {                  // the tile's loads go out first
+        const uint32_t S = expand((H << TB) | el1(r, t), v);
+        x[r] = F[S] + Rc[S | bv];
+    }
+    if constexpr (kBases) {                         // while they are in flight
+        if (t < 32) gamma_offsets(n, v, reinterpret_cast<const float*>(F),
+                                  reinterpret_cast<const float*>(Rc), off_s, &sh_s, &fvrel_s);
+    }
+    __syncthreads();
     T mx = Lg::ninf();
+    const int sh = kBases ? sh_s : 0;
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
-        const uint32_t el = el1(r, t);
-        const uint32_t S = expand((H << TB) | el, v);
-        x[r] = F[S] + Rc[S | bv];
+        const uint32_t S = expand((H << TB) | el1(r, t), v);
+        if constexpr (kBases) x[r] += off_s[__popc(S >> sh)];
         if (Q) x[r] += lq_s[__popc(S)];
         mx = x[r] > mx ? x[r] : mx;
     }
@@ -1011,7 +1024,9 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         T L = Lg::ninf();                           // relevance cut (see above)
         if (Aup) {
             const T at = job_ptr(Aup, js)[((size_t)v << (n - 1)) + (((size_t)H << TB) | (TN - 1))];
-            L = F[((size_t)1 << n) - 1] - margin - at;
+            // log P(D) in the units of s (FP32: relative to the integer Z)
+            const T fv = kBases ? (T)fvrel_s : F[((size_t)1 << n) - 1];
+            L = fv - margin - at;
         }
         const T floorv = L - Window<T>::gap;
         if (M < L) {                                // nothing in the tile matters

@@ -20,7 +20,6 @@ oracle would need about 130 GB plus scratch and several minutes; it runs only
 when the memory is there, and the FP32 path is always checked against the
 GPU FP64 path, itself checked against the oracle at n=26 above.
 """
-import os
 import time
 
 import numpy as np
@@ -131,19 +130,24 @@ def test_n26_fp32_bench_launch_config_matches_oracle(ctx, oracle26):
     assert abs(lpd - ref["log_PD"]) < 1e-3 * n
 
 
-def test_n29_served_job_fp32_vs_fp64(ctx):
-    """The served workload's big job (n=29, d=3, m=2000, FP32 arrays of about
-    36 GB): FP32 against the GPU FP64 path at 1e-4, and against the oracle
-    when the host has the memory for it."""
-    ds, d = datagen.served_job(0, big=True)
+@pytest.mark.parametrize("j", range(6))
+def test_n29_served_job_fp32_vs_fp64(ctx, j):
+    """The served workload's big jobs (n=29, d=3, m=2000, FP32 arrays of
+    about 36 GB; one every 10 s of the 60 s trace): FP32 against the GPU FP64
+    path at 1e-4, and against the oracle when the host has the memory for it.
+    At this size the FP32 forward sums reach thousands in log2 units, which
+    the per-level bases of F and R' keep near zero."""
+    ds, d = datagen.served_job(j, big=True)
     p32, l32 = ctx.edge_posteriors(ds.data, ds.arity, d, precision="fp32")
     p64, l64 = ctx.edge_posteriors(ds.data, ds.arity, d, precision="fp64")
     err = float(np.abs(p32 - p64).max())
-    print(f"n=29 served job: max |fp32 - fp64| = {err:.3e}")
+    print(f"n=29 served job {j}: max |fp32 - fp64| = {err:.3e}")
     np.testing.assert_allclose(p32, p64, atol=1e-4, rtol=0)
     assert abs(l32 - l64) < 1e-3 * ds.n
+    if j > 0:                             # the oracle, if at all, on the first of them
+        return
     need, have = oracle_bytes(ds.n), mem_available()
-    if have < 1.2 * need or os.environ.get("BN_SKIP_N29_ORACLE") == "1":
+    if have < 1.2 * need:
         print(f"oracle skipped: RAM ({have / 2**30:.0f} GiB available, "
               f"{need / 2**30:.0f} GiB needed)")
         return
