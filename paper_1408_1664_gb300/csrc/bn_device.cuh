@@ -148,6 +148,30 @@ __device__ __forceinline__ void gamma_offsets(int n, int v, const float* F, cons
     if (lane == 0) *sh = kLevelShift;
 }
 
+// The down-zeta offsets of every endpoint, built once per job before the
+// down-zeta phase 1 (launch_gamma_p1): after the level words of R', 32 floats
+// per endpoint v: off[0..29], then the shift (int bits) and F(V) - Z.
+constexpr int kGammaTabWords = 32 * 32;
+__host__ __device__ __forceinline__ float* gamma_table(float* Rc, int n)
+{
+    return reinterpret_cast<float*>(level_words(Rc, n) + kLevelWords);
+}
+__host__ __device__ __forceinline__ const float* gamma_table(const float* Rc, int n)
+{
+    return reinterpret_cast<const float*>(level_words(Rc, n) + kLevelWords);
+}
+// Threads 0..31 of a block copy endpoint v's offsets into shared memory.
+__device__ __forceinline__ void load_gamma_offsets(const float* Rc, int n, int v, float* off,
+                                                   int* sh, float* fvrel)
+{
+    if (threadIdx.x < 32) {
+        const float x = gamma_table(Rc, n)[v * 32 + threadIdx.x];
+        off[threadIdx.x] = x;
+        if (threadIdx.x == 30) *sh = __float_as_int(x);
+        if (threadIdx.x == 31) *fvrel = x;
+    }
+}
+
 // Number of subsets of an nb-element set with at most d elements.
 __device__ __forceinline__ uint32_t num_small_subsets(int nb, int d)
 {

@@ -1031,21 +1031,18 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
     const uint32_t H = blockIdx.x;
     const uint32_t bv = 1u << v;
     constexpr bool kBases = sizeof(T) == 4;         // FP32: per-level bases of F and R'
-    __shared__ float off_s[kBases ? 32 : 1];
+    __shared__ float off_s[32];
     __shared__ int sh_s;
     __shared__ float fvrel_s;
+    if constexpr (kBases) {
+        load_gamma_offsets(reinterpret_cast<const float*>(Rc), n, v, off_s, &sh_s, &fvrel_s);
+        __syncthreads();
+    }
     for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) {
         const uint32_t S = expand((H << b) | t, v);
         vals[t] = F[S] + Rc[S | bv];
+        if constexpr (kBases) vals[t] += off_s[__popc(S >> sh_s)];
         if (lq) vals[t] += lq[v * n + __popc(S)];   // q_v(S) of Eq. 12
-    }
-    if constexpr (kBases) {
-        if (threadIdx.x < 32)
-            gamma_offsets(n, v, reinterpret_cast<const float*>(F),
-                          reinterpret_cast<const float*>(Rc), off_s, &sh_s, &fvrel_s);
-        __syncthreads();
-        for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x)
-            vals[t] += off_s[__popc(expand((H << b) | t, v) >> sh_s)];
     }
     __syncthreads();
     for (int j = 0; j < b; ++j) {
@@ -1059,6 +1056,24 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
     T* row = W + (size_t)H * nlow;
     for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x)
         if (__popc(t) <= d) row[small_subset_rank(t, b)] = vals[t];
+}
+
+// FP32: the down-zeta offsets of endpoint blockIdx.x (one warp; bn_device.cuh).
+__global__ void k_gamma_table(int n, const float* __restrict__ F, float* __restrict__ Rc, size_t js)
+{
+    F = job_ptr(F, js);
+    Rc = job_ptr(Rc, js);
+    const int v = blockIdx.x;
+    __shared__ float off[32];
+    __shared__ int sh;
+    __shared__ float fvrel;
+    if (threadIdx.x < 32) off[threadIdx.x] = 0.f;
+    __syncwarp();
+    gamma_offsets(n, v, F, Rc, off, &sh, &fvrel);
+    __syncwarp();
+    float* tab = gamma_table(Rc, n) + v * 32;
+    const int l = threadIdx.x;
+    tab[l] = l < 30 ? off[l] : l == 30 ? __int_as_float(sh) : fvrel;
 }
 
 template <typename T>
@@ -1703,10 +1718,21 @@ size_t gamma_p2_smem_bytes(const Plan& P)
     return ((size_t)1 << P.hc_g) * es + nout * es + nout * 4 + 16;
 }
 
+cudaError_t launch_gamma_table(const Plan& P, const void* F, const void* Rc, cudaStream_t s)
+{
+    k_gamma_table<<<dim3(P.n, P.nj), 32, 0, s>>>(P.n, (const float*)F, (float*)const_cast<void*>(Rc),
+                                                 P.js);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const uint16_t* rk13,
                             void* W, cudaStream_t s, const void* lq, const void* A)
 {
     if (use_tile13_gamma(P)) return launch_gamma13_p1(P, F, Rc, rk13, W, s, lq, A);
+    if (P.prec != 0) {
+        const cudaError_t e = launch_gamma_table(P, F, Rc, s);
+        if (e != cudaSuccess) return e;
+    }
     const int h = P.n - 1 - P.b_g;
     const size_t sm1 = gamma_p1_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);

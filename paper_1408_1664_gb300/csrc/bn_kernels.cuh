@@ -105,6 +105,9 @@ cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const 
                             void* W, cudaStream_t s, const void* lq = nullptr,
                             const void* A = nullptr);
 cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s);
+// FP32: the per-endpoint offsets of the down-zeta input (one small launch,
+// made by launch_gamma_p1 itself; stored after the level words of Rc).
+cudaError_t launch_gamma_table(const Plan& P, const void* F, const void* Rc, cudaStream_t s);
 // Step 5 (three launches); acc: n * (n + 1) scratch words.
 cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                          const uint32_t* masks, const void* Gam, const void* F,

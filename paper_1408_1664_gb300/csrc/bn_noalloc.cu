@@ -208,7 +208,7 @@ try {
                  o_rk = take(bn::needs_rank13(P) ? bn::kRank13Bytes : 0),
                  o_A = take(((size_t)P.n << (P.n - 1)) * es),
                  o_F = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4),
-                 o_Rc = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4),
+                 o_Rc = take(((size_t)1 << P.n) * es + (bn::kLevelWords + bn::kGammaTabWords) * 4),
                  o_W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es), o_G = take(nK * es),
                  o_ea = take((size_t)P.n * (P.n + 1) * 8);
     if (o > (size_t)BN_STATIC_SCRATCH_BYTES) return BN_ENOMEM;   // job too large

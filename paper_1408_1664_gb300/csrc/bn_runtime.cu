@@ -93,7 +93,7 @@ Layout make_layout(const Plan& P, size_t dbg_cells, bool feature = false)
     L.A = take(((size_t)P.n << (P.n - 1)) * es);
     // F and R' are each followed by the per-level words of the FP32 bases
     L.F = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4);
-    L.Rc = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4);
+    L.Rc = take(((size_t)1 << P.n) * es + (bn::kLevelWords + bn::kGammaTabWords) * 4);
     L.W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es);   // one slice per endpoint
     L.Gam = take(nK * es);
     L.eacc = take((size_t)P.n * (P.n + 1) * 8);
@@ -436,7 +436,7 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     if (ev) CK(cudaEventRecord(ev->ev[5], s));
     CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
     if (ev) CK(cudaEventRecord(ev->ev[6], s));
-    nl += 2;
+    nl += P.prec != 0 ? 3 : 2;                  // FP32: the offset table first
     CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
                         B.at<void>(L.Gam), B.at<void>(L.F), err,
                         B.at<unsigned long long>(L.eacc), post_dev, logPD_dev, s));

@@ -983,7 +983,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     __shared__ O tmax_s;
     __shared__ T sfull_s;
     __shared__ T lq_s[Q ? 32 : 1];                  // q_v by |S| (Eq. 12), when given
-    __shared__ float off_s[kBases ? 32 : 1];        // F + R' - Z by level (bn_device.cuh)
+    __shared__ float off_s[32];                     // F + R' - Z by level (bn_device.cuh)
     __shared__ int sh_s;
     __shared__ float fvrel_s;
     if (t == 0) tmax_s = ord_enc(Lg::ninf());
@@ -994,18 +994,24 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         const uint32_t S = expand((H << TB) | el1(r, t), v);
         x[r] = F[S] + Rc[S | bv];
     }
-    if constexpr (kBases) {                         // while they are in flight
-        if (t < 32) gamma_offsets(n, v, reinterpret_cast<const float*>(F),
-                                  reinterpret_cast<const float*>(Rc), off_s, &sh_s, &fvrel_s);
-    }
+    if constexpr (kBases)                           // while they are in flight
+        load_gamma_offsets(reinterpret_cast<const float*>(Rc), n, v, off_s, &sh_s, &fvrel_s);
     __syncthreads();
     T mx = Lg::ninf();
-    const int sh = kBases ? sh_s : 0;
+    // The level of element el1(r, t) is |S >> 4| = |H| + |t without its low
+    // bits| + |r| (bit v, outside S, shifts the low bits of t by one when
+    // v < 4), so a thread needs six offsets, indexed by |r| <= 5.
+    float offr[6];
+    if constexpr (kBases) {
+        const int lowm = v >= kLevelShift ? 15 : 7;
+        const int bt = sh_s == kLevelShift ? __popc(H) + __popc(t & ~lowm) : 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) offr[k] = off_s[sh_s == kLevelShift ? bt + k : 0];
+    }
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
-        const uint32_t S = expand((H << TB) | el1(r, t), v);
-        if constexpr (kBases) x[r] += off_s[__popc(S >> sh)];
-        if (Q) x[r] += lq_s[__popc(S)];
+        if constexpr (kBases) x[r] += offr[__popc(r)];
+        if (Q) x[r] += lq_s[__popc(expand((H << TB) | el1(r, t), v))];
         mx = x[r] > mx ? x[r] : mx;
     }
     for (int o = 16; o; o >>= 1) {
@@ -1217,6 +1223,10 @@ cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
                               const uint16_t* rank13, void* W, cudaStream_t s, const void* lq,
                               const void* A)
 {
+    if (P.prec != 0) {
+        const cudaError_t e = launch_gamma_table(P, F, Rc, s);
+        if (e != cudaSuccess) return e;
+    }
     const int h = P.n - 1 - TB;
     const size_t sm = gamma13_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);
