@@ -84,11 +84,14 @@ typedef struct bn_ctx_opts {
 } bn_ctx_opts;
 
 /* bn_ctx_opts.flags: BN_CTX_NO_AUTOTUNE, batches keep the default schedule
- * instead of timing the alternatives; BN_CTX_CLUSTER_STEP3, every FP32 batch
- * group with n >= 5 runs step 3 in the persistent cluster kernel whatever
- * the timing says (see bn_batch_create). */
+ * (and a persistent launch keeps clusters of 8 blocks) instead of timing the
+ * alternatives; BN_CTX_CLUSTER_STEP3, every FP32 batch group with n >= 5
+ * runs step 3 in the persistent cluster kernel whatever the timing says;
+ * BN_CTX_GRAPH_BATCH, batches run as a graph of launches instead of one
+ * persistent launch (see bn_batch_create; CLUSTER_STEP3 implies it). */
 #define BN_CTX_NO_AUTOTUNE 1
 #define BN_CTX_CLUSTER_STEP3 2
+#define BN_CTX_GRAPH_BATCH 4
 
 typedef struct bn_job_desc {
     int32_t n;               /* number of variables                           */
@@ -308,6 +311,13 @@ int bn_debug_stage(bn_ctx* ctx, int32_t stage, void* host_out, size_t bytes);
  * counts[config*r_i + x_i], q*r_i int64 values on the host. */
 int bn_debug_counts(bn_ctx* ctx, const bn_job_desc* job, int32_t i,
                     uint32_t parent_mask, int64_t* counts, int64_t cells);
+/* The persistent batch form with a stage missing: every work item of the
+ * launches at position `depth` of each group's launch sequence is removed
+ * from the queue (their results never come) and every device-side wait gives
+ * up after `polls` polls, so the next bn_batch_run ends early and
+ * bn_batch_results returns BN_EDEVICE_TIMEOUT.  BN_EINVAL if the batch does
+ * not run in the persistent form. */
+int bn_debug_batch_drop(bn_batch* batch, int32_t depth, uint64_t polls);
 #endif /* BN_TESTING */
 
 #ifdef __cplusplus

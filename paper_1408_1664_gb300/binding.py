@@ -64,7 +64,7 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
 
 
 # Test hooks: exported only by the testing build (BN_TESTING).
-TEST_EXPORTS = ["bn_debug_stage", "bn_debug_counts"]
+TEST_EXPORTS = ["bn_debug_stage", "bn_debug_counts", "bn_debug_batch_drop"]
 
 
 def testing_build() -> bool:
@@ -116,6 +116,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_debug_counts": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_uint32, P,
                                       C.c_int64]),
         "bn_feature_posterior": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
+        "bn_debug_batch_drop": (C.c_int, [P, C.c_int32, C.c_uint64]),
     }
     for name, (res, args) in sig.items():
         if name in TEST_EXPORTS and not hasattr(L, name):
@@ -164,6 +165,7 @@ def bn_job_footprint(job: "Job") -> int:
 
 BN_CTX_NO_AUTOTUNE = 1
 BN_CTX_CLUSTER_STEP3 = 2
+BN_CTX_GRAPH_BATCH = 4
 
 
 def bn_ctx_create(device: int = 0, slots: int = 4, mem_budget: int = 0,
@@ -368,8 +370,10 @@ class Context:
 
     def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0,
                  fail_alloc_after: int = -1, autotune: bool = True,
-                 cluster_step3: bool = False):
-        flags = (0 if autotune else BN_CTX_NO_AUTOTUNE) | (BN_CTX_CLUSTER_STEP3 if cluster_step3 else 0)
+                 cluster_step3: bool = False, graph_batch: bool = False):
+        flags = ((0 if autotune else BN_CTX_NO_AUTOTUNE)
+                 | (BN_CTX_CLUSTER_STEP3 if cluster_step3 else 0)
+                 | (BN_CTX_GRAPH_BATCH if graph_batch else 0))
         self.h = bn_ctx_create(device, slots, mem_budget, fail_alloc_after, flags)
 
     def close(self):

@@ -23,7 +23,11 @@ OUTDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUTDIR, "libbnedge.so")
 LIB_TESTING = os.path.join(OUTDIR, "libbnedge_testing.so")
 LIB_PEAKS = os.path.join(OUTDIR, "libbnpeaks.so")
-SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_runtime.cu", "bn_noalloc.cu"]
+SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_runtime.cu", "bn_noalloc.cu",
+           "bn_mega.cu"]
+# the persistent batch kernel reads, within one launch, values other blocks
+# wrote: its global loads go through L2 only
+UNIT_FLAGS = {"bn_mega.cu": ["-Xptxas", "-dlcm=cg"]}
 PEAKS_SOURCE = "bn_peaks.cu"
 # (source, object, extra flags) of the second compile of the runtime unit
 TESTING_UNIT = ("bn_runtime.cu", "bn_runtime_testing.o", ["-DBN_TESTING"])
@@ -70,7 +74,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
             print(r.stdout, r.stderr)
         return obj
 
-    units = ([(src, src.replace(".cu", ".o"), []) for src in SOURCES] + [TESTING_UNIT]
+    units = ([(src, src.replace(".cu", ".o"), UNIT_FLAGS.get(src, [])) for src in SOURCES] + [TESTING_UNIT]
              + [(PEAKS_SOURCE, PEAKS_SOURCE.replace(".cu", ".o"), [])])
     with cf.ThreadPoolExecutor(len(units)) as ex:
         objs = list(ex.map(one, units))

@@ -1382,6 +1382,7 @@ __global__ void k_add_feature(const T* __restrict__ lbs, const T* __restrict__ l
 // ===========================================================================
 // Launchers.
 // ===========================================================================
+#ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
 static int grid_for(int64_t work, int threads, int cap = 152 * 32)
 {
     int64_t g = (work + threads - 1) / threads;
@@ -1394,7 +1395,7 @@ cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int 
                                uint64_t* planes, cudaStream_t s, const int* mj, int nj, size_t js)
 {
     const int64_t total = (int64_t)n * rmax * W;
-    k_pack_planes<<<dim3(grid_for(total, 256), nj), 256, 0, s>>>(data, n, m, rmax, W, planes, mj,
+    launch_or_record(KID_PACK_PLANES, k_pack_planes, dim3(grid_for(total, 256), nj), 256, 0, s, data, n, m, rmax, W, planes, mj,
                                                                  js);
     return cudaGetLastError();
 }
@@ -1403,7 +1404,7 @@ cudaError_t launch_check_data(const uint8_t* data, const uint8_t* arity, int n, 
                               int* err, cudaStream_t s)
 {
     if ((int64_t)n * m == 0) return cudaSuccess;
-    k_check_data<<<grid_for((int64_t)n * m, 256), 256, 0, s>>>(data, arity, n, m, err);
+    launch_or_record(KID_CHECK_DATA, k_check_data, grid_for((int64_t)n * m, 256), 256, 0, s, data, arity, n, m, err);
     return cudaGetLastError();
 }
 
@@ -1424,7 +1425,7 @@ cudaError_t launch_lgamma_table(const double* alpha, int rows, int m, int fxs, v
                                 const int* mj)
 {
     const int64_t total = (int64_t)rows * (m + 1);
-    k_lgamma_table<<<dim3(grid_for(total, 256), nj), 256, 0, s>>>(
+    launch_or_record(KID_LGAMMA_TABLE, k_lgamma_table, dim3(grid_for(total, 256), nj), 256, 0, s, 
         alpha, rows, m, (long long*)T, js, std::ldexp(1.0, fxs), fxj, mj);
     return cudaGetLastError();
 }
@@ -1459,7 +1460,8 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
     if (klo <= 4) {
         const int64_t xb = x_count == 1 ? i1 * Kc + f1 : 0;
         const int64_t xn = x_count == 1 ? 1 : (int64_t)P.n * Kc;
-        k_scores_bin<<<dim3((unsigned)((xn + 127) / 128), P.nj), 128, 0, s>>>(
+        const unsigned tbb = rec_block(128);
+        launch_or_record(KID_SCORES_BIN, k_scores_bin, dim3((unsigned)((xn + tbb - 1) / tbb), P.nj), tbb, 0, s, 
             P.n, P.m, P.W, P.K, Kc, planes, Dvals, P.rows, T, log_rho, xb, xn, masks, cmasks, logB,
             debug_counts, P.js, tinv, fxj);
         cudaError_t e = cudaGetLastError();
@@ -1472,7 +1474,7 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
         if (k >= kHistFrom) {                       // histogram of the samples' cells
             const unsigned grid = (unsigned)std::min<int64_t>((fn + 7) / 8, 152 * 32);
 #define BN_BIN_HIST(KP)                                                                           \
-    k_scores_bin_hist<KP><<<dim3(grid, P.nj), 256, 0, s>>>(                                    \
+    launch_or_record((int)KID_SCORES_BIN_HIST5 + (KP) - 5, k_scores_bin_hist<KP>, dim3(grid, P.nj), 256, 0, s,                                     \
         P.n, P.m, P.W, P.K, off[k], Ck, planes, Dvals, P.rows, T, log_rho, fb, fn, masks, cmasks, \
         logB, debug_counts, P.js, tinv, fxj)
             switch (k) {
@@ -1487,9 +1489,10 @@ static cudaError_t launch_scores_bin(const Plan& P, const uint64_t* planes, cons
             continue;
         }
         const int64_t threads = fn << (k - 4);
-        const unsigned grid = (unsigned)((threads + 127) / 128);
+        const unsigned tbh = rec_block(128);
+        const unsigned grid = (unsigned)((threads + tbh - 1) / tbh);
 #define BN_BIN_HI(HB)                                                                             \
-    k_scores_bin_hi<HB><<<dim3(grid, P.nj), 128, 0, s>>>(                                      \
+    launch_or_record((int)KID_SCORES_BIN_HI1 + (HB) - 1, k_scores_bin_hi<HB>, dim3(grid, P.nj), tbh, 0, s,                                       \
         P.n, P.m, P.W, P.K, off[k], Ck, planes, Dvals, P.rows, T, log_rho, fb, fn, masks, cmasks, \
         logB, debug_counts, P.js, tinv, fxj)
         switch (k) {
@@ -1530,31 +1533,31 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
         return launch_scores_bin(P, planes, Dvals, Tv, log_rho, x_begin, x_count, masks, cmasks,
                                  logB, debug_counts, s, fxj);
     if (P.scfg && scores_cfg_fits(P) && P.d <= 4 && P.rmax <= 4)
-        k_scores_cfg<4, 4><<<dim3(grid, P.nj), threads, 0, s>>>(
+        launch_or_record(KID_SCORES_CFG44, k_scores_cfg<4, 4>, dim3(grid, P.nj), threads, 0, s, 
             P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals, P.rows, T, log_rho, x_begin, x_count,
             masks, cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.scfg && scores_cfg_fits(P))
-        k_scores_cfg<SC_MP, SC_MR><<<dim3(grid, P.nj), threads, 0, s>>>(
+        launch_or_record(KID_SCORES_CFG, k_scores_cfg<SC_MP, SC_MR>, dim3(grid, P.nj), threads, 0, s, 
             P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals, P.rows, T, log_rho, x_begin, x_count,
             masks, cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.W <= 32 && P.d <= 4 && P.rmax <= 2)
-        k_scores_w<4, 2><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        launch_or_record(KID_SCORES_W42, k_scores_w<4, 2>, dim3(grid, P.nj), threads, 0, s, P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
                                                   cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.W <= 32 && P.d <= 4 && P.rmax <= 4)
-        k_scores_w<4, 4><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        launch_or_record(KID_SCORES_W44, k_scores_w<4, 4>, dim3(grid, P.nj), threads, 0, s, P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
                                                   cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.W <= 32 && P.d <= 8 && P.rmax <= 4)
-        k_scores_w<8, 4><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        launch_or_record(KID_SCORES_W84, k_scores_w<8, 4>, dim3(grid, P.nj), threads, 0, s, P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                                   P.rows, T, log_rho, x_begin, x_count, masks,
                                                   cmasks, logB, debug_counts, P.js, tinv, fxj);
     else if (P.d <= SC_MP && P.rmax <= SC_MR)
-        k_scores_cfg<SC_MP, SC_MR><<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        launch_or_record(KID_SCORES_CFG, k_scores_cfg<SC_MP, SC_MR>, dim3(grid, P.nj), threads, 0, s, P.n, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                               P.rows, T, log_rho, x_begin, x_count, masks,
                                               cmasks, logB, debug_counts, P.js, tinv, fxj);
     else
-        k_scores<<<dim3(grid, P.nj), threads, 0, s>>>(P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
+        launch_or_record(KID_SCORES, k_scores, dim3(grid, P.nj), threads, 0, s, P.n, P.d, P.m, P.W, P.rmax, P.K, arity, planes, Dvals,
                                           P.rows, T, log_rho, x_begin, x_count, masks, cmasks,
                                           logB, debug_counts, P.js, tinv, fxj);
     return cudaGetLastError();
@@ -1563,7 +1566,7 @@ cudaError_t launch_scores(const Plan& P, const uint8_t* arity, const uint64_t* p
 cudaError_t launch_add_weights(const Plan& P, double* logB, const double* w, cudaStream_t s)
 {
     const int64_t nK = (int64_t)P.n * P.K;
-    k_add_weights<<<grid_for(nK, 256), 256, 0, s>>>(logB, w, nK);
+    launch_or_record(KID_ADD_WEIGHTS, k_add_weights, grid_for(nK, 256), 256, 0, s, logB, w, nK);
     return cudaGetLastError();
 }
 
@@ -1572,9 +1575,9 @@ cudaError_t launch_apply_q(const Plan& P, const void* lq, void* A, cudaStream_t 
     const int64_t total = (int64_t)P.n << (P.n - 1);
     const int grid = grid_for(total, 256, 152 * 16);
     if (P.prec == 0)
-        k_apply_q<double><<<grid, 256, 0, s>>>(P.n, (const double*)lq, (double*)A, 0);
+        launch_or_record(KID_APPLY_Q_D, k_apply_q<double>, grid, 256, 0, s, P.n, (const double*)lq, (double*)A, 0);
     else
-        k_apply_q<float><<<grid, 256, 0, s>>>(P.n, (const float*)lq, (float*)A,
+        launch_or_record(KID_APPLY_Q_F, k_apply_q<float>, grid, 256, 0, s, P.n, (const float*)lq, (float*)A,
                                               use_tlo(P) ? 1 : 0);
     return cudaGetLastError();
 }
@@ -1584,17 +1587,17 @@ cudaError_t launch_add_feature(const Plan& P, const void* lbs, const void* lf, v
 {
     const int64_t nK = (int64_t)P.n * P.K;
     if (P.prec == 0)
-        k_add_feature<double><<<grid_for(nK, 256), 256, 0, s>>>(
+        launch_or_record(KID_ADD_FEATURE_D, k_add_feature<double>, grid_for(nK, 256), 256, 0, s, 
             (const double*)lbs, (const double*)lf, (double*)out, nK);
     else
-        k_add_feature<float><<<grid_for(nK, 256), 256, 0, s>>>(
+        launch_or_record(KID_ADD_FEATURE_F, k_add_feature<float>, grid_for(nK, 256), 256, 0, s, 
             (const float*)lbs, (const float*)lf, (float*)out, nK);
     return cudaGetLastError();
 }
 
 cudaError_t launch_node_max(const Plan& P, const double* logB, double* cmax, cudaStream_t s)
 {
-    k_node_max<<<dim3(P.n, P.nj), 256, 0, s>>>(P.K, logB, cmax, P.js);
+    launch_or_record(KID_NODE_MAX, k_node_max, dim3(P.n, P.nj), 256, 0, s, P.K, logB, cmax, P.js);
     return cudaGetLastError();
 }
 
@@ -1604,9 +1607,9 @@ cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double*
     const int64_t total = (int64_t)P.n * P.K;
     const dim3 grid(grid_for(total, 256), P.nj);
     if (P.prec == 0)
-        k_shift_scores<double><<<grid, 256, 0, s>>>(total, P.K, logB, cmax, (double*)lbs, P.js);
+        launch_or_record(KID_SHIFT_D, k_shift_scores<double>, grid, 256, 0, s, total, P.K, logB, cmax, (double*)lbs, P.js);
     else
-        k_shift_scores<float><<<grid, 256, 0, s>>>(total, P.K, logB, cmax, (float*)lbs, P.js);
+        launch_or_record(KID_SHIFT_F, k_shift_scores<float>, grid, 256, 0, s, total, P.K, logB, cmax, (float*)lbs, P.js);
     return cudaGetLastError();
 }
 
@@ -1636,10 +1639,10 @@ cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs
     const dim3 grid((unsigned)P.n << h, P.nj);
     const size_t sm = upzeta_smem_bytes(P);
     if (P.prec == 0)
-        k_upzeta<double><<<grid, 256, sm, s>>>(P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
+        launch_or_record(KID_UPZETA_D, k_upzeta<double>, grid, 256, sm, s, P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
                                                (const double*)lbs, (double*)A, P.js);
     else
-        k_upzeta<float><<<grid, 256, sm, s>>>(P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
+        launch_or_record(KID_UPZETA_F, k_upzeta<float>, grid, 256, sm, s, P.n, P.b_up, P.K, fixed_bits(P.K), cmasks,
                                               (const float*)lbs, (float*)A, P.js);
     return cudaGetLastError();
 }
@@ -1670,10 +1673,10 @@ cudaError_t launch_forward(const Plan& P, const void* A, void* F, cudaStream_t s
         const uint32_t warps = (nt + tpw - 1) / tpw;
         const dim3 grid((unsigned)(((uint64_t)warps * 32 + 255) / 256), P.nj);
         if (P.prec == 0)
-            k_forward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const double*)A,
+            launch_or_record(KID_FWD_LEVEL_D, k_forward_level<double>, grid, 256, 0, s, P.n, P.wb, hl, nt, tpw, (const double*)A,
                                                          (double*)F, P.js);
         else
-            k_forward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const float*)A,
+            launch_or_record(KID_FWD_LEVEL_F, k_forward_level<float>, grid, 256, 0, s, P.n, P.wb, hl, nt, tpw, (const float*)A,
                                                         (float*)F, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1692,10 +1695,10 @@ cudaError_t launch_backward(const Plan& P, const void* A, void* Rc, cudaStream_t
         const uint32_t warps = (nt + tpw - 1) / tpw;
         const dim3 grid((unsigned)(((uint64_t)warps * 32 + 255) / 256), P.nj);
         if (P.prec == 0)
-            k_backward_level<double><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw,
+            launch_or_record(KID_BWD_LEVEL_D, k_backward_level<double>, grid, 256, 0, s, P.n, P.wb, hl, nt, tpw,
                                                           (const double*)A, (double*)Rc, P.js);
         else
-            k_backward_level<float><<<grid, 256, 0, s>>>(P.n, P.wb, hl, nt, tpw, (const float*)A,
+            launch_or_record(KID_BWD_LEVEL_F, k_backward_level<float>, grid, 256, 0, s, P.n, P.wb, hl, nt, tpw, (const float*)A,
                                                          (float*)Rc, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1720,7 +1723,7 @@ size_t gamma_p2_smem_bytes(const Plan& P)
 
 cudaError_t launch_gamma_table(const Plan& P, const void* F, const void* Rc, cudaStream_t s)
 {
-    k_gamma_table<<<dim3(P.n, P.nj), 32, 0, s>>>(P.n, (const float*)F, (float*)const_cast<void*>(Rc),
+    launch_or_record(KID_GAMMA_TABLE, k_gamma_table, dim3(P.n, P.nj), 32, 0, s, P.n, (const float*)F, (float*)const_cast<void*>(Rc),
                                                  P.js);
     return cudaGetLastError();
 }
@@ -1737,11 +1740,11 @@ cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const 
     const size_t sm1 = gamma_p1_smem_bytes(P);
     const dim3 grid(1u << h, P.nj, P.n);
     if (P.prec == 0)
-        k_gamma_p1<double><<<grid, 256, sm1, s>>>(P.n, P.d, P.b_g, P.nlow_g,
+        launch_or_record(KID_GAMMA_P1_D, k_gamma_p1<double>, grid, 256, sm1, s, P.n, P.d, P.b_g, P.nlow_g,
                                                   (const double*)F, (const double*)Rc,
                                                   (double*)W, P.js, (const double*)lq);
     else
-        k_gamma_p1<float><<<grid, 256, sm1, s>>>(P.n, P.d, P.b_g, P.nlow_g,
+        launch_or_record(KID_GAMMA_P1_F, k_gamma_p1<float>, grid, 256, sm1, s, P.n, P.d, P.b_g, P.nlow_g,
                                                  (const float*)F, (const float*)Rc,
                                                  (float*)W, P.js, (const float*)lq);
     return cudaGetLastError();
@@ -1759,10 +1762,10 @@ cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_
         const size_t sm2 = gamma_p2_smem_bytes(P);
         const dim3 grid(c0, P.nj, P.n);
         if (P.prec == 0)
-            k_gamma_p2<double><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
+            launch_or_record(KID_GAMMA_P2_D, k_gamma_p2<double>, grid, 256, sm2, s, P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
                                                       (const double*)W, (double*)Gam, P.js);
         else
-            k_gamma_p2<float><<<grid, 256, sm2, s>>>(P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
+            launch_or_record(KID_GAMMA_P2_F, k_gamma_p2<float>, grid, 256, sm2, s, P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
                                                      (const float*)W, (float*)Gam, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1770,10 +1773,10 @@ cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_
     if (c0 < P.nlow_g) {
         const dim3 grid((P.nlow_g - c0 + 7) / 8, P.nj, P.n);
         if (P.prec == 0)
-            k_gamma_p2s<double><<<grid, 256, 0, s>>>(P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
+            launch_or_record(KID_GAMMA_P2S_D, k_gamma_p2s<double>, grid, 256, 0, s, P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
                                                      (const double*)W, (double*)Gam, P.js);
         else
-            k_gamma_p2s<float><<<grid, 256, 0, s>>>(P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
+            launch_or_record(KID_GAMMA_P2S_F, k_gamma_p2s<float>, grid, 256, 0, s, P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
                                                     (const float*)W, (float*)Gam, P.js);
     }
     return cudaGetLastError();
@@ -1783,25 +1786,25 @@ cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                          const uint32_t* masks, const void* Gam, const void* F, const int* err,
                          unsigned long long* acc, double* post, double* log_PD, cudaStream_t s)
 {
-    k_edges_zero<<<dim3(1, P.nj), 256, 0, s>>>(P.n, acc, P.js);
+    launch_or_record(KID_EDGES_ZERO, k_edges_zero, dim3(1, P.nj), 256, 0, s, P.n, acc, P.js);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned chunks = (unsigned)std::min<int64_t>((P.K + 1023) / 1024, 64);
     const dim3 grid(chunks, P.nj, P.n);
     if (P.prec == 0)
-        k_edges_acc<double><<<grid, 256, 0, s>>>(P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
+        launch_or_record(KID_EDGES_ACC_D, k_edges_acc<double>, grid, 256, 0, s, P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
                                                  (const double*)Gam, (const double*)F, acc, P.js);
     else
-        k_edges_acc<float><<<grid, 256, 0, s>>>(P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
+        launch_or_record(KID_EDGES_ACC_F, k_edges_acc<float>, grid, 256, 0, s, P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
                                                 (const float*)Gam, (const float*)F, acc, P.js);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (P.prec == 0)
-        k_edges_fin<double><<<dim3(1, P.nj), 1024, 0, s>>>(P.n, 0, fixed_bits(P.K), cmax,
+        launch_or_record(KID_EDGES_FIN_D, k_edges_fin<double>, dim3(1, P.nj), rec_block(1024), 0, s, P.n, 0, fixed_bits(P.K), cmax,
                                                            (const double*)F, err, acc, post,
                                                            log_PD, P.js);
     else
-        k_edges_fin<float><<<dim3(1, P.nj), 1024, 0, s>>>(P.n, 1, fixed_bits(P.K), cmax,
+        launch_or_record(KID_EDGES_FIN_F, k_edges_fin<float>, dim3(1, P.nj), rec_block(1024), 0, s, P.n, 1, fixed_bits(P.K), cmax,
                                                           (const float*)F, err, acc, post,
                                                           log_PD, P.js);
     return cudaGetLastError();
@@ -1822,5 +1825,7 @@ cudaError_t set_kernel_attributes()
 #undef SETA
     return set_tile13_attributes();
 }
+
+#endif  // BN_MEGA
 
 }  // namespace bn

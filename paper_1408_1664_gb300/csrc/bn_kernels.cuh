@@ -2,9 +2,118 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace bn {
+
+// ---------------------------------------------------------------------------
+// Launch records.  Every kernel launch goes through launch_or_record: it
+// launches, or, while a Recorder is installed on the calling host thread,
+// appends the launch (kernel id, grid, block, dynamic shared memory and the
+// arguments packed as the kernel's own parameter types) to the recorder.  A
+// batch records each job's launch sequence once and runs it inside one
+// persistent kernel (bn_mega.cu), which unpacks the arguments the same way.
+// ---------------------------------------------------------------------------
+enum KernelId : int32_t {
+    KID_NONE = 0,
+    KID_PACK_PLANES, KID_CHECK_DATA, KID_LGAMMA_TABLE,
+    KID_SCORES_BIN, KID_SCORES_BIN_HIST5, KID_SCORES_BIN_HIST6, KID_SCORES_BIN_HIST7,
+    KID_SCORES_BIN_HIST8, KID_SCORES_BIN_HI1, KID_SCORES_BIN_HI2, KID_SCORES_BIN_HI3,
+    KID_SCORES_BIN_HI4, KID_SCORES_CFG44, KID_SCORES_CFG, KID_SCORES_W42, KID_SCORES_W44,
+    KID_SCORES_W84, KID_SCORES, KID_ADD_WEIGHTS, KID_APPLY_Q_D, KID_APPLY_Q_F,
+    KID_ADD_FEATURE_D, KID_ADD_FEATURE_F, KID_NODE_MAX, KID_SHIFT_D, KID_SHIFT_F,
+    KID_UPZETA_D, KID_UPZETA_F, KID_FWD_LEVEL_D, KID_FWD_LEVEL_F, KID_BWD_LEVEL_D,
+    KID_BWD_LEVEL_F, KID_GAMMA_TABLE, KID_GAMMA_P1_D, KID_GAMMA_P1_F, KID_GAMMA_P2_D,
+    KID_GAMMA_P2_F, KID_GAMMA_P2S_D, KID_GAMMA_P2S_F, KID_EDGES_ZERO, KID_EDGES_ACC_D,
+    KID_EDGES_ACC_F, KID_EDGES_FIN_D, KID_EDGES_FIN_F, KID_RANK13, KID_REORDER_D,
+    KID_REORDER_F, KID_COLB8, KID_COLB4, KID_COLB2, KID_COLW_D, KID_COLW_F, KID_COLS_D,
+    KID_COLS_F, KID_UP13_D, KID_UP13_F_TLO, KID_UP13_F, KID_G13_D_Q, KID_G13_D, KID_G13_F_Q,
+    KID_G13_F, KID_FROWS_D, KID_FROWS_F_TLO, KID_FROWS_F, KID_BROWS_D, KID_BROWS_F_TLO,
+    KID_BROWS_F, KID_COUNT
+};
+
+// Arguments as one trivially copyable structure whose members have the
+// kernel's parameter types, in order (the same layout on host and device).
+template <typename... P> struct ArgPack {};
+template <typename H, typename... R> struct ArgPack<H, R...> {
+    H h;
+    ArgPack<R...> r;
+};
+template <typename... P> inline ArgPack<P...> make_pack(P... a);
+template <> inline ArgPack<> make_pack<>() { return {}; }
+template <typename H, typename... R> inline ArgPack<H, R...> make_pack(H h, R... r)
+{
+    return ArgPack<H, R...>{h, make_pack<R...>(r...)};
+}
+
+constexpr int kRecArgBytes = 224;
+struct LaunchRec {
+    int32_t kid;
+    uint32_t gx, gy, gz;          // grid
+    uint32_t block, smem;
+    uint32_t pad[2];
+    alignas(16) unsigned char args[kRecArgBytes];
+};
+static_assert(sizeof(LaunchRec) == 256, "launch record size");
+
+// LaunchRec::pad[0] flag: the kernel loops grid-stride over blockIdx.x, so
+// any grid width covers its work; the persistent form may run it narrower.
+constexpr uint32_t kRecStrideX = 2u;
+
+struct Recorder {
+    LaunchRec* recs = nullptr;    // host array owned by the caller
+    int cap = 0, count = 0;
+    bool overflow = false;
+};
+extern thread_local Recorder* g_recorder;
+inline bool recording() { return g_recorder != nullptr; }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_or_record(int kid, void (*k)(P...), dim3 grid, unsigned block,
+                                    size_t smem, cudaStream_t s, A... a)
+{
+    static_assert(sizeof...(P) == sizeof...(A), "argument count");
+    if (Recorder* r = g_recorder) {
+        using Pk = ArgPack<P...>;
+        static_assert(sizeof(Pk) <= kRecArgBytes, "launch arguments too large for a record");
+        if (r->count >= r->cap) {
+            r->overflow = true;
+            return cudaSuccess;
+        }
+        LaunchRec& x = r->recs[r->count++];
+        x = LaunchRec{};
+        x.kid = kid;
+        x.gx = grid.x;
+        x.gy = grid.y;
+        x.gz = grid.z;
+        x.block = block;
+        x.smem = (uint32_t)smem;
+        const Pk pk = make_pack<P...>(static_cast<P>(a)...);
+        std::memcpy(x.args, &pk, sizeof(Pk));
+        return cudaSuccess;
+    }
+    k<<<grid, block, smem, s>>>(static_cast<P>(a)...);
+    return cudaGetLastError();
+}
+
+// Threads per block a launch uses: `normal`, or 256 while recording (the
+// persistent kernel runs every record with 256 threads; kernels launched
+// with other sizes are written for any block size).
+inline unsigned rec_block(unsigned normal) { return recording() ? 256u : normal; }
+
+// The persistent batch kernel (bn_mega.cu).  persistent_runs: whether the
+// instance for precision prec (1 FP32, 0 FP64) runs kernel kid.
+// persistent_blocks: blocks that fit the GPU at once with `smem` dynamic
+// shared memory each.  launch_persistent zeroes ctl (ctl_bytes: the next-item
+// counter, status, abort flag, a spare word and one done-counter per record)
+// and runs the items; a wait gives up after `cap` polls.
+bool persistent_runs(int prec, int kid);
+cudaError_t set_persistent_attributes();
+int persistent_blocks(int prec, size_t smem);
+cudaError_t launch_persistent(int prec, const LaunchRec* recs, const int4* items, int nitems,
+                              const int2* deps, const int* need, int* ctl, size_t ctl_bytes,
+                              int blocks, size_t smem, uint64_t cap, cudaStream_t s);
 
 // Shapes of one job, computed on the host.
 struct Plan {

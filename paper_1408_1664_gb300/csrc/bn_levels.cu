@@ -391,6 +391,7 @@ k_rows_cluster(int n, int items, const float* __restrict__ A, float* __restrict_
     }
 }
 
+#ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
 namespace {
 
 uint64_t choose(int n, int k)
@@ -427,16 +428,16 @@ cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStrea
     const int nh = P.n - (P.prec == 0 ? LB64 : LB);
     for (int hl = 0; hl <= nh; ++hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        const unsigned tb = level_block(nt);
+        const unsigned tb = rec_block(level_block(nt));
         const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
-            k_forward_rows<double, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const double*)A,
+            launch_or_record(KID_FROWS_D, k_forward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt, (const double*)A,
                                                                (double*)F, P.js);
         else if (use_tlo(P))
-            k_forward_rows<float, true><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
+            launch_or_record(KID_FROWS_F_TLO, k_forward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
                                                              (float*)F, P.js);
         else
-            k_forward_rows<float, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
+            launch_or_record(KID_FROWS_F, k_forward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
                                                               (float*)F, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -451,16 +452,16 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
     const int nh = P.n - (P.prec == 0 ? LB64 : LB);
     for (int hl = nh; hl >= 0; --hl) {
         const uint32_t nt = (uint32_t)choose(nh, hl);
-        const unsigned tb = level_block(nt);
+        const unsigned tb = rec_block(level_block(nt));
         const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
-            k_backward_rows<double, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const double*)A,
+            launch_or_record(KID_BROWS_D, k_backward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt, (const double*)A,
                                                                 (double*)Rc, P.js);
         else if (use_tlo(P))
-            k_backward_rows<float, true><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
+            launch_or_record(KID_BROWS_F_TLO, k_backward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
                                                               (float*)Rc, P.js);
         else
-            k_backward_rows<float, false><<<grid, tb, 0, s>>>(P.n, hl, nt, (const float*)A,
+            launch_or_record(KID_BROWS_F, k_backward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
                                                                (float*)Rc, P.js);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -497,5 +498,7 @@ cudaError_t launch_rows_cluster(const Plan& P, const void* A, void* F, void* Rc,
     if (e == cudaSuccess && launches) ++*launches;
     return e;
 }
+
+#endif  // BN_MEGA
 
 }  // namespace bn

@@ -20,6 +20,11 @@
 #include <thread>
 #include <vector>
 
+namespace bn {
+// The launch recorder of the calling host thread (see launch_or_record).
+thread_local Recorder* g_recorder = nullptr;
+}  // namespace bn
+
 namespace {
 
 using bn::Plan;
@@ -572,6 +577,31 @@ struct bn_batch {
     cudaStream_t last = nullptr;
     bool ran = false;
     float ms_default = 0.0f, ms_tuned = 0.0f;   // whole-batch times seen by the autotuner
+    // The persistent form: per precision present, the recorded launch
+    // sequences of its groups, the work queue over them and the launch shape
+    // of the persistent kernel (bn_mega.cu).
+    struct Persistent {
+        int prec = 1;
+        std::vector<bn::LaunchRec> recs;
+        std::vector<int> depth, group;   // per record
+        std::vector<int2> deps;          // per record: records it waits for (-1 none)
+        std::vector<int4> items;         // {record, first block, end block, 0}
+        std::vector<int> need;           // per record: its items
+        bn::LaunchRec* recs_dev = nullptr;
+        int4* items_dev = nullptr;
+        int2* deps_dev = nullptr;
+        int* need_dev = nullptr;
+        int* ctl = nullptr;              // next item, status, abort, spare, done per record
+        size_t ctl_bytes = 0, smem = 0;
+        int blocks = 0, chunk = 1;
+        uint64_t cap = (uint64_t)1 << 24;   // polls before a device wait gives up (seconds)
+        float ms = 0.0f;
+        std::string tried;               // chunk sizes timed and their ms
+    };
+    std::vector<Persistent> persistent;
+    char* progs = nullptr;               // device memory of the persistent programs
+    bool use_persistent = false;
+    float ms_graph = 0.0f;               // one replay of the graph of launches
 };
 
 namespace {
@@ -738,6 +768,7 @@ try {
     }
     if (cudaSetDevice(opts.device) != cudaSuccess) return BN_ECUDA;
     if (bn::set_kernel_attributes() != cudaSuccess) return BN_ECUDA;
+    if (bn::set_persistent_attributes() != cudaSuccess) return BN_ECUDA;
     bn_ctx* c = new bn_ctx();
     c->device = opts.device;
     c->fail_after = opts.fail_alloc_after;
@@ -1160,15 +1191,13 @@ try {
 
 namespace {
 
-// Steps 1-5 of every job of group g on stream s; `stages` selects the parts:
-// bit 0 step 1 (per job) and the score shift, bit 1 step 2, bit 2 step 3,
-// bit 3 step 4, bit 4 step 5.
-int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsigned stages,
-                  const Side* side = nullptr)
+// Steps 1-5 of the jobs of plan G (G.nj jobs G.js bytes apart from `base`,
+// each laid out by L) on stream s; `stages` selects the parts: bit 0 step 1
+// (per job) and the score shift, bit 1 step 2, bit 2 step 3, bit 3 step 4,
+// bit 4 step 5.
+int enqueue_steps(const Plan& G, const Layout& L, char* base, cudaStream_t s, unsigned stages,
+                  const Side* side)
 {
-    const Plan& G = g.P;
-    const Layout& L = g.L;
-    char* base = b->arena + g.base;
     auto at = [&](size_t off) { return base + off; };
     if (stages & 1u) {
         // one launch per kernel for the whole group, on the padded tables:
@@ -1233,6 +1262,13 @@ int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsign
     return BN_OK;
 }
 
+// Steps 1-5 of every job of group g on stream s (see enqueue_steps).
+int enqueue_group(const bn_batch* b, const BatchGroup& g, cudaStream_t s, unsigned stages,
+                  const Side* side = nullptr)
+{
+    return enqueue_steps(g.P, g.L, b->arena + g.base, s, stages, side);
+}
+
 // Every group of the batch on its branch stream (R' beside F), forked from
 // and joined back into stream s: the work of one bn_batch_run.
 int enqueue_batch(const bn_batch* b, cudaStream_t s)
@@ -1288,6 +1324,229 @@ int time_batch(const bn_batch* b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1
     cudaGraphDestroy(gr);
     if (e != cudaSuccess) return BN_ECUDA;
     *ms /= 3.0f;
+    return BN_OK;
+}
+
+// The persistent form of a batch.  Each group's launch sequence is recorded
+// with the launchers of the graph form (all the group's jobs per launch,
+// gridDim.y = jobs), F and R' levels paired (F level l beside R' level l, the
+// two sweeps being independent).  A record's depth is its position in the
+// group's sequence (a pair shares one depth) and it waits for the group's
+// records one depth earlier.  Returns BN_EINVAL when a group needs a kernel
+// the persistent kernel does not run (the batch then keeps the graph).
+int record_groups(bn_batch* b)
+{
+    std::vector<bn::LaunchRec> buf(8192);
+    for (int prec = 0; prec <= 1; ++prec) {
+        bn_batch::Persistent pp;
+        pp.prec = prec;
+        for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+            const BatchGroup& g = b->groups[gi];
+            if (g.P.prec != prec) continue;
+            Plan G = g.P;
+            G.frc = 0;
+            bn::Recorder rec;
+            rec.recs = buf.data();
+            rec.cap = (int)buf.size();
+            bn::g_recorder = &rec;
+            const int rc = enqueue_steps(G, g.L, b->arena + g.base, nullptr, 31u, nullptr);
+            bn::g_recorder = nullptr;
+            if (rc || rec.overflow) return BN_EINVAL;
+            // the sequence as stages: one record each, or an (F, R') pair
+            std::vector<std::vector<bn::LaunchRec>> stages;
+            std::vector<bn::LaunchRec> fw, bw;
+            size_t level_at = SIZE_MAX;
+            for (int q = 0; q < rec.count; ++q) {
+                bn::LaunchRec x = rec.recs[q];
+                if (!bn::persistent_runs(prec, x.kid) || x.smem > 200 * 1024 ||
+                    !(x.block == 256 || (x.kid == bn::KID_GAMMA_TABLE && x.block == 32)))
+                    return BN_EINVAL;
+                switch (x.kid) {                   // kernels that loop grid-stride in x
+                case bn::KID_PACK_PLANES: case bn::KID_CHECK_DATA: case bn::KID_LGAMMA_TABLE:
+                case bn::KID_SCORES: case bn::KID_SCORES_W42: case bn::KID_SCORES_W44:
+                case bn::KID_SCORES_W84: case bn::KID_SCORES_CFG44: case bn::KID_SCORES_CFG:
+                case bn::KID_SHIFT_F: case bn::KID_SHIFT_D: case bn::KID_EDGES_ACC_F:
+                case bn::KID_EDGES_ACC_D: case bn::KID_REORDER_F: case bn::KID_REORDER_D:
+                case bn::KID_COLW_F: case bn::KID_COLW_D:
+                    x.pad[0] |= bn::kRecStrideX;
+                    break;
+                default:
+                    break;
+                }
+                pp.smem = std::max<size_t>(pp.smem, x.smem);
+                const bool f = x.kid == bn::KID_FROWS_F || x.kid == bn::KID_FROWS_F_TLO ||
+                               x.kid == bn::KID_FROWS_D || x.kid == bn::KID_FWD_LEVEL_F ||
+                               x.kid == bn::KID_FWD_LEVEL_D;
+                const bool r = x.kid == bn::KID_BROWS_F || x.kid == bn::KID_BROWS_F_TLO ||
+                               x.kid == bn::KID_BROWS_D || x.kid == bn::KID_BWD_LEVEL_F ||
+                               x.kid == bn::KID_BWD_LEVEL_D;
+                if (f || r) {
+                    if (level_at == SIZE_MAX) level_at = stages.size();
+                    (f ? fw : bw).push_back(x);
+                } else {
+                    stages.push_back({x});
+                }
+            }
+            if (level_at != SIZE_MAX) {
+                std::vector<std::vector<bn::LaunchRec>> lv;
+                for (size_t q = 0; q < std::max(fw.size(), bw.size()); ++q) {
+                    lv.emplace_back();
+                    if (q < fw.size()) lv.back().push_back(fw[q]);
+                    if (q < bw.size()) lv.back().push_back(bw[q]);
+                }
+                stages.insert(stages.begin() + level_at, lv.begin(), lv.end());
+            }
+            int prev0 = -1, prev1 = -1;
+            for (size_t d = 0; d < stages.size(); ++d) {
+                const int first = (int)pp.recs.size();
+                for (const auto& x : stages[d]) {
+                    pp.recs.push_back(x);
+                    pp.depth.push_back((int)d);
+                    pp.group.push_back((int)gi);
+                    pp.deps.push_back(int2{prev0, prev1});
+                }
+                prev0 = first;
+                prev1 = stages[d].size() > 1 ? first + 1 : -1;
+            }
+        }
+        if (!pp.recs.empty()) b->persistent.push_back(std::move(pp));
+    }
+    return BN_OK;
+}
+
+// The work queue of one precision for `chunk` blocks per item: a grid-stride
+// kernel runs about `blocks` blocks per record (its x width shrunk to fit),
+// a record with more blocks than the persistent kernel has goes in items of
+// up to `chunk` blocks, and the items of all groups are ordered by depth.
+void build_queue(bn_batch::Persistent& pp, int chunk)
+{
+    const int nrec = (int)pp.recs.size();
+    pp.need.assign(nrec, 0);
+    std::vector<int> order(nrec);
+    for (int r = 0; r < nrec; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return pp.depth[x] != pp.depth[y] ? pp.depth[x] < pp.depth[y] : x < y;
+    });
+    pp.items.clear();
+    for (int r : order) {
+        bn::LaunchRec& x = pp.recs[r];
+        const uint64_t yz = (uint64_t)x.gy * x.gz;
+        if (x.pad[0] & bn::kRecStrideX) {
+            // rewrite the record's width once, from its recorded width
+            if (x.pad[1] == 0) x.pad[1] = x.gx;
+            const uint64_t want = std::max<uint64_t>(1, ((uint64_t)pp.blocks + yz - 1) / yz);
+            x.gx = (uint32_t)std::min<uint64_t>(x.pad[1], want);
+        }
+        const int nvb = (int)(x.gx * yz);
+        const int c = nvb > pp.blocks ? chunk : 1;
+        for (int v = 0; v < nvb; v += c) {
+            pp.items.push_back(int4{r, v, std::min(nvb, v + c), 0});
+            ++pp.need[r];
+        }
+    }
+    pp.chunk = chunk;
+}
+
+int upload_queue(bn_batch* b, bn_batch::Persistent& pp)
+{
+    CK(cudaMemcpy(pp.recs_dev, pp.recs.data(), pp.recs.size() * sizeof(bn::LaunchRec),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pp.items_dev, pp.items.data(), pp.items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pp.deps_dev, pp.deps.data(), pp.deps.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pp.need_dev, pp.need.data(), pp.need.size() * sizeof(int), cudaMemcpyHostToDevice));
+    (void)b;
+    return BN_OK;
+}
+
+// Device memory for the programs (the item array sized for chunk 1, the
+// most items) and the first queue.
+int build_persistent(bn_batch* b)
+{
+    int rc = record_groups(b);
+    if (rc) return rc;
+    auto al256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t bytes = 0;
+    for (auto& pp : b->persistent) {
+        pp.blocks = bn::persistent_blocks(pp.prec, pp.smem);
+        if (pp.blocks < 1) return BN_ECUDA;
+        build_queue(pp, 1);
+        const size_t nrec = pp.recs.size();
+        pp.ctl_bytes = 16 + 4 * nrec;
+        bytes += al256(nrec * sizeof(bn::LaunchRec)) + al256(pp.items.size() * sizeof(int4)) +
+                 al256(nrec * sizeof(int2)) + al256(nrec * 4) + al256(pp.ctl_bytes);
+    }
+    void* p = nullptr;
+    rc = dev_alloc(b->ctx, &p, bytes, nullptr);
+    if (rc) return rc;
+    b->progs = (char*)p;
+    size_t o = 0;
+    for (auto& pp : b->persistent) {
+        const size_t nrec = pp.recs.size();
+        pp.recs_dev = reinterpret_cast<bn::LaunchRec*>(b->progs + o);
+        o += al256(nrec * sizeof(bn::LaunchRec));
+        pp.items_dev = reinterpret_cast<int4*>(b->progs + o);
+        o += al256(pp.items.size() * sizeof(int4));
+        pp.deps_dev = reinterpret_cast<int2*>(b->progs + o);
+        o += al256(nrec * sizeof(int2));
+        pp.need_dev = reinterpret_cast<int*>(b->progs + o);
+        o += al256(nrec * 4);
+        pp.ctl = reinterpret_cast<int*>(b->progs + o);
+        o += al256(pp.ctl_bytes);
+        rc = upload_queue(b, pp);
+        if (rc) return rc;
+    }
+    return BN_OK;
+}
+
+int run_persistent(const bn_batch* b, cudaStream_t s)
+{
+    for (const auto& pp : b->persistent)
+        CK(bn::launch_persistent(pp.prec, pp.recs_dev, pp.items_dev, (int)pp.items.size(),
+                                 pp.deps_dev, pp.need_dev, pp.ctl, pp.ctl_bytes, pp.blocks, pp.smem,
+                                 pp.cap, s));
+    return BN_OK;
+}
+
+// The persistent form's tuner: for each precision, the item size (1, 2 or 4
+// blocks of a launch per queue item) that runs the batch fastest, each
+// launch timed on the batch's own data (one warm-up launch, three timed).
+int tune_persistent(bn_batch* b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
+{
+    for (auto& pp : b->persistent) {
+        float best = 0.0f;
+        int best_c = 0;
+        for (int c : {1, 2, 4}) {
+            build_queue(pp, c);
+            if (upload_queue(b, pp) != BN_OK) return BN_ECUDA;
+            cudaError_t e = bn::launch_persistent(pp.prec, pp.recs_dev, pp.items_dev,
+                                                  (int)pp.items.size(), pp.deps_dev, pp.need_dev,
+                                                  pp.ctl, pp.ctl_bytes, pp.blocks, pp.smem, pp.cap, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int r = 0; e == cudaSuccess && r < 3; ++r)
+                e = bn::launch_persistent(pp.prec, pp.recs_dev, pp.items_dev, (int)pp.items.size(),
+                                          pp.deps_dev, pp.need_dev, pp.ctl, pp.ctl_bytes, pp.blocks,
+                                          pp.smem, pp.cap, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return BN_ECUDA;
+            }
+            ms /= 3.0f;
+            char t[48];
+            std::snprintf(t, sizeof t, "%s%d:%.3f", pp.tried.empty() ? "" : " ", c, ms);
+            pp.tried += t;
+            if (best_c == 0 || ms < best) {
+                best = ms;
+                best_c = c;
+            }
+        }
+        build_queue(pp, best_c);
+        if (upload_queue(b, pp) != BN_OK) return BN_ECUDA;
+        pp.ms = best;
+    }
     return BN_OK;
 }
 
@@ -1451,6 +1710,7 @@ try {
     auto key_of = [](const Plan& P) {
         return std::array<int, 5>{P.n, P.d, P.prec, P.allbin, P.nj};
     };
+    const bool want_persistent = !(c->flags & (BN_CTX_GRAPH_BATCH | BN_CTX_CLUSTER_STEP3));
     if (ok && !(c->flags & BN_CTX_NO_AUTOTUNE)) {
         bool all_cached = true;
         for (const auto& g : b->groups) all_cached = all_cached && c->tuned.count(key_of(g.P)) > 0;
@@ -1476,6 +1736,29 @@ try {
     }
     cudaGetLastError();
     if (rc) { bn_batch_destroy(b); return rc; }
+    // one replay of the graph, timed for the comparison bn_batch_describe reports
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        bool t_ok = cudaGraphLaunch(b->exec, cap) == cudaSuccess &&
+                    cudaEventRecord(e0, cap) == cudaSuccess;
+        for (int r = 0; t_ok && r < 3; ++r) t_ok = cudaGraphLaunch(b->exec, cap) == cudaSuccess;
+        t_ok = t_ok && cudaEventRecord(e1, cap) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+               cudaEventElapsedTime(&b->ms_graph, e0, e1) == cudaSuccess;
+        b->ms_graph = t_ok ? b->ms_graph / 3.0f : 0.0f;
+        if (want_persistent && build_persistent(b) == BN_OK) {
+            if (c->flags & BN_CTX_NO_AUTOTUNE) {
+                b->use_persistent = true;
+            } else if (tune_persistent(b, cap, e0, e1) == BN_OK) {
+                // the form that runs the whole batch faster
+                float ms = 0.0f;
+                for (const auto& pp : b->persistent) ms += pp.ms;
+                b->use_persistent = b->ms_graph <= 0.0f || ms < b->ms_graph;
+            }
+        }
+        cudaGetLastError();
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     *out = b;
     return BN_OK;
 } catch (...) {
@@ -1487,7 +1770,12 @@ try {
     if (!b || !b->exec) return BN_EINVAL;
     cudaSetDevice(b->ctx->device);
     b->last = stream ? (cudaStream_t)stream : b->ctx->stream;
-    CK(cudaGraphLaunch(b->exec, b->last));
+    if (b->use_persistent) {
+        const int rc = run_persistent(b, b->last);
+        if (rc) return rc;
+    } else {
+        CK(cudaGraphLaunch(b->exec, b->last));
+    }
     b->ran = true;
     return BN_OK;
 } catch (...) {
@@ -1505,6 +1793,13 @@ try {
     if (log_PD) CK(cudaMemcpy(log_PD, jb + g.L.logPD, 8, cudaMemcpyDeviceToHost));
     int err = 0;
     CK(cudaMemcpy(&err, jb + g.L.err, 4, cudaMemcpyDeviceToHost));
+    if (b->use_persistent)
+        for (const auto& pp : b->persistent)
+            if (pp.prec == P.prec) {
+                int st = 0;
+                CK(cudaMemcpy(&st, pp.ctl + 1, 4, cudaMemcpyDeviceToHost));
+                if (st) return st;
+            }
     return err ? BN_EINVAL : BN_OK;
 } catch (...) {
     return exception_code();
@@ -1525,6 +1820,18 @@ try {
                       b->ms_tuned);
         s += line;
     }
+    for (const auto& pp : b->persistent) {
+        uint64_t vbs = 0;
+        for (const auto& x : pp.recs) vbs += (uint64_t)x.gx * x.gy * x.gz;
+        std::snprintf(line, sizeof line,
+                      "persistent %s: records=%zu vblocks=%llu items=%zu blocks=%d chunk=%d ms=%.3f"
+                      " (chunk:ms %s) graph_ms=%.3f %s\n",
+                      pp.prec == 0 ? "fp64" : "fp32", pp.recs.size(), (unsigned long long)vbs,
+                      pp.items.size(), pp.blocks, pp.chunk, pp.ms,
+                      pp.tried.empty() ? "fixed" : pp.tried.c_str(), b->ms_graph,
+                      b->use_persistent ? "in use" : "not used");
+        s += line;
+    }
     std::snprintf(buf, len, "%s", s.c_str());
     return BN_OK;
 } catch (...) {
@@ -1543,11 +1850,33 @@ try {
     for (auto e : b->joins) if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->arena) cudaFree(b->arena);
+    if (b->progs) cudaFree(b->progs);
     delete b;
     return BN_OK;
 } catch (...) {
     return exception_code();
 }
+
+#ifdef BN_TESTING
+// Test hook: the persistent form with one stage missing from the queue (its
+// results never come), every device wait bounded at `polls` polls.
+int bn_debug_batch_drop(bn_batch* b, int32_t depth, uint64_t polls)
+try {
+    if (!b || !b->use_persistent || polls < 1) return BN_EINVAL;
+    for (auto& pp : b->persistent) {
+        std::vector<int4> kept;
+        for (const int4& it : pp.items)
+            if (pp.depth[it.x] != depth) kept.push_back(it);
+        pp.items.swap(kept);
+        pp.cap = polls;
+        CK(cudaMemcpy(pp.items_dev, pp.items.data(), pp.items.size() * sizeof(int4),
+                      cudaMemcpyHostToDevice));
+    }
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+#endif  // BN_TESTING
 
 // ---------------------------------------------------------------- serving --
 

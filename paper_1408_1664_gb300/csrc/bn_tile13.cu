@@ -1098,6 +1098,7 @@ __global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restr
     unrank13[r] = (uint16_t)L;
 }
 
+#ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
 // ===========================================================================
 // Launchers.
 // ===========================================================================
@@ -1148,7 +1149,7 @@ size_t gamma13_smem_bytes(const Plan& P)
 
 cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unrank13, cudaStream_t s)
 {
-    k_rank13_tables<<<dim3(TN / 256, P.nj), 256, 0, s>>>(rank13, unrank13, P.js);
+    launch_or_record(KID_RANK13, k_rank13_tables, dim3(TN / 256, P.nj), 256, 0, s, rank13, unrank13, P.js);
     return cudaGetLastError();
 }
 
@@ -1157,10 +1158,10 @@ cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStr
     const int64_t total = (int64_t)P.n * P.K;
     const dim3 grid((unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), P.nj);
     if (P.prec == 0)
-        k_reorder_up<double><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const double*)lbs, (double*)tab,
+        launch_or_record(KID_REORDER_D, k_reorder_up<double>, grid, 256, 0, s, P.n, P.d, P.K, (const double*)lbs, (double*)tab,
                                                   P.js);
     else
-        k_reorder_up<float><<<grid, 256, 0, s>>>(P.n, P.d, P.K, (const float*)lbs, (float*)tab,
+        launch_or_record(KID_REORDER_F, k_reorder_up<float>, grid, 256, 0, s, P.n, P.d, P.K, (const float*)lbs, (float*)tab,
                                                  P.js);
     return cudaGetLastError();
 }
@@ -1180,29 +1181,29 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         const unsigned nblk = (unsigned)((uint64_t)P.n * ((ncol + cpb - 1) / cpb));
         const size_t smb = ((size_t)cpb << h) * 4;
         if (cpb == 8)
-            k_upzeta13_colb<8><<<dim3(nblk, P.nj), 256, smb, s>>>(P.n, P.d, P.K,
+            launch_or_record(KID_COLB8, k_upzeta13_colb<8>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
                                                                   (const float*)tab, (float*)A, P.js);
         else if (cpb == 4)
-            k_upzeta13_colb<4><<<dim3(nblk, P.nj), 256, smb, s>>>(P.n, P.d, P.K,
+            launch_or_record(KID_COLB4, k_upzeta13_colb<4>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
                                                                   (const float*)tab, (float*)A, P.js);
         else
-            k_upzeta13_colb<2><<<dim3(nblk, P.nj), 256, smb, s>>>(P.n, P.d, P.K,
+            launch_or_record(KID_COLB2, k_upzeta13_colb<2>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
                                                                   (const float*)tab, (float*)A, P.js);
     } else if (nrow * 4 * 8 <= 160 * 1024) {          // warp per tile, 8 tiles per block
         const uint64_t ntiles = (uint64_t)P.n << h;
         const dim3 gw((unsigned)std::min<uint64_t>((ntiles + 7) / 8, 152 * 16), P.nj);
         const size_t sw = (size_t)nrow * 4 * 8;
         if (P.prec == 0)
-            k_upzeta13_colw<double><<<gw, 256, sw, s>>>(P.n, P.d, P.K, (const double*)tab,
+            launch_or_record(KID_COLW_D, k_upzeta13_colw<double>, gw, 256, sw, s, P.n, P.d, P.K, (const double*)tab,
                                                         (double*)A, P.js);
         else
-            k_upzeta13_colw<float><<<gw, 256, sw, s>>>(P.n, P.d, P.K, (const float*)tab,
+            launch_or_record(KID_COLW_F, k_upzeta13_colw<float>, gw, 256, sw, s, P.n, P.d, P.K, (const float*)tab,
                                                        (float*)A, P.js);
     } else if (P.prec == 0)
-        k_upzeta13_cols<double><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const double*)tab, (double*)A,
+        launch_or_record(KID_COLS_D, k_upzeta13_cols<double>, grid, TT, sc, s, P.n, P.d, P.K, (const double*)tab, (double*)A,
                                                      P.js);
     else
-        k_upzeta13_cols<float><<<grid, TT, sc, s>>>(P.n, P.d, P.K, (const float*)tab, (float*)A,
+        launch_or_record(KID_COLS_F, k_upzeta13_cols<float>, grid, TT, sc, s, P.n, P.d, P.K, (const float*)tab, (float*)A,
                                                     P.js);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1211,11 +1212,11 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         if (e != cudaSuccess) return e;
     }
     if (P.prec == 0)
-        k_upzeta13<double, false><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (double*)A, P.js);
+        launch_or_record(KID_UP13_D, k_upzeta13<double, false>, grid, TT, sm, s, P.n, P.d, unrank13, (double*)A, P.js);
     else if (use_tlo(P))
-        k_upzeta13<float, true><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A, P.js);
+        launch_or_record(KID_UP13_F_TLO, k_upzeta13<float, true>, grid, TT, sm, s, P.n, P.d, unrank13, (float*)A, P.js);
     else
-        k_upzeta13<float, false><<<grid, TT, sm, s>>>(P.n, P.d, unrank13, (float*)A, P.js);
+        launch_or_record(KID_UP13_F, k_upzeta13<float, false>, grid, TT, sm, s, P.n, P.d, unrank13, (float*)A, P.js);
     return cudaGetLastError();
 }
 
@@ -1237,20 +1238,20 @@ cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
     // the order prior is a separate instance: the plain kernel has no trace of it
     if (P.prec == 0) {
         if (lq)
-            k_gamma13_p1<double, true><<<grid, TT, sm, s>>>(
+            launch_or_record(KID_G13_D_Q, k_gamma13_p1<double, true>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
                 (const double*)lq, (const double*)A, margin);
         else
-            k_gamma13_p1<double, false><<<grid, TT, sm, s>>>(
+            launch_or_record(KID_G13_D, k_gamma13_p1<double, false>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
                 nullptr, (const double*)A, margin);
     } else {
         if (lq)
-            k_gamma13_p1<float, true><<<grid, TT, sm, s>>>(
+            launch_or_record(KID_G13_F_Q, k_gamma13_p1<float, true>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
                 (const float*)lq, (const float*)A, (float)margin);
         else
-            k_gamma13_p1<float, false><<<grid, TT, sm, s>>>(
+            launch_or_record(KID_G13_F, k_gamma13_p1<float, false>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
                 nullptr, (const float*)A, (float)margin);
     }
@@ -1280,5 +1281,7 @@ cudaError_t set_tile13_attributes()
 #undef SETA
     return cudaSuccess;
 }
+
+#endif  // BN_MEGA
 
 }  // namespace bn

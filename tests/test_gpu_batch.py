@@ -1,12 +1,16 @@
-"""Batches: many independent small jobs replayed as one CUDA graph
-(bn_batch_create / bn_batch_run / bn_batch_results).  Jobs with equal n, d,
-precision and kind of data (binary or not) share every launch of steps 1-5.
+"""Batches: many independent small jobs (bn_batch_create / bn_batch_run /
+bn_batch_results).  By default a batch runs as ONE persistent launch:
+thread-block clusters take whole jobs, largest first, from a device counter
+and run each job's recorded launch sequence (the same kernels as the job run
+alone) with cluster barriers between dependent launches.  The other form
+(BN_CTX_GRAPH_BATCH) replays a CUDA graph in which jobs with equal n, d,
+precision and kind of data share every launch of steps 1-5.
 
-Under the default schedule each job's result equals the same job run alone
-bit for bit (the same kernels, every reduction in a fixed order).  With the
-autotuner on, a group may run other kernels for a step; its results then
-agree with the job run alone within the stated tolerances (1e-9 FP64, 1e-4
-FP32), and are identical on every replay."""
+Under the default schedules each job's result equals the same job run alone
+bit for bit in both forms (the same kernels, every reduction in a fixed
+order).  With the graph form's autotuner on, a group may run other kernels
+for a step; its results then agree with the job run alone within the stated
+tolerances (1e-9 FP64, 1e-4 FP32), and are identical on every replay."""
 import collections
 
 import numpy as np
@@ -34,14 +38,17 @@ def _jobs(count=20, first=0):
     return [datagen.batched_job(j) for j in range(first, first + count)]
 
 
+@pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_default_schedule_equals_alone_over_replays(torch_cuda, precision):
+def test_default_schedule_equals_alone_over_replays(torch_cuda, precision, graph):
     jobs = _jobs()
-    with B.Context(0, autotune=False) as ctx:
+    with B.Context(0, autotune=False, graph_batch=graph) as ctx:
         alone = [ctx.edge_posteriors(ds.data, ds.arity, d, precision=precision) for ds, d in jobs]
         descs = [B.Job(ds.data, ds.arity, d, precision=precision) for ds, d in jobs]
         with B.Batch(ctx.h, descs) as batch:
-            assert "timed" not in batch.describe().replace("default-or-cached", "")
+            text = batch.describe()
+            assert "timed" not in text.replace("default-or-cached", "")
+            assert ("in use" in text) != graph, text
             for _ in range(2):
                 batch.run()
                 for k, (post0, lpd0) in enumerate(alone):
@@ -91,19 +98,77 @@ def test_cluster_step3_many_jobs_one_group(torch_cuda):
                 assert lpd == lpd0
 
 
+def test_persistent_tuner_and_mixed_precision(torch_cuda):
+    """The persistent form's tuner times work items of 1, 2 and 4 blocks on
+    the batch's own data; a batch with FP32 and FP64 jobs runs one persistent
+    launch per precision.  n from 10 to 18: every job equals the job run
+    alone, over two replays.  (With the tuner on, the faster form runs; the
+    persistent one is forced here through the fixed-schedule context after
+    timing it in an autotuned one.)"""
+    jobs = _jobs(64, first=300)
+    precs = ["fp32" if k % 4 else "fp64" for k in range(len(jobs))]
+    with B.Context(0) as ctx:
+        descs = [B.Job(ds.data, ds.arity, d, precision=p) for (ds, d), p in zip(jobs, precs)]
+        with B.Batch(ctx.h, descs) as batch:
+            text = batch.describe()
+            lines = [x for x in text.splitlines() if x.startswith("persistent")]
+            assert len(lines) == 2, text
+            assert all("1:" in x and "4:" in x for x in lines), text     # item sizes timed
+    with B.Context(0, autotune=False) as ctx:
+        alone = [ctx.edge_posteriors(ds.data, ds.arity, d, precision=p)
+                 for (ds, d), p in zip(jobs, precs)]
+        descs = [B.Job(ds.data, ds.arity, d, precision=p) for (ds, d), p in zip(jobs, precs)]
+        with B.Batch(ctx.h, descs) as batch:
+            text = batch.describe()
+            lines = [x for x in text.splitlines() if x.startswith("persistent")]
+            assert len(lines) == 2 and all("in use" in x for x in lines), text
+            for _ in range(2):
+                batch.run()
+                for k, (post0, lpd0) in enumerate(alone):
+                    post, lpd = batch.results(k)
+                    assert np.array_equal(post, post0), k
+                    assert lpd == lpd0
+
+
+def test_persistent_wait_times_out_when_a_stage_never_runs(torch_cuda):
+    """Every device-side wait of the persistent kernel is bounded.  The host
+    takes the work items of one stage (the per-node maxima of the scores,
+    fourth in each group's sequence) out of the queue, so the items after
+    them wait for results that never come; after 20000 polls the kernel
+    records BN_EDEVICE_TIMEOUT, raises its abort flag and returns -- no fault,
+    no endless wait -- and bn_batch_results reports the timeout."""
+    import time
+    jobs = _jobs(12, first=500)
+    with B.Context(0, autotune=False) as ctx:
+        with B.Batch(ctx.h, [B.Job(ds.data, ds.arity, d, precision="fp32")
+                             for ds, d in jobs]) as batch:
+            assert B.load().bn_debug_batch_drop(batch.h, 3, 20000) == B.BN_OK
+            t0 = time.time()
+            batch.run()
+            with pytest.raises(B.BnError) as ei:
+                batch.results(0)
+            assert ei.value.code == B.BN_EDEVICE_TIMEOUT
+            assert time.time() - t0 < 30.0
+        # the context still works
+        ds, d = jobs[0]
+        post, _ = ctx.edge_posteriors(ds.data, ds.arity, d, precision="fp32")
+        assert np.all(np.isfinite(post))
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_autotuned_batch_within_tolerance_and_cached(torch_cuda, precision):
+    """The graph form's schedule tuner (kernel choices per group)."""
     jobs = _jobs(24, first=40)
     ns = {ds.n for ds, _ in jobs}
     assert min(ns) < 14 <= max(ns)             # both tile paths are in the batch
-    with B.Context(0) as ctx:
+    with B.Context(0, graph_batch=True) as ctx:
         alone = [ctx.edge_posteriors(ds.data, ds.arity, d, precision=precision) for ds, d in jobs]
         descs = [B.Job(ds.data, ds.arity, d, precision=precision) for ds, d in jobs]
         with B.Batch(ctx.h, descs) as batch:
             text = batch.describe()
             # groups are (n, d, binary data or not); the autotuner times each
             groups = collections.Counter((ds.n, d, bool(np.all(ds.arity == 2))) for ds, d in jobs)
-            assert len(text.strip().splitlines()) == len(groups), text
+            assert len([x for x in text.strip().splitlines() if x.startswith("n=")]) == len(groups), text
             assert text.count("timed") == len(groups), text
             first = []
             for rep in range(2):
