@@ -254,6 +254,22 @@ typedef struct bn_batch bn_batch;
 int bn_batch_create(bn_ctx* ctx, const bn_job_desc* jobs, int32_t count, bn_batch** batch);
 int bn_batch_run(bn_batch* batch, void* stream);
 int bn_batch_results(bn_batch* batch, int32_t k, double* post, double* log_PD);
+/* New data for every job of the batch, in job order (count = the batch's
+ * job count): the same n, d, m, arities, precision, ess and log_rho as at
+ * bn_batch_create (BN_EINVAL otherwise, or for a value not below its arity;
+ * host data only).  The data go through one pinned staging buffer and one
+ * host-to-device copy into the batch's arena, enqueued on `stream` (NULL =
+ * the context's stream) without host synchronisation; the next bn_batch_run
+ * on that stream computes on them.  The caller's buffers may be reused when
+ * the call returns. */
+int bn_batch_upload(bn_batch* batch, const bn_job_desc* jobs, int32_t count, void* stream);
+/* Every job's results at once after bn_batch_run: post_all receives the
+ * jobs' n*n posteriors one after another in job order (sum of n_k^2
+ * doubles), log_PD_all (NULL allowed) one log P(D) per job.  One gather
+ * launch and one device-to-host copy; waits for the last run.  BN_EINVAL if
+ * some job's device-side input check failed, BN_EDEVICE_TIMEOUT if the
+ * persistent launch gave up a wait. */
+int bn_batch_download(bn_batch* batch, double* post_all, double* log_PD_all);
 /* One line per group into buf (NUL-terminated, truncated to len): its n, d,
  * precision, kind of data, jobs and the schedule it runs, and whether that
  * was timed.

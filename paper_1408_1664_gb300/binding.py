@@ -60,7 +60,7 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror",
            "bn_edge_posteriors_static", "bn_job_footprint", "bn_batch_create",
            "bn_batch_run", "bn_batch_results", "bn_batch_describe", "bn_batch_destroy",
-           "bn_feature_posterior"]
+           "bn_feature_posterior", "bn_batch_upload", "bn_batch_download"]
 
 
 # Test hooks: exported only by the testing build (BN_TESTING).
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_batch_run": (C.c_int, [P, P]),
         "bn_batch_results": (C.c_int, [P, C.c_int32, P, P]),
         "bn_batch_describe": (C.c_int, [P, C.c_char_p, C.c_size_t]),
+        "bn_batch_upload": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, P]),
+        "bn_batch_download": (C.c_int, [P, P, P]),
         "bn_batch_destroy": (C.c_int, [P]),
         "bn_debug_stage": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
         "bn_debug_counts": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_uint32, P,
@@ -336,6 +338,29 @@ class Batch:
         rc = load().bn_batch_run(self.h, _ptr(stream))
         if rc:
             raise BnError(rc, "bn_batch_run")
+
+    def upload(self, jobs: list, stream=None) -> None:
+        """New data for every job (same shapes as at creation)."""
+        self._up = list(jobs)
+        arr = (bn_job_desc * len(self._up))(*[j.desc for j in self._up])
+        self._up_arr = arr
+        rc = load().bn_batch_upload(self.h, arr, len(self._up), _ptr(stream))
+        if rc:
+            raise BnError(rc, "bn_batch_upload")
+
+    def download(self):
+        """Every job's posteriors (a list of n x n arrays) and log P(D)s."""
+        sizes = [j.n * j.n for j in self.jobs]
+        flat = np.zeros(sum(sizes))
+        lpd = np.zeros(len(self.jobs))
+        rc = load().bn_batch_download(self.h, _ptr(flat), _ptr(lpd))
+        if rc:
+            raise BnError(rc, "bn_batch_download")
+        out, o = [], 0
+        for j, sz in zip(self.jobs, sizes):
+            out.append(flat[o:o + sz].reshape(j.n, j.n))
+            o += sz
+        return out, lpd
 
     def describe(self) -> str:
         buf = C.create_string_buffer(1 << 14)

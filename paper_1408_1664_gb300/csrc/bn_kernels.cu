@@ -1379,6 +1379,17 @@ __global__ void k_add_feature(const T* __restrict__ lbs, const T* __restrict__ l
         out[x] = lbs[x] + lf[x];
 }
 
+// Byte copies between scattered device regions, one block per segment: the
+// batch upload (a staging buffer to every job's data) and download (every
+// job's results to a staging buffer).
+__global__ void k_copy_segments(const CopySeg* __restrict__ segs, int nseg)
+{
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+        const CopySeg sg = segs[q];
+        for (uint64_t i = threadIdx.x; i < sg.bytes; i += blockDim.x) sg.dst[i] = sg.src[i];
+    }
+}
+
 // ===========================================================================
 // Launchers.
 // ===========================================================================
@@ -1808,6 +1819,13 @@ cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
                                                           (const float*)F, err, acc, post,
                                                           log_PD, P.js);
     return cudaGetLastError();
+}
+
+cudaError_t launch_copy_segments(const CopySeg* segs, int nseg, cudaStream_t s)
+{
+    if (nseg < 1) return cudaSuccess;
+    return launch_or_record(KID_NONE, k_copy_segments, dim3((unsigned)std::min(nseg, 152 * 8)), 256,
+                            0, s, segs, nseg);
 }
 
 cudaError_t set_kernel_attributes()

@@ -115,6 +115,14 @@ cudaError_t launch_persistent(int prec, const LaunchRec* recs, const int4* items
                               const int2* deps, const int* need, int* ctl, size_t ctl_bytes,
                               int blocks, size_t smem, uint64_t cap, cudaStream_t s);
 
+// Byte copies between device regions (one block per segment).
+struct CopySeg {
+    const unsigned char* src;
+    unsigned char* dst;
+    uint64_t bytes;
+};
+cudaError_t launch_copy_segments(const CopySeg* segs, int nseg, cudaStream_t s);
+
 // Shapes of one job, computed on the host.
 struct Plan {
     int n, d, m;          // d already clamped to n-1

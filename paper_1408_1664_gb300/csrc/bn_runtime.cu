@@ -599,6 +599,13 @@ struct bn_batch {
         std::string tried;               // chunk sizes timed and their ms
     };
     std::vector<Persistent> persistent;
+    // bn_batch_upload / bn_batch_download: segment tables and staging buffers
+    bn::CopySeg* segs_dev = nullptr;     // upload segments, then download segments
+    unsigned char* dstage = nullptr;     // device staging: inputs, then results
+    unsigned char* hstage = nullptr;     // pinned host staging, same layout
+    size_t in_bytes = 0, out_bytes = 0;
+    std::vector<size_t> in_off, out_off; // per job
+    cudaEvent_t up_done = nullptr;       // the last upload's host-to-device copy
     char* progs = nullptr;               // device memory of the persistent programs
     bool use_persistent = false;
     float ms_graph = 0.0f;               // one replay of the graph of launches
@@ -1851,8 +1858,141 @@ try {
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->arena) cudaFree(b->arena);
     if (b->progs) cudaFree(b->progs);
+    if (b->dstage) cudaFree(b->dstage);
+    if (b->hstage) cudaFreeHost(b->hstage);
+    if (b->up_done) cudaEventDestroy(b->up_done);
     delete b;
     return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+namespace {
+
+// Staging for bn_batch_upload / bn_batch_download, made on first use: every
+// job's data packed in job order, then every job's results (n*n posteriors,
+// log P(D), the input-check word), each part 16-byte aligned.
+int ensure_e2e(bn_batch* b)
+{
+    if (b->dstage) return BN_OK;
+    const int count = (int)b->jobs.size();
+    auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    b->in_off.resize(count);
+    b->out_off.resize(count);
+    size_t o = 0;
+    for (int k = 0; k < count; ++k) {
+        b->in_off[k] = o;
+        o += al16((size_t)b->jobs[k].P.m * b->jobs[k].P.n);
+    }
+    b->in_bytes = o;
+    for (int k = 0; k < count; ++k) {
+        b->out_off[k] = o;
+        o += al16((size_t)b->jobs[k].P.n * b->jobs[k].P.n * 8) + 16;
+    }
+    b->out_bytes = o - b->in_bytes;
+    std::vector<bn::CopySeg> segs;
+    void* p = nullptr;
+    int rc = dev_alloc(b->ctx, &p, std::max<size_t>(o, 16) + (size_t)4 * count * sizeof(bn::CopySeg),
+                       nullptr);
+    if (rc) return rc;
+    b->dstage = (unsigned char*)p;
+    b->segs_dev = reinterpret_cast<bn::CopySeg*>(b->dstage + ((std::max<size_t>(o, 16) + 15) & ~size_t(15)));
+    for (int k = 0; k < count; ++k) {              // staging -> each job's data
+        const BatchGroup& g = b->groups[b->group_of[k]];
+        unsigned char* jb = (unsigned char*)b->arena + g.base + (size_t)b->slot_of[k] * g.P.js;
+        segs.push_back({b->dstage + b->in_off[k], jb + g.L.data,
+                        (uint64_t)b->jobs[k].P.m * b->jobs[k].P.n});
+    }
+    for (int k = 0; k < count; ++k) {              // each job's results -> staging
+        const BatchGroup& g = b->groups[b->group_of[k]];
+        const size_t n2 = (size_t)b->jobs[k].P.n * b->jobs[k].P.n * 8;
+        unsigned char* jb = (unsigned char*)b->arena + g.base + (size_t)b->slot_of[k] * g.P.js;
+        unsigned char* to = b->dstage + b->out_off[k];
+        segs.push_back({jb + g.L.post, to, n2});
+        segs.push_back({jb + g.L.logPD, to + ((n2 + 15) & ~size_t(15)), 8});
+        segs.push_back({jb + g.L.err, to + ((n2 + 15) & ~size_t(15)) + 8, 4});
+    }
+    CK(cudaMemcpy(b->segs_dev, segs.data(), segs.size() * sizeof(bn::CopySeg), cudaMemcpyHostToDevice));
+    if (cudaMallocHost(&p, std::max<size_t>(o, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return BN_ENOMEM;
+    }
+    b->hstage = (unsigned char*)p;
+    CK(cudaEventCreateWithFlags(&b->up_done, cudaEventDisableTiming));
+    return BN_OK;
+}
+
+}  // namespace
+
+int bn_batch_upload(bn_batch* b, const bn_job_desc* jobs, int32_t count, void* stream)
+try {
+    if (!b || !jobs || count != (int32_t)b->jobs.size()) return BN_EINVAL;
+    for (int k = 0; k < count; ++k) {
+        const bn_job_desc& j = jobs[k];
+        const HostJob& hj = b->jobs[k];
+        const Plan& P = hj.P;
+        if (j.data_on_device || j.n != P.n || j.m != P.m || j.precision != P.prec * BN_FP32_SHIFTED ||
+            std::min(j.d, j.n - 1) != P.d || !j.arity || !(j.ess == hj.ess) || j.log_q || j.log_w ||
+            (P.m > 0 && !j.data))
+            return BN_EINVAL;
+        for (int v = 0; v < P.n; ++v)
+            if (j.arity[v] != hj.arity[v]) return BN_EINVAL;
+        for (int t = 0; t <= P.d; ++t) {
+            const double lr = j.log_rho ? j.log_rho[t] : 0.0;
+            const double had = t < (int)hj.log_rho.size() ? hj.log_rho[t] : 0.0;
+            if (!(lr == had)) return BN_EINVAL;
+        }
+        for (size_t x = 0; x < (size_t)P.m * P.n; ++x)
+            if (j.data[x] >= hj.arity[x % P.n]) return BN_EINVAL;
+    }
+    if (cudaSetDevice(b->ctx->device) != cudaSuccess) return BN_ECUDA;
+    int rc = ensure_e2e(b);
+    if (rc) return rc;
+    cudaStream_t s = stream ? (cudaStream_t)stream : b->ctx->stream;
+    CK(cudaEventSynchronize(b->up_done));          // the staging buffer is free again
+    for (int k = 0; k < count; ++k)
+        if (b->jobs[k].P.m > 0)
+            std::memcpy(b->hstage + b->in_off[k], jobs[k].data, (size_t)b->jobs[k].P.m * b->jobs[k].P.n);
+    CK(cudaMemcpyAsync(b->dstage, b->hstage, b->in_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(b->up_done, s));
+    CK(bn::launch_copy_segments(b->segs_dev, count, s));
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_batch_download(bn_batch* b, double* post_all, double* log_PD_all)
+try {
+    if (!b || !post_all || !b->ran) return BN_EINVAL;
+    if (cudaSetDevice(b->ctx->device) != cudaSuccess) return BN_ECUDA;
+    int rc = ensure_e2e(b);
+    if (rc) return rc;
+    const int count = (int)b->jobs.size();
+    cudaStream_t s = b->last;
+    CK(bn::launch_copy_segments(b->segs_dev + count, 3 * count, s));
+    CK(cudaMemcpyAsync(b->hstage + b->in_bytes, b->dstage + b->in_bytes, b->out_bytes,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int bad = 0;
+    size_t po = 0;
+    for (int k = 0; k < count; ++k) {
+        const size_t n2 = (size_t)b->jobs[k].P.n * b->jobs[k].P.n * 8;
+        const unsigned char* from = b->hstage + b->out_off[k];
+        std::memcpy(post_all + po, from, n2);
+        po += n2 / 8;
+        const size_t tail = (n2 + 15) & ~size_t(15);
+        if (log_PD_all) std::memcpy(log_PD_all + k, from + tail, 8);
+        int err = 0;
+        std::memcpy(&err, from + tail + 8, 4);
+        bad |= err;
+    }
+    if (b->use_persistent)
+        for (const auto& pp : b->persistent) {
+            int st = 0;
+            CK(cudaMemcpy(&st, pp.ctl + 1, 4, cudaMemcpyDeviceToHost));
+            if (st) return st;
+        }
+    return bad ? BN_EINVAL : BN_OK;
 } catch (...) {
     return exception_code();
 }

@@ -190,6 +190,33 @@ def test_autotuned_batch_within_tolerance_and_cached(torch_cuda, precision):
                 assert np.array_equal(post, first[k][0]) and lpd == first[k][1]
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_upload_new_data_and_download_all(torch_cuda, graph):
+    """bn_batch_upload replaces every job's data (same shapes) and
+    bn_batch_download returns every job's results at once: after a first
+    run, new data drawn from other seeds give, in the same batch, the results
+    of the new jobs run alone; data of another shape are rejected."""
+    jobs = _jobs(16, first=700)
+    other = [(datagen.random_dag_data(ds.n, ds.m, ds.arity, 3, 1.0, seed=9000 + k), d)
+             for k, (ds, d) in enumerate(jobs)]
+    with B.Context(0, autotune=False, graph_batch=graph) as ctx:
+        want1 = [ctx.edge_posteriors(ds.data, ds.arity, d, precision="fp32") for ds, d in jobs]
+        want2 = [ctx.edge_posteriors(ds.data, ds.arity, d, precision="fp32") for ds, d in other]
+        with B.Batch(ctx.h, [B.Job(ds.data, ds.arity, d, precision="fp32")
+                             for ds, d in jobs]) as batch:
+            for want, src in ((want1, None), (want2, other), (want1, jobs)):
+                if src is not None:
+                    batch.upload([B.Job(ds.data, ds.arity, d, precision="fp32") for ds, d in src])
+                batch.run()
+                posts, lpds = batch.download()
+                for k, (post0, lpd0) in enumerate(want):
+                    assert np.array_equal(posts[k], post0), k
+                    assert lpds[k] == lpd0
+            bad = [B.Job(ds.data[:-1], ds.arity, d, precision="fp32") for ds, d in jobs]
+            with pytest.raises(B.BnError):
+                batch.upload(bad)
+
+
 def test_batch_jobs_match_the_oracle(torch_cuda):
     jobs = _jobs(6, first=7)
     with B.Context(0) as ctx:
