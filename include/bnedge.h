@@ -243,10 +243,21 @@ int bn_edge_posteriors_static(const bn_job_desc* job, double* post_dev,
  * all cached takes them without timing.  Every schedule gives the same
  * values up to rounding (within the stated tolerances, 1e-9 FP64 and 1e-4
  * FP32, of the job run alone; equal bit for bit under the default schedule
- * and with the cluster kernel).  The launches of all groups are
- * recorded into one CUDA graph, one branch per group.  bn_batch_run replays
- * the graph on `stream` (NULL = the context's stream) without host
- * synchronisation: one graph launch runs the whole batch.  bn_batch_results
+ * and with the cluster kernel).  The batch then exists in two forms: the
+ * launches of all groups recorded into one CUDA graph, one branch per
+ * group; and, unless the context has BN_CTX_GRAPH_BATCH or
+ * BN_CTX_CLUSTER_STEP3, one persistent launch per precision that runs the
+ * same kernels, in the same order per job, from a device work queue: one
+ * item per block of every recorded launch, ordered by stage depth, each
+ * item waiting (by bounded polls of a per-launch completion counter) for
+ * the launch before it in its job's chain.  With autotuning the faster form
+ * on this batch is kept (both are timed; bn_batch_describe reports both
+ * times), without it the persistent form.  A wait that exceeds its bound
+ * sets an abort flag: every block stops taking items and the batch reports
+ * BN_EDEVICE_TIMEOUT from bn_batch_results / bn_batch_download.  bn_batch_run
+ * runs the chosen form on `stream` (NULL = the context's stream) without host
+ * synchronisation: one graph launch or one kernel launch per precision runs
+ * the whole batch.  bn_batch_results
  * waits for the last run and copies job k's posteriors (n*n doubles) and
  * log P(D).  Device data pointers are not accepted (BN_EINVAL).  The arena
  * counts against the context's budget (BN_ENOMEM). */
@@ -276,6 +287,62 @@ int bn_batch_download(bn_batch* batch, double* post_all, double* log_PD_all);
  * BN_EINVAL for NULL arguments. */
 int bn_batch_describe(bn_batch* batch, char* buf, size_t len);
 int bn_batch_destroy(bn_batch* batch);
+
+/* Shards: one job split over W = 2^k ranks (one GPU each, k <= n - 4 on
+ * the FP32 path, n - 3 on the FP64 path; the paper runs everything on one
+ * device and has no split).  The split follows Section 3.1.1's level order:
+ * the subsets S are grouped into tiles by their top n - 4 (FP32) or n - 3
+ * (FP64) variables, and the top k of those fix the rank, so rank r computes
+ * the tiles whose top k bits equal r, at every popcount level, and holds the
+ * full 2^n arrays of A, F and R'.
+ *
+ *   bn_shard_create   validates the job (host data or device data of this
+ *                     rank's device; no batch restrictions) and allocates
+ *                     the rank's arrays (counted in the context's budget);
+ *                     BN_EINVAL when W is not a power of two up to 32, rank
+ *                     is out of range or W is too large for n;
+ *   bn_shard_prepare  uploads the inputs and runs steps 1-2 (scores and A,
+ *                     Eq. 6-7) in full on every rank: A is read by every
+ *                     tile, and computing it costs less than moving it;
+ *   bn_shard_level    computes level hl (0..H, H = n - 4 FP32 / n - 3 FP64)
+ *                     of the forward sum F (sweep 0, Eq. 9; hl = 0..H in
+ *                     turn) or of R'(T) = R(V - T) (sweep 1, Eq. 10;
+ *                     hl = H..0) for this rank's tiles;
+ *   bn_shard_exchange_bytes  the size of one rank's exchange buffer of
+ *                     level hl (the same on every rank): a 16-byte header
+ *                     and the largest rank's rows;
+ *   bn_shard_pack     writes this rank's level-hl rows (and, FP32, the
+ *                     level's floored maximum, the per-level base the FP32
+ *                     arrays are stored against) into a device buffer;
+ *   bn_shard_unpack   stores rank `from`'s packed level-hl rows into this
+ *                     rank's arrays and takes the maximum of the level
+ *                     words (from == this rank: nothing to do);
+ *   bn_shard_finish   runs steps 4-5 (Eq. 11-12) for the endpoints v with
+ *                     v mod W = rank: post_dev (n*n device doubles) gets
+ *                     those columns and zeros elsewhere, log_PD_dev (NULL
+ *                     allowed) log P(D).  The sum over ranks of post_dev is
+ *                     the job's posterior matrix.
+ *
+ * Every level of a sweep must be packed by every rank and unpacked by every
+ * rank before any rank computes the next level of that sweep (an
+ * all-gather per level; the two sweeps are independent of each other), and
+ * both sweeps must be complete before bn_shard_finish.  The caller moves
+ * the buffers (NCCL all-gather, or device copies between contexts); the
+ * library does no communication.  Every call is enqueued on `stream` (NULL =
+ * the context's stream) without host synchronisation.  The result equals
+ * the job run whole, bit for bit: every tile is computed from the same
+ * values in the same order. */
+typedef struct bn_shard bn_shard;
+int bn_shard_create(bn_ctx* ctx, const bn_job_desc* job, int32_t rank, int32_t world,
+                    bn_shard** shard);
+int bn_shard_prepare(bn_shard* shard, void* stream);
+int bn_shard_level(bn_shard* shard, int32_t sweep, int32_t hl, void* stream);
+int bn_shard_exchange_bytes(const bn_shard* shard, int32_t hl, uint64_t* bytes);
+int bn_shard_pack(bn_shard* shard, int32_t sweep, int32_t hl, void* buf_dev, void* stream);
+int bn_shard_unpack(bn_shard* shard, int32_t sweep, int32_t hl, int32_t from,
+                    const void* buf_dev, void* stream);
+int bn_shard_finish(bn_shard* shard, double* post_dev, double* log_PD_dev, void* stream);
+int bn_shard_destroy(bn_shard* shard);
 
 /* Serving.  bn_submit copies the inputs, admits the job when a slot and
  * enough device memory (by its n*2^n footprint) are free -- queuing it

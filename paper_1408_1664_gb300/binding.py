@@ -60,7 +60,9 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_cancel", "bn_job_stats", "bn_stats_history", "bn_strerror",
            "bn_edge_posteriors_static", "bn_job_footprint", "bn_batch_create",
            "bn_batch_run", "bn_batch_results", "bn_batch_describe", "bn_batch_destroy",
-           "bn_feature_posterior", "bn_batch_upload", "bn_batch_download"]
+           "bn_feature_posterior", "bn_batch_upload", "bn_batch_download",
+           "bn_shard_create", "bn_shard_prepare", "bn_shard_level", "bn_shard_exchange_bytes",
+           "bn_shard_pack", "bn_shard_unpack", "bn_shard_finish", "bn_shard_destroy"]
 
 
 # Test hooks: exported only by the testing build (BN_TESTING).
@@ -119,6 +121,15 @@ def load(build_if_missing: bool = False) -> C.CDLL:
                                       C.c_int64]),
         "bn_feature_posterior": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
         "bn_debug_batch_drop": (C.c_int, [P, C.c_int32, C.c_uint64]),
+        "bn_shard_create": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_int32,
+                                      C.POINTER(P)]),
+        "bn_shard_prepare": (C.c_int, [P, P]),
+        "bn_shard_level": (C.c_int, [P, C.c_int32, C.c_int32, P]),
+        "bn_shard_exchange_bytes": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
+        "bn_shard_pack": (C.c_int, [P, C.c_int32, C.c_int32, P, P]),
+        "bn_shard_unpack": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, P]),
+        "bn_shard_finish": (C.c_int, [P, P, P, P]),
+        "bn_shard_destroy": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         if name in TEST_EXPORTS and not hasattr(L, name):
@@ -381,6 +392,59 @@ class Batch:
     def close(self):
         if self.h:
             load().bn_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Shard:
+    """Owns one bn_shard: rank `rank` of a job split over `world` ranks
+    (include/bnedge.h, "Shards").  Buffers are device tensors or addresses;
+    `stream` a torch stream or a cudaStream_t address (None = the context's
+    stream)."""
+
+    def __init__(self, ctx: int, job: Job, rank: int, world: int):
+        self.job, self.rank, self.world = job, int(rank), int(world)
+        h = C.c_void_p()
+        rc = load().bn_shard_create(ctx, C.byref(job.desc), self.rank, self.world, C.byref(h))
+        if rc:
+            raise BnError(rc, "bn_shard_create")
+        self.h = h.value
+        # tile levels of the step-3 sweeps: n - 4 (FP32) or n - 3 (FP64)
+        self.levels = job.n - (4 if job.desc.precision == PRECISIONS["fp32"] else 3)
+
+    def _call(self, name, *args):
+        rc = getattr(load(), name)(self.h, *args)
+        if rc:
+            raise BnError(rc, name)
+
+    def prepare(self, stream=None) -> None:
+        self._call("bn_shard_prepare", _ptr(stream))
+
+    def level(self, sweep: int, hl: int, stream=None) -> None:
+        self._call("bn_shard_level", sweep, hl, _ptr(stream))
+
+    def exchange_bytes(self, hl: int) -> int:
+        b = C.c_uint64()
+        self._call("bn_shard_exchange_bytes", hl, C.byref(b))
+        return int(b.value)
+
+    def pack(self, sweep: int, hl: int, buf, stream=None) -> None:
+        self._call("bn_shard_pack", sweep, hl, _ptr(buf), _ptr(stream))
+
+    def unpack(self, sweep: int, hl: int, src: int, buf, stream=None) -> None:
+        self._call("bn_shard_unpack", sweep, hl, src, _ptr(buf), _ptr(stream))
+
+    def finish(self, post_dev, log_PD_dev=None, stream=None) -> None:
+        self._call("bn_shard_finish", _ptr(post_dev), _ptr(log_PD_dev), _ptr(stream))
+
+    def close(self):
+        if self.h:
+            load().bn_shard_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -1018,9 +1018,11 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
-           const T* __restrict__ Rc, T* __restrict__ W, size_t js, const T* __restrict__ lq)
+           const T* __restrict__ Rc, T* __restrict__ W, size_t js, const T* __restrict__ lq,
+           uint32_t vsel)
 {
     const int v = blockIdx.z;                       // endpoint: one slice of W each
+    if (!(vsel >> v & 1u)) return;                  // an endpoint another rank computes
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
     W = job_ptr(W, js) + (size_t)v * gridDim.x * nlow;
@@ -1059,11 +1061,13 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
 }
 
 // FP32: the down-zeta offsets of endpoint blockIdx.x (one warp; bn_device.cuh).
-__global__ void k_gamma_table(int n, const float* __restrict__ F, float* __restrict__ Rc, size_t js)
+__global__ void k_gamma_table(int n, const float* __restrict__ F, float* __restrict__ Rc, size_t js,
+                              uint32_t vsel)
 {
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
     const int v = blockIdx.x;
+    if (!(vsel >> v & 1u)) return;
     __shared__ float off[32];
     __shared__ int sh;
     __shared__ float fvrel;
@@ -1079,9 +1083,10 @@ __global__ void k_gamma_table(int n, const float* __restrict__ F, float* __restr
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, int64_t K, const T* __restrict__ W,
-           T* __restrict__ Gam, size_t js)
+           T* __restrict__ Gam, size_t js, uint32_t vsel)
 {
     const int v = blockIdx.z;                       // endpoint: its slice of W, its K outputs
+    if (!(vsel >> v & 1u)) return;
     W = job_ptr(W, js) + ((size_t)v << (n - 1 - b)) * nlow;
     Gam = job_ptr(Gam, js) + (size_t)v * K;
     using L = LogOps<T>;
@@ -1190,10 +1195,11 @@ __device__ __forceinline__ T warp_lse(T m, T s)
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gamma_p2s(int n, int d, int b, uint32_t nlow, uint32_t c0, int64_t K, const T* __restrict__ W,
-            T* __restrict__ Gam, size_t js)
+            T* __restrict__ Gam, size_t js, uint32_t vsel)
 {
     constexpr int MB = 13;                          // high bits from 5 up (h <= 17)
     const int v = blockIdx.z;
+    if (!(vsel >> v & 1u)) return;
     W = job_ptr(W, js) + ((size_t)v << (n - 1 - b)) * nlow;
     Gam = job_ptr(Gam, js) + (size_t)v * K;
     using L = LogOps<T>;
@@ -1260,8 +1266,9 @@ __global__ void __launch_bounds__(256)
 k_edges_acc(int n, int64_t K, int qbits, const double* __restrict__ logB,
             const double* __restrict__ cmax, const uint32_t* __restrict__ masks,
             const T* __restrict__ Gam, const T* __restrict__ F,
-            unsigned long long* __restrict__ acc, size_t js)
+            unsigned long long* __restrict__ acc, size_t js, uint32_t vsel)
 {
+    if (!(vsel >> blockIdx.z & 1u)) return;         // an endpoint another rank computes
     logB = job_ptr(logB, js);
     cmax = job_ptr(cmax, js);
     masks = job_ptr(masks, js);
@@ -1302,7 +1309,8 @@ template <typename T>
 __global__ void k_edges_fin(int n, int use_z, int qbits, const double* __restrict__ cmax,
                             const T* __restrict__ F, const int* __restrict__ err,
                             const unsigned long long* __restrict__ acc,
-                            double* __restrict__ post, double* __restrict__ log_PD, size_t js)
+                            double* __restrict__ post, double* __restrict__ log_PD, size_t js,
+                            uint32_t vsel)
 {
     cmax = job_ptr(cmax, js);
     F = job_ptr(F, js);
@@ -1319,7 +1327,7 @@ __global__ void k_edges_fin(int n, int use_z, int qbits, const double* __restric
         if (u != v && num > 0ull)
             p = use_z ? __ull2double_rn(num) / __ull2double_rn(acc[(size_t)n * n + v])
                       : __ull2double_rn(num) / qscale;
-        post[t] = bad ? NAN : p;
+        post[t] = bad ? NAN : (vsel >> v & 1u) ? p : 0.0;   // other ranks' endpoints: 0
     }
     if (threadIdx.x == 0 && log_PD) {
         double c = 0.0;
@@ -1735,7 +1743,7 @@ size_t gamma_p2_smem_bytes(const Plan& P)
 cudaError_t launch_gamma_table(const Plan& P, const void* F, const void* Rc, cudaStream_t s)
 {
     launch_or_record(KID_GAMMA_TABLE, k_gamma_table, dim3(P.n, P.nj), 32, 0, s, P.n, (const float*)F, (float*)const_cast<void*>(Rc),
-                                                 P.js);
+                                                 P.js, P.vsel);
     return cudaGetLastError();
 }
 
@@ -1753,11 +1761,11 @@ cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const 
     if (P.prec == 0)
         launch_or_record(KID_GAMMA_P1_D, k_gamma_p1<double>, grid, 256, sm1, s, P.n, P.d, P.b_g, P.nlow_g,
                                                   (const double*)F, (const double*)Rc,
-                                                  (double*)W, P.js, (const double*)lq);
+                                                  (double*)W, P.js, (const double*)lq, P.vsel);
     else
         launch_or_record(KID_GAMMA_P1_F, k_gamma_p1<float>, grid, 256, sm1, s, P.n, P.d, P.b_g, P.nlow_g,
                                                  (const float*)F, (const float*)Rc,
-                                                 (float*)W, P.js, (const float*)lq);
+                                                 (float*)W, P.js, (const float*)lq, P.vsel);
     return cudaGetLastError();
 }
 
@@ -1774,10 +1782,10 @@ cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_
         const dim3 grid(c0, P.nj, P.n);
         if (P.prec == 0)
             launch_or_record(KID_GAMMA_P2_D, k_gamma_p2<double>, grid, 256, sm2, s, P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
-                                                      (const double*)W, (double*)Gam, P.js);
+                                                      (const double*)W, (double*)Gam, P.js, P.vsel);
         else
             launch_or_record(KID_GAMMA_P2_F, k_gamma_p2<float>, grid, 256, sm2, s, P.n, P.d, P.b_g, P.hc_g, P.nlow_g, P.K,
-                                                     (const float*)W, (float*)Gam, P.js);
+                                                     (const float*)W, (float*)Gam, P.js, P.vsel);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1785,10 +1793,10 @@ cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_
         const dim3 grid((P.nlow_g - c0 + 7) / 8, P.nj, P.n);
         if (P.prec == 0)
             launch_or_record(KID_GAMMA_P2S_D, k_gamma_p2s<double>, grid, 256, 0, s, P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
-                                                     (const double*)W, (double*)Gam, P.js);
+                                                     (const double*)W, (double*)Gam, P.js, P.vsel);
         else
             launch_or_record(KID_GAMMA_P2S_F, k_gamma_p2s<float>, grid, 256, 0, s, P.n, P.d, P.b_g, P.nlow_g, c0, P.K,
-                                                    (const float*)W, (float*)Gam, P.js);
+                                                    (const float*)W, (float*)Gam, P.js, P.vsel);
     }
     return cudaGetLastError();
 }
@@ -1804,20 +1812,20 @@ cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
     const dim3 grid(chunks, P.nj, P.n);
     if (P.prec == 0)
         launch_or_record(KID_EDGES_ACC_D, k_edges_acc<double>, grid, 256, 0, s, P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
-                                                 (const double*)Gam, (const double*)F, acc, P.js);
+                                                 (const double*)Gam, (const double*)F, acc, P.js, P.vsel);
     else
         launch_or_record(KID_EDGES_ACC_F, k_edges_acc<float>, grid, 256, 0, s, P.n, P.K, fixed_bits(P.K), logB, cmax, masks,
-                                                (const float*)Gam, (const float*)F, acc, P.js);
+                                                (const float*)Gam, (const float*)F, acc, P.js, P.vsel);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (P.prec == 0)
         launch_or_record(KID_EDGES_FIN_D, k_edges_fin<double>, dim3(1, P.nj), rec_block(1024), 0, s, P.n, 0, fixed_bits(P.K), cmax,
                                                            (const double*)F, err, acc, post,
-                                                           log_PD, P.js);
+                                                           log_PD, P.js, P.vsel);
     else
         launch_or_record(KID_EDGES_FIN_F, k_edges_fin<float>, dim3(1, P.nj), rec_block(1024), 0, s, P.n, 1, fixed_bits(P.K), cmax,
                                                           (const float*)F, err, acc, post,
-                                                          log_PD, P.js);
+                                                          log_PD, P.js, P.vsel);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,13 @@ struct Plan {
     // the launches of steps 2-5 cover all of them (gridDim.y = nj).
     int nj = 1;
     size_t js = 0;
+    // A job split over 2^shard_k ranks by its top shard_k variables (the
+    // rank's bits shard_r): the step-3 row kernels compute only the tiles of
+    // this rank's sub-lattice; steps 4-5 only the endpoints v whose bit is
+    // set in vsel (every endpoint by default).
+    int shard_k = 0;
+    uint32_t shard_r = 0;
+    uint32_t vsel = 0xffffffffu;
 };
 
 // Step 1.  A batch group passes nj jobs js bytes apart (mj: each job's own
@@ -204,6 +211,16 @@ cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs
 bool rows_levels_fit(const Plan& P);      // FP32 and 5 <= n < 32
 bool rows64_fit(const Plan& P);           // FP64 and 4 <= n < 31: 8-subset row tiles
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
+// One level of a shard's sweep (sweep 0 F, 1 R'; the row kernels, with the
+// plan's shard_k / shard_r): nothing when the shard has no tile there.
+cudaError_t launch_rows_level(const Plan& P, int sweep, int hl, const void* A, void* X, cudaStream_t s);
+// Tiles (rows of 16 FP32 or 8 FP64 values) of level hl in the sub-lattice
+// whose top shard_k tile bits are r; dir 0 copies those rows of X to the
+// contiguous buf, dir 1 back.
+uint32_t shard_rows_count(const Plan& P, uint32_t r, int hl);
+cudaError_t launch_word_max(int* word, const int* other, cudaStream_t s);
+cudaError_t launch_level_rows(const Plan& P, uint32_t r, int hl, void* X, void* buf, int dir,
+                              cudaStream_t s);
 // F and R' of every job of a batch group in one persistent launch of
 // thread-block clusters (FP32, rows_levels_fit); one launch.
 cudaError_t launch_rows_cluster(const Plan& P, const void* A, void* F, void* Rc, cudaStream_t s,

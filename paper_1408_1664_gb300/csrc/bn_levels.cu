@@ -118,6 +118,16 @@ __device__ __forceinline__ uint32_t tile_of(uint32_t g, int hl, int nh, const ui
     return H;
 }
 
+// Tile g of level hl within the sub-lattice whose top kfix of the nh tile
+// bits are rfix (a shard of a job split by its top variables; kfix = 0: the
+// whole level).
+__device__ __forceinline__ uint32_t level_tile(uint32_t g, int hl, int nh, uint32_t rfix, int kfix,
+                                               const uint32_t (*bt)[BT])
+{
+    if (kfix == 0) return tile_of(g, hl, nh, bt);
+    return tile_of(g, hl - __popc(rfix), nh - kfix, bt) | (rfix << (nh - kfix));
+}
+
 __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
 {
     for (int x = threadIdx.x; x < BT * BT; x += blockDim.x) bt[x / BT][x % BT] = g_binom_lanes.v[x / BT][x % BT];
@@ -283,7 +293,7 @@ __device__ __forceinline__ uint32_t cluster_blocks()
 template <typename T, bool TLO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ F,
-               size_t js)
+               size_t js, uint32_t rfix, int kfix)
 {
     constexpr int B = sizeof(T) == 4 ? LB : LB64;
     constexpr bool kBases = sizeof(T) == 4;
@@ -297,7 +307,7 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __res
         int* lw = level_words(reinterpret_cast<float*>(F), n);
         const T rebase = hl > 0 ? (T)level_delta(lw, hl - 1) : T(0);
         T mx = LogOps<T>::ninf();
-        if (g < ntiles) mx = forward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, F, rebase);
+        if (g < ntiles) mx = forward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, F, rebase);
         if (hl == 0) {
             if (g == 0) level_words_start(lw, 0, mx);
         } else {
@@ -305,14 +315,14 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __res
         }
     } else {
         if (g >= ntiles) return;
-        forward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, F);
+        forward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, F);
     }
 }
 
 template <typename T, bool TLO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ Rc,
-                size_t js)
+                size_t js, uint32_t rfix, int kfix)
 {
     constexpr int B = sizeof(T) == 4 ? LB : LB64;
     constexpr bool kBases = sizeof(T) == 4;
@@ -327,7 +337,7 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __re
         int* lw = level_words(reinterpret_cast<float*>(Rc), n);
         const T rebase = hl < nh ? (T)level_delta(lw, hl + 1) : T(0);
         T mx = LogOps<T>::ninf();
-        if (g < ntiles) mx = backward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, nh, bt), A, Rc, rebase);
+        if (g < ntiles) mx = backward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, nh, rfix, kfix, bt), A, Rc, rebase);
         if (hl == nh) {
             if (g == 0) level_words_start(lw, nh, mx);
         } else {
@@ -335,7 +345,7 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __re
         }
     } else {
         if (g >= ntiles) return;
-        backward_tile<T, LD_PLAIN, B, TLO>(n, tile_of(g, hl, n - B, bt), A, Rc);
+        backward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, Rc);
     }
 }
 
@@ -391,6 +401,33 @@ k_rows_cluster(int n, int items, const float* __restrict__ A, float* __restrict_
     }
 }
 
+// The rows (2^B values each) of one level's tiles of the sub-lattice rsrc
+// (top kfix tile bits), in tile order: dir 0 copies them from X into buf,
+// dir 1 from buf into X.  The exchange of a job split over several ranks.
+template <typename T>
+__global__ void k_level_rows(int n, int hl, uint32_t ntiles, uint32_t rsrc, int kfix, T* __restrict__ X,
+                             T* __restrict__ buf, int dir)
+{
+    constexpr int B = sizeof(T) == 4 ? LB : LB64;
+    __shared__ uint32_t bt[BT][BT];
+    fill_table(bt);
+    __syncthreads();
+    const uint64_t total = (uint64_t)ntiles << B;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = (uint32_t)(x >> B);
+        const size_t pos = ((size_t)level_tile(g, hl, n - B, rsrc, kfix, bt) << B) | (x & ((1u << B) - 1u));
+        if (dir == 0) buf[x] = X[pos];
+        else X[pos] = buf[x];
+    }
+}
+
+// *word = max(*word, *other): another rank's floored level maximum.
+__global__ void k_word_max(int* __restrict__ word, const int* __restrict__ other)
+{
+    if (threadIdx.x == 0 && *other != kLevelUnset) atomicMax(word, *other);
+}
+
 #ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
 namespace {
 
@@ -423,6 +460,68 @@ static unsigned level_block(uint32_t nt)
     return 64;
 }
 
+uint32_t shard_level_tiles(const Plan& P, int hl)
+{
+    const int nh = P.n - (P.prec == 0 ? LB64 : LB);
+    const int k = P.shard_k, hr = __builtin_popcount(P.shard_r);
+    if (hl - hr < 0 || hl - hr > nh - k) return 0;
+    return (uint32_t)choose(nh - k, hl - hr);
+}
+
+cudaError_t launch_rows_level(const Plan& P, int sweep, int hl, const void* A, void* X, cudaStream_t s)
+{
+    const uint32_t nt = shard_level_tiles(P, hl);
+    if (nt == 0) return cudaSuccess;
+    const unsigned tb = rec_block(level_block(nt));
+    const dim3 grid((nt + tb - 1) / tb, P.nj);
+    const uint32_t rf = P.shard_r;
+    const int kf = P.shard_k;
+    if (sweep == 0) {
+        if (P.prec == 0)
+            return launch_or_record(KID_FROWS_D, k_forward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt,
+                                    (const double*)A, (double*)X, P.js, rf, kf);
+        if (use_tlo(P))
+            return launch_or_record(KID_FROWS_F_TLO, k_forward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt,
+                                    (const float*)A, (float*)X, P.js, rf, kf);
+        return launch_or_record(KID_FROWS_F, k_forward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt,
+                                (const float*)A, (float*)X, P.js, rf, kf);
+    }
+    if (P.prec == 0)
+        return launch_or_record(KID_BROWS_D, k_backward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt,
+                                (const double*)A, (double*)X, P.js, rf, kf);
+    if (use_tlo(P))
+        return launch_or_record(KID_BROWS_F_TLO, k_backward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt,
+                                (const float*)A, (float*)X, P.js, rf, kf);
+    return launch_or_record(KID_BROWS_F, k_backward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt,
+                            (const float*)A, (float*)X, P.js, rf, kf);
+}
+
+cudaError_t launch_word_max(int* word, const int* other, cudaStream_t s)
+{
+    k_word_max<<<1, 32, 0, s>>>(word, other);
+    return cudaGetLastError();
+}
+
+uint32_t shard_rows_count(const Plan& P, uint32_t r, int hl)
+{
+    Plan Q = P;
+    Q.shard_r = r;
+    return shard_level_tiles(Q, hl);
+}
+
+cudaError_t launch_level_rows(const Plan& P, uint32_t r, int hl, void* X, void* buf, int dir,
+                              cudaStream_t s)
+{
+    const uint32_t nt = shard_rows_count(P, r, hl);
+    if (nt == 0) return cudaSuccess;
+    const unsigned grid = std::min<uint64_t>(((uint64_t)nt * 16 + 255) / 256, 152 * 8);
+    if (P.prec == 0)
+        k_level_rows<double><<<grid, 256, 0, s>>>(P.n, hl, nt, r, P.shard_k, (double*)X, (double*)buf, dir);
+    else
+        k_level_rows<float><<<grid, 256, 0, s>>>(P.n, hl, nt, r, P.shard_k, (float*)X, (float*)buf, dir);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches)
 {
     const int nh = P.n - (P.prec == 0 ? LB64 : LB);
@@ -432,13 +531,13 @@ cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStrea
         const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
             launch_or_record(KID_FROWS_D, k_forward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt, (const double*)A,
-                                                               (double*)F, P.js);
+                                                               (double*)F, P.js, 0u, 0);
         else if (use_tlo(P))
             launch_or_record(KID_FROWS_F_TLO, k_forward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                             (float*)F, P.js);
+                                                             (float*)F, P.js, 0u, 0);
         else
             launch_or_record(KID_FROWS_F, k_forward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                              (float*)F, P.js);
+                                                              (float*)F, P.js, 0u, 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
@@ -456,13 +555,13 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
         const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
             launch_or_record(KID_BROWS_D, k_backward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt, (const double*)A,
-                                                                (double*)Rc, P.js);
+                                                                (double*)Rc, P.js, 0u, 0);
         else if (use_tlo(P))
             launch_or_record(KID_BROWS_F_TLO, k_backward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                              (float*)Rc, P.js);
+                                                              (float*)Rc, P.js, 0u, 0);
         else
             launch_or_record(KID_BROWS_F, k_backward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                               (float*)Rc, P.js);
+                                                               (float*)Rc, P.js, 0u, 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;

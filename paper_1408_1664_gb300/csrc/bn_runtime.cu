@@ -2018,6 +2018,199 @@ try {
 }
 #endif  // BN_TESTING
 
+// ----------------------------------------------------------------- shards --
+
+struct bn_shard {
+    bn_ctx* ctx = nullptr;
+    HostJob hj;
+    Layout L{};
+    char* mem = nullptr;                 // the shard's own device arrays
+    int rank = 0, world = 1, nh = 0;
+    bool prepared = false;
+};
+
+namespace {
+
+size_t shard_header() { return 16; }     // the level word, padded
+
+}  // namespace
+
+int bn_shard_create(bn_ctx* c, const bn_job_desc* job, int32_t rank, int32_t world, bn_shard** out)
+try {
+    if (!c || !job || !out || world < 1 || world > 32 || (world & (world - 1)) || rank < 0 ||
+        rank >= world)
+        return BN_EINVAL;
+    *out = nullptr;
+    bn_shard* sh = new bn_shard();
+    sh->ctx = c;
+    int rc = validate_and_plan(job, sh->hj);
+    if (rc) { delete sh; return rc; }
+    Plan& P = sh->hj.P;
+    const bool rows = P.prec != 0 ? bn::rows_levels_fit(P) : bn::rows64_fit(P);
+    int k = 0;
+    while ((1 << k) < world) ++k;
+    sh->nh = P.n - (P.prec == 0 ? 3 : 4);
+    if (!rows || k > sh->nh) { delete sh; return BN_EINVAL; }
+    P.frows = P.prec != 0 ? 1 : 0;       // step 3 by the level row kernels, one launch per level
+    P.frc = 0;
+    P.shard_k = k;
+    P.shard_r = (uint32_t)rank;
+    P.vsel = 0;
+    for (int v = 0; v < P.n; ++v)
+        if (v % world == rank) P.vsel |= 1u << v;
+    sh->rank = rank;
+    sh->world = world;
+    if (!sh->hj.data_on_device && P.m > 0) {
+        sh->hj.data_copy.assign(job->data, job->data + (size_t)P.m * P.n);
+        sh->hj.data = sh->hj.data_copy.data();
+    }
+    sh->L = make_layout(P, 0);
+    if (sh->L.total > c->budget) { delete sh; return BN_ENOMEM; }
+    if (cudaSetDevice(c->device) != cudaSuccess) { delete sh; return BN_ECUDA; }
+    void* p = nullptr;
+    rc = dev_alloc(c, &p, sh->L.total, nullptr);
+    if (rc) { delete sh; return rc; }
+    sh->mem = (char*)p;
+    *out = sh;
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_shard_prepare(bn_shard* sh, void* stream)
+try {
+    if (!sh) return BN_EINVAL;
+    const HostJob& hj = sh->hj;
+    const Plan& P = hj.P;
+    const Layout& L = sh->L;
+    cudaStream_t s = stream ? (cudaStream_t)stream : sh->ctx->stream;
+    Bufs B{sh->mem, L};
+    const uint8_t* data_dev = B.at<uint8_t>(L.data);
+    if (P.m > 0) {
+        if (hj.data_on_device) data_dev = hj.data;
+        else CK(cudaMemcpyAsync(B.at<uint8_t>(L.data), hj.data, (size_t)P.m * P.n,
+                                cudaMemcpyHostToDevice, s));
+    }
+    std::vector<double> lr(P.d + 1, 0.0), alpha(P.rows);
+    for (size_t t = 0; t < hj.log_rho.size(); ++t) lr[t] = hj.log_rho[t];
+    for (int r = 0; r < P.rows; ++r) alpha[r] = hj.ess / hj.Dvals[r];
+    CK(cudaMemcpyAsync(B.at<char>(L.arity), hj.arity.data(), P.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.log_rho), lr.data(), lr.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.Dvals), hj.Dvals.data(), hj.Dvals.size() * 8,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.at<char>(L.alpha), alpha.data(), alpha.size() * 8, cudaMemcpyHostToDevice, s));
+    int rc = upload_priors(hj, B, s);
+    if (rc) return rc;
+    int nl = 0;
+    rc = enqueue_step1(hj, B, data_dev, s, &nl);
+    if (rc) return rc;
+    rc = enqueue_upzeta(P, B, B.at<void>(L.lbs), s, &nl, nullptr);
+    if (rc) return rc;
+    if (P.prec != 0) {                        // every rank starts both sweeps' level words
+        int w[bn::kLevelWords];
+        for (int q = 0; q < bn::kLevelWords; ++q) w[q] = bn::kLevelUnset;
+        w[bn::kLevelMode] = bn::kLevelShift;
+        const size_t N4 = ((size_t)1 << P.n) * 4;
+        CK(cudaMemcpyAsync(B.at<char>(L.F) + N4, w, sizeof w, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(B.at<char>(L.Rc) + N4, w, sizeof w, cudaMemcpyHostToDevice, s));
+    }
+    sh->prepared = true;
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_shard_level(bn_shard* sh, int32_t sweep, int32_t hl, void* stream)
+try {
+    if (!sh || !sh->prepared || sweep < 0 || sweep > 1 || hl < 0 || hl > sh->nh) return BN_EINVAL;
+    const Layout& L = sh->L;
+    cudaStream_t s = stream ? (cudaStream_t)stream : sh->ctx->stream;
+    CK(bn::launch_rows_level(sh->hj.P, sweep, hl, sh->mem + L.A, sh->mem + (sweep ? L.Rc : L.F), s));
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_shard_exchange_bytes(const bn_shard* sh, int32_t hl, uint64_t* bytes)
+try {
+    if (!sh || !bytes || hl < 0 || hl > sh->nh) return BN_EINVAL;
+    uint64_t mx = 0;
+    for (int q = 0; q < sh->world; ++q)
+        mx = std::max<uint64_t>(mx, (uint64_t)bn::shard_rows_count(sh->hj.P, (uint32_t)q, hl) * 64);
+    *bytes = shard_header() + mx;
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_shard_pack(bn_shard* sh, int32_t sweep, int32_t hl, void* buf_dev, void* stream)
+try {
+    if (!sh || !buf_dev || sweep < 0 || sweep > 1 || hl < 0 || hl > sh->nh) return BN_EINVAL;
+    const Plan& P = sh->hj.P;
+    cudaStream_t s = stream ? (cudaStream_t)stream : sh->ctx->stream;
+    char* X = sh->mem + (sweep ? sh->L.Rc : sh->L.F);
+    char* buf = (char*)buf_dev;
+    if (P.prec != 0)
+        CK(cudaMemcpyAsync(buf, X + ((size_t)1 << P.n) * 4 + (size_t)hl * 4, 4, cudaMemcpyDeviceToDevice, s));
+    else
+        CK(cudaMemsetAsync(buf, 0, 4, s));   // FP64 keeps no level words
+    CK(bn::launch_level_rows(P, P.shard_r, hl, X, buf + shard_header(), 0, s));
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_shard_unpack(bn_shard* sh, int32_t sweep, int32_t hl, int32_t from, const void* buf_dev,
+                    void* stream)
+try {
+    if (!sh || !buf_dev || sweep < 0 || sweep > 1 || hl < 0 || hl > sh->nh || from < 0 ||
+        from >= sh->world)
+        return BN_EINVAL;
+    if (from == sh->rank) return BN_OK;
+    const Plan& P = sh->hj.P;
+    cudaStream_t s = stream ? (cudaStream_t)stream : sh->ctx->stream;
+    char* X = sh->mem + (sweep ? sh->L.Rc : sh->L.F);
+    const char* buf = (const char*)buf_dev;
+    if (P.prec != 0)
+        CK(bn::launch_word_max(reinterpret_cast<int*>(X + ((size_t)1 << P.n) * 4) + hl,
+                               reinterpret_cast<const int*>(buf), s));
+    CK(bn::launch_level_rows(P, (uint32_t)from, hl, X, const_cast<char*>(buf) + shard_header(), 1, s));
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_shard_finish(bn_shard* sh, double* post_dev, double* log_PD_dev, void* stream)
+try {
+    if (!sh || !sh->prepared || !post_dev) return BN_EINVAL;
+    const Plan& P = sh->hj.P;
+    const Layout& L = sh->L;
+    cudaStream_t s = stream ? (cudaStream_t)stream : sh->ctx->stream;
+    Bufs B{sh->mem, L};
+    CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
+                           B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr,
+                           B.at<void>(L.A)));
+    CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
+    CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
+                        B.at<void>(L.Gam), B.at<void>(L.F), B.at<int>(L.err),
+                        B.at<unsigned long long>(L.eacc), post_dev,
+                        log_PD_dev ? log_PD_dev : B.at<double>(L.logPD), s));
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
+int bn_shard_destroy(bn_shard* sh)
+try {
+    if (!sh) return BN_EINVAL;
+    cudaSetDevice(sh->ctx->device);
+    if (sh->mem) cudaFree(sh->mem);          // waits for the shard's work in flight
+    delete sh;
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
 // ---------------------------------------------------------------- serving --
 
 int bn_submit(bn_ctx* c, const bn_job_desc* job, uint64_t* id)

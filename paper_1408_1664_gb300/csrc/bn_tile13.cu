@@ -963,9 +963,11 @@ template <typename T, bool Q>
 __global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 3 : 1)
 k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
              const T* __restrict__ Rc, const uint16_t* __restrict__ rank13, T* __restrict__ W,
-             size_t js, const T* __restrict__ lq, const T* __restrict__ Aup, T margin)
+             size_t js, const T* __restrict__ lq, const T* __restrict__ Aup, T margin,
+             uint32_t vsel)
 {
     const int v = blockIdx.z;                       // endpoint: one slice of W each
+    if (!(vsel >> v & 1u)) return;                  // an endpoint another rank computes
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
     rank13 = job_ptr(rank13, js);
@@ -1240,20 +1242,20 @@ cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
         if (lq)
             launch_or_record(KID_G13_D_Q, k_gamma13_p1<double, true>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
-                (const double*)lq, (const double*)A, margin);
+                (const double*)lq, (const double*)A, margin, P.vsel);
         else
             launch_or_record(KID_G13_D, k_gamma13_p1<double, false>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const double*)F, (const double*)Rc, rank13, (double*)W, P.js,
-                nullptr, (const double*)A, margin);
+                nullptr, (const double*)A, margin, P.vsel);
     } else {
         if (lq)
             launch_or_record(KID_G13_F_Q, k_gamma13_p1<float, true>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
-                (const float*)lq, (const float*)A, (float)margin);
+                (const float*)lq, (const float*)A, (float)margin, P.vsel);
         else
             launch_or_record(KID_G13_F, k_gamma13_p1<float, false>, grid, TT, sm, s, 
                 P.n, P.d, P.nlow_g, (const float*)F, (const float*)Rc, rank13, (float*)W, P.js,
-                nullptr, (const float*)A, (float)margin);
+                nullptr, (const float*)A, (float)margin, P.vsel);
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,88 @@
+"""A job split over W ranks (include/bnedge.h, "Shards"), all ranks in this
+process on one GPU with the exchange done by device-buffer reads
+(shard.run_virtual): the summed posteriors must equal the job run whole bit
+for bit (every tile is computed from the same values in the same order), and
+the oracle within the method's tolerances (1e-9 FP64, 1e-4 FP32).  Each
+rank's matrix holds only its endpoints' columns.  The sizes span several
+tile levels, ranks that own no tile of a level, and the largest split the
+tile index allows (W = 2^(n-4) FP32, 2^(n-3) FP64, here capped at 32)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1408_1664_gb300 import binding as B
+from paper_1408_1664_gb300 import datagen
+from paper_1408_1664_gb300 import shard as sh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load(build_if_missing=True)
+    c = B.Context(0)
+    yield torch, c
+    c.close()
+
+
+def run_split(torch, ctx, job, world):
+    n = job.n
+    shards = [B.Shard(ctx.h, job, r, world) for r in range(world)]
+    try:
+        nb = sh.max_step_bytes(shards[0])
+        bufs = [torch.zeros(nb, dtype=torch.uint8, device="cuda") for _ in shards]
+        parts = [torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+                 for _ in shards]
+        lpd = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        stream = torch.cuda.Stream()          # not handle 0 (= the context's stream)
+        with torch.cuda.stream(stream):
+            sh.run_virtual(shards, bufs, parts, lpd, stream)
+        stream.synchronize()
+        return [p.cpu().numpy() for p in parts], float(lpd.item())
+    finally:
+        for s in shards:
+            s.close()
+
+
+CASES = [
+    # n, d, arity, precision, world
+    (9, 3, 2, "fp64", 2),
+    (12, 3, 2, "fp64", 4),
+    (12, 3, 3, "fp64", 32),
+    (13, 3, 2, "fp32", 2),
+    (16, 4, 2, "fp32", 4),
+    (18, 3, 3, "fp32", 8),
+    (14, 3, 2, "fp32", 32),
+]
+
+
+@pytest.mark.parametrize("n,d,arity,prec,world", CASES)
+def test_split_job_equals_whole_job_and_oracle(torch_ctx, n, d, arity, prec, world):
+    torch, ctx = torch_ctx
+    ds = datagen.random_dag_data(n=n, m=400, arity=arity, max_parents=3, alpha=1.0, seed=n + world)
+    job = B.Job(ds.data, ds.arity, d, precision=prec)
+    parts, lpd = run_split(torch, ctx, job, world)
+    for r, p in enumerate(parts):
+        own = np.array([v % world == r for v in range(n)])
+        assert np.all(p[:, ~own] == 0.0), f"rank {r} wrote another rank's endpoint"
+    post = np.sum(parts, axis=0)
+    whole, lpd_whole = ctx.edge_posteriors(ds.data, ds.arity, d, precision=prec)
+    assert np.array_equal(post, whole), float(np.abs(post - whole).max())
+    assert lpd == lpd_whole
+    ref = orc.edge_posteriors(ds.data, ds.arity, d)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
+
+
+def test_split_rejects_bad_worlds(torch_ctx):
+    torch, ctx = torch_ctx
+    ds = datagen.random_dag_data(n=8, m=100, arity=2, max_parents=2, alpha=1.0, seed=3)
+    job = B.Job(ds.data, ds.arity, 2, precision="fp32")
+    for rank, world in ((0, 3), (2, 2), (-1, 2), (0, 64), (0, 32)):   # n - 4 = 4: W <= 16
+        with pytest.raises(B.BnError) as e:
+            B.Shard(ctx.h, job, rank, world)
+        assert e.value.code == B.BN_EINVAL
