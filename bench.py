@@ -159,6 +159,24 @@ def committed_traffic(kernel: str, workload: str, precision: str):
     return None
 
 
+def committed_fp64_ops() -> float | None:
+    """FP64 pipe operations (DFMA + DADD + DMUL, per thread) per subset-DP
+    cell of the FP64 path, from the committed ncu count in
+    profiles/fp64_ops.txt, only while the kernels' sources hash as at the
+    capture."""
+    path = os.path.join(ROOT, "profiles", "fp64_ops.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if ("ops_per_cell" in kv and "src" in kv
+                and kv.get("src_sha") == kernel_source_sha(tuple(kv["src"].split("+")))):
+            return float(kv["ops_per_cell"])
+    return None
+
+
 def stage_table(n: int, d: int, es: int) -> dict:
     """Per kernel: algorithmic HBM bytes per launch, launches per job and how
     to read its device time from bn_stats.  "bytes" counts only the method's
@@ -817,6 +835,16 @@ def run_ours(args):
                                                   "ms_backward", "ms_gamma_p1", "ms_gamma_p2",
                                                   "ms_edges")},
             "max_abs_diff_vs_fp32": err}
+        # the FP64 path is bound by the FP64 pipe: its operations per cell
+        # (ncu count) at the pipe's measured rate (a DFMA, a DADD and a DMUL
+        # each take one slot; the FMA probe counts 2 flops per slot)
+        opc = committed_fp64_ops()
+        if opc and p64:
+            achieved = opc * cells / (ms64 / 1e3)
+            extra["fp64_path"]["roofline"] = {
+                "bound": "alu", "pipe": "fp64", "ops_per_cell": opc,
+                "achieved": achieved, "peak": p64 / 2, "unit": "FP64 thread-ops/s",
+                "frac": achieved / (p64 / 2), "peak_kind": "measured (bn_peak_fp64_fma)"}
 
     if rank == 0 and not args.no_serve:
         extra["serving"] = run_serving(binding, local, args.serve_seconds)

@@ -1,10 +1,12 @@
 """Batches: many independent small jobs (bn_batch_create / bn_batch_run /
-bn_batch_results).  By default a batch runs as ONE persistent launch:
-thread-block clusters take whole jobs, largest first, from a device counter
-and run each job's recorded launch sequence (the same kernels as the job run
-alone) with cluster barriers between dependent launches.  The other form
-(BN_CTX_GRAPH_BATCH) replays a CUDA graph in which jobs with equal n, d,
-precision and kind of data share every launch of steps 1-5.
+bn_batch_results).  Jobs with equal n, d, precision and kind of data form a
+group that shares every launch of steps 1-5.  A batch exists in two forms:
+a CUDA graph of those launches, and one persistent launch per precision
+whose blocks take items (runs of the virtual blocks of one recorded launch)
+from a device queue ordered by stage depth, each item first waiting, by
+bounded polls, for the completion count of the launch before it in its
+group's chain.  Without autotuning the persistent form runs; with it, the
+faster of the two (BN_CTX_GRAPH_BATCH keeps the graph).
 
 Under the default schedules each job's result equals the same job run alone
 bit for bit in both forms (the same kernels, every reduction in a fixed
