@@ -401,6 +401,18 @@ int bn_debug_counts(bn_ctx* ctx, const bn_job_desc* job, int32_t i,
  * bn_batch_results returns BN_EDEVICE_TIMEOUT.  BN_EINVAL if the batch does
  * not run in the persistent form. */
 int bn_debug_batch_drop(bn_batch* batch, int32_t depth, uint64_t polls);
+/* Index checks.  The BN_CHECK_BOUNDS build of the library
+ * (_build/libbnedge_checked.so, a debug build with the test hooks) checks
+ * the global-memory offsets its kernels form -- rows of A, F and R', the
+ * down-zeta gathers and outputs, the column sums, the score and Gamma
+ * outputs, the packed levels of a split job -- against their arrays'
+ * sizes; a failing access records its source line and goes to offset 0
+ * instead (no fault, no trap).  This call waits for the device and returns
+ * the first failure since the last call: *unit = 1 (bn_kernels.cu),
+ * 2 (bn_tile13.cu), 3 (bn_levels.cu) or 4 (bn_mega.cu) and *line its source
+ * line, or both 0 when every check passed.  In the other builds *line = -1
+ * (no checks compiled). */
+int bn_debug_bounds(int32_t* line, int32_t* unit);
 #endif /* BN_TESTING */
 
 #ifdef __cplusplus

@@ -66,7 +66,7 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
 
 
 # Test hooks: exported only by the testing build (BN_TESTING).
-TEST_EXPORTS = ["bn_debug_stage", "bn_debug_counts", "bn_debug_batch_drop"]
+TEST_EXPORTS = ["bn_debug_stage", "bn_debug_counts", "bn_debug_batch_drop", "bn_debug_bounds"]
 
 
 def testing_build() -> bool:
@@ -75,7 +75,15 @@ def testing_build() -> bool:
     return os.environ.get("BN_TESTING") == "1"
 
 
+def checked_build() -> bool:
+    """The BN_CHECK_BOUNDS debug build (index checks in the kernels, plus the
+    test hooks) is loaded when the environment sets BN_CHECK_BOUNDS=1."""
+    return os.environ.get("BN_CHECK_BOUNDS") == "1"
+
+
 def library_path() -> str:
+    if checked_build():
+        return _build.LIB_CHECKED
     return _build.LIB_TESTING if testing_build() else _build.LIB
 
 
@@ -86,7 +94,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         return _lib
     path = library_path()
     if build_if_missing:
-        _build.build()
+        _build.build_checked() if checked_build() else _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} is missing "
                            "(run __graft_entry__.build()); there is no CPU fallback")
@@ -121,6 +129,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
                                       C.c_int64]),
         "bn_feature_posterior": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
         "bn_debug_batch_drop": (C.c_int, [P, C.c_int32, C.c_uint64]),
+        "bn_debug_bounds": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "bn_shard_create": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_int32,
                                       C.POINTER(P)]),
         "bn_shard_prepare": (C.c_int, [P, P]),
@@ -322,6 +331,17 @@ def bn_debug_stage(ctx: int, stage: int, shape, dtype) -> np.ndarray:
     if rc:
         raise BnError(rc, "bn_debug_stage")
     return out
+
+
+def bn_debug_bounds() -> tuple[int, int]:
+    """(line, unit) of the first failing index check of the BN_CHECK_BOUNDS
+    build since the last call; (0, 0) when none failed, (-1, 0) in the other
+    builds."""
+    line, unit = C.c_int32(), C.c_int32()
+    rc = load().bn_debug_bounds(C.byref(line), C.byref(unit))
+    if rc:
+        raise BnError(rc, "bn_debug_bounds")
+    return int(line.value), int(unit.value)
 
 
 def bn_debug_counts(ctx: int, job: Job, i: int, mask: int, cells: int) -> np.ndarray:

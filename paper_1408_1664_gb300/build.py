@@ -5,8 +5,11 @@ with a plain C ABI (``include/bnedge.h``): ``_build/libbnedge.so`` (the
 release build) and ``_build/libbnedge_testing.so``, the same objects plus the
 test hooks of the header's BN_TESTING section (the runtime unit compiled a
 second time with BN_TESTING defined).  ``_build/libbnpeaks.so`` holds the
-arithmetic-rate probes the benchmark uses for its ALU rooflines.  No torch
-headers are involved.
+arithmetic-rate probes the benchmark uses for its ALU rooflines.
+``build_checked`` makes a third, debug library on request,
+``_build/libbnedge_checked.so``: every unit compiled with BN_CHECK_BOUNDS
+(the kernels check the offsets they form; bn_device.cuh) and the test hooks.
+No torch headers are involved.
 """
 from __future__ import annotations
 
@@ -23,6 +26,7 @@ OUTDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUTDIR, "libbnedge.so")
 LIB_TESTING = os.path.join(OUTDIR, "libbnedge_testing.so")
 LIB_PEAKS = os.path.join(OUTDIR, "libbnpeaks.so")
+LIB_CHECKED = os.path.join(OUTDIR, "libbnedge_checked.so")
 SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_runtime.cu", "bn_noalloc.cu",
            "bn_mega.cu"]
 # the persistent batch kernel reads, within one launch, values other blocks
@@ -88,6 +92,39 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, out)
     return LIB
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """Compile (if needed) and return the path of the BN_CHECK_BOUNDS debug
+    library (with the BN_TESTING hooks)."""
+    if (not force and os.path.exists(LIB_CHECKED)
+            and all(os.path.getmtime(f) <= os.path.getmtime(LIB_CHECKED) for f in _inputs())):
+        return LIB_CHECKED
+    odir = os.path.join(OUTDIR, "checked")
+    os.makedirs(odir, exist_ok=True)
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+                    "-I", CSRC, "--expt-relaxed-constexpr", "-DBN_CHECK_BOUNDS"]
+
+    def one(src):
+        obj = os.path.join(odir, src.replace(".cu", ".o"))
+        more = UNIT_FLAGS.get(src, []) + (["-DBN_TESTING"] if src == TESTING_UNIT[0] else [])
+        cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags + more
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose:
+            print(r.stdout, r.stderr)
+        return obj
+
+    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
+        objs = list(ex.map(one, SOURCES))
+    tmp = LIB_CHECKED + ".tmp"
+    r = subprocess.run([nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_CHECKED)
+    return LIB_CHECKED
 
 
 if __name__ == "__main__":

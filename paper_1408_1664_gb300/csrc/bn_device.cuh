@@ -34,6 +34,39 @@ __device__ __forceinline__ uint32_t binom(int n, int k)
     return (k < 0 || k > n) ? 0u : c_binom.v[n][k];
 }
 
+// ---------------------------------------------------------------------------
+// Index checks of the BN_CHECK_BOUNDS build (a debug build of the library;
+// the release and testing builds compile BN_AT to the offset itself).  An
+// access of `width` elements at offset `off` of an array of `size` elements
+// that does not fit records the source line in the translation unit's word
+// (the first failure wins) and goes to offset 0 instead, so the kernel
+// neither faults nor traps; the host reads the word through
+// bn_debug_bounds.  Every array checked has at least `width` elements.
+// ---------------------------------------------------------------------------
+#ifdef BN_CHECK_BOUNDS
+static __device__ unsigned int g_bounds_line;       // one per translation unit
+__device__ __forceinline__ size_t bounds_check(size_t off, size_t width, size_t size, int line)
+{
+    if (off <= size && width <= size - off) return off;
+    atomicCAS(&g_bounds_line, 0u, (unsigned)line);
+    return 0;
+}
+#define BN_AT(off, width, size) \
+    ::bn::bounds_check((size_t)(off), (size_t)(width), (size_t)(size), __LINE__)
+// Host: the unit's first failing line (0: none), cleared by the read.
+#define BN_BOUNDS_READER(name)                                              \
+    unsigned int name()                                                     \
+    {                                                                       \
+        unsigned int v = 0, z = 0;                                          \
+        if (cudaMemcpyFromSymbol(&v, g_bounds_line, sizeof v) != cudaSuccess) \
+            return ~0u;                                                     \
+        cudaMemcpyToSymbol(g_bounds_line, &z, sizeof z);                    \
+        return v;                                                           \
+    }
+#else
+#define BN_AT(off, width, size) ((size_t)(off))
+#endif
+
 // Jobs of one batch group share a launch: the arrays of job blockIdx.y lie
 // js bytes after those of job blockIdx.y - 1 (js = 0 for a single job).
 template <typename P>

@@ -216,9 +216,12 @@ k_scores(int n, int d, int m, int W, int rmax, int64_t K, const uint8_t* __restr
         }
         acc = warp_sum(acc);
         if (lane == 0) {
-            logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
-            masks[x] = G;
-            cmasks[x] = cm;
+            {
+                const size_t xc = BN_AT(x, 1, (size_t)n * K);
+                logB[xc] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
+                masks[xc] = G;
+                cmasks[xc] = cm;
+            }
         }
     }
     (void)d;
@@ -319,9 +322,12 @@ k_scores_bin(int n, int m, int W, int64_t K, int64_t Kc, const uint64_t* __restr
         for (int c = 0; c < 32; ++c)
             if (c < cells) debug_counts[c] = cnt[c];
     }
-    logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
-    masks[x] = G;
-    cmasks[x] = cm;
+    {
+        const size_t xc = BN_AT(x, 1, (size_t)n * K);
+        logB[xc] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
+        masks[xc] = G;
+        cmasks[xc] = cm;
+    }
 }
 
 // Scores of the families with exactly k = 4 + HB parents (5 <= k <= 8), for
@@ -430,9 +436,12 @@ k_scores_bin_hi(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
     }
     if (h == 0) {
         const int64_t x = (int64_t)i * K + off + (int64_t)(g % Ck);
-        logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
-        masks[x] = G;
-        cmasks[x] = cm;
+        {
+            const size_t xc = BN_AT(x, 1, (size_t)n * K);
+            logB[xc] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
+            masks[xc] = G;
+            cmasks[xc] = cm;
+        }
     }
 }
 
@@ -529,9 +538,12 @@ k_scores_bin_hist(int n, int m, int W, int64_t K, int64_t off, int64_t Ck,
         acc = warp_sum(acc);
         if (lane == 0) {
             const int64_t x = (int64_t)i * K + off + rank;
-            logB[x] = (double)acc * tinv + (log_rho ? log_rho[KP] : 0.0);
-            masks[x] = G;
-            cmasks[x] = cm;
+            {
+                const size_t xc = BN_AT(x, 1, (size_t)n * K);
+                logB[xc] = (double)acc * tinv + (log_rho ? log_rho[KP] : 0.0);
+                masks[xc] = G;
+                cmasks[xc] = cm;
+            }
         }
     }
 }
@@ -635,9 +647,12 @@ k_scores_w(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict__
         if ((q & 31) != 0 && lane < (q & 31)) acc -= Tq[curj];
         acc = warp_sum(acc);
         if (lane == 0) {
-            logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
-            masks[x] = G;
-            cmasks[x] = cm;
+            {
+                const size_t xc = BN_AT(x, 1, (size_t)n * K);
+                logB[xc] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
+                masks[xc] = G;
+                cmasks[xc] = cm;
+            }
         }
     }
 }
@@ -727,9 +742,12 @@ k_scores_cfg(int n, int m, int W, int rmax, int64_t K, const uint8_t* __restrict
         }
         acc = warp_sum(acc);
         if (lane == 0) {
-            logB[x] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
-            masks[x] = G;
-            cmasks[x] = cm;
+            {
+                const size_t xc = BN_AT(x, 1, (size_t)n * K);
+                logB[xc] = (double)acc * tinv + (log_rho ? log_rho[k] : 0.0);
+                masks[xc] = G;
+                cmasks[xc] = cm;
+            }
         }
     }
 }
@@ -937,7 +955,7 @@ k_forward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __rest
                 Fv = mm + L::lg(ss);
             }
         }
-        if (active) F[S] = Fv;
+        if (active) F[BN_AT(S, 1, (size_t)1 << n)] = Fv;
         if (Ht) Ht = colex_next(Ht);
     }
 }
@@ -997,7 +1015,7 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
                 Rv = mm + L::lg(ss);
             }
         }
-        if (active) Rc[Tm] = Rv;
+        if (active) Rc[BN_AT(Tm, 1, (size_t)1 << n)] = Rv;
         if (Ht) Ht = colex_next(Ht);
     }
 }
@@ -1042,8 +1060,8 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
     }
     for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x) {
         const uint32_t S = expand((H << b) | t, v);
-        vals[t] = F[S] + Rc[S | bv];
-        if constexpr (kBases) vals[t] += off_s[__popc(S >> sh_s)];
+        vals[t] = F[BN_AT(S, 1, (size_t)1 << n)] + Rc[BN_AT(S | bv, 1, (size_t)1 << n)];
+        if constexpr (kBases) vals[t] += off_s[BN_AT(__popc(S >> sh_s), 1, 32)];
         if (lq) vals[t] += lq[v * n + __popc(S)];   // q_v(S) of Eq. 12
     }
     __syncthreads();
@@ -1057,7 +1075,7 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
     }
     T* row = W + (size_t)H * nlow;
     for (uint32_t t = threadIdx.x; t < tileN; t += blockDim.x)
-        if (__popc(t) <= d) row[small_subset_rank(t, b)] = vals[t];
+        if (__popc(t) <= d) row[BN_AT(small_subset_rank(t, b), 1, nlow)] = vals[t];
 }
 
 // FP32: the down-zeta offsets of endpoint blockIdx.x (one warp; bn_device.cuh).
@@ -1116,7 +1134,7 @@ k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, int64_t K, const T* __res
     for (uint32_t Hhi = 0; Hhi < (1u << hh); ++Hhi) {
         __syncthreads();
         for (uint32_t t = threadIdx.x; t < chunkN; t += blockDim.x)
-            vals[t] = W[(size_t)((Hhi << hc) | t) * nlow + col];
+            vals[t] = W[BN_AT((size_t)((Hhi << hc) | t) * nlow + col, 1, ((size_t)nlow << h))];
         __syncthreads();
         for (int j = 0; j < hc; ++j) {
             const uint32_t jm = (1u << j) - 1u;
@@ -1139,7 +1157,7 @@ k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, int64_t K, const T* __res
         for (int s = 0; s < k; ++s) f += binom(n - 1, s);
         int t = 1;
         for (uint32_t x = cm; x; x &= x - 1, ++t) f += binom(__ffs(x) - 1, t);
-        Gam[f] = acc[o];
+        Gam[BN_AT(f, 1, K)] = acc[o];
     }
 }
 
@@ -1218,7 +1236,7 @@ k_gamma_p2s(int n, int d, int b, uint32_t nlow, uint32_t c0, int64_t K, const T*
     for (int q = 0; q < MB; ++q) { mb[q] = L::ninf(); sb[q] = T(0); }
     const uint32_t nH = 1u << h;
     for (uint32_t H = lane; H < nH; H += 32) {
-        const T w = W[(size_t)H * nlow + col];
+        const T w = W[BN_AT((size_t)H * nlow + col, 1, (size_t)nlow << h)];
         lse_lazy_k(m0, s0, w);
         if (one) {
 #pragma unroll
@@ -1227,18 +1245,18 @@ k_gamma_p2s(int n, int d, int b, uint32_t nlow, uint32_t c0, int64_t K, const T*
         }
     }
     const T all = warp_lse(m0, s0);
-    if (lane == 0) Gam[family_index(g, n)] = all;
+    if (lane == 0) Gam[BN_AT(family_index(g, n), 1, K)] = all;
     if (!one) return;
     for (int bb = 0; bb < h && bb < 5; ++bb) {
         const bool in = lane >> bb & 1;
         const T x = warp_lse(in ? m0 : L::ninf(), in ? s0 : T(0));
-        if (lane == 0) Gam[family_index(g | (1u << (b + bb)), n)] = x;
+        if (lane == 0) Gam[BN_AT(family_index(g | (1u << (b + bb)), n), 1, K)] = x;
     }
 #pragma unroll
     for (int q = 0; q < MB; ++q) {
         if (5 + q >= h) break;
         const T x = warp_lse(mb[q], sb[q]);
-        if (lane == 0) Gam[family_index(g | (1u << (b + 5 + q)), n)] = x;
+        if (lane == 0) Gam[BN_AT(family_index(g | (1u << (b + 5 + q)), n), 1, K)] = x;
     }
 }
 
@@ -1296,7 +1314,7 @@ k_edges_acc(int n, int64_t K, int qbits, const double* __restrict__ logB,
         const double e = exp(logB[x] - cv + L::to_ln((double)Gam[x]) - lnFV);
         const unsigned long long q = __double2ull_rn(e * qscale);
         z += q;
-        for (uint32_t g = masks[x]; g; g &= g - 1) atomicAdd(&Nu[__ffs(g) - 1], q);
+        for (uint32_t g = masks[x]; g; g &= g - 1) atomicAdd(&Nu[BN_AT(__ffs(g) - 1, 1, 32)], q);
     }
     for (int o = 16; o; o >>= 1) z += __shfl_xor_sync(FULL, z, o);
     if ((tid & 31) == 0) atomicAdd(&Nz, z);
@@ -1402,6 +1420,9 @@ __global__ void k_copy_segments(const CopySeg* __restrict__ segs, int nseg)
 // Launchers.
 // ===========================================================================
 #ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
+#ifdef BN_CHECK_BOUNDS
+BN_BOUNDS_READER(bounds_line_kernels)
+#endif
 static int grid_for(int64_t work, int threads, int cap = 152 * 32)
 {
     int64_t g = (work + threads - 1) / threads;

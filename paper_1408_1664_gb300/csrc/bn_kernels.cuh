@@ -218,6 +218,14 @@ cudaError_t launch_rows_level(const Plan& P, int sweep, int hl, const void* A, v
 // whose top shard_k tile bits are r; dir 0 copies those rows of X to the
 // contiguous buf, dir 1 back.
 uint32_t shard_rows_count(const Plan& P, uint32_t r, int hl);
+#ifdef BN_CHECK_BOUNDS
+// The first failing index check of each translation unit (0: none), cleared
+// by the read (bn_device.cuh).
+unsigned int bounds_line_kernels();
+unsigned int bounds_line_tile13();
+unsigned int bounds_line_levels();
+unsigned int bounds_line_mega();
+#endif
 cudaError_t launch_word_max(int* word, const int* other, cudaStream_t s);
 cudaError_t launch_level_rows(const Plan& P, uint32_t r, int hl, void* X, void* buf, int dir,
                               cudaStream_t s);

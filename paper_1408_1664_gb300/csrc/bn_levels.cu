@@ -161,8 +161,8 @@ __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restric
         const uint32_t Hm = Ht & ~(1u << j);
         T a[LN], f[LN];
         const uint32_t row = TLO ? tlo_row(squeeze(Hm, j), 9) : squeeze(Hm, j);
-        load_row(A + (size_t)(B + j) * half + ((size_t)row << B), a, LD_STREAM);
-        load_row(F + ((size_t)Hm << B), f, FMODE);
+        load_row(A + BN_AT((size_t)(B + j) * half + ((size_t)row << B), LN, n * half), a, LD_STREAM);
+        load_row(F + BN_AT((size_t)Hm << B, LN, 2 * half), f, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + f[l]);
     }
@@ -174,8 +174,9 @@ __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restric
     T ai[B][LN / 2];
 #pragma unroll
     for (int i = 0; i < B; ++i)
-        load_row(A + (size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)), ai[i],
-                 LD_STREAM);
+        load_row(A + BN_AT((size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)),
+                           LN / 2, n * half),
+                 ai[i], LD_STREAM);
     T Fv[LN];
     Fv[0] = Ht == 0u ? T(0) : m[0] + L::lg(s[0]);
 #pragma unroll
@@ -185,7 +186,7 @@ __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restric
             if (l >> i & 1) lazy_add(m[l], s[l], ai[i][squeeze4(l ^ (1 << i), i)] + Fv[l ^ (1 << i)]);
         Fv[l] = m[l] + L::lg(s[l]);
     }
-    store_row(F + ((size_t)Ht << B), Fv);
+    store_row(F + BN_AT((size_t)Ht << B, LN, 2 * half), Fv);
     T mx = Fv[0];
 #pragma unroll
     for (int l = 1; l < LN; ++l) mx = Fv[l] > mx ? Fv[l] : mx;
@@ -211,8 +212,8 @@ __device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restri
         const int j = __ffs(rest) - 1;
         T a[LN], r[LN];
         const uint32_t row = TLO ? tlo_row(squeeze(Ht, j), 9) : squeeze(Ht, j);
-        load_row(A + (size_t)(B + j) * half + ((size_t)row << B), a, LD_STREAM);
-        load_row(Rc + ((size_t)(Ht | (1u << j)) << B), r, FMODE);
+        load_row(A + BN_AT((size_t)(B + j) * half + ((size_t)row << B), LN, n * half), a, LD_STREAM);
+        load_row(Rc + BN_AT((size_t)(Ht | (1u << j)) << B, LN, 2 * half), r, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + r[l]);
     }
@@ -222,8 +223,9 @@ __device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restri
     T ai[B][LN / 2];
 #pragma unroll
     for (int i = 0; i < B; ++i)
-        load_row(A + (size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)), ai[i],
-                 LD_STREAM);
+        load_row(A + BN_AT((size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)),
+                           LN / 2, n * half),
+                 ai[i], LD_STREAM);
     T Rv[LN];
     Rv[LN - 1] = Ht == hmask ? T(0) : m[LN - 1] + L::lg(s[LN - 1]);
 #pragma unroll
@@ -233,7 +235,7 @@ __device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restri
             if (!(l >> i & 1)) lazy_add(m[l], s[l], ai[i][squeeze4(l, i)] + Rv[l | (1 << i)]);
         Rv[l] = m[l] + L::lg(s[l]);
     }
-    store_row(Rc + ((size_t)Ht << B), Rv);
+    store_row(Rc + BN_AT((size_t)Ht << B, LN, 2 * half), Rv);
     T mx = Rv[0];
 #pragma unroll
     for (int l = 1; l < LN; ++l) mx = Rv[l] > mx ? Rv[l] : mx;
@@ -416,7 +418,9 @@ __global__ void k_level_rows(int n, int hl, uint32_t ntiles, uint32_t rsrc, int 
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
          x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t g = (uint32_t)(x >> B);
-        const size_t pos = ((size_t)level_tile(g, hl, n - B, rsrc, kfix, bt) << B) | (x & ((1u << B) - 1u));
+        const size_t pos = BN_AT(((size_t)level_tile(g, hl, n - B, rsrc, kfix, bt) << B) |
+                                     (x & ((1u << B) - 1u)),
+                                 1, (size_t)1 << n);
         if (dir == 0) buf[x] = X[pos];
         else X[pos] = buf[x];
     }
@@ -429,6 +433,9 @@ __global__ void k_word_max(int* __restrict__ word, const int* __restrict__ other
 }
 
 #ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
+#ifdef BN_CHECK_BOUNDS
+BN_BOUNDS_READER(bounds_line_levels)
+#endif
 namespace {
 
 uint64_t choose(int n, int k)

@@ -253,6 +253,10 @@ template __global__ void k_batch_persistent<0>(const LaunchRec*, const int4*, in
 template __global__ void k_batch_persistent<1>(const LaunchRec*, const int4*, int, const int2*, const int*,
                                                int*, uint64_t);
 
+#ifdef BN_CHECK_BOUNDS
+BN_BOUNDS_READER(bounds_line_mega)
+#endif
+
 bool persistent_runs(int prec, int kid)
 {
     switch (kid) {

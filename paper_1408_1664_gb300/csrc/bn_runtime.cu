@@ -2016,6 +2016,30 @@ try {
 } catch (...) {
     return exception_code();
 }
+
+// Test hook: the first failing index check of the BN_CHECK_BOUNDS build.
+int bn_debug_bounds(int32_t* line, int32_t* unit)
+try {
+    if (!line || !unit) return BN_EINVAL;
+    *line = -1;
+    *unit = 0;
+#ifdef BN_CHECK_BOUNDS
+    CK(cudaDeviceSynchronize());
+    const unsigned int v[4] = {bn::bounds_line_kernels(), bn::bounds_line_tile13(),
+                               bn::bounds_line_levels(), bn::bounds_line_mega()};
+    *line = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (v[k] == ~0u) return BN_ECUDA;
+        if (v[k] && *unit == 0) {
+            *line = (int32_t)v[k];
+            *unit = k + 1;
+        }
+    }
+#endif
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
 #endif  // BN_TESTING
 
 // ----------------------------------------------------------------- shards --

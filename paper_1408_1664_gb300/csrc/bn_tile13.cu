@@ -676,7 +676,7 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
                 uint32_t r = 0;                     // colex rank of H among kh-subsets
                 int t = 1;
                 for (uint32_t x = H; x; x &= x - 1, ++t) r += sb_binom(sb, __ffs(x) - 1, t);
-                val = tb[rowoff_k[kh] + r * off13[min(d - kh, TB) + 1] + c];
+                val = tb[BN_AT(rowoff_k[kh] + r * off13[min(d - kh, TB) + 1] + c, 1, K)];
             }
         }
         v[e] = val;
@@ -695,7 +695,7 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
     float* Ai = A + ((size_t)i << (n - 1));
     for (uint32_t e = threadIdx.x; e < H2 * CPB; e += blockDim.x) {
         const uint32_t H = e / CPB, c = c0 + e % CPB;
-        if (c < ncol) Ai[((size_t)H << TB) + c] = v[e];
+        if (c < ncol) Ai[BN_AT(((size_t)H << TB) + c, 1, (size_t)1 << (n - 1))] = v[e];
     }
 }
 
@@ -737,7 +737,7 @@ k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
         const int i = (int)(tile >> h);
         const uint32_t H = tile & ((1u << h) - 1u);
         const T* tb = tab + (size_t)i * K;
-        T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
+        T* out = A + BN_AT(((size_t)i << (n - 1)) + ((size_t)H << TB), TN, (size_t)n << (n - 1));
         const int hc = __popc(H);
         uint32_t total = 0;                      // rows of size <= d inside H
         for (int k = 0; k <= d && k <= hc; ++k) total += sb_binom(sb, hc, k);
@@ -762,14 +762,14 @@ k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
             for (int k = 0; k <= d - j && k <= hc; ++k) rend += sb_binom(sb, hc, k);
             T m = Lg::ninf(), s = T(0);
 #pragma unroll 4
-            for (uint32_t rp = 0; rp < rend; ++rp) lse_lazy(m, s, tb[rowbase[rp] + c]);
+            for (uint32_t rp = 0; rp < rend; ++rp) lse_lazy(m, s, tb[BN_AT(rowbase[rp] + c, 1, K)]);
             out[c] = m + Lg::lg(s);
         }
         const uint32_t rmid = 1u + (uint32_t)hc;               // d - 1 low elements
         for (uint32_t c = nlong + lane; c < ncopy; c += 32) {
             T m = Lg::ninf(), s = T(0);
 #pragma unroll 4
-            for (uint32_t rp = 0; rp < rmid; ++rp) lse_lazy(m, s, tb[rowbase[rp] + c]);
+            for (uint32_t rp = 0; rp < rmid; ++rp) lse_lazy(m, s, tb[BN_AT(rowbase[rp] + c, 1, K)]);
             out[c] = m + Lg::lg(s);
         }
         for (uint32_t c = ncopy + lane; c < ncol; c += 32) out[c] = tb[c];   // d low elements
@@ -802,7 +802,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     const int t = threadIdx.x, lane = t & 31;
     const int i = (int)(blockIdx.x >> h);
     const uint32_t H = blockIdx.x & ((1u << h) - 1u);
-    T* out = A + ((size_t)i << (n - 1)) + ((size_t)H << TB);
+    T* out = A + BN_AT(((size_t)i << (n - 1)) + ((size_t)H << TB), TN, (size_t)n << (n - 1));
     // place of element e in the tile's block
     const int lw = i < 4 ? 3 : 4;                // row width of A_i in step 3
     const uint32_t lmask = (1u << lw) - 1u;
@@ -819,7 +819,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     T tm = Lg::ninf();
     for (uint32_t c = t; c < ncol; c += TT) {
         const T v = out[c];
-        const uint32_t sw = swz(unrank13[c]);
+        const uint32_t sw = swz(BN_AT(unrank13[c], 1, TN));
         A0[sw] = A1[sw] = v;
         tm = v > tm ? v : tm;
     }
@@ -869,7 +869,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
                 // a run of 8 consecutive elements stays inside one row (lw >= 3)
 #pragma unroll
                 for (int q = 0; q < TR / 8; ++q) {
-                    float4* p = reinterpret_cast<float4*>(out + opos(el3(8 * q, t)));
+                    float4* p = reinterpret_cast<float4*>(out + BN_AT(opos(el3(8 * q, t)), 8, TN));
                     p[0] = make_float4(x[8 * q], x[8 * q + 1], x[8 * q + 2], x[8 * q + 3]);
                     p[1] = make_float4(x[8 * q + 4], x[8 * q + 5], x[8 * q + 6], x[8 * q + 7]);
                 }
@@ -884,7 +884,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
             // row: their places start at run3[q]
             uint32_t run3[TR / 8];
 #pragma unroll
-            for (int q = 0; q < TR / 8; ++q) run3[q] = opos(el3(8 * q, t));
+            for (int q = 0; q < TR / 8; ++q) run3[q] = BN_AT(opos(el3(8 * q, t)), 8, TN);
             T sp = M - Wn::top;
             for (int p = 0; p < npass; ++p, sp -= Wn::win) {
                 const bool last = p + 1 == npass;
@@ -938,7 +938,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     T sc[TR];
     sum_pass<true>(v, sc, A1, A0, t, d);
 #pragma unroll
-    for (int r = 0; r < TR; ++r) out[opos(el1(r, t))] = scaled_log(v[r], sc[r]);
+    for (int r = 0; r < TR; ++r) out[BN_AT(opos(el1(r, t)), 1, TN)] = scaled_log(v[r], sc[r]);
 }
 
 // ===========================================================================
@@ -994,7 +994,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
 #pragma unroll
     for (int r = 0; r < TR; ++r) {                  // the tile's loads go out first
         const uint32_t S = expand((H << TB) | el1(r, t), v);
-        x[r] = F[S] + Rc[S | bv];
+        x[r] = F[BN_AT(S, 1, (size_t)1 << n)] + Rc[BN_AT(S | bv, 1, (size_t)1 << n)];
     }
     if constexpr (kBases)                           // while they are in flight
         load_gamma_offsets(reinterpret_cast<const float*>(Rc), n, v, off_s, &sh_s, &fvrel_s);
@@ -1008,7 +1008,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         const int lowm = v >= kLevelShift ? 15 : 7;
         const int bt = sh_s == kLevelShift ? __popc(H) + __popc(t & ~lowm) : 0;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) offr[k] = off_s[sh_s == kLevelShift ? bt + k : 0];
+        for (int k = 0; k < 6; ++k) offr[k] = off_s[BN_AT(sh_s == kLevelShift ? bt + k : 0, 1, 32)];
     }
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
@@ -1031,7 +1031,8 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         const T M = ord_dec(tmax_s) + T(TB);
         T L = Lg::ninf();                           // relevance cut (see above)
         if (Aup) {
-            const T at = job_ptr(Aup, js)[((size_t)v << (n - 1)) + (((size_t)H << TB) | (TN - 1))];
+            const T at = job_ptr(Aup, js)[BN_AT(((size_t)v << (n - 1)) + (((size_t)H << TB) | (TN - 1)), 1,
+                                                (size_t)n << (n - 1))];
             // log P(D) in the units of s (FP32: relative to the integer Z)
             const T fv = kBases ? (T)fvrel_s : F[((size_t)1 << n) - 1];
             L = fv - margin - at;
@@ -1041,7 +1042,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
                 const uint32_t el = el3(r, t);
-                if (__popc(el) <= d) row[rank13[el]] = floorv;
+                if (__popc(el) <= d) row[BN_AT(rank13[el], 1, nlow)] = floorv;
             }
             return;
         }
@@ -1062,7 +1063,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
             for (int r = 0; r < TR; ++r) {
                 const uint32_t el = el3(r, t);
                 const T o = sp + Lg::lg(x[r]);
-                if (__popc(el) <= d) row[rank13[el]] = o > floorv ? o : floorv;
+                if (__popc(el) <= d) row[BN_AT(rank13[el], 1, nlow)] = o > floorv ? o : floorv;
             }
             return;
         }
@@ -1083,7 +1084,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     const int pt = __popc((uint32_t)t);
 #pragma unroll
     for (int r = 0; r < TR; ++r)
-        if (pt + __popc((uint32_t)r) <= d) row[rank13[el1(r, t)]] = scaled_log(x[r], sc[r]);
+        if (pt + __popc((uint32_t)r) <= d) row[BN_AT(rank13[el1(r, t)], 1, nlow)] = scaled_log(x[r], sc[r]);
 }
 
 // rank13[L] = position of L among the subsets of 13 bits ordered by size then
@@ -1101,6 +1102,9 @@ __global__ void k_rank13_tables(uint16_t* __restrict__ rank13, uint16_t* __restr
 }
 
 #ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
+#ifdef BN_CHECK_BOUNDS
+BN_BOUNDS_READER(bounds_line_tile13)
+#endif
 // ===========================================================================
 // Launchers.
 // ===========================================================================
