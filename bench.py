@@ -63,7 +63,9 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="only the 256-job batched workload (prints its JSON object)")
     ap.add_argument("--batch-reps", type=int, default=5,
-                    help="timed replays of the batch graph")
+                    help="timed runs of the batch")
+    ap.add_argument("--batch-graph", action="store_true",
+                    help="with --batched-only: the graph form instead of the persistent launch")
     ap.add_argument("--degree", type=int, default=0,
                     help="override the workload's in-degree bound d (profiling)")
     ap.add_argument("--shard", action="store_true",
@@ -555,16 +557,17 @@ def run_batched(binding, torch, device: int, jobs_n: int = 256, reps: int = 5) -
 
 
 def run_batched_only(args) -> None:
-    """The 256-job batch under the default schedule (what the autotuner
-    keeps for this workload): two warm-up replays and --batch-reps timed
-    replays of its graph; used for launch lists."""
+    """The 256-job batch without autotuning, in its persistent form (one
+    launch per precision) or, with --batch-graph, as the graph of launches:
+    two warm-up runs and --batch-reps timed runs; used for launch lists and
+    for timing either form alone."""
     import torch
 
     from paper_1408_1664_gb300 import binding
 
     binding.load(build_if_missing=True)
     jobs = [datagen.batched_job(j) for j in range(256)]
-    with binding.Context(0, autotune=False) as ctx:
+    with binding.Context(0, autotune=False, graph_batch=args.batch_graph) as ctx:
         batch = binding.Batch(ctx.h, [binding.Job(ds.data, ds.arity, d, precision="fp32")
                                       for ds, d in jobs])
         stream = torch.cuda.Stream()
@@ -578,9 +581,11 @@ def run_batched_only(args) -> None:
         e1.record(stream)
         stream.synchronize()
         ms = e0.elapsed_time(e1) / args.batch_reps
-        groups = len(batch.describe().strip().splitlines())
+        groups = sum(1 for x in batch.describe().strip().splitlines()
+                     if not x.startswith("persistent"))
         batch.close()
-    print(json.dumps({"batched_default_schedule": {"jobs": 256, "groups": groups,
+    form = "graph" if args.batch_graph else "persistent"
+    print(json.dumps({f"batched_{form}_default_schedule": {"jobs": 256, "groups": groups,
                                                    "ms_per_batch": ms,
                                                    "jobs_per_s": 256 / (ms / 1e3)}}))
 

@@ -29,9 +29,8 @@ LIB_PEAKS = os.path.join(OUTDIR, "libbnpeaks.so")
 LIB_CHECKED = os.path.join(OUTDIR, "libbnedge_checked.so")
 SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_runtime.cu", "bn_noalloc.cu",
            "bn_mega.cu"]
-# the persistent batch kernel reads, within one launch, values other blocks
-# wrote: its global loads go through L2 only
-UNIT_FLAGS = {"bn_mega.cu": ["-Xptxas", "-dlcm=cg"]}
+# extra nvcc flags per translation unit
+UNIT_FLAGS: dict = {}
 PEAKS_SOURCE = "bn_peaks.cu"
 # (source, object, extra flags) of the second compile of the runtime unit
 TESTING_UNIT = ("bn_runtime.cu", "bn_runtime_testing.o", ["-DBN_TESTING"])

@@ -6,23 +6,28 @@
 // all of them from one device work queue.  A work item is a range of blocks
 // of one launch record; the items of all groups are queued in order of the
 // record's depth in its group's sequence, so the first steps of every group
-// come first.  A block takes the next item (one atomic), waits until every
-// record the item's record depends on has completed (the record before it in
-// its group's sequence; an F level and an R' level of equal depth are
+// come first.  A block holds one item and has already claimed the next (one
+// atomic, issued while the current item runs); it waits until every record
+// the item's record depends on has completed (the record before it in its
+// group's sequence; an F level and an R' level of equal depth are
 // independent of each other), runs the item's blocks, and counts the item
-// done.  Every item an item waits on sits earlier in the queue and was taken
-// by a running block, so the waits always end; even so each wait is bounded:
-// after `cap` polls the block records BN_EDEVICE_TIMEOUT in the status word,
-// raises the abort flag every block checks, and the kernel returns.
+// done.  Every item an item waits on sits earlier in the queue, and a block
+// runs the items it claimed in claim order, so by induction over the queue
+// every item runs and every wait ends; even so each wait is bounded: after
+// `cap` polls the block records BN_EDEVICE_TIMEOUT in the status word, raises
+// the abort flag every block checks, and the kernel returns.
 //
 // The kernels are compiled here a second time, as device functions: this
 // file includes the three kernel sources with __global__ turned into
 // __device__ __noinline__ and blockIdx / gridDim redirected to the virtual
 // block being run.  Values one block writes are read by other blocks within
-// the same launch, so every global load goes through L2: the unit is
-// compiled with -Xptxas -dlcm=cg, the kernels' __restrict__ qualifiers
-// (which allow the read-only cache) are dropped here, and their explicit
-// cache hints are read as L2 loads.
+// the same launch.  A producer's writes are ordered before its count by a
+// fence; the consumer's first thread reads the count with ld.acquire.gpu and
+// the block meets at a barrier before any thread loads, so by the PTX memory
+// model every thread's ordinary loads (through L1) see the writes.  The
+// non-coherent read-only path is outside that guarantee, so the kernels'
+// __restrict__ qualifiers (which allow it) are dropped here and their
+// explicit cache hints are read as L2 loads.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -196,20 +201,24 @@ k_batch_persistent(const LaunchRec* __restrict__ recs, const int4* __restrict__ 
                    const int2* __restrict__ deps, const int* __restrict__ need, int* __restrict__ ctl,
                    uint64_t cap)
 {
-    __shared__ int it_s, go_s;
-    __shared__ __align__(16) unsigned char args_s[kRecArgBytes];
+    __shared__ int it_s, next_s, go_s;
+    __shared__ __align__(16) LaunchRec rec_s;
     int* next = ctl;
     int* status = ctl + 1;
     int* abort = ctl + 2;
     int* done = ctl + 4;
+    // A block holds its current item and has claimed the next one: every
+    // item claimed earlier than another runs first in its block, so by
+    // induction over the queue every item runs and every wait ends.
+    if (threadIdx.x == 0) it_s = atomicAdd(next, 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) it_s = atomicAdd(next, 1);
-        __syncthreads();
         const int it = it_s;
         if (it >= nitems) break;
         const int4 item = __ldcg(items + it);
         const int r = item.x;
         if (threadIdx.x == 0) {
+            next_s = atomicAdd(next, 1);            // the next item, claimed now
             const int2 dp = __ldcg(deps + r);
             bool ok = true;
             if (dp.x >= 0) ok = wait_count(done + dp.x, __ldcg(need + dp.x), abort, cap);
@@ -220,22 +229,21 @@ k_batch_persistent(const LaunchRec* __restrict__ recs, const int4* __restrict__ 
             }
             go_s = ok;
         }
-        const LaunchRec* rec = recs + r;
-        if (threadIdx.x < kRecArgBytes / 16)
-            reinterpret_cast<int4*>(args_s)[threadIdx.x] =
-                __ldcg(reinterpret_cast<const int4*>(rec->args) + threadIdx.x);
+        if (threadIdx.x < sizeof(LaunchRec) / 16)
+            reinterpret_cast<int4*>(&rec_s)[threadIdx.x] =
+                __ldcg(reinterpret_cast<const int4*>(recs + r) + threadIdx.x);
         __syncthreads();
         if (!go_s) break;
-        const int kid = __ldcg(&rec->kid);
-        const unsigned gx = __ldcg(&rec->gx), gy = __ldcg(&rec->gy), gz = __ldcg(&rec->gz);
-        const unsigned block = __ldcg(&rec->block);
+        const int kid = rec_s.kid;
+        const unsigned gx = rec_s.gx, gy = rec_s.gy, gz = rec_s.gz;
+        const unsigned block = rec_s.block;
         for (int v = item.y; v < item.z; ++v) {
             if (threadIdx.x == 0) {
-                bn_mega_bidx = make_uint3((unsigned)v % gx, ((unsigned)v / gx) % gy, (unsigned)v / (gx * gy));
+                bn_mega_bidx = make_uint3((unsigned)v % gx, (((unsigned)v / gx) % gy), (unsigned)v / (gx * gy));
                 bn_mega_gdim = make_uint3(gx, gy, gz);
             }
             bar1();
-            if (threadIdx.x < block && !dispatch<PREC>(kid, args_s)) go_s = 0;
+            if (threadIdx.x < block && !dispatch<PREC>(kid, rec_s.args)) go_s = 0;
             bar1();
         }
         // the item's writes are done (barrier), then visible GPU-wide (fence)
@@ -244,7 +252,9 @@ k_batch_persistent(const LaunchRec* __restrict__ recs, const int4* __restrict__ 
             if (!go_s) atomicCAS(status, 0, (int)BN_EINVAL);
             __threadfence();
             atomicAdd(done + r, 1);
+            it_s = next_s;
         }
+        __syncthreads();
     }
 }
 
