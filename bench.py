@@ -70,6 +70,8 @@ def parse():
                     help="override the workload's in-degree bound d (profiling)")
     ap.add_argument("--shard", action="store_true",
                     help="one job split over the ranks (strong scaling) instead of replicas")
+    ap.add_argument("--divide-a", action="store_true",
+                    help="with --shard: each rank holds only its slabs of A")
     return ap.parse_args()
 
 
@@ -924,7 +926,8 @@ def run_shard(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     job = binding.Job(ds.data, ds.arity, d, precision=args.precision)
-    shard = binding.Shard(ctx.h, job, rank, world)
+    shard = binding.Shard(ctx.h, job, rank, world, divide_a=args.divide_a)
+    shard_bytes = shard.bytes()
     nb = sh.max_step_bytes(shard)
     xbytes = sum(sum(sh.step_bytes(shard, hf, hr)) for hf, hr in sh.steps(shard.levels))
     buf = torch.zeros(nb, dtype=torch.uint8, device="cuda")
@@ -973,7 +976,8 @@ def run_shard(args):
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": name, "n": n, "d": d, "m": ds.m,
                        "precision": args.precision, "cells_per_job": cells,
-                       "parallelism": f"shard{world}",
+                       "parallelism": f"shard{world}" + ("_divided_A" if args.divide_a else ""),
+                       "device_bytes_per_rank": shard_bytes,
                        "packed_bytes_per_rank_per_job": xbytes,
                        "l2": "no flush: each step streams a >4 GB DP working set (L2 129 MB)"},
             "split_vs_whole_max_abs_diff": float(np.abs(split_post - whole).max()),

@@ -300,10 +300,26 @@ int bn_batch_destroy(bn_batch* batch);
  *                     rank's device; no batch restrictions) and allocates
  *                     the rank's arrays (counted in the context's budget);
  *                     BN_EINVAL when W is not a power of two up to 32, rank
- *                     is out of range or W is too large for n;
+ *                     is out of range or W is too large for n.  flags:
+ *                     0, or BN_SHARD_DIVIDE_A (below);
  *   bn_shard_prepare  uploads the inputs and runs steps 1-2 (scores and A,
- *                     Eq. 6-7) in full on every rank: A is read by every
- *                     tile, and computing it costs less than moving it;
+ *                     Eq. 6-7).  Without BN_SHARD_DIVIDE_A every rank
+ *                     computes all of A (read by every tile; computing it
+ *                     costs less than moving it).  With it, a rank holds
+ *                     only the entries its tiles read: for the low
+ *                     n - k variables the A_i(S) whose top k variables are
+ *                     the rank's bits, for each top variable t its A_t over
+ *                     the subsets of the low variables plus the rank's
+ *                     other top bits -- about (n + k) 2^(n-1-k) values
+ *                     instead of n 2^(n-1).  It computes them with no
+ *                     exchange, as truncated zeta transforms over the low
+ *                     variables of the score table folded over the rank's
+ *                     top bits (every rank holds the small score table).
+ *                     It needs n - k >= 14 and no order prior (BN_EINVAL);
+ *                     results agree with the whole job to rounding
+ *                     (the folded sums add in another order), and the
+ *                     down-zeta runs without its relevance cut;
+ *   bn_shard_bytes    the device bytes the shard holds;
  *   bn_shard_level    computes level hl (0..H, H = n - 4 FP32 / n - 3 FP64)
  *                     of the forward sum F (sweep 0, Eq. 9; hl = 0..H in
  *                     turn) or of R'(T) = R(V - T) (sweep 1, Eq. 10;
@@ -318,7 +334,8 @@ int bn_batch_destroy(bn_batch* batch);
  *                     rank's arrays and takes the maximum of the level
  *                     words (from == this rank: nothing to do);
  *   bn_shard_finish   runs steps 4-5 (Eq. 11-12) for the endpoints v with
- *                     v mod W = rank: post_dev (n*n device doubles) gets
+ *                     v mod W = rank (its down-zeta scratch is sized for
+ *                     those endpoints only): post_dev (n*n device doubles) gets
  *                     those columns and zeros elsewhere, log_PD_dev (NULL
  *                     allowed) log P(D).  The sum over ranks of post_dev is
  *                     the job's posterior matrix.
@@ -329,12 +346,14 @@ int bn_batch_destroy(bn_batch* batch);
  * both sweeps must be complete before bn_shard_finish.  The caller moves
  * the buffers (NCCL all-gather, or device copies between contexts); the
  * library does no communication.  Every call is enqueued on `stream` (NULL =
- * the context's stream) without host synchronisation.  The result equals
- * the job run whole, bit for bit: every tile is computed from the same
- * values in the same order. */
+ * the context's stream) without host synchronisation.  Without
+ * BN_SHARD_DIVIDE_A the result equals the job run whole, bit for bit: every
+ * tile is computed from the same values in the same order. */
 typedef struct bn_shard bn_shard;
+#define BN_SHARD_DIVIDE_A 1
 int bn_shard_create(bn_ctx* ctx, const bn_job_desc* job, int32_t rank, int32_t world,
-                    bn_shard** shard);
+                    int32_t flags, bn_shard** shard);
+int bn_shard_bytes(const bn_shard* shard, uint64_t* bytes);
 int bn_shard_prepare(bn_shard* shard, void* stream);
 int bn_shard_level(bn_shard* shard, int32_t sweep, int32_t hl, void* stream);
 int bn_shard_exchange_bytes(const bn_shard* shard, int32_t hl, uint64_t* bytes);

@@ -20,6 +20,7 @@ BN_OK, BN_EINVAL, BN_ENOMEM, BN_EAGAIN, BN_ETIMEOUT = 0, -1, -2, -3, -4
 BN_EDEVICE_TIMEOUT, BN_ECUDA, BN_ECANCELED, BN_ENOTFOUND = -5, -6, -7, -8
 BN_FP64, BN_FP32_SHIFTED = 0, 1
 PRECISIONS = {"fp64": BN_FP64, "fp32": BN_FP32_SHIFTED}
+BN_SHARD_DIVIDE_A = 1
 (BN_STAGE_LOGB, BN_STAGE_MASKS, BN_STAGE_SHIFT, BN_STAGE_A, BN_STAGE_F, BN_STAGE_RC,
  BN_STAGE_GAMMA) = range(1, 8)
 
@@ -62,7 +63,8 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
            "bn_batch_run", "bn_batch_results", "bn_batch_describe", "bn_batch_destroy",
            "bn_feature_posterior", "bn_batch_upload", "bn_batch_download",
            "bn_shard_create", "bn_shard_prepare", "bn_shard_level", "bn_shard_exchange_bytes",
-           "bn_shard_pack", "bn_shard_unpack", "bn_shard_finish", "bn_shard_destroy"]
+           "bn_shard_pack", "bn_shard_unpack", "bn_shard_finish", "bn_shard_destroy",
+           "bn_shard_bytes"]
 
 
 # Test hooks: exported only by the testing build (BN_TESTING).
@@ -130,8 +132,9 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_feature_posterior": (C.c_int, [P, C.POINTER(bn_job_desc), P, P, P]),
         "bn_debug_batch_drop": (C.c_int, [P, C.c_int32, C.c_uint64]),
         "bn_debug_bounds": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-        "bn_shard_create": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_int32,
+        "bn_shard_create": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_int32, C.c_int32,
                                       C.POINTER(P)]),
+        "bn_shard_bytes": (C.c_int, [P, C.POINTER(C.c_uint64)]),
         "bn_shard_prepare": (C.c_int, [P, P]),
         "bn_shard_level": (C.c_int, [P, C.c_int32, C.c_int32, P]),
         "bn_shard_exchange_bytes": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
@@ -427,10 +430,11 @@ class Shard:
     `stream` a torch stream or a cudaStream_t address (None = the context's
     stream)."""
 
-    def __init__(self, ctx: int, job: Job, rank: int, world: int):
+    def __init__(self, ctx: int, job: Job, rank: int, world: int, divide_a: bool = False):
         self.job, self.rank, self.world = job, int(rank), int(world)
         h = C.c_void_p()
-        rc = load().bn_shard_create(ctx, C.byref(job.desc), self.rank, self.world, C.byref(h))
+        rc = load().bn_shard_create(ctx, C.byref(job.desc), self.rank, self.world,
+                                    BN_SHARD_DIVIDE_A if divide_a else 0, C.byref(h))
         if rc:
             raise BnError(rc, "bn_shard_create")
         self.h = h.value
@@ -447,6 +451,12 @@ class Shard:
 
     def level(self, sweep: int, hl: int, stream=None) -> None:
         self._call("bn_shard_level", sweep, hl, _ptr(stream))
+
+    def bytes(self) -> int:
+        """Device bytes the shard holds."""
+        b = C.c_uint64()
+        self._call("bn_shard_bytes", C.byref(b))
+        return int(b.value)
 
     def exchange_bytes(self, hl: int) -> int:
         b = C.c_uint64()

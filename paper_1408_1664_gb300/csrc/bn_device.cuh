@@ -67,6 +67,18 @@ __device__ __forceinline__ size_t bounds_check(size_t off, size_t width, size_t 
 #define BN_AT(off, width, size) ((size_t)(off))
 #endif
 
+// The slice of the down-zeta scratch W that endpoint v uses: v itself when
+// every endpoint is computed, its rank among the computed ones (vsel) when a
+// split job's rank computes only some.
+__host__ __device__ __forceinline__ uint32_t endpoint_slot(uint32_t vsel, int v)
+{
+#ifdef __CUDA_ARCH__
+    return (uint32_t)__popc(vsel & ((1u << v) - 1u));
+#else
+    return (uint32_t)__builtin_popcount(vsel & ((1u << v) - 1u));
+#endif
+}
+
 // Jobs of one batch group share a launch: the arrays of job blockIdx.y lie
 // js bytes after those of job blockIdx.y - 1 (js = 0 for a single job).
 template <typename P>

@@ -1043,7 +1043,7 @@ k_gamma_p1(int n, int d, int b, uint32_t nlow, const T* __restrict__ F,
     if (!(vsel >> v & 1u)) return;                  // an endpoint another rank computes
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
-    W = job_ptr(W, js) + (size_t)v * gridDim.x * nlow;
+    W = job_ptr(W, js) + (size_t)endpoint_slot(vsel, v) * gridDim.x * nlow;
     using L = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* vals = reinterpret_cast<T*>(smem_raw);
@@ -1105,7 +1105,7 @@ k_gamma_p2(int n, int d, int b, int hc, uint32_t nlow, int64_t K, const T* __res
 {
     const int v = blockIdx.z;                       // endpoint: its slice of W, its K outputs
     if (!(vsel >> v & 1u)) return;
-    W = job_ptr(W, js) + ((size_t)v << (n - 1 - b)) * nlow;
+    W = job_ptr(W, js) + ((size_t)endpoint_slot(vsel, v) << (n - 1 - b)) * nlow;
     Gam = job_ptr(Gam, js) + (size_t)v * K;
     using L = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1218,7 +1218,7 @@ k_gamma_p2s(int n, int d, int b, uint32_t nlow, uint32_t c0, int64_t K, const T*
     constexpr int MB = 13;                          // high bits from 5 up (h <= 17)
     const int v = blockIdx.z;
     if (!(vsel >> v & 1u)) return;
-    W = job_ptr(W, js) + ((size_t)v << (n - 1 - b)) * nlow;
+    W = job_ptr(W, js) + ((size_t)endpoint_slot(vsel, v) << (n - 1 - b)) * nlow;
     Gam = job_ptr(Gam, js) + (size_t)v * K;
     using L = LogOps<T>;
     const int h = n - 1 - b;

@@ -157,7 +157,15 @@ struct Plan {
     int shard_k = 0;
     uint32_t shard_r = 0;
     uint32_t vsel = 0xffffffffu;
+    // Step 2 over `nodes` score tables that share the n-1-bit index space of
+    // a node (0: the n nodes of the job; a split job's divided A has more).
+    int nodes = 0;
+    // A split job whose ranks hold only their slabs of A: step 3 reads the
+    // low n - shard_k nodes' slabs (top bits = the rank's) and, for each top
+    // variable, a slab over the low variables.
+    int slab = 0;
 };
+inline int up_nodes(const Plan& P) { return P.nodes ? P.nodes : P.n; }
 
 // Step 1.  A batch group passes nj jobs js bytes apart (mj: each job's own
 // sample count, at the same stride); a single job leaves the defaults.
@@ -213,7 +221,8 @@ bool rows64_fit(const Plan& P);           // FP64 and 4 <= n < 31: 8-subset row 
 cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStream_t s, int* launches);
 // One level of a shard's sweep (sweep 0 F, 1 R'; the row kernels, with the
 // plan's shard_k / shard_r): nothing when the shard has no tile there.
-cudaError_t launch_rows_level(const Plan& P, int sweep, int hl, const void* A, void* X, cudaStream_t s);
+cudaError_t launch_rows_level(const Plan& P, int sweep, int hl, const void* A, void* X, cudaStream_t s,
+                              const void* Atop = nullptr);
 // Tiles (rows of 16 FP32 or 8 FP64 values) of level hl in the sub-lattice
 // whose top shard_k tile bits are r; dir 0 copies those rows of X to the
 // contiguous buf, dir 1 back.
@@ -227,6 +236,12 @@ unsigned int bounds_line_levels();
 unsigned int bounds_line_mega();
 #endif
 cudaError_t launch_word_max(int* word, const int* other, cudaStream_t s);
+// A split job's divided A: the folded score tables of the rank's virtual job
+// (nl low variables, nl + 2 (n - nl) tables of Kv families) and the top
+// variables' slabs from its A (bn_levels.cu).
+cudaError_t launch_fold_scores(const Plan& P, int nl, int64_t Kv, uint32_t r, const void* lbs, void* out,
+                               cudaStream_t s);
+cudaError_t launch_top_slabs(const Plan& V, int k, const void* Av, void* Atop, cudaStream_t s);
 cudaError_t launch_level_rows(const Plan& P, uint32_t r, int hl, void* X, void* buf, int dir,
                               cudaStream_t s);
 // F and R' of every job of a batch group in one persistent launch of

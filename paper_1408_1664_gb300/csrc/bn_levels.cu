@@ -144,12 +144,22 @@ __device__ __forceinline__ void fill_table(uint32_t (*bt)[BT])
 // rebase: the previous level's stored values are relative to a base larger by
 // this much than this level's (the FP32 per-level bases, bn_device.cuh; 0
 // otherwise).  Returns the largest value written.
-template <typename T, int FMODE, int B, bool TLO = false>
+//
+// SLAB (a split job with divided A): A holds the rank's slabs of the nl = n -
+// k low nodes, each over the nl - 1 low bits of its index (the top k bits are
+// the rank's); Atop holds, for each top variable t = nl + q, its slab over
+// the nl low variables.  A term of a low node reads its slab with the top
+// bits of the row index dropped; a term of a top variable reads Atop.
+template <typename T, int FMODE, int B, bool TLO = false, bool SLAB = false>
 __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restrict__ A,
-                                          T* __restrict__ F, T rebase = T(0))
+                                          T* __restrict__ F, T rebase = T(0), int nl = 0,
+                                          const T* __restrict__ Atop = nullptr)
 {
     constexpr int LN = 1 << B;
-    const size_t half = (size_t)1 << (n - 1);
+    const size_t full = (size_t)1 << n;
+    const size_t half = (size_t)1 << ((SLAB ? nl : n) - 1);
+    const uint32_t rmask = SLAB ? (1u << (nl - 1 - B)) - 1u : ~0u;   // slab row bits
+    const uint32_t lmask = SLAB ? (1u << (nl - B)) - 1u : ~0u;       // low tile bits
     using L = LogOps<T>;
 
     T m[LN], s[LN];
@@ -160,9 +170,17 @@ __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restric
         const int j = __ffs(rest) - 1;
         const uint32_t Hm = Ht & ~(1u << j);
         T a[LN], f[LN];
-        const uint32_t row = TLO ? tlo_row(squeeze(Hm, j), 9) : squeeze(Hm, j);
-        load_row(A + BN_AT((size_t)(B + j) * half + ((size_t)row << B), LN, n * half), a, LD_STREAM);
-        load_row(F + BN_AT((size_t)Hm << B, LN, 2 * half), f, FMODE);
+        if (SLAB && B + j >= nl) {                  // a top variable: its slab
+            load_row(Atop + BN_AT(((size_t)(B + j - nl) << nl) + ((size_t)(Ht & lmask) << B), LN,
+                                  (size_t)(n - nl) << nl),
+                     a, LD_STREAM);
+        } else {
+            const uint32_t row = TLO ? tlo_row(squeeze(Hm, j) & rmask, 9) : squeeze(Hm, j) & rmask;
+            load_row(A + BN_AT((size_t)(B + j) * half + ((size_t)row << B), LN,
+                               (SLAB ? nl : n) * half),
+                     a, LD_STREAM);
+        }
+        load_row(F + BN_AT((size_t)Hm << B, LN, full), f, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + f[l]);
     }
@@ -174,8 +192,8 @@ __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restric
     T ai[B][LN / 2];
 #pragma unroll
     for (int i = 0; i < B; ++i)
-        load_row(A + BN_AT((size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)),
-                           LN / 2, n * half),
+        load_row(A + BN_AT((size_t)i * half + ((size_t)(TLO ? tlo_row(Ht & lmask, 10) : Ht & lmask) << (B - 1)),
+                           LN / 2, (SLAB ? nl : n) * half),
                  ai[i], LD_STREAM);
     T Fv[LN];
     Fv[0] = Ht == 0u ? T(0) : m[0] + L::lg(s[0]);
@@ -186,7 +204,7 @@ __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restric
             if (l >> i & 1) lazy_add(m[l], s[l], ai[i][squeeze4(l ^ (1 << i), i)] + Fv[l ^ (1 << i)]);
         Fv[l] = m[l] + L::lg(s[l]);
     }
-    store_row(F + BN_AT((size_t)Ht << B, LN, 2 * half), Fv);
+    store_row(F + BN_AT((size_t)Ht << B, LN, full), Fv);
     T mx = Fv[0];
 #pragma unroll
     for (int l = 1; l < LN; ++l) mx = Fv[l] > mx ? Fv[l] : mx;
@@ -195,14 +213,18 @@ __device__ __forceinline__ T forward_tile(int n, uint32_t Ht, const T* __restric
 
 // The 2^B values of R' in tile Ht (the tiles of the level above written):
 //   R'(T) = sum_{i not in T} A_i(T) R'(T + {i}),  R'(V) = 1
-template <typename T, int FMODE, int B, bool TLO = false>
+template <typename T, int FMODE, int B, bool TLO = false, bool SLAB = false>
 __device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restrict__ A,
-                                           T* __restrict__ Rc, T rebase = T(0))
+                                           T* __restrict__ Rc, T rebase = T(0), int nl = 0,
+                                           const T* __restrict__ Atop = nullptr)
 {
     constexpr int LN = 1 << B;
     const int nh = n - B;
     const uint32_t hmask = (1u << nh) - 1u;
-    const size_t half = (size_t)1 << (n - 1);
+    const size_t full = (size_t)1 << n;
+    const size_t half = (size_t)1 << ((SLAB ? nl : n) - 1);
+    const uint32_t rmask = SLAB ? (1u << (nl - 1 - B)) - 1u : ~0u;
+    const uint32_t lmask = SLAB ? (1u << (nl - B)) - 1u : ~0u;
     using L = LogOps<T>;
 
     T m[LN], s[LN];
@@ -211,9 +233,17 @@ __device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restri
     for (uint32_t rest = ~Ht & hmask; rest; rest &= rest - 1) {
         const int j = __ffs(rest) - 1;
         T a[LN], r[LN];
-        const uint32_t row = TLO ? tlo_row(squeeze(Ht, j), 9) : squeeze(Ht, j);
-        load_row(A + BN_AT((size_t)(B + j) * half + ((size_t)row << B), LN, n * half), a, LD_STREAM);
-        load_row(Rc + BN_AT((size_t)(Ht | (1u << j)) << B, LN, 2 * half), r, FMODE);
+        if (SLAB && B + j >= nl) {
+            load_row(Atop + BN_AT(((size_t)(B + j - nl) << nl) + ((size_t)(Ht & lmask) << B), LN,
+                                  (size_t)(n - nl) << nl),
+                     a, LD_STREAM);
+        } else {
+            const uint32_t row = TLO ? tlo_row(squeeze(Ht, j) & rmask, 9) : squeeze(Ht, j) & rmask;
+            load_row(A + BN_AT((size_t)(B + j) * half + ((size_t)row << B), LN,
+                               (SLAB ? nl : n) * half),
+                     a, LD_STREAM);
+        }
+        load_row(Rc + BN_AT((size_t)(Ht | (1u << j)) << B, LN, full), r, FMODE);
 #pragma unroll
         for (int l = 0; l < LN; ++l) lazy_add(m[l], s[l], a[l] + r[l]);
     }
@@ -223,8 +253,8 @@ __device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restri
     T ai[B][LN / 2];
 #pragma unroll
     for (int i = 0; i < B; ++i)
-        load_row(A + BN_AT((size_t)i * half + ((size_t)(TLO ? tlo_row(Ht, 10) : Ht) << (B - 1)),
-                           LN / 2, n * half),
+        load_row(A + BN_AT((size_t)i * half + ((size_t)(TLO ? tlo_row(Ht & lmask, 10) : Ht & lmask) << (B - 1)),
+                           LN / 2, (SLAB ? nl : n) * half),
                  ai[i], LD_STREAM);
     T Rv[LN];
     Rv[LN - 1] = Ht == hmask ? T(0) : m[LN - 1] + L::lg(s[LN - 1]);
@@ -235,7 +265,7 @@ __device__ __forceinline__ T backward_tile(int n, uint32_t Ht, const T* __restri
             if (!(l >> i & 1)) lazy_add(m[l], s[l], ai[i][squeeze4(l, i)] + Rv[l | (1 << i)]);
         Rv[l] = m[l] + L::lg(s[l]);
     }
-    store_row(Rc + BN_AT((size_t)Ht << B, LN, 2 * half), Rv);
+    store_row(Rc + BN_AT((size_t)Ht << B, LN, full), Rv);
     T mx = Rv[0];
 #pragma unroll
     for (int l = 1; l < LN; ++l) mx = Rv[l] > mx ? Rv[l] : mx;
@@ -292,10 +322,10 @@ __device__ __forceinline__ uint32_t cluster_blocks()
 // FP32 keeps the per-level bases (bn_device.cuh): level hl reads the
 // previous level's word (its values' base minus this level's base), and
 // every block adds its largest written value to the level's word.
-template <typename T, bool TLO>
+template <typename T, bool TLO, bool SLAB = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ F,
-               size_t js, uint32_t rfix, int kfix)
+               size_t js, uint32_t rfix, int kfix, const T* __restrict__ Atop)
 {
     constexpr int B = sizeof(T) == 4 ? LB : LB64;
     constexpr bool kBases = sizeof(T) == 4;
@@ -309,7 +339,9 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __res
         int* lw = level_words(reinterpret_cast<float*>(F), n);
         const T rebase = hl > 0 ? (T)level_delta(lw, hl - 1) : T(0);
         T mx = LogOps<T>::ninf();
-        if (g < ntiles) mx = forward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, F, rebase);
+        if (g < ntiles)
+            mx = forward_tile<T, LD_PLAIN, B, TLO, SLAB>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, F,
+                                                         rebase, n - kfix, Atop);
         if (hl == 0) {
             if (g == 0) level_words_start(lw, 0, mx);
         } else {
@@ -317,14 +349,15 @@ k_forward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __res
         }
     } else {
         if (g >= ntiles) return;
-        forward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, F);
+        forward_tile<T, LD_PLAIN, B, TLO, SLAB>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, F, T(0),
+                                                n - kfix, Atop);
     }
 }
 
-template <typename T, bool TLO>
+template <typename T, bool TLO, bool SLAB = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __restrict__ Rc,
-                size_t js, uint32_t rfix, int kfix)
+                size_t js, uint32_t rfix, int kfix, const T* __restrict__ Atop)
 {
     constexpr int B = sizeof(T) == 4 ? LB : LB64;
     constexpr bool kBases = sizeof(T) == 4;
@@ -339,7 +372,9 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __re
         int* lw = level_words(reinterpret_cast<float*>(Rc), n);
         const T rebase = hl < nh ? (T)level_delta(lw, hl + 1) : T(0);
         T mx = LogOps<T>::ninf();
-        if (g < ntiles) mx = backward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, nh, rfix, kfix, bt), A, Rc, rebase);
+        if (g < ntiles)
+            mx = backward_tile<T, LD_PLAIN, B, TLO, SLAB>(n, level_tile(g, hl, nh, rfix, kfix, bt), A, Rc,
+                                                          rebase, n - kfix, Atop);
         if (hl == nh) {
             if (g == 0) level_words_start(lw, nh, mx);
         } else {
@@ -347,7 +382,8 @@ k_backward_rows(int n, int hl, uint32_t ntiles, const T* __restrict__ A, T* __re
         }
     } else {
         if (g >= ntiles) return;
-        backward_tile<T, LD_PLAIN, B, TLO>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, Rc);
+        backward_tile<T, LD_PLAIN, B, TLO, SLAB>(n, level_tile(g, hl, n - B, rfix, kfix, bt), A, Rc, T(0),
+                                                 n - kfix, Atop);
     }
 }
 
@@ -426,6 +462,99 @@ __global__ void k_level_rows(int n, int hl, uint32_t ntiles, uint32_t rsrc, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// A split job's divided A (Eq. 7 restricted to a rank's sub-lattice).  With
+// the top k variables V_t = {nl, .., n - 1} (nl = n - k) fixed to the rank's
+// bits r, every entry a rank's tiles read is a truncated zeta transform over
+// the nl low variables alone:
+//   low node i < nl:  A_i(r + L) = sum over G <= L of B'_i(G),
+//                     B'_i(G) = sum over G_t <= r, |G_t| + |G| <= d of B_i(G_t + G);
+//   top variable t:   A_t(r' + L), r' = r - {t}, L over all nl low variables,
+//                     = X1(L - {0}) when 0 is not in L, X1 + X2 when it is,
+//                     X1, X2 the transforms over the low variables but 0 of
+//                     the families G_t + G (0 not in G) and G_t + G + {0},
+//                     G_t <= r'.
+// So a rank forms the folded score tables of a virtual job of nl variables
+// with nl + 2k tables over the same nl - 1-bit index space (table i < nl:
+// node i, bit i squeezed out; tables nl + 2q and nl + 2q + 1: X1 and X2 of
+// top variable nl + q, bit 0 squeezed out), runs the step-2 kernels on it,
+// and combines X1 and X2 into each top variable's slab.  No exchange is
+// needed: the score table is small and every rank holds it.
+// ---------------------------------------------------------------------------
+
+// The folded tables, in the virtual job's canonical family order (Kv per
+// table), from the job's shifted scores lbs (K per node, the same shift).
+template <typename T>
+__global__ void k_fold_scores(int n, int nl, int d, int64_t K, int64_t Kv, uint32_t r,
+                              const T* __restrict__ lbs, T* __restrict__ out)
+{
+    using L = LogOps<T>;
+    const int k = n - nl;
+    const int64_t total = (int64_t)(nl + 2 * k) * Kv;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int u = (int)(x / Kv);
+        uint32_t f = (uint32_t)(x % Kv);
+        int sz = 0;
+        while (f >= binom(nl - 1, sz)) { f -= binom(nl - 1, sz); ++sz; }
+        const uint32_t cm = colex_unrank(f, sz, nl - 1);
+        int node;
+        uint32_t G, tops;
+        if (u < nl) {
+            node = u;
+            G = expand(cm, u);                          // over the nl low variables
+            tops = r;
+        } else {
+            const int q = (u - nl) >> 1;
+            node = nl + q;
+            G = (cm << 1) | (uint32_t)((u - nl) & 1);   // X2: variable 0 in the family
+            tops = r & ~(1u << q);
+        }
+        const int g = __popc(G);
+        T m = L::ninf(), s = T(0);
+        if (g <= d) {
+            for (uint32_t t = tops;; t = (t - 1) & tops) {
+                if (g + __popc(t) <= d) {
+                    const uint32_t c = squeeze(G | (t << nl), node);   // node's own index
+                    const T v = lbs[BN_AT((size_t)node * K + small_subset_rank(c, n - 1), 1, (size_t)n * K)];
+                    if (v != L::ninf()) {
+                        if (v > m) {
+                            s = s * L::ex(m - v) + T(1);
+                            m = v;
+                        } else {
+                            s += L::ex(v - m);
+                        }
+                    }
+                }
+                if (t == 0) break;
+            }
+        }
+        out[x] = m == L::ninf() ? m : m + L::lg(s);
+    }
+}
+
+// The top variables' slabs (plain order over the nl low variables) from the
+// X1 and X2 tables of the virtual job's A (its own layout: tile-level row
+// order when TLO, rows of 16 for tables >= 4).
+template <typename T, bool TLO>
+__global__ void k_top_slabs(int nl, int k, const T* __restrict__ Av, T* __restrict__ Atop)
+{
+    using L = LogOps<T>;
+    const size_t per = (size_t)1 << nl;
+    const size_t half = per >> 1;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < per * (size_t)k;
+         x += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = x >> nl;
+        const uint32_t Lw = (uint32_t)(x & (per - 1));
+        const uint32_t c = Lw >> 1;
+        const uint32_t pos = TLO ? (tlo_row(c >> 4, 9) << 4) | (c & 15u) : c;
+        const T* X1 = Av + (size_t)(nl + 2 * q) * half;
+        T v = X1[BN_AT(pos, 1, half)];
+        if (Lw & 1u) v = L::lse(v, X1[half + BN_AT(pos, 1, half)]);
+        Atop[x] = v;
+    }
+}
+
 // *word = max(*word, *other): another rank's floored level maximum.
 __global__ void k_word_max(int* __restrict__ word, const int* __restrict__ other)
 {
@@ -475,32 +604,72 @@ uint32_t shard_level_tiles(const Plan& P, int hl)
     return (uint32_t)choose(nh - k, hl - hr);
 }
 
-cudaError_t launch_rows_level(const Plan& P, int sweep, int hl, const void* A, void* X, cudaStream_t s)
+// One level of a split job's sweep: the rank's tiles (P.shard_r, P.shard_k).
+// With P.slab, A holds the rank's slabs of the low nodes and Atop the top
+// variables' slabs (the kernels' SLAB form, launched directly: a split job
+// is never recorded into a batch).
+template <typename T, bool TLO>
+static cudaError_t rows_level(const Plan& P, int sweep, int hl, uint32_t nt, unsigned tb, dim3 grid,
+                              const void* A, void* X, const void* Atop, cudaStream_t s)
+{
+    const uint32_t rf = P.shard_r;
+    const int kf = P.shard_k;
+    const T* a = (const T*)A;
+    const T* at = (const T*)Atop;
+    if (P.slab) {
+        if (sweep == 0)
+            k_forward_rows<T, TLO, true><<<grid, tb, 0, s>>>(P.n, hl, nt, a, (T*)X, P.js, rf, kf, at);
+        else
+            k_backward_rows<T, TLO, true><<<grid, tb, 0, s>>>(P.n, hl, nt, a, (T*)X, P.js, rf, kf, at);
+        return cudaGetLastError();
+    }
+    const int kid = sizeof(T) == 8 ? (sweep == 0 ? KID_FROWS_D : KID_BROWS_D)
+                    : TLO ? (sweep == 0 ? KID_FROWS_F_TLO : KID_BROWS_F_TLO)
+                          : (sweep == 0 ? KID_FROWS_F : KID_BROWS_F);
+    if (sweep == 0)
+        return launch_or_record(kid, k_forward_rows<T, TLO>, grid, tb, 0, s, P.n, hl, nt, a, (T*)X, P.js,
+                                rf, kf, at);
+    return launch_or_record(kid, k_backward_rows<T, TLO>, grid, tb, 0, s, P.n, hl, nt, a, (T*)X, P.js, rf,
+                            kf, at);
+}
+
+cudaError_t launch_rows_level(const Plan& P, int sweep, int hl, const void* A, void* X, cudaStream_t s,
+                              const void* Atop)
 {
     const uint32_t nt = shard_level_tiles(P, hl);
     if (nt == 0) return cudaSuccess;
     const unsigned tb = rec_block(level_block(nt));
     const dim3 grid((nt + tb - 1) / tb, P.nj);
-    const uint32_t rf = P.shard_r;
-    const int kf = P.shard_k;
-    if (sweep == 0) {
-        if (P.prec == 0)
-            return launch_or_record(KID_FROWS_D, k_forward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt,
-                                    (const double*)A, (double*)X, P.js, rf, kf);
-        if (use_tlo(P))
-            return launch_or_record(KID_FROWS_F_TLO, k_forward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt,
-                                    (const float*)A, (float*)X, P.js, rf, kf);
-        return launch_or_record(KID_FROWS_F, k_forward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt,
-                                (const float*)A, (float*)X, P.js, rf, kf);
-    }
+    if (P.prec == 0) return rows_level<double, false>(P, sweep, hl, nt, tb, grid, A, X, Atop, s);
+    if (use_tlo(P)) return rows_level<float, true>(P, sweep, hl, nt, tb, grid, A, X, Atop, s);
+    return rows_level<float, false>(P, sweep, hl, nt, tb, grid, A, X, Atop, s);
+}
+
+cudaError_t launch_fold_scores(const Plan& P, int nl, int64_t Kv, uint32_t r, const void* lbs, void* out,
+                               cudaStream_t s)
+{
+    const int64_t total = (int64_t)(nl + 2 * (P.n - nl)) * Kv;
+    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
     if (P.prec == 0)
-        return launch_or_record(KID_BROWS_D, k_backward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt,
-                                (const double*)A, (double*)X, P.js, rf, kf);
-    if (use_tlo(P))
-        return launch_or_record(KID_BROWS_F_TLO, k_backward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt,
-                                (const float*)A, (float*)X, P.js, rf, kf);
-    return launch_or_record(KID_BROWS_F, k_backward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt,
-                            (const float*)A, (float*)X, P.js, rf, kf);
+        k_fold_scores<double><<<grid, 256, 0, s>>>(P.n, nl, P.d, P.K, Kv, r, (const double*)lbs, (double*)out);
+    else
+        k_fold_scores<float><<<grid, 256, 0, s>>>(P.n, nl, P.d, P.K, Kv, r, (const float*)lbs, (float*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_top_slabs(const Plan& V, int k, const void* Av, void* Atop, cudaStream_t s)
+{
+    const int nl = V.n;
+    const uint64_t total = (uint64_t)k << nl;
+    if (total == 0) return cudaSuccess;                 // no top variables (one rank)
+    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 152 * 16);
+    if (V.prec == 0)
+        k_top_slabs<double, false><<<grid, 256, 0, s>>>(nl, k, (const double*)Av, (double*)Atop);
+    else if (use_tlo(V))
+        k_top_slabs<float, true><<<grid, 256, 0, s>>>(nl, k, (const float*)Av, (float*)Atop);
+    else
+        k_top_slabs<float, false><<<grid, 256, 0, s>>>(nl, k, (const float*)Av, (float*)Atop);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_word_max(int* word, const int* other, cudaStream_t s)
@@ -538,13 +707,13 @@ cudaError_t launch_forward_rows(const Plan& P, const void* A, void* F, cudaStrea
         const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
             launch_or_record(KID_FROWS_D, k_forward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt, (const double*)A,
-                                                               (double*)F, P.js, 0u, 0);
+                                                               (double*)F, P.js, 0u, 0, (const double*)nullptr);
         else if (use_tlo(P))
             launch_or_record(KID_FROWS_F_TLO, k_forward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                             (float*)F, P.js, 0u, 0);
+                                                             (float*)F, P.js, 0u, 0, (const float*)nullptr);
         else
             launch_or_record(KID_FROWS_F, k_forward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                              (float*)F, P.js, 0u, 0);
+                                                              (float*)F, P.js, 0u, 0, (const float*)nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
@@ -562,13 +731,13 @@ cudaError_t launch_backward_rows(const Plan& P, const void* A, void* Rc, cudaStr
         const dim3 grid((nt + tb - 1) / tb, P.nj);
         if (P.prec == 0)
             launch_or_record(KID_BROWS_D, k_backward_rows<double, false>, grid, tb, 0, s, P.n, hl, nt, (const double*)A,
-                                                                (double*)Rc, P.js, 0u, 0);
+                                                                (double*)Rc, P.js, 0u, 0, (const double*)nullptr);
         else if (use_tlo(P))
             launch_or_record(KID_BROWS_F_TLO, k_backward_rows<float, true>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                              (float*)Rc, P.js, 0u, 0);
+                                                              (float*)Rc, P.js, 0u, 0, (const float*)nullptr);
         else
             launch_or_record(KID_BROWS_F, k_backward_rows<float, false>, grid, tb, 0, s, P.n, hl, nt, (const float*)A,
-                                                               (float*)Rc, P.js, 0u, 0);
+                                                               (float*)Rc, P.js, 0u, 0, (const float*)nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;

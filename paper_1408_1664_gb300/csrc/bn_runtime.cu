@@ -95,11 +95,13 @@ Layout make_layout(const Plan& P, size_t dbg_cells, bool feature = false)
     // sized for every schedule that fits, so that a plan can switch kernels
     L.tab = take(bn::tile13_up_fits(P) ? nK * es : 0);
     L.rk13 = take(bn::tile13_gamma_fits(P) ? bn::kRank13Bytes : 0);
-    L.A = take(((size_t)P.n << (P.n - 1)) * es);
+    L.A = take(P.slab ? 0 : ((size_t)P.n << (P.n - 1)) * es);   // a split job with divided A: its own slabs
     // F and R' are each followed by the per-level words of the FP32 bases
     L.F = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4);
     L.Rc = take(((size_t)1 << P.n) * es + (bn::kLevelWords + bn::kGammaTabWords) * 4);
-    L.W = take((size_t)P.n * ((size_t)1 << hg) * P.nlow_g * es);   // one slice per endpoint
+    // one slice per endpoint computed (all n, or a split job's rank's)
+    const size_t nv = (size_t)__builtin_popcount(P.vsel & (uint32_t)(((uint64_t)1 << P.n) - 1));
+    L.W = take(nv * ((size_t)1 << hg) * P.nlow_g * es);
     L.Gam = take(nK * es);
     L.eacc = take((size_t)P.n * (P.n + 1) * 8);
     L.post = take((size_t)P.n * P.n * 8);
@@ -2051,6 +2053,12 @@ struct bn_shard {
     char* mem = nullptr;                 // the shard's own device arrays
     int rank = 0, world = 1, nh = 0;
     bool prepared = false;
+    // divided A (BN_SHARD_DIVIDE_A): the virtual job of the rank's slabs and
+    // its arrays (folded scores, their reordered table, its A, the top
+    // variables' slabs), in one more allocation
+    Plan V{};
+    char* slab = nullptr;
+    size_t o_lbs = 0, o_tab = 0, o_A = 0, o_top = 0, slab_bytes = 0;
 };
 
 namespace {
@@ -2059,10 +2067,11 @@ size_t shard_header() { return 16; }     // the level word, padded
 
 }  // namespace
 
-int bn_shard_create(bn_ctx* c, const bn_job_desc* job, int32_t rank, int32_t world, bn_shard** out)
+int bn_shard_create(bn_ctx* c, const bn_job_desc* job, int32_t rank, int32_t world, int32_t flags,
+                    bn_shard** out)
 try {
     if (!c || !job || !out || world < 1 || world > 32 || (world & (world - 1)) || rank < 0 ||
-        rank >= world)
+        rank >= world || (flags & ~BN_SHARD_DIVIDE_A))
         return BN_EINVAL;
     *out = nullptr;
     bn_shard* sh = new bn_shard();
@@ -2088,13 +2097,43 @@ try {
         sh->hj.data_copy.assign(job->data, job->data + (size_t)P.m * P.n);
         sh->hj.data = sh->hj.data_copy.data();
     }
+    if (flags & BN_SHARD_DIVIDE_A) {
+        // the virtual job of nl = n - k low variables and nl + 2k tables
+        // runs the 13-dimension up-zeta tiles (nl >= 14); no order prior
+        const int nl = P.n - k;
+        if (nl < 14 || P.hasq) { delete sh; return BN_EINVAL; }
+        P.slab = 1;
+        Plan& V = sh->V;
+        V = P;
+        V.n = nl;
+        V.K = bn_num_families(nl, P.d);
+        V.nodes = nl + 2 * k;
+        V.hasq = 0;
+        V.up13 = 1;
+        V.slab = 0;
+        V.shard_k = 0;
+        V.shard_r = 0;
+        const size_t es = P.prec == 0 ? 8 : 4;
+        auto al256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+        size_t o = 0;
+        sh->o_lbs = o;  o += al256((size_t)V.nodes * V.K * es);
+        sh->o_tab = o;  o += al256((size_t)V.nodes * V.K * es);
+        sh->o_A = o;    o += al256(((size_t)V.nodes << (nl - 1)) * es);
+        sh->o_top = o;  o += al256(((size_t)k << nl) * es);
+        sh->slab_bytes = o;
+    }
     sh->L = make_layout(P, 0);
-    if (sh->L.total > c->budget) { delete sh; return BN_ENOMEM; }
+    if (sh->L.total + sh->slab_bytes > c->budget) { delete sh; return BN_ENOMEM; }
     if (cudaSetDevice(c->device) != cudaSuccess) { delete sh; return BN_ECUDA; }
     void* p = nullptr;
     rc = dev_alloc(c, &p, sh->L.total, nullptr);
     if (rc) { delete sh; return rc; }
     sh->mem = (char*)p;
+    if (sh->slab_bytes) {
+        rc = dev_alloc(c, &p, sh->slab_bytes, nullptr);
+        if (rc) { cudaFree(sh->mem); delete sh; return rc; }
+        sh->slab = (char*)p;
+    }
     *out = sh;
     return BN_OK;
 } catch (...) {
@@ -2128,8 +2167,17 @@ try {
     int nl = 0;
     rc = enqueue_step1(hj, B, data_dev, s, &nl);
     if (rc) return rc;
-    rc = enqueue_upzeta(P, B, B.at<void>(L.lbs), s, &nl, nullptr);
-    if (rc) return rc;
+    if (P.slab) {
+        // the rank's slabs of A from the folded scores (no exchange)
+        const Plan& V = sh->V;
+        CK(bn::launch_fold_scores(P, V.n, V.K, P.shard_r, B.at<void>(L.lbs), sh->slab + sh->o_lbs, s));
+        CK(bn::launch_upzeta(V, nullptr, sh->slab + sh->o_lbs, sh->slab + sh->o_tab,
+                             B.at<uint16_t>(L.rk13), sh->slab + sh->o_A, s, nullptr));
+        CK(bn::launch_top_slabs(V, P.shard_k, sh->slab + sh->o_A, sh->slab + sh->o_top, s));
+    } else {
+        rc = enqueue_upzeta(P, B, B.at<void>(L.lbs), s, &nl, nullptr);
+        if (rc) return rc;
+    }
     if (P.prec != 0) {                        // every rank starts both sweeps' level words
         int w[bn::kLevelWords];
         for (int q = 0; q < bn::kLevelWords; ++q) w[q] = bn::kLevelUnset;
@@ -2149,7 +2197,11 @@ try {
     if (!sh || !sh->prepared || sweep < 0 || sweep > 1 || hl < 0 || hl > sh->nh) return BN_EINVAL;
     const Layout& L = sh->L;
     cudaStream_t s = stream ? (cudaStream_t)stream : sh->ctx->stream;
-    CK(bn::launch_rows_level(sh->hj.P, sweep, hl, sh->mem + L.A, sh->mem + (sweep ? L.Rc : L.F), s));
+    if (sh->slab)
+        CK(bn::launch_rows_level(sh->hj.P, sweep, hl, sh->slab + sh->o_A, sh->mem + (sweep ? L.Rc : L.F), s,
+                                 sh->slab + sh->o_top));
+    else
+        CK(bn::launch_rows_level(sh->hj.P, sweep, hl, sh->mem + L.A, sh->mem + (sweep ? L.Rc : L.F), s));
     return BN_OK;
 } catch (...) {
     return exception_code();
@@ -2211,9 +2263,11 @@ try {
     const Layout& L = sh->L;
     cudaStream_t s = stream ? (cudaStream_t)stream : sh->ctx->stream;
     Bufs B{sh->mem, L};
+    // divided A: no rank holds A_v over every tile, so the down-zeta runs
+    // without its relevance cut (the same values; every output computed)
     CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
                            B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr,
-                           B.at<void>(L.A)));
+                           P.slab ? nullptr : B.at<void>(L.A)));
     CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
     CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
                         B.at<void>(L.Gam), B.at<void>(L.F), B.at<int>(L.err),
@@ -2224,11 +2278,21 @@ try {
     return exception_code();
 }
 
+int bn_shard_bytes(const bn_shard* sh, uint64_t* bytes)
+try {
+    if (!sh || !bytes) return BN_EINVAL;
+    *bytes = sh->L.total + sh->slab_bytes;
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
 int bn_shard_destroy(bn_shard* sh)
 try {
     if (!sh) return BN_EINVAL;
     cudaSetDevice(sh->ctx->device);
     if (sh->mem) cudaFree(sh->mem);          // waits for the shard's work in flight
+    if (sh->slab) cudaFree(sh->slab);
     delete sh;
     return BN_OK;
 } catch (...) {

@@ -436,12 +436,12 @@ __device__ __forceinline__ uint32_t row_offset(int h, int d, int kh, uint32_t ra
 
 template <typename T>
 __global__ void k_reorder_up(int n, int d, int64_t K, const T* __restrict__ lbs, T* __restrict__ tab,
-                             size_t js)
+                             size_t js, int nodes)
 {
     lbs = job_ptr(lbs, js);
     tab = job_ptr(tab, js);
     const int h = n - 1 - TB;
-    const int64_t total = (int64_t)n * K;
+    const int64_t total = (int64_t)nodes * K;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(x / K);
@@ -701,7 +701,8 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A, size_t js)
+k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A, size_t js,
+                int nodes)
 {
     tab = job_ptr(tab, js);
     A = job_ptr(A, js);
@@ -731,13 +732,13 @@ k_upzeta13_colw(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
     const uint32_t ncol = num_small_subsets(TB, d);
     const uint32_t nlong = d >= 2 ? off13[min(d - 2, TB) + 1] : 0u;
     const uint32_t ncopy = off13[min(d, TB + 1)];
-    const uint32_t ntiles = (uint32_t)n << h;
+    const uint32_t ntiles = (uint32_t)nodes << h;
     const uint32_t wpb = blockDim.x >> 5;
     for (uint32_t tile = blockIdx.x * wpb + warp; tile < ntiles; tile += gridDim.x * wpb) {
         const int i = (int)(tile >> h);
         const uint32_t H = tile & ((1u << h) - 1u);
         const T* tb = tab + (size_t)i * K;
-        T* out = A + BN_AT(((size_t)i << (n - 1)) + ((size_t)H << TB), TN, (size_t)n << (n - 1));
+        T* out = A + BN_AT(((size_t)i << (n - 1)) + ((size_t)H << TB), TN, (size_t)nodes << (n - 1));
         const int hc = __popc(H);
         uint32_t total = 0;                      // rows of size <= d inside H
         for (int k = 0; k <= d && k <= hc; ++k) total += sb_binom(sb, hc, k);
@@ -802,7 +803,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     const int t = threadIdx.x, lane = t & 31;
     const int i = (int)(blockIdx.x >> h);
     const uint32_t H = blockIdx.x & ((1u << h) - 1u);
-    T* out = A + BN_AT(((size_t)i << (n - 1)) + ((size_t)H << TB), TN, (size_t)n << (n - 1));
+    T* out = A + BN_AT(((size_t)i << (n - 1)) + ((size_t)H << TB), TN, (size_t)gridDim.x << TB);
     // place of element e in the tile's block
     const int lw = i < 4 ? 3 : 4;                // row width of A_i in step 3
     const uint32_t lmask = (1u << lw) - 1u;
@@ -971,7 +972,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
     rank13 = job_ptr(rank13, js);
-    W = job_ptr(W, js) + (size_t)v * gridDim.x * nlow;
+    W = job_ptr(W, js) + (size_t)endpoint_slot(vsel, v) * gridDim.x * nlow;
     using Lg = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
@@ -1161,14 +1162,14 @@ cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unra
 
 cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s)
 {
-    const int64_t total = (int64_t)P.n * P.K;
+    const int64_t total = (int64_t)up_nodes(P) * P.K;
     const dim3 grid((unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), P.nj);
     if (P.prec == 0)
         launch_or_record(KID_REORDER_D, k_reorder_up<double>, grid, 256, 0, s, P.n, P.d, P.K, (const double*)lbs, (double*)tab,
-                                                  P.js);
+                                                  P.js, up_nodes(P));
     else
         launch_or_record(KID_REORDER_F, k_reorder_up<float>, grid, 256, 0, s, P.n, P.d, P.K, (const float*)lbs, (float*)tab,
-                                                 P.js);
+                                                 P.js, up_nodes(P));
     return cudaGetLastError();
 }
 
@@ -1176,7 +1177,8 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
                             cudaStream_t s, cudaEvent_t sums_done)
 {
     const int h = P.n - 1 - TB;
-    const dim3 grid((unsigned)P.n << h, P.nj);
+    const int nodes = up_nodes(P);
+    const dim3 grid((unsigned)nodes << h, P.nj);
     const size_t sc = upzeta13_cols_smem_bytes(P), sm = upzeta13_smem_bytes(P);
     uint64_t nrow = 0;
     for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
@@ -1184,7 +1186,7 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         const int cpb = h <= 11 ? 8 : (h == 12 ? 4 : 2);
         uint64_t ncol = 0;
         for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
-        const unsigned nblk = (unsigned)((uint64_t)P.n * ((ncol + cpb - 1) / cpb));
+        const unsigned nblk = (unsigned)((uint64_t)nodes * ((ncol + cpb - 1) / cpb));
         const size_t smb = ((size_t)cpb << h) * 4;
         if (cpb == 8)
             launch_or_record(KID_COLB8, k_upzeta13_colb<8>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
@@ -1196,15 +1198,15 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
             launch_or_record(KID_COLB2, k_upzeta13_colb<2>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
                                                                   (const float*)tab, (float*)A, P.js);
     } else if (nrow * 4 * 8 <= 160 * 1024) {          // warp per tile, 8 tiles per block
-        const uint64_t ntiles = (uint64_t)P.n << h;
+        const uint64_t ntiles = (uint64_t)nodes << h;
         const dim3 gw((unsigned)std::min<uint64_t>((ntiles + 7) / 8, 152 * 16), P.nj);
         const size_t sw = (size_t)nrow * 4 * 8;
         if (P.prec == 0)
             launch_or_record(KID_COLW_D, k_upzeta13_colw<double>, gw, 256, sw, s, P.n, P.d, P.K, (const double*)tab,
-                                                        (double*)A, P.js);
+                                                        (double*)A, P.js, nodes);
         else
             launch_or_record(KID_COLW_F, k_upzeta13_colw<float>, gw, 256, sw, s, P.n, P.d, P.K, (const float*)tab,
-                                                       (float*)A, P.js);
+                                                       (float*)A, P.js, nodes);
     } else if (P.prec == 0)
         launch_or_record(KID_COLS_D, k_upzeta13_cols<double>, grid, TT, sc, s, P.n, P.d, P.K, (const double*)tab, (double*)A,
                                                      P.js);

@@ -28,9 +28,9 @@ def torch_ctx():
     c.close()
 
 
-def run_split(torch, ctx, job, world):
+def run_split(torch, ctx, job, world, divide_a=False):
     n = job.n
-    shards = [B.Shard(ctx.h, job, r, world) for r in range(world)]
+    shards = [B.Shard(ctx.h, job, r, world, divide_a) for r in range(world)]
     try:
         nb = sh.max_step_bytes(shards[0])
         bufs = [torch.zeros(nb, dtype=torch.uint8, device="cuda") for _ in shards]
@@ -42,6 +42,7 @@ def run_split(torch, ctx, job, world):
         with torch.cuda.stream(stream):
             sh.run_virtual(shards, bufs, parts, lpd, stream)
         stream.synchronize()
+        run_split.bytes = [x.bytes() for x in shards]
         return [p.cpu().numpy() for p in parts], float(lpd.item())
     finally:
         for s in shards:
@@ -76,6 +77,53 @@ def test_split_job_equals_whole_job_and_oracle(torch_ctx, n, d, arity, prec, wor
     ref = orc.edge_posteriors(ds.data, ds.arity, d)
     tol = 1e-9 if prec == "fp64" else 1e-4
     np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
+
+
+DIVIDED = [
+    # n, d, arity, precision, world: n - log2(world) >= 14 low variables
+    (15, 3, 2, "fp32", 2),
+    (16, 3, 2, "fp32", 4),
+    (17, 4, 3, "fp32", 8),
+    (15, 3, 2, "fp64", 2),
+    (16, 2, 3, "fp64", 4),
+]
+
+
+@pytest.mark.parametrize("n,d,arity,prec,world", DIVIDED)
+def test_divided_A_split_job(torch_ctx, n, d, arity, prec, world):
+    """BN_SHARD_DIVIDE_A: every rank holds only its slabs of A, computed
+    from the score table folded over its top bits.  The posteriors agree
+    with the whole job and the oracle within the method's tolerances, and a
+    rank holds well under the undivided shard's bytes."""
+    torch, ctx = torch_ctx
+    ds = datagen.random_dag_data(n=n, m=400, arity=arity, max_parents=3, alpha=1.0, seed=n + 7 * world)
+    job = B.Job(ds.data, ds.arity, d, precision=prec)
+    parts, lpd = run_split(torch, ctx, job, world, divide_a=True)
+    divided = run_split.bytes
+    for r, p in enumerate(parts):
+        own = np.array([v % world == r for v in range(n)])
+        assert np.all(p[:, ~own] == 0.0)
+    post = np.sum(parts, axis=0)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    whole, lpd_whole = ctx.edge_posteriors(ds.data, ds.arity, d, precision=prec)
+    np.testing.assert_allclose(post, whole, atol=tol, rtol=0)
+    assert abs(lpd - lpd_whole) <= (1e-9 if prec == "fp64" else 1e-3) * max(1.0, abs(lpd_whole))
+    ref = orc.edge_posteriors(ds.data, ds.arity, d)
+    np.testing.assert_allclose(post, ref["post"], atol=tol, rtol=0)
+    run_split(torch, ctx, job, world)
+    undivided = run_split.bytes
+    print(f"n={n} W={world} {prec}: bytes per rank {divided[0]} divided, {undivided[0]} whole A; "
+          f"max |split - whole| {np.abs(post - whole).max():.2e}")
+    assert max(divided) < 0.8 * min(undivided)
+
+
+def test_divided_A_needs_14_low_variables(torch_ctx):
+    torch, ctx = torch_ctx
+    ds = datagen.random_dag_data(n=15, m=100, arity=2, max_parents=2, alpha=1.0, seed=5)
+    job = B.Job(ds.data, ds.arity, 2, precision="fp32")
+    with pytest.raises(B.BnError) as e:
+        B.Shard(ctx.h, job, 0, 4, divide_a=True)     # 13 low variables
+    assert e.value.code == B.BN_EINVAL
 
 
 def test_split_rejects_bad_worlds(torch_ctx):
