@@ -1790,14 +1790,27 @@ cudaError_t launch_gamma_p1(const Plan& P, const void* F, const void* Rc, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s)
+// Phase 2's columns: those before c0 (at least two high elements left) go to
+// the block butterfly kernel, the others (at least d - 1 low elements) to
+// the warp kernel.
+uint32_t gamma_p2_split(const Plan& P)
 {
-    // columns with at least d - 1 low elements: the warp kernel; the others
-    // (at least two high elements left): the block butterfly kernel
     const int h = P.n - 1 - P.b_g;
     uint32_t c0 = 0;
     for (int k = 0; k <= P.d - 2 && k <= P.b_g; ++k) c0 += host_binom(P.b_g, k);
     if (h > 17) c0 = P.nlow_g;                      // beyond the warp kernel's bit count
+    return c0;
+}
+
+int gamma_launches(const Plan& P)
+{
+    const uint32_t c0 = gamma_p2_split(P);
+    return 1 + (P.prec != 0 ? 1 : 0) + (c0 > 0 ? 1 : 0) + (c0 < P.nlow_g ? 1 : 0);
+}
+
+cudaError_t launch_gamma_p2(const Plan& P, const void* W, void* Gam, cudaStream_t s)
+{
+    const uint32_t c0 = gamma_p2_split(P);
     if (c0 > 0) {
         const size_t sm2 = gamma_p2_smem_bytes(P);
         const dim3 grid(c0, P.nj, P.n);

@@ -167,6 +167,20 @@ struct Plan {
 };
 inline int up_nodes(const Plan& P) { return P.nodes ? P.nodes : P.n; }
 
+// Host check of m x n row-major data: every value below its variable's
+// arity.  Column maxima first (a loop the compiler vectorises), then one
+// comparison per variable.
+inline bool data_below_arity(const uint8_t* data, int m, int n, const uint8_t* arity)
+{
+    uint8_t mx[32] = {0};
+    const uint8_t* row = data;
+    for (int s = 0; s < m; ++s, row += n)
+        for (int v = 0; v < n; ++v) mx[v] = row[v] > mx[v] ? row[v] : mx[v];
+    for (int v = 0; v < n; ++v)
+        if (m > 0 && mx[v] >= arity[v]) return false;
+    return true;
+}
+
 // Step 1.  A batch group passes nj jobs js bytes apart (mj: each job's own
 // sample count, at the same stride); a single job leaves the defaults.
 cudaError_t launch_pack_planes(const uint8_t* data, int n, int m, int rmax, int W,
@@ -236,6 +250,8 @@ unsigned int bounds_line_levels();
 unsigned int bounds_line_mega();
 #endif
 cudaError_t launch_word_max(int* word, const int* other, cudaStream_t s);
+// Launches of step 4 (phase 1, the FP32 offset table, the phase-2 kernels).
+int gamma_launches(const Plan& P);
 // A split job's divided A: the folded score tables of the rank's virtual job
 // (nl low variables, nl + 2 (n - nl) tables of Kv families) and the top
 // variables' slabs from its A (bn_levels.cu).

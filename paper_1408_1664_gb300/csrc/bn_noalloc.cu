@@ -169,9 +169,8 @@ try {
             log_rho[k] = j->log_rho[k];
             if (!std::isfinite(log_rho[k])) return BN_EINVAL;
         }
-    if (!j->data_on_device)
-        for (size_t s = 0; s < (size_t)P.m * P.n; ++s)
-            if (j->data[s] >= arity[s % P.n]) return BN_EINVAL;
+    if (!j->data_on_device && P.m > 0 && !bn::data_below_arity(j->data, P.m, P.n, arity))
+        return BN_EINVAL;
     P.K = 0;
     for (int k = 0; k <= P.d; ++k) P.K += binom64(P.n - 1, k);
     P.W = P.m > 0 ? (P.m + 63) / 64 : 1;

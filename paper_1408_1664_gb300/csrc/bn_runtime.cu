@@ -200,10 +200,8 @@ int validate_and_plan(const bn_job_desc* j, HostJob& hj)
     hj.ess = j->ess;
     hj.data = j->data;
     hj.data_on_device = j->data_on_device != 0;
-    if (!hj.data_on_device && P.m > 0) {
-        for (size_t s = 0; s < (size_t)P.m * P.n; ++s)
-            if (j->data[s] >= hj.arity[s % P.n]) return BN_EINVAL;
-    }
+    if (!hj.data_on_device && P.m > 0 && !bn::data_below_arity(j->data, P.m, P.n, hj.arity.data()))
+        return BN_EINVAL;
     P.K = families(P.n, P.d);
     if (j->log_q) {
         if (log_weights(j->log_q, (size_t)P.n * P.n, hj.log_q)) return BN_EINVAL;
@@ -443,7 +441,7 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     if (ev) CK(cudaEventRecord(ev->ev[5], s));
     CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
     if (ev) CK(cudaEventRecord(ev->ev[6], s));
-    nl += P.prec != 0 ? 3 : 2;                  // FP32: the offset table first
+    nl += bn::gamma_launches(P);
     CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
                         B.at<void>(L.Gam), B.at<void>(L.F), err,
                         B.at<unsigned long long>(L.eacc), post_dev, logPD_dev, s));
@@ -1944,8 +1942,7 @@ try {
             const double had = t < (int)hj.log_rho.size() ? hj.log_rho[t] : 0.0;
             if (!(lr == had)) return BN_EINVAL;
         }
-        for (size_t x = 0; x < (size_t)P.m * P.n; ++x)
-            if (j.data[x] >= hj.arity[x % P.n]) return BN_EINVAL;
+        if (P.m > 0 && !bn::data_below_arity(j.data, P.m, P.n, hj.arity.data())) return BN_EINVAL;
     }
     if (cudaSetDevice(b->ctx->device) != cudaSuccess) return BN_ECUDA;
     int rc = ensure_e2e(b);
