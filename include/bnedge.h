@@ -432,6 +432,11 @@ int bn_debug_batch_drop(bn_batch* batch, int32_t depth, uint64_t polls);
  * line, or both 0 when every check passed.  In the other builds *line = -1
  * (no checks compiled). */
 int bn_debug_bounds(int32_t* line, int32_t* unit);
+/* The FP64 path's table-driven exp and log (after Tang's method) beside
+ * CUDA's own exp and log, evaluated on the current device for `count`
+ * host doubles x: out (4 * count host doubles) receives, per x, the
+ * library's exp, CUDA's exp, the library's log, CUDA's log. */
+int bn_debug_explog(const double* x, int64_t count, double* out);
 #endif /* BN_TESTING */
 
 #ifdef __cplusplus

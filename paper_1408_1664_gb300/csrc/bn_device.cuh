@@ -7,6 +7,8 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
+#include "bn_explog_tables.h"
+
 namespace bn {
 
 // ---------------------------------------------------------------------------
@@ -338,13 +340,80 @@ __device__ __forceinline__ float lg2_approx(float x)
     return y;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 exp and log by table-driven reduction (P. T. P. Tang, ACM TOMS 15(2),
+// 1989 and 16(4), 1990; tables in bn_explog_tables.h).  They take about half
+// the FP64 instructions of the CUDA functions, which bound the FP64 path.
+//   exp: x = k ln2/64 + r, |r| <= ln2/128 (k by one rounding, r by a two-part
+//        ln2/64); exp(x) = 2^(k>>6) 2^((k&63)/64) (1 + expm1(r)).  Below the
+//        normal range (x <
+//        -708.3) it returns 0, where the CUDA function returns a subnormal:
+//        every use here adds the result to terms larger by 2^50 or more.
+//        expm1 to degree 6: truncation below 2^-67.
+//   log: x = 2^e m, m in [1, 2); c_j = 1 + (2j + 1)/256 nearest m (j = the
+//        top 7 bits of m's fraction), m - c_j exact, r = (m - c_j)/c_j,
+//        |r| < 2^-8; log x = e ln2 + log c_j + log1p(r), log1p to degree 7
+//        (truncation below 2^-67).  The results are checked against CUDA's
+//        exp and log by a test (bn_debug_explog).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double exp_t(double x)
+{
+    using namespace explog;
+    if (!(x > -708.3)) return x != x ? x : 0.0;
+    if (x > 709.7) return __longlong_as_double(0x7ff0000000000000LL);
+    const double shifter = 6755399441055744.0;        // 1.5 * 2^52: rounds to an integer
+    const double t = fma(x, kInvLn2x64, shifter);
+    const int k = __double2loint(t);
+    const double kd = t - shifter;
+    double r = fma(-kd, kLn2x64Hi, x);
+    r = fma(-kd, kLn2x64Lo, r);
+    double p = fma(r, 1.0 / 720, 1.0 / 120);
+    p = fma(p, r, 1.0 / 24);
+    p = fma(p, r, 1.0 / 6);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p *= r;                                           // expm1(r)
+    const double tj = kExp2Frac[k & 63];
+    const double y = fma(tj, p, tj);
+    return y * __longlong_as_double((long long)((k >> 6) + 1023) << 52);
+}
+
+__device__ __forceinline__ double log_t(double x)
+{
+    using namespace explog;
+    long long bits = __double_as_longlong(x);
+    if (!(x > 0.0) || bits >= 0x7ff0000000000000LL) {  // 0, negative, NaN, +inf
+        if (x == 0.0) return __longlong_as_double((long long)0xfff0000000000000ULL);
+        return x > 0.0 ? x : __longlong_as_double(0x7ff8000000000000LL);
+    }
+    int e = 0;
+    if (bits < 0x0010000000000000LL) {                 // subnormal: scale up by 2^54
+        x *= 18014398509481984.0;
+        bits = __double_as_longlong(x);
+        e = -54;
+    }
+    e += (int)(bits >> 52) - 1023;
+    const int j = (int)(bits >> 45) & 127;
+    const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const double c = __longlong_as_double(0x3ff0000000000000LL | ((long long)(2 * j + 1) << 44));
+    const double r = (m - c) * kInvC[j];
+    double p = fma(r, -1.0 / 7, 1.0 / 6);            // log1p(r) = r + r^2 (-1/2 + r/3 - ...)
+    p = fma(p, -r, 0.2);
+    p = fma(p, r, -0.25);
+    p = fma(p, r, 1.0 / 3);
+    p = fma(p, r, -0.5);
+    const double q = fma(r * r, p, r);
+    const double ed = (double)e;
+    return fma(ed, kLn2Hi, kLogCHi[j]) + (fma(ed, kLn2Lo, kLogCLo[j]) + q);
+}
+
 template <typename T> struct LogOps;
 
 template <> struct LogOps<double> {
     static __device__ __forceinline__ double ninf() { return __longlong_as_double((long long)0xfff0000000000000ull); }
     // exp and log in this value's base
-    static __device__ __forceinline__ double ex(double x) { return exp(x); }
-    static __device__ __forceinline__ double lg(double x) { return log(x); }
+    static __device__ __forceinline__ double ex(double x) { return exp_t(x); }
+    static __device__ __forceinline__ double lg(double x) { return log_t(x); }
     // log(exp(a) + exp(b))
     static __device__ __forceinline__ double lse(double a, double b)
     {

@@ -1419,6 +1419,20 @@ __global__ void k_copy_segments(const CopySeg* __restrict__ segs, int nseg)
 // ===========================================================================
 // Launchers.
 // ===========================================================================
+// exp_t / log_t (bn_device.cuh) beside CUDA's exp / log, for the test of
+// the table-driven functions: out[4i..4i+3] = exp_t, exp, log_t, log of x[i].
+__global__ void k_explog_check(const double* __restrict__ x, int64_t count, double* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        out[4 * i] = exp_t(v);
+        out[4 * i + 1] = exp(v);
+        out[4 * i + 2] = log_t(v);
+        out[4 * i + 3] = log(v);
+    }
+}
+
 #ifndef BN_MEGA  // host launchers (bn_mega.cu includes only the device code)
 #ifdef BN_CHECK_BOUNDS
 BN_BOUNDS_READER(bounds_line_kernels)
@@ -1860,6 +1874,13 @@ cudaError_t launch_edges(const Plan& P, const double* logB, const double* cmax,
         launch_or_record(KID_EDGES_FIN_F, k_edges_fin<float>, dim3(1, P.nj), rec_block(1024), 0, s, P.n, 1, fixed_bits(P.K), cmax,
                                                           (const float*)F, err, acc, post,
                                                           log_PD, P.js, P.vsel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_explog_check(const double* x, int64_t count, double* out, cudaStream_t s)
+{
+    if (count < 1) return cudaSuccess;
+    k_explog_check<<<(unsigned)std::min<int64_t>((count + 255) / 256, 152 * 8), 256, 0, s>>>(x, count, out);
     return cudaGetLastError();
 }
 

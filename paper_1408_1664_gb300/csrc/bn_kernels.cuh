@@ -250,6 +250,7 @@ unsigned int bounds_line_levels();
 unsigned int bounds_line_mega();
 #endif
 cudaError_t launch_word_max(int* word, const int* other, cudaStream_t s);
+cudaError_t launch_explog_check(const double* x, int64_t count, double* out, cudaStream_t s);
 // Launches of step 4 (phase 1, the FP32 offset table, the phase-2 kernels).
 int gamma_launches(const Plan& P);
 // A split job's divided A: the folded score tables of the rank's virtual job

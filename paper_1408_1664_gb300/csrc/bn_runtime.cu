@@ -2016,6 +2016,29 @@ try {
     return exception_code();
 }
 
+// Test hook: the FP64 table-driven exp and log beside CUDA's, on the
+// current device.
+int bn_debug_explog(const double* x, int64_t count, double* out)
+try {
+    if (!x || !out || count < 0) return BN_EINVAL;
+    if (count == 0) return BN_OK;
+    double* dx = nullptr;
+    double* dout = nullptr;
+    CK(cudaMalloc(&dx, (size_t)count * 8));
+    if (cudaMalloc(&dout, (size_t)count * 32) != cudaSuccess) {
+        cudaFree(dx);
+        return BN_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(dx, x, (size_t)count * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = bn::launch_explog_check(dx, count, dout, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)count * 32, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dout);
+    return e == cudaSuccess ? BN_OK : BN_ECUDA;
+} catch (...) {
+    return exception_code();
+}
+
 // Test hook: the first failing index check of the BN_CHECK_BOUNDS build.
 int bn_debug_bounds(int32_t* line, int32_t* unit)
 try {
