@@ -84,7 +84,15 @@ def checked_build() -> bool:
     return os.environ.get("BN_CHECK_BOUNDS") == "1"
 
 
+def asan_build() -> bool:
+    """The host-sanitizer build (the process must preload libasan and
+    libubsan) is loaded when the environment sets BN_ASAN=1."""
+    return os.environ.get("BN_ASAN") == "1"
+
+
 def library_path() -> str:
+    if asan_build():
+        return _build.LIB_ASAN
     if checked_build():
         return _build.LIB_CHECKED
     return _build.LIB_TESTING if testing_build() else _build.LIB
@@ -97,7 +105,12 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         return _lib
     path = library_path()
     if build_if_missing:
-        _build.build_checked() if checked_build() else _build.build()
+        if asan_build():
+            _build.build_asan()
+        elif checked_build():
+            _build.build_checked()
+        else:
+            _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} is missing "
                            "(run __graft_entry__.build()); there is no CPU fallback")

@@ -6,9 +6,11 @@ release build) and ``_build/libbnedge_testing.so``, the same objects plus the
 test hooks of the header's BN_TESTING section (the runtime unit compiled a
 second time with BN_TESTING defined).  ``_build/libbnpeaks.so`` holds the
 arithmetic-rate probes the benchmark uses for its ALU rooflines.
-``build_checked`` makes a third, debug library on request,
+``build_checked`` makes a debug library on request,
 ``_build/libbnedge_checked.so``: every unit compiled with BN_CHECK_BOUNDS
-(the kernels check the offsets they form; bn_device.cuh) and the test hooks.
+(the kernels check the offsets they form; bn_device.cuh) and the test hooks;
+``build_asan`` makes ``_build/libbnedge_asan.so``, the host code built with
+AddressSanitizer and UndefinedBehaviorSanitizer.
 No torch headers are involved.
 """
 from __future__ import annotations
@@ -27,6 +29,7 @@ LIB = os.path.join(OUTDIR, "libbnedge.so")
 LIB_TESTING = os.path.join(OUTDIR, "libbnedge_testing.so")
 LIB_PEAKS = os.path.join(OUTDIR, "libbnpeaks.so")
 LIB_CHECKED = os.path.join(OUTDIR, "libbnedge_checked.so")
+LIB_ASAN = os.path.join(OUTDIR, "libbnedge_asan.so")
 SOURCES = ["bn_kernels.cu", "bn_tile13.cu", "bn_levels.cu", "bn_runtime.cu", "bn_noalloc.cu",
            "bn_mega.cu"]
 # extra nvcc flags per translation unit
@@ -93,16 +96,17 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     return LIB
 
 
-def build_checked(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if needed) and return the path of the BN_CHECK_BOUNDS debug
-    library (with the BN_TESTING hooks)."""
-    if (not force and os.path.exists(LIB_CHECKED)
-            and all(os.path.getmtime(f) <= os.path.getmtime(LIB_CHECKED) for f in _inputs())):
-        return LIB_CHECKED
-    odir = os.path.join(OUTDIR, "checked")
+def _build_variant(out: str, subdir: str, flags_extra: list, link_extra: list, force: bool,
+                   verbose: bool) -> str:
+    """Every unit compiled once more with flags_extra (the runtime unit also
+    with BN_TESTING) and linked into `out`."""
+    if (not force and os.path.exists(out)
+            and all(os.path.getmtime(f) <= os.path.getmtime(out) for f in _inputs())):
+        return out
+    odir = os.path.join(OUTDIR, subdir)
     os.makedirs(odir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                    "-I", CSRC, "--expt-relaxed-constexpr", "-DBN_CHECK_BOUNDS"]
+                    "-I", CSRC, "--expt-relaxed-constexpr"] + flags_extra
 
     def one(src):
         obj = os.path.join(odir, src.replace(".cu", ".o"))
@@ -117,13 +121,38 @@ def build_checked(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(one, SOURCES))
-    tmp = LIB_CHECKED + ".tmp"
-    r = subprocess.run([nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"],
+    tmp = out + ".tmp"
+    r = subprocess.run([nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"] + link_extra,
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_CHECKED)
-    return LIB_CHECKED
+    os.replace(tmp, out)
+    return out
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """Compile (if needed) and return the path of the BN_CHECK_BOUNDS debug
+    library (with the BN_TESTING hooks)."""
+    return _build_variant(LIB_CHECKED, "checked", ["-DBN_CHECK_BOUNDS"], [], force, verbose)
+
+
+# one flag per sanitizer: nvcc splits -Xcompiler arguments at commas
+SANITIZE = ["-fsanitize=address", "-fsanitize=undefined", "-fno-omit-frame-pointer",
+            "-fno-sanitize-recover=all"]
+
+
+def build_asan(force: bool = False, verbose: bool = False) -> str:
+    """Compile (if needed) and return the path of the library whose host code
+    is built with AddressSanitizer and UndefinedBehaviorSanitizer (and the
+    BN_TESTING hooks).  A process loading it must preload the sanitizer
+    runtimes (LD_PRELOAD of libasan and libubsan)."""
+    flags = []
+    for f in SANITIZE:
+        flags += ["-Xcompiler", f]
+    link = []
+    for f in SANITIZE[:2]:
+        link += ["-Xcompiler", f]
+    return _build_variant(LIB_ASAN, "asan", flags + ["-g"], link, force, verbose)
 
 
 if __name__ == "__main__":
