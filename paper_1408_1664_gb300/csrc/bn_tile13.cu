@@ -796,8 +796,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* A0 = reinterpret_cast<T*>(smem_raw);
     T* A1 = A0 + TN;
-    using O = typename OrdInt<T>::type;
-    O* tmax = reinterpret_cast<O*>(A1 + TN);     // largest column sum
+    T* wmax = A1 + TN;                           // each warp's largest column sum
     const uint32_t ncol = num_small_subsets(TB, d);
     const int h = n - 1 - TB;
     const int t = threadIdx.x, lane = t & 31;
@@ -816,7 +815,6 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     // |el1(r, t)| = |r| + |t| (disjoint bits): the slots with more than d
     // elements are no column (no input)
     const int pt = __popc(t);
-    if (t == 0) *tmax = ord_enc(Lg::ninf());
     T tm = Lg::ninf();
     for (uint32_t c = t; c < ncol; c += TT) {
         const T v = out[c];
@@ -828,9 +826,11 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
         const T o2 = __shfl_xor_sync(FULLMASK, tm, o);
         tm = o2 > tm ? o2 : tm;
     }
-    __syncthreads();                             // tmax initialised; column reads done
-    if (lane == 0) atomicMax(tmax, ord_enc(tm));
-    __syncthreads();
+    if (lane == 0) wmax[t >> 5] = tm;
+    __syncthreads();                             // columns placed, warp maxima written
+    T tmx = wmax[0];
+#pragma unroll
+    for (int w = 1; w < TT / 32; ++w) tmx = wmax[w] > tmx ? wmax[w] : tmx;
 
     // --- single-scale passes (Window): pass p sums linear values 2^(x - s_p)
     //     (e^(x - s_p) in FP64) with s_p = M - top - p * win and writes the
@@ -840,7 +840,7 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     //     Window::max_pass passes take the banded path below.
     {
         using Wn = Window<T>;
-        const T M = ord_dec(*tmax) + T(TB);
+        const T M = tmx + T(TB);
         const T span = M - A1[0];
         // spans past max_pass windows (a zero weight held as -1e7 nats gives an
         // empty-set column far below the rest) and NaN go to the exact path
@@ -1140,7 +1140,7 @@ size_t upzeta13_cols_smem_bytes(const Plan& P)
 size_t upzeta13_smem_bytes(const Plan& P)
 {
     const size_t es = P.prec == 0 ? 8 : 4;
-    return (size_t)TN * (2 * es) + 16;
+    return (size_t)TN * (2 * es) + (TT / 32) * es;   // A0, A1, the warps' maxima
 }
 
 bool tile13_up_fits(const Plan& P)
