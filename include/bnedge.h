@@ -30,7 +30,7 @@
  *     lowest-numbered parent least significant; cell = config*r_i + x_i;
  *   - post is n x n row-major, post[u*n + v] = P(u->v | D), diagonal 0;
  *   - an in-degree bound d > n-1 is treated as d = n-1;
- *   - limits: 1 <= n <= 31, d >= 0, m >= 0 (m = 0 is valid input),
+ *   - limits: 1 <= n <= 32, d >= 0, m >= 0 (m = 0 is valid input),
  *     1 <= arity[i] <= 255, at most 65536 cells (q*r_i) per family.
  *
  * Errors: every function returns BN_OK (0) or a negative BN_E* code and never
@@ -174,7 +174,17 @@ int bn_feature_posterior(bn_ctx* ctx, const bn_job_desc* job, const double* log_
                          double* log_PfD);
 
 /* Steps 1-5 (Algorithm 1).  post: n*n host doubles; log_PD: host double or
- * NULL.  Blocks until the result is in the host buffers. */
+ * NULL.  Blocks until the result is in the host buffers.
+ *
+ * Jobs larger than the device budget (this and bn_edge_posteriors_async):
+ * when a job's arrays exceed the context's mem_budget, A (Eq. 7, the
+ * n 2^(n-1) values that dominate) moves to one managed allocation: as much
+ * of it as the budget leaves beside the other arrays is kept in device
+ * memory, the rest in host memory, which the kernels read and write in place
+ * over the CPU-GPU link (the same kernels and order: the results equal the
+ * in-core run bit for bit, only slower).  BN_ENOMEM when the other arrays
+ * alone exceed the budget or the host part exceeds 3/4 of the host memory
+ * available.  This is how n = 32 runs on one GB300 (FP32: A is 275 GB). */
 int bn_edge_posteriors(bn_ctx* ctx, const bn_job_desc* job, double* post,
                        double* log_PD);
 

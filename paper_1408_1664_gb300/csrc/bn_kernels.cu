@@ -978,7 +978,7 @@ k_backward_level(int n, int wb, int hl, uint32_t ntiles, int tpw, const T* __res
     const uint32_t wmask = (1u << wb) - 1u;
     const uint32_t lb = (uint32_t)lane & wmask;
     const bool active = lane < (1 << wb);
-    const uint32_t full = (1u << n) - 1u;
+    const uint32_t full = (uint32_t)(((uint64_t)1 << n) - 1);   // n <= 32
     const uint32_t hmask = (1u << nh) - 1u;
     const size_t half = (size_t)1 << (n - 1);
     uint32_t Ht = colex_unrank(first, hl, nh);
@@ -1215,7 +1215,7 @@ __global__ void __launch_bounds__(256)
 k_gamma_p2s(int n, int d, int b, uint32_t nlow, uint32_t c0, int64_t K, const T* __restrict__ W,
             T* __restrict__ Gam, size_t js, uint32_t vsel)
 {
-    constexpr int MB = 13;                          // high bits from 5 up (h <= 17)
+    constexpr int MB = 14;                          // high bits from 5 up (h <= 18, n <= 32)
     const int v = blockIdx.z;
     if (!(vsel >> v & 1u)) return;
     W = job_ptr(W, js) + ((size_t)endpoint_slot(vsel, v) << (n - 1 - b)) * nlow;
@@ -1300,7 +1300,7 @@ k_edges_acc(int n, int64_t K, int qbits, const double* __restrict__ logB,
     if (tid < 32) Nu[tid] = 0ull;
     if (tid == 0) Nz = 0ull;
     __syncthreads();
-    const uint32_t full = (1u << n) - 1u;
+    const uint32_t full = (uint32_t)(((uint64_t)1 << n) - 1);   // n <= 32
     // FP32: Gamma is relative to the integer Z = floor of log P(D) in the
     // level-based units (see gamma_offsets), so P(D) enters as F(V) - Z
     const double fv = (double)F[full];
@@ -1350,7 +1350,7 @@ __global__ void k_edges_fin(int n, int use_z, int qbits, const double* __restric
     if (threadIdx.x == 0 && log_PD) {
         double c = 0.0;
         for (int i = 0; i < n; ++i) c += cmax[i];
-        double fv = (double)F[(1u << n) - 1u];
+        double fv = (double)F[((size_t)1 << n) - 1];
         if (sizeof(T) == 4)                       // FP32: add the level base of F(V)
             fv += level_base_fwd(level_words(reinterpret_cast<const float*>(F), n), n - kLevelShift);
         *log_PD = bad ? NAN : LogOps<T>::to_ln(fv) + c;
@@ -1812,7 +1812,7 @@ uint32_t gamma_p2_split(const Plan& P)
     const int h = P.n - 1 - P.b_g;
     uint32_t c0 = 0;
     for (int k = 0; k <= P.d - 2 && k <= P.b_g; ++k) c0 += host_binom(P.b_g, k);
-    if (h > 17) c0 = P.nlow_g;                      // beyond the warp kernel's bit count
+    if (h > 18) c0 = P.nlow_g;                      // beyond the warp kernel's bit count
     return c0;
 }
 

@@ -164,6 +164,10 @@ struct Plan {
     // low n - shard_k nodes' slabs (top bits = the rank's) and, for each top
     // variable, a slab over the low variables.
     int slab = 0;
+    // A in a managed allocation outside the layout: its first part resident
+    // in device memory, the rest in host memory that the GPU reads and
+    // writes directly (a job whose arrays exceed the device budget).
+    int spill = 0;
 };
 inline int up_nodes(const Plan& P) { return P.nodes ? P.nodes : P.n; }
 

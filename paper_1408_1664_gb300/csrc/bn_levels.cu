@@ -28,7 +28,7 @@ namespace {
 
 constexpr int LB = 4;             // low bits of an FP32 tile
 constexpr int LB64 = 3;           // low bits of an FP64 tile
-constexpr int BT = 28;            // binomial table rows (n - B < 28)
+constexpr int BT = 29;            // binomial table rows (n - B < 29: n <= 32 in FP32)
 
 __device__ const BinomTable g_binom_lanes = make_binom_table();
 

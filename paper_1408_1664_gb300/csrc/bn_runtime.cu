@@ -10,6 +10,7 @@
 #include <stdexcept>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <array>
@@ -95,7 +96,9 @@ Layout make_layout(const Plan& P, size_t dbg_cells, bool feature = false)
     // sized for every schedule that fits, so that a plan can switch kernels
     L.tab = take(bn::tile13_up_fits(P) ? nK * es : 0);
     L.rk13 = take(bn::tile13_gamma_fits(P) ? bn::kRank13Bytes : 0);
-    L.A = take(P.slab ? 0 : ((size_t)P.n << (P.n - 1)) * es);   // a split job with divided A: its own slabs
+    // a split job with divided A holds its own slabs; a spilled job's A is a
+    // managed allocation of its own
+    L.A = take((P.slab || P.spill) ? 0 : ((size_t)P.n << (P.n - 1)) * es);
     // F and R' are each followed by the per-level words of the FP32 bases
     L.F = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4);
     L.Rc = take(((size_t)1 << P.n) * es + (bn::kLevelWords + bn::kGammaTabWords) * 4);
@@ -173,7 +176,7 @@ std::vector<char> working_logs(const std::vector<double>& v, int prec)
 int validate_and_plan(const bn_job_desc* j, HostJob& hj)
 {
     if (!j) return BN_EINVAL;
-    if (j->n < 1 || j->n > 31 || j->d < 0 || j->m < 0 || !j->arity) return BN_EINVAL;
+    if (j->n < 1 || j->n > 32 || j->d < 0 || j->m < 0 || !j->arity) return BN_EINVAL;
     if (j->m > 0 && !j->data) return BN_EINVAL;
     if (!(j->ess > 0.0) || !std::isfinite(j->ess)) return BN_EINVAL;
     if (j->precision != BN_FP64 && j->precision != BN_FP32_SHIFTED) return BN_EINVAL;
@@ -289,7 +292,9 @@ struct Events {
 struct Bufs {
     char* base = nullptr;
     Layout L{};
+    char* A_ext = nullptr;           // A outside the layout (a job whose A is spilled)
     template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+    void* A() const { return A_ext ? (void*)A_ext : (void*)(base + L.A); }
 };
 
 int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, double* post_dev,
@@ -395,9 +400,9 @@ int enqueue_upzeta(const Plan& P, const Bufs& B, const void* lbs, cudaStream_t s
 {
     const Layout& L = B.L;
     CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), lbs, B.at<void>(L.tab),
-                         B.at<uint16_t>(L.rk13), B.at<void>(L.A), s, sums_done));
+                         B.at<uint16_t>(L.rk13), B.A(), s, sums_done));
     *nl += bn::use_tile13_up(P) ? 3 : 1;
-    if (P.hasq) { CK(bn::launch_apply_q(P, B.at<void>(L.logq), B.at<void>(L.A), s)); ++*nl; }
+    if (P.hasq) { CK(bn::launch_apply_q(P, B.at<void>(L.logq), B.A(), s)); ++*nl; }
     return BN_OK;
 }
 
@@ -419,16 +424,16 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
     if (side && side->s) {
         CK(cudaEventRecord(side->fork, s));
         CK(cudaStreamWaitEvent(side->s, side->fork, 0));
-        CK(bn::launch_backward(P, B.at<void>(L.A), B.at<void>(L.Rc), side->s, &nl));
+        CK(bn::launch_backward(P, B.A(), B.at<void>(L.Rc), side->s, &nl));
         if (ev) CK(cudaEventRecord(ev->ev[kEvR], side->s));
         CK(cudaEventRecord(side->join, side->s));
-        CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
+        CK(bn::launch_forward(P, B.A(), B.at<void>(L.F), s, &nl));
         if (ev) CK(cudaEventRecord(ev->ev[3], s));
         CK(cudaStreamWaitEvent(s, side->join, 0));
     } else {
-        CK(bn::launch_forward(P, B.at<void>(L.A), B.at<void>(L.F), s, &nl));
+        CK(bn::launch_forward(P, B.A(), B.at<void>(L.F), s, &nl));
         if (ev) CK(cudaEventRecord(ev->ev[3], s));
-        CK(bn::launch_backward(P, B.at<void>(L.A), B.at<void>(L.Rc), s, &nl));
+        CK(bn::launch_backward(P, B.A(), B.at<void>(L.Rc), s, &nl));
         if (ev) CK(cudaEventRecord(ev->ev[kEvR], s));
     }
     if (ev) {
@@ -436,8 +441,7 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
         ev->overlap = side && side->s;
     }
     CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
-                           B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr,
-                           B.at<void>(L.A)));
+                           B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr, B.A()));
     if (ev) CK(cudaEventRecord(ev->ev[5], s));
     CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
     if (ev) CK(cudaEventRecord(ev->ev[6], s));
@@ -526,6 +530,10 @@ struct bn_ctx {
     // direct path workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
+    // a spilled job's A: managed memory, its first spill_dev bytes preferred
+    // in device memory, the rest in host memory mapped for the GPU
+    char* spill = nullptr;
+    size_t spill_bytes = 0, spill_dev = 0;
     char* pin = nullptr;
     size_t pin_bytes = 0;
     static constexpr int kRing = 32;
@@ -659,18 +667,91 @@ size_t small_bytes(const Plan& P)
     return al(P.n) + al((size_t)(P.d + 1) * 8) + 2 * al((size_t)P.rows * 8) + 1024;
 }
 
+// Host memory the kernel reports available (bytes; 0 if unknown).
+size_t host_available()
+{
+    FILE* f = std::fopen("/proc/meminfo", "r");
+    if (!f) return 0;
+    char line[256];
+    size_t kb = 0;
+    while (std::fgets(line, sizeof line, f))
+        if (std::sscanf(line, "MemAvailable: %zu kB", &kb) == 1) break;
+    std::fclose(f);
+    return kb * 1024;
+}
+
+// A spilled job's A (a_bytes): one managed allocation, its first dev_part
+// bytes preferred in device memory and prefetched there, the rest preferred
+// in host memory, mapped for the GPU (which reads and writes it in place over
+// the CPU-GPU link) and prefetched there.  Kept for the next job of the
+// same size.
+int ensure_spill(bn_ctx* c, size_t a_bytes, size_t dev_part, cudaStream_t s)
+{
+    if (c->spill && c->spill_bytes == a_bytes && c->spill_dev == dev_part) return BN_OK;
+    if (c->spill) {
+        cudaStreamSynchronize(s);
+        cudaFree(c->spill);
+        c->spill = nullptr;
+        c->spill_bytes = c->spill_dev = 0;
+    }
+    if (c->fail_after >= 0 && c->allocs >= c->fail_after) return BN_ENOMEM;
+    void* p = nullptr;
+    if (cudaMallocManaged(&p, a_bytes, cudaMemAttachGlobal) != cudaSuccess) {
+        cudaGetLastError();
+        return BN_ENOMEM;
+    }
+    ++c->allocs;
+    c->spill = (char*)p;
+    c->spill_bytes = a_bytes;
+    c->spill_dev = dev_part;
+    cudaMemLocation gpu{}, host{};
+    gpu.type = cudaMemLocationTypeDevice;
+    gpu.id = c->device;
+    host.type = cudaMemLocationTypeHost;
+    host.id = 0;
+    const size_t host_part = a_bytes - dev_part;
+    if (dev_part) {
+        CK(cudaMemAdvise(c->spill, dev_part, cudaMemAdviseSetPreferredLocation, gpu));
+        CK(cudaMemPrefetchAsync(c->spill, dev_part, gpu, 0, s));
+    }
+    if (host_part) {
+        CK(cudaMemAdvise(c->spill + dev_part, host_part, cudaMemAdviseSetPreferredLocation, host));
+        CK(cudaMemAdvise(c->spill + dev_part, host_part, cudaMemAdviseSetAccessedBy, gpu));
+        CK(cudaMemPrefetchAsync(c->spill + dev_part, host_part, host, 0, s));
+    }
+    return BN_OK;
+}
+
 int run_direct(bn_ctx* c, const bn_job_desc* job, HostJob& hj, double* post_dev,
                double* logPD_dev, cudaStream_t s)
 {
-    const Layout L = make_layout(hj.P, 0);
+    Layout L = make_layout(hj.P, 0);
+    size_t a_bytes = 0, dev_part = 0;
+    if (L.total > c->budget) {
+        // the job's arrays exceed the device budget: A goes to managed
+        // memory, as much of it in device memory as the budget leaves, the
+        // rest in host memory (at most 3/4 of what the host has available)
+        Plan& P = hj.P;
+        P.spill = 1;
+        L = make_layout(P, 0);
+        a_bytes = ((size_t)P.n << (P.n - 1)) * (P.prec == 0 ? 8 : 4);
+        if (L.total >= c->budget) return BN_ENOMEM;
+        const size_t gran = (size_t)2 << 20;
+        dev_part = std::min<size_t>(a_bytes, (size_t)(c->budget - L.total)) / gran * gran;
+        if (a_bytes - dev_part > host_available() / 4 * 3) return BN_ENOMEM;
+    }
     char* old_ws = c->ws;
     int rc = ensure_ws(c, L.total);
     if (rc) return rc;
+    if (a_bytes) {
+        rc = ensure_spill(c, a_bytes, dev_part, s);
+        if (rc) return rc;
+    }
     rc = ensure_pin(&c->pin, &c->pin_bytes, small_bytes(hj.P) + 64);
     if (rc) return rc;
     Events& ev = c->ring[c->ring_pos % bn_ctx::kRing];
     if (!ev.ok && (rc = ev.create())) return rc;
-    Bufs B{c->ws, L};
+    Bufs B{c->ws, L, a_bytes ? c->spill : nullptr};
     // The small tables (arity, log rho, lgamma rows) are uploaded only when
     // they differ from the ones already in the workspace; the pinned staging
     // buffer is rewritten only after earlier work has drained.
@@ -823,6 +904,7 @@ try {
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     if (c->ws) cudaFree(c->ws);
+    if (c->spill) cudaFree(c->spill);
     if (c->pin) cudaFreeHost(c->pin);
     for (auto& e : c->ring) e.destroy();
     c->side.destroy();
@@ -1152,7 +1234,8 @@ try {
     }
     if (bytes != want) return BN_EINVAL;
     CK(cudaStreamSynchronize(c->stream));
-    CK(cudaMemcpy(host_out, c->ws + off, want, cudaMemcpyDeviceToHost));
+    const char* src = (stage == BN_STAGE_A && P.spill) ? c->spill : c->ws + off;   // a spilled A
+    CK(cudaMemcpy(host_out, src, want, cudaMemcpyDeviceToHost));
     if (stage == BN_STAGE_A && bn::use_tlo(P)) tlo_to_plain(P.n, static_cast<float*>(host_out));
     if (P.prec != 0 && (stage == BN_STAGE_F || stage == BN_STAGE_RC || stage == BN_STAGE_GAMMA))
         undo_level_bases(c, P, L, stage, static_cast<float*>(host_out));
