@@ -60,7 +60,7 @@ BAD = {
     "log_q_nan": lambda: _job(log_q=np.full((6, 6), np.nan)),
     "log_w_plus_inf": lambda: _job(log_w=np.full((6, K6), np.inf)),
     "too_many_cells": lambda: _job(data=np.zeros((3, 6), np.uint8), arity=[255] * 6),
-    "n_above_31": lambda: B.Job(np.zeros((2, 32), np.uint8), [2] * 32, 2),
+    "n_above_32": lambda: B.Job(np.zeros((2, 33), np.uint8), [2] * 33, 2),
 }
 
 
