@@ -168,6 +168,9 @@ struct Plan {
     // in device memory, the rest in host memory that the GPU reads and
     // writes directly (a job whose arrays exceed the device budget).
     int spill = 0;
+    // Step 4 in groups of vgroup endpoints (0: all at once), its scratch W
+    // sized for one group (a spilled job keeps more of A on the device).
+    int vgroup = 0;
 };
 inline int up_nodes(const Plan& P) { return P.nodes ? P.nodes : P.n; }
 

@@ -103,7 +103,8 @@ Layout make_layout(const Plan& P, size_t dbg_cells, bool feature = false)
     L.F = take(((size_t)1 << P.n) * es + bn::kLevelWords * 4);
     L.Rc = take(((size_t)1 << P.n) * es + (bn::kLevelWords + bn::kGammaTabWords) * 4);
     // one slice per endpoint computed (all n, or a split job's rank's)
-    const size_t nv = (size_t)__builtin_popcount(P.vsel & (uint32_t)(((uint64_t)1 << P.n) - 1));
+    const size_t nv = P.vgroup ? (size_t)P.vgroup
+                               : (size_t)__builtin_popcount(P.vsel & (uint32_t)(((uint64_t)1 << P.n) - 1));
     L.W = take(nv * ((size_t)1 << hg) * P.nlow_g * es);
     L.Gam = take(nK * es);
     L.eacc = take((size_t)P.n * (P.n + 1) * 8);
@@ -440,12 +441,28 @@ int enqueue_kernels(const HostJob& hj, const Bufs& B, const uint8_t* data_dev, d
         CK(cudaEventRecord(ev->ev[4], s));
         ev->overlap = side && side->s;
     }
-    CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
-                           B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr, B.A()));
-    if (ev) CK(cudaEventRecord(ev->ev[5], s));
-    CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
-    if (ev) CK(cudaEventRecord(ev->ev[6], s));
-    nl += bn::gamma_launches(P);
+    if (P.vgroup) {
+        // step 4 a group of endpoints at a time through one group's W (the
+        // phase timings then cover all groups: phase 1 ends with the last)
+        for (int v0 = 0; v0 < P.n; v0 += P.vgroup) {
+            Plan Q = P;
+            Q.vsel = 0;
+            for (int v = v0; v < std::min(P.n, v0 + P.vgroup); ++v) Q.vsel |= 1u << v;
+            CK(bn::launch_gamma_p1(Q, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
+                                   B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr, B.A()));
+            if (ev && v0 + P.vgroup >= P.n) CK(cudaEventRecord(ev->ev[5], s));
+            CK(bn::launch_gamma_p2(Q, B.at<void>(L.W), B.at<void>(L.Gam), s));
+            nl += bn::gamma_launches(Q);
+        }
+        if (ev) CK(cudaEventRecord(ev->ev[6], s));
+    } else {
+        CK(bn::launch_gamma_p1(P, B.at<void>(L.F), B.at<void>(L.Rc), B.at<uint16_t>(L.rk13),
+                               B.at<void>(L.W), s, P.hasq ? B.at<void>(L.logq) : nullptr, B.A()));
+        if (ev) CK(cudaEventRecord(ev->ev[5], s));
+        CK(bn::launch_gamma_p2(P, B.at<void>(L.W), B.at<void>(L.Gam), s));
+        if (ev) CK(cudaEventRecord(ev->ev[6], s));
+        nl += bn::gamma_launches(P);
+    }
     CK(bn::launch_edges(P, B.at<double>(L.logB), B.at<double>(L.cmax), B.at<uint32_t>(L.masks),
                         B.at<void>(L.Gam), B.at<void>(L.F), err,
                         B.at<unsigned long long>(L.eacc), post_dev, logPD_dev, s));
@@ -733,6 +750,7 @@ int run_direct(bn_ctx* c, const bn_job_desc* job, HostJob& hj, double* post_dev,
         // rest in host memory (at most 3/4 of what the host has available)
         Plan& P = hj.P;
         P.spill = 1;
+        P.vgroup = std::min(P.n, 8);              // the down-zeta scratch for 8 endpoints
         L = make_layout(P, 0);
         a_bytes = ((size_t)P.n << (P.n - 1)) * (P.prec == 0 ? 8 : 4);
         if (L.total >= c->budget) return BN_ENOMEM;
