@@ -430,6 +430,13 @@ int bn_debug_counts(bn_ctx* ctx, const bn_job_desc* job, int32_t i,
  * bn_batch_results returns BN_EDEVICE_TIMEOUT.  BN_EINVAL if the batch does
  * not run in the persistent form. */
 int bn_debug_batch_drop(bn_batch* batch, int32_t depth, uint64_t polls);
+/* The bounded wait of the persistent up-zeta tile kernel (FP32, n >= 14):
+ * one block runs with its first bulk copy of column sums withheld, so its
+ * mbarrier wait gives up after `polls` polls; *err_word receives the job
+ * error word that the kernel leaves (2: a device-side wait gave up, the
+ * value that makes a job return BN_EDEVICE_TIMEOUT).  The block returns
+ * without a fault and the context stays usable. */
+int bn_debug_copy_wait(uint32_t polls, int32_t* err_word);
 /* Index checks.  The BN_CHECK_BOUNDS build of the library
  * (_build/libbnedge_checked.so, a debug build with the test hooks) checks
  * the global-memory offsets its kernels form -- rows of A, F and R', the

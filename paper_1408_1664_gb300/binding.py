@@ -69,7 +69,7 @@ EXPORTS = ["bn_ctx_create", "bn_ctx_destroy", "bn_num_families", "bn_scores",
 
 # Test hooks: exported only by the testing build (BN_TESTING).
 TEST_EXPORTS = ["bn_debug_stage", "bn_debug_counts", "bn_debug_batch_drop", "bn_debug_bounds",
-                "bn_debug_explog"]
+                "bn_debug_explog", "bn_debug_copy_wait"]
 
 
 def testing_build() -> bool:
@@ -147,6 +147,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "bn_debug_batch_drop": (C.c_int, [P, C.c_int32, C.c_uint64]),
         "bn_debug_bounds": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "bn_debug_explog": (C.c_int, [P, C.c_int64, P]),
+        "bn_debug_copy_wait": (C.c_int, [C.c_uint32, C.POINTER(C.c_int32)]),
         "bn_shard_create": (C.c_int, [P, C.POINTER(bn_job_desc), C.c_int32, C.c_int32, C.c_int32,
                                       C.POINTER(P)]),
         "bn_shard_bytes": (C.c_int, [P, C.POINTER(C.c_uint64)]),

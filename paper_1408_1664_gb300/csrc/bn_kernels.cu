@@ -1682,12 +1682,12 @@ static int fixed_bits(int64_t terms)
 }
 
 cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
-                          const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done)
+                          const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done, int* err)
 {
     if (use_tile13_up(P)) {
         cudaError_t e = launch_reorder_up(P, lbs, tab, s);
         if (e != cudaSuccess) return e;
-        return launch_upzeta13(P, tab, rk13 + 8192, A, s, sums_done);
+        return launch_upzeta13(P, tab, rk13 + 8192, A, s, sums_done, err);
     }
     const int h = P.n - 1 - P.b_up;
     const dim3 grid((unsigned)P.n << h, P.nj);

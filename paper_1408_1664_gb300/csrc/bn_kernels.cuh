@@ -15,6 +15,11 @@ namespace bn {
 // batch records each job's launch sequence once and runs it inside one
 // persistent kernel (bn_mega.cu), which unpacks the arguments the same way.
 // ---------------------------------------------------------------------------
+// Bits of a job's device error word: 1 from the input check (a value not
+// below its variable's arity), kErrDeviceTimeout from a kernel whose bounded
+// wait for a bulk copy gave up.
+constexpr int kErrDeviceTimeout = 2;
+
 enum KernelId : int32_t {
     KID_NONE = 0,
     KID_PACK_PLANES, KID_CHECK_DATA, KID_LGAMMA_TABLE,
@@ -233,9 +238,12 @@ cudaError_t launch_shift_scores(const Plan& P, const double* logB, const double*
 // (n*K values, the scores reordered by high and low parts); smaller n use
 // one shared-memory tile per node slice and ignore `tab`.
 // `rk13` points at the two 8192-entry uint16 subset-rank tables (rank, then
-// inverse) of the 13-dimension tiles, filled by launch_rank13_tables.
+// inverse) of the 13-dimension tiles, filled by launch_rank13_tables.  `err`
+// (the job's error word) lets an FP32 single job use the persistent tile
+// kernel, which reports a bulk copy that never landed there.
 cudaError_t launch_upzeta(const Plan& P, const uint32_t* cmasks, const void* lbs, void* tab,
-                          const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done = nullptr);
+                          const uint16_t* rk13, void* A, cudaStream_t s, cudaEvent_t sums_done = nullptr,
+                          int* err = nullptr);
 // Step 3 in FP32 with one thread per 16-subset tile (bn_levels.cu).
 bool rows_levels_fit(const Plan& P);      // FP32 and 5 <= n < 32
 bool rows64_fit(const Plan& P);           // FP64 and 4 <= n < 31: 8-subset row tiles
@@ -300,7 +308,9 @@ size_t upzeta_smem_bytes(const Plan& P);
 cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStream_t s);
 cudaError_t launch_rank13_tables(const Plan& P, uint16_t* rank13, uint16_t* unrank13, cudaStream_t s);
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
-                            cudaStream_t s, cudaEvent_t sums_done = nullptr);
+                            cudaStream_t s, cudaEvent_t sums_done = nullptr, int* err = nullptr);
+cudaError_t launch_upzeta13p_withheld(float* A, uint16_t* rank13, uint16_t* unrank13, int* err,
+                                      uint32_t polls, cudaStream_t s);
 cudaError_t launch_gamma13_p1(const Plan& P, const void* F, const void* Rc,
                               const uint16_t* rank13, void* W, cudaStream_t s,
                               const void* lq = nullptr, const void* A = nullptr);

@@ -401,7 +401,7 @@ int enqueue_upzeta(const Plan& P, const Bufs& B, const void* lbs, cudaStream_t s
 {
     const Layout& L = B.L;
     CK(bn::launch_upzeta(P, B.at<uint32_t>(L.cmasks), lbs, B.at<void>(L.tab),
-                         B.at<uint16_t>(L.rk13), B.A(), s, sums_done));
+                         B.at<uint16_t>(L.rk13), B.A(), s, sums_done, B.at<int>(L.err)));
     *nl += bn::use_tile13_up(P) ? 3 : 1;
     if (P.hasq) { CK(bn::launch_apply_q(P, B.at<void>(L.logq), B.A(), s)); ++*nl; }
     return BN_OK;
@@ -824,6 +824,14 @@ static int exception_code() noexcept
     }
 }
 
+// A job's device error word as a status: the input check's bit is an
+// invalid input, kErrDeviceTimeout a device-side wait that gave up.
+static int err_word_status(int err) noexcept
+{
+    if (!err) return BN_OK;
+    return (err & bn::kErrDeviceTimeout) ? BN_EDEVICE_TIMEOUT : BN_EINVAL;
+}
+
 extern "C" {
 
 const char* bn_strerror(int code)
@@ -964,7 +972,7 @@ try {
     CK(cudaMemcpyAsync(&lpd, c->ws + L.logPD, 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&err, c->ws + L.err, 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (err) return BN_EINVAL;
+    if (err) return err_word_status(err);
     if (log_PD) *log_PD = lpd;
     Events& ev = c->ring[(c->ring_pos + bn_ctx::kRing - 1) % bn_ctx::kRing];
     fill_stats(P, ev, c->last_launches, &c->last_stats);
@@ -1101,7 +1109,7 @@ try {
     CK(cudaMemcpyAsync(cmax.data(), B.at<char>(L.cmax), (size_t)P.n * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&err, B.at<char>(L.err), 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (err) return BN_EINVAL;
+    if (err) return err_word_status(err);
     for (int k = 0; k < 2; ++k) {
         if (P.prec == 0) {
             std::memcpy(&fv[k], raw[k], 8);
@@ -2140,6 +2148,30 @@ try {
     return exception_code();
 }
 
+// Test hook: the persistent up-zeta tile kernel's bounded wait for a bulk
+// copy that never comes.
+int bn_debug_copy_wait(uint32_t polls, int32_t* err_word)
+try {
+    if (!err_word) return BN_EINVAL;
+    char* buf = nullptr;
+    const size_t abytes = 8192 * 4, tbytes = 2 * 8192 * 2;
+    CK(cudaMalloc(&buf, abytes + tbytes + 16));
+    float* A = reinterpret_cast<float*>(buf);
+    uint16_t* rk = reinterpret_cast<uint16_t*>(buf + abytes);
+    int* err = reinterpret_cast<int*>(buf + abytes + tbytes);
+    cudaError_t e = cudaMemset(buf, 0, abytes + tbytes + 16);
+    if (e == cudaSuccess) e = bn::launch_upzeta13p_withheld(A, rk, rk + 8192, err, polls, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int w = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&w, err, 4, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return BN_ECUDA;
+    *err_word = w;
+    return BN_OK;
+} catch (...) {
+    return exception_code();
+}
+
 // Test hook: the first failing index check of the BN_CHECK_BOUNDS build.
 int bn_debug_bounds(int32_t* line, int32_t* unit)
 try {
@@ -2293,7 +2325,7 @@ try {
         const Plan& V = sh->V;
         CK(bn::launch_fold_scores(P, V.n, V.K, P.shard_r, B.at<void>(L.lbs), sh->slab + sh->o_lbs, s));
         CK(bn::launch_upzeta(V, nullptr, sh->slab + sh->o_lbs, sh->slab + sh->o_tab,
-                             B.at<uint16_t>(L.rk13), sh->slab + sh->o_A, s, nullptr));
+                             B.at<uint16_t>(L.rk13), sh->slab + sh->o_A, s, nullptr, B.at<int>(L.err)));
         CK(bn::launch_top_slabs(V, P.shard_k, sh->slab + sh->o_A, sh->slab + sh->o_top, s));
     } else {
         rc = enqueue_upzeta(P, B, B.at<void>(L.lbs), s, &nl, nullptr);
@@ -2519,7 +2551,7 @@ void pump(bn_ctx* c)
         sj.post.assign((double*)sl.pin, (double*)sl.pin + (size_t)P.n * P.n);
         std::memcpy(&sj.logPD, sl.pin + (size_t)P.n * P.n * 8, 8);
         fill_stats(P, sl.ev, sl.launches, &sj.stats);
-        sj.rc = err ? BN_EINVAL : sj.rc;
+        sj.rc = err ? err_word_status(err) : sj.rc;
         sj.state = Q_DONE;
         c->reserved -= sl.bytes;
         sl.bytes = 0;

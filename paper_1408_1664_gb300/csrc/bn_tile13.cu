@@ -942,6 +942,181 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
     for (int r = 0; r < TR; ++r) out[BN_AT(opos(el1(r, t)), 1, TN)] = scaled_log(v[r], sc[r]);
 }
 
+// The same tiles (FP32) in a persistent kernel: each block takes tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Thread 0 keeps the next tile's
+// column sums in flight while the block transforms the current one (one bulk
+// copy into shared memory, counted by an mbarrier), and every finished tile
+// leaves as one 32 KB bulk store from a shared-memory staging block, so the
+// block's threads issue neither the loads nor the stores.  The arithmetic
+// and the outputs are those of k_upzeta13, bit for bit.  Shared memory: A0
+// (exchanges), A1 (inputs), the warps' maxima, the mbarrier and a flag, the
+// staged column sums (ncol floats rounded up to 16 bytes) and the output
+// block.  A bulk copy that has not landed after `cap` polls of its mbarrier
+// sets kErrDeviceTimeout in *err and the block returns after one more bounded
+// wait for it.  `hold` (a test hook, 0 otherwise) withholds the block's first
+// copy, so that its wait runs out.
+template <bool TLO>
+__global__ void __launch_bounds__(TT, 2)
+k_upzeta13p(int n, int d, const uint16_t* __restrict__ unrank13, float* __restrict__ A, uint32_t ntiles,
+            int* __restrict__ err, uint32_t cap, int hold)
+{
+    using Lg = LogOps<float>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* A0 = reinterpret_cast<float*>(smem_raw);
+    float* A1 = A0 + TN;
+    float* wmax = A1 + TN;                               // TT / 32 floats
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wmax + TT / 32);
+    int* gave_up = reinterpret_cast<int*>(bar + 1);
+    float* S = reinterpret_cast<float*>(bar + 2);       // staged column sums
+    const uint32_t ncol = num_small_subsets(TB, d);
+    const uint32_t sbytes = (ncol * 4u + 15u) & ~15u;
+    float* OUT = S + sbytes / 4;                         // the finished tile
+    const int h = n - 1 - TB;
+    const size_t asize = (size_t)ntiles << TB;
+    const int t = threadIdx.x, lane = t & 31;
+    const int pt = __popc(t);
+    if (t == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t tile = blockIdx.x;
+    if (t == 0 && tile < ntiles && !hold) bulk_load(S, A + BN_AT((size_t)tile << TB, TN, asize), sbytes, bar);
+    for (uint32_t parity = 0; tile < ntiles; tile += gridDim.x, parity ^= 1u) {
+        const int i = (int)(tile >> h);
+        float* out = A + BN_AT((size_t)tile << TB, TN, asize);
+        const int lw = i < 4 ? 3 : 4;
+        const uint32_t lmask = (1u << lw) - 1u;
+        auto opos = [&](uint32_t e) -> uint32_t {
+            if (!TLO) return e;
+            const uint32_t r = e >> lw;
+            return ((lw == 4 ? g_place.p9[r] : g_place.p10[r]) << lw) | (e & lmask);
+        };
+        if (t == 0) {
+            bulk_wait_read();                            // the last tile's store has read OUT
+            *gave_up = mbar_wait_bounded(bar, parity, cap) ? 0 : 1;
+        }
+        __syncthreads();
+        if (*gave_up) {
+            if (t == 0) {
+                atomicOr(err, kErrDeviceTimeout);
+                mbar_wait_bounded(bar, parity, cap);     // let a copy in flight land
+                bulk_wait();
+            }
+            return;
+        }
+        // |el1(r, t)| = |r| + |t| (disjoint bits): the slots with more than d
+        // elements are no column (no input)
+        float tm = Lg::ninf();
+        for (uint32_t c = t; c < ncol; c += TT) {
+            const float v = S[c];
+            A1[swz(BN_AT(unrank13[c], 1, TN))] = v;
+            tm = v > tm ? v : tm;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const float o2 = __shfl_xor_sync(FULLMASK, tm, o);
+            tm = o2 > tm ? o2 : tm;
+        }
+        if (lane == 0) wmax[t >> 5] = tm;
+        fence_async_shared();                            // S is read: the next copy may land
+        __syncthreads();
+        if (t == 0 && tile + gridDim.x < ntiles)
+            bulk_load(S, A + BN_AT((size_t)(tile + gridDim.x) << TB, TN, asize), sbytes, bar);
+        float tmx = wmax[0];
+#pragma unroll
+        for (int w = 1; w < TT / 32; ++w) tmx = wmax[w] > tmx ? wmax[w] : tmx;
+
+        // single-scale passes as in k_upzeta13
+        using Wn = Window<float>;
+        const float M = tmx + float(TB);
+        const float span = M - A1[0];
+        const int npass = span < Wn::win ? 1
+                          : span < float(Wn::max_pass) * Wn::win ? (int)ceilf(span / Wn::win)
+                                                                 : Wn::max_pass + 1;
+        if (npass == 1) {
+            const float sp = M - Wn::top;
+            float x[TR];
+            ld1(A1, x, t);
+#pragma unroll
+            for (int r = 0; r < TR; ++r) x[r] = (__popc(r) + pt <= d) ? Lg::ex(x[r] - sp) : 0.0f;
+            bfly_plain<true>(x, 0, 5);
+            st1(A0, x, t);
+            __syncthreads();
+            ld2(A0, x, t);
+            bfly_plain<true>(x, 0, 5);
+            st2(A0, x, t);
+            __syncthreads();
+            ld3(A0, x, t);
+            bfly_plain<true>(x, 0, 3);
+#pragma unroll
+            for (int r = 0; r < TR; ++r) x[r] = sp + Lg::lg(x[r]);
+            // a run of 8 consecutive elements stays inside one row (lw >= 3)
+#pragma unroll
+            for (int q = 0; q < TR / 8; ++q) {
+                float4* p = reinterpret_cast<float4*>(OUT + BN_AT(opos(el3(8 * q, t)), 8, TN));
+                p[0] = make_float4(x[8 * q], x[8 * q + 1], x[8 * q + 2], x[8 * q + 3]);
+                p[1] = make_float4(x[8 * q + 4], x[8 * q + 5], x[8 * q + 6], x[8 * q + 7]);
+            }
+        } else if (npass <= Wn::max_pass) {
+            uint32_t done = 0u;                          // bit r: output el3(r, t) written
+            uint32_t run3[TR / 8];
+#pragma unroll
+            for (int q = 0; q < TR / 8; ++q) run3[q] = BN_AT(opos(el3(8 * q, t)), 8, TN);
+            float sp = M - Wn::top;
+            for (int p = 0; p < npass; ++p, sp -= Wn::win) {
+                const bool last = p + 1 == npass;
+                float x[TR];
+                ld1(A1, x, t);
+#pragma unroll
+                for (int r = 0; r < TR; ++r) x[r] = (__popc(r) + pt <= d) ? Lg::ex(x[r] - sp) : 0.0f;
+                bfly_plain<true>(x, 0, 5);
+                st1(A0, x, t);
+                __syncthreads();
+                ld2(A0, x, t);
+                bfly_plain<true>(x, 0, 5);
+                st2(A0, x, t);
+                __syncthreads();
+                ld3(A0, x, t);
+                bfly_plain<true>(x, 0, 3);
+#pragma unroll
+                for (int r = 0; r < TR; ++r) {
+                    const float lx = Lg::lg(x[r]);
+                    if (!(done >> r & 1u) && (last || lx >= Wn::lo)) {
+                        OUT[run3[r >> 3] + (r & 7)] = sp + lx;
+                        done |= 1u << r;
+                    }
+                }
+                if (last) break;
+                if (__syncthreads_and(done == 0xffffffffu)) break;   // also guards A0 reuse
+            }
+        } else {
+            // max-plus pass, then the exact sum pass (k_upzeta13)
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const uint32_t sw = swz(el1(r, t));
+                A0[sw] = __popc(r) + pt > d ? Lg::ninf() : A1[sw];
+            }
+            __syncthreads();
+            float v[TR];
+            ld1(A0, v, t);
+            bfly_max<true>(v, 0, 5);
+            st1(A0, v, t);
+            __syncthreads();
+            ld2(A0, v, t);
+            bfly_max<true>(v, 0, 5);
+            st2(A0, v, t);
+            __syncthreads();
+            ld3(A0, v, t);
+            bfly_max<true>(v, 0, 3);
+            float sc[TR];
+            sum_pass<true>(v, sc, A1, A0, t, d);
+#pragma unroll
+            for (int r = 0; r < TR; ++r) OUT[BN_AT(opos(el1(r, t)), 1, TN)] = scaled_log(v[r], sc[r]);
+        }
+        fence_async_shared();                            // OUT is written: the store may read it
+        __syncthreads();
+        if (t == 0) bulk_store(out, OUT, TN * 4u);
+    }
+    if (t == 0) bulk_wait();
+}
+
 // ===========================================================================
 // Step 4, phase 1 for n >= 14: one block per tile H of the n-1 bits of S
 // (bit v removed); s_v(S) = F(S) + R'(S + {v}); keeps the outputs with at
@@ -1178,8 +1353,25 @@ cudaError_t launch_reorder_up(const Plan& P, const void* lbs, void* tab, cudaStr
     return cudaGetLastError();
 }
 
+size_t upzeta13p_smem_bytes(const Plan& P)
+{
+    uint64_t ncol = 0;
+    for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
+    // A0, A1, the warps' maxima, the mbarrier and a flag, the staged column
+    // sums (16-byte multiple), the output block
+    return (size_t)TN * 4 * 2 + (TT / 32) * 4 + 16 + ((ncol * 4 + 15) & ~(uint64_t)15) + (size_t)TN * 4;
+}
+
+// The persistent FP32 tile kernel runs single jobs whose A is in device
+// memory (a spilled A may sit in host memory, where no bulk copy goes) and
+// that are launched directly, not recorded for the persistent batch kernel.
+static bool use_upzeta13p(const Plan& P, const int* err)
+{
+    return err && P.prec != 0 && P.nj == 1 && !P.spill && !recording();
+}
+
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
-                            cudaStream_t s, cudaEvent_t sums_done)
+                            cudaStream_t s, cudaEvent_t sums_done, int* err)
 {
     const int h = P.n - 1 - TB;
     const int nodes = up_nodes(P);
@@ -1224,12 +1416,47 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         e = cudaEventRecord(sums_done, s);
         if (e != cudaSuccess) return e;
     }
+    if (use_upzeta13p(P, err)) {
+        const uint32_t ntiles = (uint32_t)nodes << h;
+        const size_t smp = upzeta13p_smem_bytes(P);
+        int dev = 0, nsm = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = use_tlo(P) ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upzeta13p<true>, TT, smp)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upzeta13p<false>, TT, smp);
+        if (e != cudaSuccess) return e;
+        const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)std::max(per_sm, 1) * nsm);
+        if (use_tlo(P))
+            k_upzeta13p<true><<<blocks, TT, smp, s>>>(P.n, P.d, unrank13, (float*)A, ntiles, err, kCopySpinCap, 0);
+        else
+            k_upzeta13p<false><<<blocks, TT, smp, s>>>(P.n, P.d, unrank13, (float*)A, ntiles, err, kCopySpinCap, 0);
+        return cudaGetLastError();
+    }
     if (P.prec == 0)
         launch_or_record(KID_UP13_D, k_upzeta13<double, false>, grid, TT, sm, s, P.n, P.d, unrank13, (double*)A, P.js);
     else if (use_tlo(P))
         launch_or_record(KID_UP13_F_TLO, k_upzeta13<float, true>, grid, TT, sm, s, P.n, P.d, unrank13, (float*)A, P.js);
     else
         launch_or_record(KID_UP13_F, k_upzeta13<float, false>, grid, TT, sm, s, P.n, P.d, unrank13, (float*)A, P.js);
+    return cudaGetLastError();
+}
+
+// One block of the persistent tile kernel (n = 14, d = 4: one tile) with its
+// first bulk copy withheld: its wait gives up after `polls` polls and sets
+// kErrDeviceTimeout in *err.  A holds one tile (8192 floats); unrank13 is
+// filled here.
+cudaError_t launch_upzeta13p_withheld(float* A, uint16_t* rank13, uint16_t* unrank13, int* err,
+                                      uint32_t polls, cudaStream_t s)
+{
+    cudaError_t e = allow_max_dynamic_smem(k_upzeta13p<false>);
+    if (e != cudaSuccess) return e;
+    k_rank13_tables<<<TN / 256, 256, 0, s>>>(rank13, unrank13, 0);
+    Plan P{};
+    P.n = 14;
+    P.d = 4;
+    P.prec = 1;
+    k_upzeta13p<false><<<1, TT, upzeta13p_smem_bytes(P), s>>>(14, 4, unrank13, A, 1u, err, polls, 1);
     return cudaGetLastError();
 }
 
@@ -1287,6 +1514,8 @@ cudaError_t set_tile13_attributes()
     SETA((k_upzeta13<double, false>))
     SETA((k_upzeta13<float, false>))
     SETA((k_upzeta13<float, true>))
+    SETA(k_upzeta13p<false>)
+    SETA(k_upzeta13p<true>)
     SETA((k_gamma13_p1<double, false>))
     SETA((k_gamma13_p1<float, false>))
     SETA((k_gamma13_p1<double, true>))
