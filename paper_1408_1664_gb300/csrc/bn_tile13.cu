@@ -623,18 +623,22 @@ __device__ __forceinline__ void lse_lazy(T& m, T& s, T x)
 // Columns with d low elements are copies, those with d - 1 take the 1 + |H|
 // rows of at most one high element, the others every row of size at most
 // d - |G_L|.
-// Column sums by butterflies over the h high dimensions (FP32): one block per
-// node i and run of CPB consecutive low columns c.  The 2^h values
-// B_i(G_H + G_L) of each column (zero where |G_H| > d - |G_L|) are gathered
-// from the reordered table, the truncated upward zeta over the subsets of
-// every H follows in shared memory with a log-sum-exp per step (h * 2^(h-1)
-// per column, against sum_H C(|H|, <= d - |G_L|) terms summed directly: the
-// better order once d is large), and each C_H(G_L) goes to slot c of tile
-// (i, H), the CPB columns of a run side by side (32-byte writes).
+// Column sums by butterflies over the h high dimensions (FP32).  Blocks below
+// nodes * ceil(ncb / CPB) take one node i and a run of CPB consecutive low
+// columns c < ncb: the 2^h values B_i(G_H + G_L) of each column (zero where
+// |G_H| > d - |G_L|) are gathered from the reordered table, the upward zeta
+// over the subsets of every H follows in shared memory with a log-sum-exp
+// per step (h * 2^(h-1) per column, against sum_H C(|H|, <= d - |G_L|)
+// terms summed directly: the better order once a column has many rows), and
+// each C_H(G_L) goes to slot c of tile (i, H), the CPB columns of a run side
+// by side.  The steps run three dimensions at a time in registers (eight
+// values per thread), the columns held one after another in shared memory.
+// The blocks after those copy the columns from ncb on, whose sums have a
+// single row (the empty high set), a warp per tile.
 template <int CPB>
 __global__ void __launch_bounds__(256)
 k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* __restrict__ A,
-                size_t js)
+                size_t js, int nodes, uint32_t ncb)
 {
     tab = job_ptr(tab, js);
     A = job_ptr(A, js);
@@ -643,9 +647,21 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
     __shared__ uint32_t off13[16];
     __shared__ uint32_t rowoff_k[32];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* v = reinterpret_cast<float*>(smem_raw);  // [H][column of the run]
+    float* v = reinterpret_cast<float*>(smem_raw);  // [column of the run][H]
     const int h = n - 1 - TB;
     const uint32_t H2 = 1u << h;
+    const uint32_t ncol = num_small_subsets(TB, d);
+    const uint32_t nrun = (ncb + CPB - 1) / CPB;
+    const uint32_t nbb = (uint32_t)nodes * nrun;
+    const size_t asize = (size_t)nodes << (n - 1);
+    if (blockIdx.x >= nbb) {                         // copies: a warp per tile
+        const uint32_t tile = (blockIdx.x - nbb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (tile >= ((uint32_t)nodes << h)) return;
+        const float* tb = tab + (size_t)(tile >> h) * K;
+        float* out = A + BN_AT((size_t)tile << TB, TN, asize);
+        for (uint32_t c = ncb + (threadIdx.x & 31); c < ncol; c += 32) out[c] = tb[BN_AT(c, 1, K)];
+        return;
+    }
     fill_sbinom(sb);
     if (threadIdx.x < 16) {
         uint32_t o = 0;
@@ -660,42 +676,65 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
         rowoff_k[threadIdx.x] = o;
     }
     __syncthreads();
-    const uint32_t ncol = num_small_subsets(TB, d);
-    const uint32_t nrun = (ncol + CPB - 1) / CPB;
     const int i = (int)(blockIdx.x / nrun);
     const uint32_t c0 = (blockIdx.x % nrun) * CPB;
     const float* tb = tab + (size_t)i * K;
-    for (uint32_t e = threadIdx.x; e < H2 * CPB; e += blockDim.x) {
-        const uint32_t H = e / CPB, c = c0 + e % CPB;
-        float val = Lg::ninf();
-        if (c < ncol) {
-            int kl = 0;
-            while (off13[kl + 1] <= c) ++kl;
-            const int kh = __popc(H);
-            if (kh <= d - kl) {
-                uint32_t r = 0;                     // colex rank of H among kh-subsets
-                int t = 1;
-                for (uint32_t x = H; x; x &= x - 1, ++t) r += sb_binom(sb, __ffs(x) - 1, t);
-                val = tb[BN_AT(rowoff_k[kh] + r * off13[min(d - kh, TB) + 1] + c, 1, K)];
-            }
+    int kl[CPB];                                     // low elements of each column (-1: none)
+#pragma unroll
+    for (int cc = 0; cc < CPB; ++cc) {
+        const uint32_t c = c0 + cc;
+        int k = 0;
+        while (k < TB && off13[k + 1] <= c) ++k;
+        kl[cc] = c < ncb ? k : -1;
+    }
+    for (uint32_t H = threadIdx.x; H < H2; H += blockDim.x) {
+        const int kh = __popc(H);
+        uint32_t r = 0;                              // colex rank of H among kh-subsets
+        int t = 1;
+        for (uint32_t x = H; x; x &= x - 1, ++t) r += sb_binom(sb, __ffs(x) - 1, t);
+        // the row of G_H in the node's table (only formed where some column reads it)
+        const uint32_t row = kh <= d ? rowoff_k[kh] + r * off13[min(d - kh, TB) + 1] : 0u;
+#pragma unroll
+        for (int cc = 0; cc < CPB; ++cc) {
+            const bool in = kl[cc] >= 0 && kh <= d - kl[cc];
+            v[cc * H2 + H] = in ? tb[BN_AT(row + c0 + cc, 1, K)] : Lg::ninf();
         }
-        v[e] = val;
     }
     __syncthreads();
-    for (int j = 0; j < h; ++j) {
-        const uint32_t jm = (1u << j) - 1u;
-        for (uint32_t e = threadIdx.x; e < (H2 >> 1) * CPB; e += blockDim.x) {
-            const uint32_t p = e / CPB, cc = e % CPB;
-            const uint32_t lo = ((p & ~jm) << 1) | (p & jm);
-            const uint32_t hi = lo | (1u << j);
-            v[hi * CPB + cc] = Lg::lse(v[hi * CPB + cc], v[lo * CPB + cc]);
+    for (int j0 = 0; j0 < h; j0 += 3) {
+        const int nb = min(3, h - j0);
+        const uint32_t lowm = (1u << j0) - 1u;
+        const uint32_t np = H2 >> nb;
+        for (uint32_t g = threadIdx.x; g < np * CPB; g += blockDim.x) {
+            const uint32_t cc = g / np, p = g % np;
+            const uint32_t base = cc * H2 + (((p & ~lowm) << nb) | (p & lowm));
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < (1 << nb)) x[q] = v[base + ((uint32_t)q << j0)];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (k >= nb) continue;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < (1 << nb) && (q >> k & 1)) x[q] = Lg::lse(x[q], x[q ^ (1 << k)]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < (1 << nb)) v[base + ((uint32_t)q << j0)] = x[q];
         }
         __syncthreads();
     }
     float* Ai = A + ((size_t)i << (n - 1));
-    for (uint32_t e = threadIdx.x; e < H2 * CPB; e += blockDim.x) {
-        const uint32_t H = e / CPB, c = c0 + e % CPB;
-        if (c < ncol) Ai[BN_AT(((size_t)H << TB) + c, 1, (size_t)1 << (n - 1))] = v[e];
+    for (uint32_t H = threadIdx.x; H < H2; H += blockDim.x) {
+        float* o = Ai + BN_AT(((size_t)H << TB) + c0, CPB, (size_t)H2 << TB);
+        if (CPB == 4 && c0 + 4 <= ncb) {
+            *reinterpret_cast<float4*>(o) = make_float4(v[H], v[H2 + H], v[2 * H2 + H], v[3 * H2 + H]);
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < CPB; ++cc)
+                if (c0 + cc < ncb) o[cc] = v[cc * H2 + H];
+        }
     }
 }
 
@@ -1289,9 +1328,19 @@ BN_BOUNDS_READER(bounds_line_tile13)
 // ===========================================================================
 // Launchers.
 // ===========================================================================
+// Columns whose sums take more than one row: the low patterns with fewer
+// than d elements.
+static uint32_t colb_columns(const Plan& P)
+{
+    uint64_t c = 0;
+    for (int k = 0; k < P.d && k <= TB; ++k) c += binom_host(TB, k);
+    return (uint32_t)c;
+}
+
 // FP32 column sums by butterflies over the h high dimensions when they take
-// at most two thirds of the steps of the direct sums and a column run fits 64 KB of
-// shared memory (h <= 13): the high in-degree bounds (d >= 6 at n = 25).
+// at most four fifths of the steps of the direct sums (the columns with d low
+// elements are copies either way; a butterfly step and a direct term cost
+// about the same) and a column run fits 64 KB of shared memory (h <= 13).
 bool use_colb(const Plan& P)
 {
     const int h = P.n - 1 - TB;
@@ -1304,8 +1353,9 @@ bool use_colb(const Plan& P)
             rows += (double)binom_host(h, kh) * std::ldexp(1.0, h - kh);
         direct += (double)binom_host(TB, kl) * rows;
     }
-    const double bfly = ncol * h * std::ldexp(1.0, h - 1);
-    return direct >= 1.5 * bfly;
+    const double ncb = colb_columns(P);
+    const double bfly = ncb * h * std::ldexp(1.0, h - 1) + (ncol - ncb) * std::ldexp(1.0, h);
+    return direct >= 1.25 * bfly;
 }
 
 size_t upzeta13_cols_smem_bytes(const Plan& P)
@@ -1383,17 +1433,20 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         const int cpb = h <= 11 ? 8 : (h == 12 ? 4 : 2);
         uint64_t ncol = 0;
         for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
-        const unsigned nblk = (unsigned)((uint64_t)nodes * ((ncol + cpb - 1) / cpb));
+        const uint32_t ncb = colb_columns(P);
+        const uint64_t ntiles = (uint64_t)nodes << h;
+        const unsigned nblk = (unsigned)((uint64_t)nodes * ((ncb + cpb - 1) / cpb) +
+                                         (ncb < ncol ? (ntiles + 7) / 8 : 0));
         const size_t smb = ((size_t)cpb << h) * 4;
         if (cpb == 8)
             launch_or_record(KID_COLB8, k_upzeta13_colb<8>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
-                                                                  (const float*)tab, (float*)A, P.js);
+                             (const float*)tab, (float*)A, P.js, nodes, ncb);
         else if (cpb == 4)
             launch_or_record(KID_COLB4, k_upzeta13_colb<4>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
-                                                                  (const float*)tab, (float*)A, P.js);
+                             (const float*)tab, (float*)A, P.js, nodes, ncb);
         else
             launch_or_record(KID_COLB2, k_upzeta13_colb<2>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
-                                                                  (const float*)tab, (float*)A, P.js);
+                             (const float*)tab, (float*)A, P.js, nodes, ncb);
     } else if (nrow * 4 * 8 <= 160 * 1024) {          // warp per tile, 8 tiles per block
         const uint64_t ntiles = (uint64_t)nodes << h;
         const dim3 gw((unsigned)std::min<uint64_t>((ntiles + 7) / 8, 152 * 16), P.nj);
