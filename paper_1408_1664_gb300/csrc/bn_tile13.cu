@@ -1191,6 +1191,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
     F = job_ptr(F, js);
     Rc = job_ptr(Rc, js);
     rank13 = job_ptr(rank13, js);
+    const uint16_t* unrank13 = rank13 + TN;         // the inverse table follows
     W = job_ptr(W, js) + (size_t)endpoint_slot(vsel, v) * ntile * nlow;
     using Lg = LogOps<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1259,11 +1260,7 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
         }
         const T floorv = L - Window<T>::gap;
         if (M < L) {                                // nothing in the tile matters
-#pragma unroll
-            for (int r = 0; r < TR; ++r) {
-                const uint32_t el = el3(r, t);
-                if (__popc(el) <= d) row[BN_AT(rank13[el], 1, nlow)] = floorv;
-            }
+            for (uint32_t c = t; c < nlow; c += TT) row[BN_AT(c, 1, nlow)] = floorv;
             return;
         }
         if (M - (L > sfull_s ? L : sfull_s) < Window<T>::win) {
@@ -1279,11 +1276,25 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
             __syncthreads();
             ld3(A0, x, t);
             bfly_plain<false>(x, 0, 3);
+            if constexpr (sizeof(T) == 8) {
+                // only the outputs with at most d elements are kept: back to
+                // shared memory (each thread rewrites the slots it read), then
+                // a logarithm (many FP64 instructions) per kept output, stored
+                // in rank order
+                st3(A0, x, t);
+                __syncthreads();
+                for (uint32_t c = t; c < nlow; c += TT) {
+                    const T o = sp + Lg::lg(A0[swz(BN_AT(unrank13[c], 1, TN))]);
+                    row[BN_AT(c, 1, nlow)] = o > floorv ? o : floorv;
+                }
+            } else {
+                // FP32: a logarithm per register, kept outputs stored in place
 #pragma unroll
-            for (int r = 0; r < TR; ++r) {
-                const uint32_t el = el3(r, t);
-                const T o = sp + Lg::lg(x[r]);
-                if (__popc(el) <= d) row[BN_AT(rank13[el], 1, nlow)] = o > floorv ? o : floorv;
+                for (int r = 0; r < TR; ++r) {
+                    const uint32_t el = el3(r, t);
+                    const T o = sp + Lg::lg(x[r]);
+                    if (__popc(el) <= d) row[BN_AT(rank13[el], 1, nlow)] = o > floorv ? o : floorv;
+                }
             }
             return;
         }
@@ -1301,10 +1312,22 @@ k_gamma13_p1(int n, int d, uint32_t nlow, const T* __restrict__ F,
 
     T sc[TR];
     sum_pass<false>(x, sc, A1, A0, t, d);
-    const int pt = __popc((uint32_t)t);
+    if constexpr (sizeof(T) == 8) {
+        // the kept outputs in rank order, as in the single-scale pass; each
+        // thread rewrites the layout-1 slots it has just read
+        st1(A0, x, t);
+        st1(A1, sc, t);
+        __syncthreads();
+        for (uint32_t c = t; c < nlow; c += TT) {
+            const uint32_t e = swz(BN_AT(unrank13[c], 1, TN));
+            row[BN_AT(c, 1, nlow)] = scaled_log(A0[e], A1[e]);
+        }
+    } else {
+        const int pt = __popc((uint32_t)t);
 #pragma unroll
-    for (int r = 0; r < TR; ++r)
-        if (pt + __popc((uint32_t)r) <= d) row[BN_AT(rank13[el1(r, t)], 1, nlow)] = scaled_log(x[r], sc[r]);
+        for (int r = 0; r < TR; ++r)
+            if (pt + __popc((uint32_t)r) <= d) row[BN_AT(rank13[el1(r, t)], 1, nlow)] = scaled_log(x[r], sc[r]);
+    }
 }
 
 // rank13[L] = position of L among the subsets of 13 bits ordered by size then
