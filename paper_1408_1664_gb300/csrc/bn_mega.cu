@@ -129,9 +129,9 @@ __device__ __forceinline__ bool dispatch(int kid, const unsigned char* a)
         case KID_EDGES_ACC_F: run(k_edges_acc<float>, a); return true;
         case KID_EDGES_FIN_F: run(k_edges_fin<float>, a); return true;
         case KID_REORDER_F: run(k_reorder_up<float>, a); return true;
-        case KID_COLB8: run(k_upzeta13_colb<8>, a); return true;
-        case KID_COLB4: run(k_upzeta13_colb<4>, a); return true;
-        case KID_COLB2: run(k_upzeta13_colb<2>, a); return true;
+        case KID_COLB8: run(k_upzeta13_colb<float, 8>, a); return true;
+        case KID_COLB4: run(k_upzeta13_colb<float, 4>, a); return true;
+        case KID_COLB2: run(k_upzeta13_colb<float, 2>, a); return true;
         case KID_COLW_F: run(k_upzeta13_colw<float>, a); return true;
         case KID_COLS_F: run(k_upzeta13_cols<float>, a); return true;
         case KID_UP13_F_TLO: run(k_upzeta13<float, true>, a); return true;
@@ -156,6 +156,9 @@ __device__ __forceinline__ bool dispatch(int kid, const unsigned char* a)
         case KID_EDGES_FIN_D: run(k_edges_fin<double>, a); return true;
         case KID_REORDER_D: run(k_reorder_up<double>, a); return true;
         case KID_COLW_D: run(k_upzeta13_colw<double>, a); return true;
+        case KID_COLB4_D: run(k_upzeta13_colb<double, 4>, a); return true;
+        case KID_COLB2_D: run(k_upzeta13_colb<double, 2>, a); return true;
+        case KID_COLB1_D: run(k_upzeta13_colb<double, 1>, a); return true;
         case KID_COLS_D: run(k_upzeta13_cols<double>, a); return true;
         case KID_UP13_D: run(k_upzeta13<double, false>, a); return true;
         case KID_G13_D: run(k_gamma13_p1<double, false>, a); return true;
@@ -284,6 +287,7 @@ bool persistent_runs(int prec, int kid)
     case KID_SHIFT_D: case KID_UPZETA_D: case KID_FWD_LEVEL_D: case KID_BWD_LEVEL_D:
     case KID_GAMMA_P1_D: case KID_GAMMA_P2_D: case KID_GAMMA_P2S_D: case KID_EDGES_ACC_D:
     case KID_EDGES_FIN_D: case KID_REORDER_D: case KID_COLW_D: case KID_COLS_D: case KID_UP13_D:
+    case KID_COLB4_D: case KID_COLB2_D: case KID_COLB1_D:
     case KID_G13_D: case KID_FROWS_D: case KID_BROWS_D:
         return prec == 0;
     default:

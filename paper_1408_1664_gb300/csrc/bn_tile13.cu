@@ -623,31 +623,71 @@ __device__ __forceinline__ void lse_lazy(T& m, T& s, T x)
 // Columns with d low elements are copies, those with d - 1 take the 1 + |H|
 // rows of at most one high element, the others every row of size at most
 // d - |G_L|.
-// Column sums by butterflies over the h high dimensions (FP32).  Blocks below
+// Column sums by butterflies over the h high dimensions.  Blocks below
 // nodes * ceil(ncb / CPB) take one node i and a run of CPB consecutive low
 // columns c < ncb: the 2^h values B_i(G_H + G_L) of each column (zero where
 // |G_H| > d - |G_L|) are gathered from the reordered table, the upward zeta
-// over the subsets of every H follows in shared memory with a log-sum-exp
-// per step (h * 2^(h-1) per column, against sum_H C(|H|, <= d - |G_L|)
-// terms summed directly: the better order once a column has many rows), and
-// each C_H(G_L) goes to slot c of tile (i, H), the CPB columns of a run side
-// by side.  The steps run three dimensions at a time in registers (eight
-// values per thread), the columns held one after another in shared memory.
+// over the subsets of every H follows in shared memory (h * 2^(h-1) steps
+// per column, against sum_H C(|H|, <= d - |G_L|) terms summed directly: the
+// better order once a column has many rows), and each C_H(G_L) goes to slot
+// c of tile (i, H), the CPB columns of a run side by side.  The steps run
+// three dimensions at a time in registers (eight values per thread), the
+// columns held one after another in shared memory.
+//
+// Every output of a column lies between its H = {} value f(G_L) and its
+// largest input plus log 2^h, so when that span is under one single-scale
+// window (Window) for every column of the block, the sums run in linear
+// scale (an exponential per input, an addition per step, a logarithm per
+// output; exact as in the tiles); otherwise every step is a log-sum-exp.
 // The blocks after those copy the columns from ncb on, whose sums have a
 // single row (the empty high set), a warp per tile.
-template <int CPB>
+template <bool LIN, typename T>
+__device__ __forceinline__ void colb_steps(T* v, uint32_t H2, int h, int CPB)
+{
+    using Lg = LogOps<T>;
+    for (int j0 = 0; j0 < h; j0 += 3) {
+        const int nb = min(3, h - j0);
+        const uint32_t lowm = (1u << j0) - 1u;
+        const uint32_t np = H2 >> nb;
+        for (uint32_t g = threadIdx.x; g < np * CPB; g += blockDim.x) {
+            const uint32_t cc = g / np, p = g % np;
+            const uint32_t base = cc * H2 + (((p & ~lowm) << nb) | (p & lowm));
+            T x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < (1 << nb)) x[q] = v[base + ((uint32_t)q << j0)];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (k >= nb) continue;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < (1 << nb) && (q >> k & 1)) x[q] = LIN ? x[q] + x[q ^ (1 << k)] : Lg::lse(x[q], x[q ^ (1 << k)]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < (1 << nb)) v[base + ((uint32_t)q << j0)] = x[q];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int CPB>
 __global__ void __launch_bounds__(256)
-k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* __restrict__ A,
+k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A,
                 size_t js, int nodes, uint32_t ncb)
 {
     tab = job_ptr(tab, js);
     A = job_ptr(A, js);
-    using Lg = LogOps<float>;
+    using Lg = LogOps<T>;
+    using Wn = Window<T>;
     __shared__ SBinom sb;
     __shared__ uint32_t off13[16];
     __shared__ uint32_t rowoff_k[32];
+    __shared__ T wred[8][CPB];                       // the warps' column maxima
+    __shared__ T scale_s[CPB];                       // a column's linear scale
+    __shared__ int lin_s;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* v = reinterpret_cast<float*>(smem_raw);  // [column of the run][H]
+    T* v = reinterpret_cast<T*>(smem_raw);           // [column of the run][H]
     const int h = n - 1 - TB;
     const uint32_t H2 = 1u << h;
     const uint32_t ncol = num_small_subsets(TB, d);
@@ -657,8 +697,8 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
     if (blockIdx.x >= nbb) {                         // copies: a warp per tile
         const uint32_t tile = (blockIdx.x - nbb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
         if (tile >= ((uint32_t)nodes << h)) return;
-        const float* tb = tab + (size_t)(tile >> h) * K;
-        float* out = A + BN_AT((size_t)tile << TB, TN, asize);
+        const T* tb = tab + (size_t)(tile >> h) * K;
+        T* out = A + BN_AT((size_t)tile << TB, TN, asize);
         for (uint32_t c = ncb + (threadIdx.x & 31); c < ncol; c += 32) out[c] = tb[BN_AT(c, 1, K)];
         return;
     }
@@ -678,14 +718,16 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
     __syncthreads();
     const int i = (int)(blockIdx.x / nrun);
     const uint32_t c0 = (blockIdx.x % nrun) * CPB;
-    const float* tb = tab + (size_t)i * K;
+    const T* tb = tab + (size_t)i * K;
     int kl[CPB];                                     // low elements of each column (-1: none)
+    T mx[CPB];
 #pragma unroll
     for (int cc = 0; cc < CPB; ++cc) {
         const uint32_t c = c0 + cc;
         int k = 0;
         while (k < TB && off13[k + 1] <= c) ++k;
         kl[cc] = c < ncb ? k : -1;
+        mx[cc] = Lg::ninf();
     }
     for (uint32_t H = threadIdx.x; H < H2; H += blockDim.x) {
         const int kh = __popc(H);
@@ -697,44 +739,61 @@ k_upzeta13_colb(int n, int d, int64_t K, const float* __restrict__ tab, float* _
 #pragma unroll
         for (int cc = 0; cc < CPB; ++cc) {
             const bool in = kl[cc] >= 0 && kh <= d - kl[cc];
-            v[cc * H2 + H] = in ? tb[BN_AT(row + c0 + cc, 1, K)] : Lg::ninf();
+            const T val = in ? tb[BN_AT(row + c0 + cc, 1, K)] : Lg::ninf();
+            v[cc * H2 + H] = val;
+            mx[cc] = val > mx[cc] ? val : mx[cc];
         }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int cc = 0; cc < CPB; ++cc) {
+        for (int o = 16; o; o >>= 1) {
+            const T y = __shfl_xor_sync(FULLMASK, mx[cc], o);
+            mx[cc] = y > mx[cc] ? y : mx[cc];
+        }
+        if (lane == 0) wred[warp][cc] = mx[cc];
     }
     __syncthreads();
-    for (int j0 = 0; j0 < h; j0 += 3) {
-        const int nb = min(3, h - j0);
-        const uint32_t lowm = (1u << j0) - 1u;
-        const uint32_t np = H2 >> nb;
-        for (uint32_t g = threadIdx.x; g < np * CPB; g += blockDim.x) {
-            const uint32_t cc = g / np, p = g % np;
-            const uint32_t base = cc * H2 + (((p & ~lowm) << nb) | (p & lowm));
-            float x[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < (1 << nb)) x[q] = v[base + ((uint32_t)q << j0)];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (k >= nb) continue;
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (q < (1 << nb) && (q >> k & 1)) x[q] = Lg::lse(x[q], x[q ^ (1 << k)]);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < (1 << nb)) v[base + ((uint32_t)q << j0)] = x[q];
+    if (threadIdx.x == 0) {
+        // a column's outputs lie in [f(G_L), its largest input + log 2^h]
+        const T hb = sizeof(T) == 4 ? T(h) : T(h) * T(0.69314718055994530942);
+        int lin = 1;
+        for (int cc = 0; cc < CPB; ++cc) {
+            T m = wred[0][cc];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wred[w][cc] > m ? wred[w][cc] : m;
+            const T top = m + hb;
+            scale_s[cc] = top - Wn::top;
+            if (kl[cc] >= 0 && !(top - v[cc * H2] < Wn::win)) lin = 0;
         }
-        __syncthreads();
+        lin_s = lin;
     }
-    float* Ai = A + ((size_t)i << (n - 1));
+    __syncthreads();
+    const bool lin = lin_s != 0;
+    if (lin) {
+        for (uint32_t e = threadIdx.x; e < H2 * CPB; e += blockDim.x) v[e] = Lg::ex(v[e] - scale_s[e / H2]);
+        __syncthreads();
+        colb_steps<true>(v, H2, h, CPB);
+    } else {
+        colb_steps<false>(v, H2, h, CPB);
+    }
+    T* Ai = A + ((size_t)i << (n - 1));
     for (uint32_t H = threadIdx.x; H < H2; H += blockDim.x) {
-        float* o = Ai + BN_AT(((size_t)H << TB) + c0, CPB, (size_t)H2 << TB);
-        if (CPB == 4 && c0 + 4 <= ncb) {
-            *reinterpret_cast<float4*>(o) = make_float4(v[H], v[H2 + H], v[2 * H2 + H], v[3 * H2 + H]);
-        } else {
+        T* o = Ai + BN_AT(((size_t)H << TB) + c0, CPB, (size_t)H2 << TB);
+        T y[CPB];
 #pragma unroll
-            for (int cc = 0; cc < CPB; ++cc)
-                if (c0 + cc < ncb) o[cc] = v[cc * H2 + H];
+        for (int cc = 0; cc < CPB; ++cc) {
+            const T x = v[cc * H2 + H];
+            y[cc] = lin ? scale_s[cc] + Lg::lg(x) : x;
         }
+        if constexpr (sizeof(T) == 4 && CPB == 4) {
+            if (c0 + 4 <= ncb) {
+                *reinterpret_cast<float4*>(o) = make_float4(y[0], y[1], y[2], y[3]);
+                continue;
+            }
+        }
+#pragma unroll
+        for (int cc = 0; cc < CPB; ++cc)
+            if (c0 + cc < ncb) o[cc] = y[cc];
     }
 }
 
@@ -1360,14 +1419,14 @@ static uint32_t colb_columns(const Plan& P)
     return (uint32_t)c;
 }
 
-// FP32 column sums by butterflies over the h high dimensions when they take
-// at most four fifths of the steps of the direct sums (the columns with d low
-// elements are copies either way; a butterfly step and a direct term cost
-// about the same) and a column run fits 64 KB of shared memory (h <= 13).
+// Column sums by butterflies over the h high dimensions when they take at
+// most four fifths (FP32; four times in FP64) of the steps of the direct sums
+// (the columns with d low elements are copies either way) and a column run
+// fits 64 KB of shared memory (h <= 13).
 bool use_colb(const Plan& P)
 {
     const int h = P.n - 1 - TB;
-    if (P.prec == 0 || h > 13) return false;
+    if (h > 13) return false;
     double direct = 0.0, ncol = 0.0;
     for (int kl = 0; kl <= P.d && kl <= TB; ++kl) {
         ncol += (double)binom_host(TB, kl);
@@ -1378,7 +1437,8 @@ bool use_colb(const Plan& P)
     }
     const double ncb = colb_columns(P);
     const double bfly = ncb * h * std::ldexp(1.0, h - 1) + (ncol - ncb) * std::ldexp(1.0, h);
-    return direct >= 1.25 * bfly;
+    // FP64: a direct term costs an FP64 exponential, a linear-scale step one addition
+    return direct >= (P.prec == 0 ? 0.25 : 1.25) * bfly;
 }
 
 size_t upzeta13_cols_smem_bytes(const Plan& P)
@@ -1453,23 +1513,37 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
     uint64_t nrow = 0;
     for (int k = 0; k <= P.d && k <= h; ++k) nrow += binom_host(h, k);
     if (use_colb(P)) {                                // butterflies over the high dims
-        const int cpb = h <= 11 ? 8 : (h == 12 ? 4 : 2);
+        // columns per block: as many as fit 64 KB, at most 8 (FP32) or 4 (FP64)
+        const size_t es = P.prec == 0 ? 8 : 4;
+        const int cpb = (int)std::min<size_t>((size_t)(64 * 1024) / (es << h), P.prec == 0 ? 4 : 8);
         uint64_t ncol = 0;
         for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
         const uint32_t ncb = colb_columns(P);
         const uint64_t ntiles = (uint64_t)nodes << h;
         const unsigned nblk = (unsigned)((uint64_t)nodes * ((ncb + cpb - 1) / cpb) +
                                          (ncb < ncol ? (ntiles + 7) / 8 : 0));
-        const size_t smb = ((size_t)cpb << h) * 4;
-        if (cpb == 8)
-            launch_or_record(KID_COLB8, k_upzeta13_colb<8>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
+        const size_t smb = ((size_t)cpb << h) * es;
+        const dim3 gb(nblk, P.nj);
+        if (P.prec == 0) {
+            if (cpb >= 4)
+                launch_or_record(KID_COLB4_D, k_upzeta13_colb<double, 4>, gb, 256, smb, s, P.n, P.d, P.K,
+                                 (const double*)tab, (double*)A, P.js, nodes, ncb);
+            else if (cpb == 2)
+                launch_or_record(KID_COLB2_D, k_upzeta13_colb<double, 2>, gb, 256, smb, s, P.n, P.d, P.K,
+                                 (const double*)tab, (double*)A, P.js, nodes, ncb);
+            else
+                launch_or_record(KID_COLB1_D, k_upzeta13_colb<double, 1>, gb, 256, smb, s, P.n, P.d, P.K,
+                                 (const double*)tab, (double*)A, P.js, nodes, ncb);
+        } else if (cpb == 8) {
+            launch_or_record(KID_COLB8, k_upzeta13_colb<float, 8>, gb, 256, smb, s, P.n, P.d, P.K,
                              (const float*)tab, (float*)A, P.js, nodes, ncb);
-        else if (cpb == 4)
-            launch_or_record(KID_COLB4, k_upzeta13_colb<4>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
+        } else if (cpb >= 4) {
+            launch_or_record(KID_COLB4, k_upzeta13_colb<float, 4>, gb, 256, smb, s, P.n, P.d, P.K,
                              (const float*)tab, (float*)A, P.js, nodes, ncb);
-        else
-            launch_or_record(KID_COLB2, k_upzeta13_colb<2>, dim3(nblk, P.nj), 256, smb, s, P.n, P.d, P.K,
+        } else {
+            launch_or_record(KID_COLB2, k_upzeta13_colb<float, 2>, gb, 256, smb, s, P.n, P.d, P.K,
                              (const float*)tab, (float*)A, P.js, nodes, ncb);
+        }
     } else if (nrow * 4 * 8 <= 160 * 1024) {          // warp per tile, 8 tiles per block
         const uint64_t ntiles = (uint64_t)nodes << h;
         const dim3 gw((unsigned)std::min<uint64_t>((ntiles + 7) / 8, 152 * 16), P.nj);
@@ -1584,9 +1658,12 @@ cudaError_t set_tile13_attributes()
     SETA(k_upzeta13_cols<float>)
     SETA(k_upzeta13_colw<double>)
     SETA(k_upzeta13_colw<float>)
-    SETA(k_upzeta13_colb<8>)
-    SETA(k_upzeta13_colb<4>)
-    SETA(k_upzeta13_colb<2>)
+    SETA((k_upzeta13_colb<float, 8>))
+    SETA((k_upzeta13_colb<float, 4>))
+    SETA((k_upzeta13_colb<float, 2>))
+    SETA((k_upzeta13_colb<double, 4>))
+    SETA((k_upzeta13_colb<double, 2>))
+    SETA((k_upzeta13_colb<double, 1>))
     SETA((k_upzeta13<double, false>))
     SETA((k_upzeta13<float, false>))
     SETA((k_upzeta13<float, true>))
