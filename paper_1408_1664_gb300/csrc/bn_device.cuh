@@ -414,12 +414,14 @@ template <> struct LogOps<double> {
     // exp and log in this value's base
     static __device__ __forceinline__ double ex(double x) { return exp_t(x); }
     static __device__ __forceinline__ double lg(double x) { return log_t(x); }
-    // log(exp(a) + exp(b))
+    // log(exp(a) + exp(b)) with the table-driven exponential and logarithm:
+    // 1 + e rounds by at most 2^-53, which moves the logarithm by at most
+    // that much, so the result carries the same absolute error as with log1p
     static __device__ __forceinline__ double lse(double a, double b)
     {
         const double mx = fmax(a, b), mn = fmin(a, b);
         if (mn == ninf()) return mx;
-        return mx + log1p(exp(mn - mx));
+        return mx + log_t(1.0 + exp_t(mn - mx));
     }
     // value in this domain from a natural log
     static __device__ __forceinline__ double from_ln(double x) { return x; }

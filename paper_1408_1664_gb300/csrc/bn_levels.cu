@@ -45,7 +45,7 @@ __device__ __forceinline__ void lazy_add(double& m, double& s, double x)
 {
     const double dd = x - m;                      // +inf while the accumulator is empty
     const bool big = dd > 40.0;
-    const double e = exp(big ? -dd : dd);
+    const double e = exp_t(big ? -dd : dd);       // the library's table-driven exponential
     s = big ? fma(s, e, 1.0) : s + e;
     m = big ? x : m;
 }
