@@ -417,6 +417,14 @@ uint64_t binom_host(int n, int k)
     return r;
 }
 
+// Low patterns with at most d of the 13 tile bits (the columns of a tile).
+uint32_t num_small_subsets_host(int d)
+{
+    uint64_t c = 0;
+    for (int k = 0; k <= d && k <= TB; ++k) c += binom_host(TB, k);
+    return (uint32_t)c;
+}
+
 
 }  // namespace
 
@@ -1048,15 +1056,21 @@ k_upzeta13(int n, int d, const uint16_t* __restrict__ unrank13, T* __restrict__ 
 // block's threads issue neither the loads nor the stores.  The arithmetic
 // and the outputs are those of k_upzeta13, bit for bit.  Shared memory: A0
 // (exchanges), A1 (inputs), the warps' maxima, the mbarrier and a flag, the
-// staged column sums (ncol floats rounded up to 16 bytes) and the output
-// block.  A bulk copy that has not landed after `cap` polls of its mbarrier
-// sets kErrDeviceTimeout in *err and the block returns after one more bounded
-// wait for it.  `hold` (a test hook, 0 otherwise) withholds the block's first
-// copy, so that its wait runs out.
+// staged column sums (ncol floats rounded up to 16 bytes, and 48 bytes more)
+// and the output block.  With ncb < ncol the columns from ncb on (d low
+// elements: the sum of one row, the empty high set) were not written by the
+// column-sum kernel; they are the first ncol entries of node i's reordered
+// score table `tab` (K entries per node, K a multiple of 4), and a second
+// bulk copy stages them, from the 16-byte boundary at or below ncb.  A bulk
+// copy that has not landed after `cap` polls of its mbarrier sets
+// kErrDeviceTimeout in *err and the block returns after one more bounded
+// wait for it.  `hold` (a test hook, 0 otherwise) withholds the block's
+// first copies, so that its wait runs out.
 template <bool TLO>
 __global__ void __launch_bounds__(TT, 2)
 k_upzeta13p(int n, int d, const uint16_t* __restrict__ unrank13, float* __restrict__ A, uint32_t ntiles,
-            int* __restrict__ err, uint32_t cap, int hold)
+            int* __restrict__ err, uint32_t cap, int hold, const float* __restrict__ tab, int64_t K,
+            uint32_t ncb)
 {
     using Lg = LogOps<float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1067,16 +1081,27 @@ k_upzeta13p(int n, int d, const uint16_t* __restrict__ unrank13, float* __restri
     int* gave_up = reinterpret_cast<int*>(bar + 1);
     float* S = reinterpret_cast<float*>(bar + 2);       // staged column sums
     const uint32_t ncol = num_small_subsets(TB, d);
-    const uint32_t sbytes = (ncol * 4u + 15u) & ~15u;
-    float* OUT = S + sbytes / 4;                         // the finished tile
+    float* OUT = S + ((ncol * 4u + 15u) & ~15u) / 4 + 12; // the finished tile
     const int h = n - 1 - TB;
     const size_t asize = (size_t)ntiles << TB;
+    // the tile's columns (before ncb) and, from the table, the rest
+    const uint32_t ncb4 = ncb & ~3u;
+    const uint32_t sbytes = (ncb * 4u + 15u) & ~15u;
+    const uint32_t tbytes = ncb < ncol ? ((ncol - ncb4) * 4u + 15u) & ~15u : 0u;
+    float* S2 = S + sbytes / 4;
     const int t = threadIdx.x, lane = t & 31;
     const int pt = __popc(t);
+    // thread 0: the copies of tile `tl` on the barrier
+    auto stage = [&](uint32_t tl) {
+        mbar_expect(bar, sbytes + tbytes);
+        bulk_copy_in(S, A + BN_AT((size_t)tl << TB, TN, asize), sbytes, bar);
+        if (tbytes)
+            bulk_copy_in(S2, tab + BN_AT((size_t)(tl >> h) * K + ncb4, 4, (size_t)(ntiles >> h) * K), tbytes, bar);
+    };
     if (t == 0) mbar_init(bar, 1);
     __syncthreads();
     uint32_t tile = blockIdx.x;
-    if (t == 0 && tile < ntiles && !hold) bulk_load(S, A + BN_AT((size_t)tile << TB, TN, asize), sbytes, bar);
+    if (t == 0 && tile < ntiles && !hold) stage(tile);
     for (uint32_t parity = 0; tile < ntiles; tile += gridDim.x, parity ^= 1u) {
         const int i = (int)(tile >> h);
         float* out = A + BN_AT((size_t)tile << TB, TN, asize);
@@ -1104,7 +1129,7 @@ k_upzeta13p(int n, int d, const uint16_t* __restrict__ unrank13, float* __restri
         // elements are no column (no input)
         float tm = Lg::ninf();
         for (uint32_t c = t; c < ncol; c += TT) {
-            const float v = S[c];
+            const float v = c < ncb ? S[c] : S2[c - ncb4];
             A1[swz(BN_AT(unrank13[c], 1, TN))] = v;
             tm = v > tm ? v : tm;
         }
@@ -1115,8 +1140,7 @@ k_upzeta13p(int n, int d, const uint16_t* __restrict__ unrank13, float* __restri
         if (lane == 0) wmax[t >> 5] = tm;
         fence_async_shared();                            // S is read: the next copy may land
         __syncthreads();
-        if (t == 0 && tile + gridDim.x < ntiles)
-            bulk_load(S, A + BN_AT((size_t)(tile + gridDim.x) << TB, TN, asize), sbytes, bar);
+        if (t == 0 && tile + gridDim.x < ntiles) stage(tile + gridDim.x);
         float tmx = wmax[0];
 #pragma unroll
         for (int w = 1; w < TT / 32; ++w) tmx = wmax[w] > tmx ? wmax[w] : tmx;
@@ -1491,8 +1515,9 @@ size_t upzeta13p_smem_bytes(const Plan& P)
     uint64_t ncol = 0;
     for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
     // A0, A1, the warps' maxima, the mbarrier and a flag, the staged column
-    // sums (16-byte multiple), the output block
-    return (size_t)TN * 4 * 2 + (TT / 32) * 4 + 16 + ((ncol * 4 + 15) & ~(uint64_t)15) + (size_t)TN * 4;
+    // sums (16-byte multiple, and 48 bytes for the two copies' rounding),
+    // the output block
+    return (size_t)TN * 4 * 2 + (TT / 32) * 4 + 16 + ((ncol * 4 + 15) & ~(uint64_t)15) + 48 + (size_t)TN * 4;
 }
 
 // The persistent FP32 tile kernel runs single jobs whose A is in device
@@ -1501,6 +1526,18 @@ size_t upzeta13p_smem_bytes(const Plan& P)
 static bool use_upzeta13p(const Plan& P, const int* err)
 {
     return err && P.prec != 0 && P.nj == 1 && !P.spill && !recording();
+}
+
+// The persistent tile kernel stages the columns with d low elements straight
+// from the reordered score table when the column sums come from the column
+// butterflies (which then leave them out), the table's node stride is a
+// multiple of 16 bytes and every node's table holds at least 3 entries past
+// its first ncol (h >= 1).
+static bool upzeta_table_copies(const Plan& P, const void* tab, const int* err)
+{
+    const int h = P.n - 1 - TB;
+    return use_upzeta13p(P, err) && use_colb(P) && colb_columns(P) < num_small_subsets_host(P.d) &&
+           P.K % 4 == 0 && ((uintptr_t)tab & 15u) == 0 && h >= 1 && P.d >= 1;
 }
 
 cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unrank13, void* A,
@@ -1520,8 +1557,10 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
         const uint32_t ncb = colb_columns(P);
         const uint64_t ntiles = (uint64_t)nodes << h;
-        const unsigned nblk = (unsigned)((uint64_t)nodes * ((ncb + cpb - 1) / cpb) +
-                                         (ncb < ncol ? (ntiles + 7) / 8 : 0));
+        // the copy blocks follow the butterfly blocks (none when the tile
+        // kernel stages those columns from the table itself)
+        const bool copies = ncb < ncol && !upzeta_table_copies(P, tab, err);
+        const unsigned nblk = (unsigned)((uint64_t)nodes * ((ncb + cpb - 1) / cpb) + (copies ? (ntiles + 7) / 8 : 0));
         const size_t smb = ((size_t)cpb << h) * es;
         const dim3 gb(nblk, P.nj);
         if (P.prec == 0) {
@@ -1577,10 +1616,14 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upzeta13p<false>, TT, smp);
         if (e != cudaSuccess) return e;
         const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)std::max(per_sm, 1) * nsm);
+        const uint32_t ncol = num_small_subsets_host(P.d);
+        const uint32_t ncb = upzeta_table_copies(P, tab, err) ? colb_columns(P) : ncol;
         if (use_tlo(P))
-            k_upzeta13p<true><<<blocks, TT, smp, s>>>(P.n, P.d, unrank13, (float*)A, ntiles, err, kCopySpinCap, 0);
+            k_upzeta13p<true><<<blocks, TT, smp, s>>>(P.n, P.d, unrank13, (float*)A, ntiles, err, kCopySpinCap, 0,
+                                                      (const float*)tab, P.K, ncb);
         else
-            k_upzeta13p<false><<<blocks, TT, smp, s>>>(P.n, P.d, unrank13, (float*)A, ntiles, err, kCopySpinCap, 0);
+            k_upzeta13p<false><<<blocks, TT, smp, s>>>(P.n, P.d, unrank13, (float*)A, ntiles, err, kCopySpinCap, 0,
+                                                       (const float*)tab, P.K, ncb);
         return cudaGetLastError();
     }
     if (P.prec == 0)
@@ -1606,7 +1649,8 @@ cudaError_t launch_upzeta13p_withheld(float* A, uint16_t* rank13, uint16_t* unra
     P.n = 14;
     P.d = 4;
     P.prec = 1;
-    k_upzeta13p<false><<<1, TT, upzeta13p_smem_bytes(P), s>>>(14, 4, unrank13, A, 1u, err, polls, 1);
+    k_upzeta13p<false><<<1, TT, upzeta13p_smem_bytes(P), s>>>(14, 4, unrank13, A, 1u, err, polls, 1, nullptr,
+                                                             int64_t(0), num_small_subsets_host(4));
     return cudaGetLastError();
 }
 
