@@ -1446,11 +1446,14 @@ static uint32_t colb_columns(const Plan& P)
 // Column sums by butterflies over the h high dimensions when they take at
 // most four fifths (FP32; four times in FP64) of the steps of the direct sums
 // (the columns with d low elements are copies either way) and a column run
-// fits 64 KB of shared memory (h <= 13).
+// fits 64 KB of shared memory (5 <= h <= 13).
 bool use_colb(const Plan& P)
 {
     const int h = P.n - 1 - TB;
-    if (h > 13) return false;
+    // below h = 5 a column has at most 32 rows: the per-tile sums are cheap,
+    // and the column kernel's many small blocks would cost a batch's
+    // persistent kernel one work item each
+    if (h > 13 || h < 5) return false;
     double direct = 0.0, ncol = 0.0;
     for (int kl = 0; kl <= P.d && kl <= TB; ++kl) {
         ncol += (double)binom_host(TB, kl);
