@@ -1235,8 +1235,16 @@ k_gamma_p2s(int n, int d, int b, uint32_t nlow, uint32_t c0, int64_t K, const T*
 #pragma unroll
     for (int q = 0; q < MB; ++q) { mb[q] = L::ninf(); sb[q] = T(0); }
     const uint32_t nH = 1u << h;
+    const size_t wsize = (size_t)nlow << h;
+    // the rows two and three steps ahead are in flight while a row is added
+    // (the loop waits on load latency, each lane reading its own row; four
+    // rows ahead cost registers: 61 against 48, one block per SM fewer)
+    T wa = lane < nH ? W[BN_AT((size_t)lane * nlow + col, 1, wsize)] : T(0);
+    T wb = lane + 32 < nH ? W[BN_AT((size_t)(lane + 32) * nlow + col, 1, wsize)] : T(0);
     for (uint32_t H = lane; H < nH; H += 32) {
-        const T w = W[BN_AT((size_t)H * nlow + col, 1, (size_t)nlow << h)];
+        const T w = wa;
+        wa = wb;
+        if (H + 64 < nH) wb = W[BN_AT((size_t)(H + 64) * nlow + col, 1, wsize)];
         lse_lazy_k(m0, s0, w);
         if (one) {
 #pragma unroll
