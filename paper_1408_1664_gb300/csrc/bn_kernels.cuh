@@ -35,7 +35,7 @@ enum KernelId : int32_t {
     KID_REORDER_F, KID_COLB8, KID_COLB4, KID_COLB2, KID_COLW_D, KID_COLW_F, KID_COLS_D,
     KID_COLS_F, KID_UP13_D, KID_UP13_F_TLO, KID_UP13_F, KID_G13_D_Q, KID_G13_D, KID_G13_F_Q,
     KID_G13_F, KID_FROWS_D, KID_FROWS_F_TLO, KID_FROWS_F, KID_BROWS_D, KID_BROWS_F_TLO,
-    KID_BROWS_F, KID_COLB4_D, KID_COLB2_D, KID_COLB1_D, KID_COUNT
+    KID_BROWS_F, KID_COLB4_D, KID_COLB2_D, KID_COLB1_D, KID_COLB1, KID_COUNT
 };
 
 // Arguments as one trivially copyable structure whose members have the

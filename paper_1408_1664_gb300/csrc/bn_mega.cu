@@ -132,6 +132,7 @@ __device__ __forceinline__ bool dispatch(int kid, const unsigned char* a)
         case KID_COLB8: run(k_upzeta13_colb<float, 8>, a); return true;
         case KID_COLB4: run(k_upzeta13_colb<float, 4>, a); return true;
         case KID_COLB2: run(k_upzeta13_colb<float, 2>, a); return true;
+        case KID_COLB1: run(k_upzeta13_colb<float, 1>, a); return true;
         case KID_COLW_F: run(k_upzeta13_colw<float>, a); return true;
         case KID_COLS_F: run(k_upzeta13_cols<float>, a); return true;
         case KID_UP13_F_TLO: run(k_upzeta13<float, true>, a); return true;
@@ -281,7 +282,7 @@ bool persistent_runs(int prec, int kid)
     case KID_SHIFT_F: case KID_UPZETA_F: case KID_FWD_LEVEL_F: case KID_BWD_LEVEL_F:
     case KID_GAMMA_TABLE: case KID_GAMMA_P1_F: case KID_GAMMA_P2_F: case KID_GAMMA_P2S_F:
     case KID_EDGES_ACC_F: case KID_EDGES_FIN_F: case KID_REORDER_F: case KID_COLB8: case KID_COLB4:
-    case KID_COLB2: case KID_COLW_F: case KID_COLS_F: case KID_UP13_F_TLO: case KID_UP13_F:
+    case KID_COLB2: case KID_COLB1: case KID_COLW_F: case KID_COLS_F: case KID_UP13_F_TLO: case KID_UP13_F:
     case KID_G13_F: case KID_FROWS_F_TLO: case KID_FROWS_F: case KID_BROWS_F_TLO: case KID_BROWS_F:
         return prec == 1;
     case KID_SHIFT_D: case KID_UPZETA_D: case KID_FWD_LEVEL_D: case KID_BWD_LEVEL_D:

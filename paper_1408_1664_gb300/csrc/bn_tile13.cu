@@ -1446,14 +1446,14 @@ static uint32_t colb_columns(const Plan& P)
 // Column sums by butterflies over the h high dimensions when they take at
 // most four fifths (FP32; four times in FP64) of the steps of the direct sums
 // (the columns with d low elements are copies either way) and a column run
-// fits 64 KB of shared memory (5 <= h <= 13).
+// fits 128 KB of shared memory (5 <= h <= 15 in FP32, h <= 14 in FP64).
 bool use_colb(const Plan& P)
 {
     const int h = P.n - 1 - TB;
     // below h = 5 a column has at most 32 rows: the per-tile sums are cheap,
     // and the column kernel's many small blocks would cost a batch's
     // persistent kernel one work item each
-    if (h > 13 || h < 5) return false;
+    if (h < 5 || ((size_t)(P.prec == 0 ? 8 : 4) << h) > 128 * 1024) return false;
     double direct = 0.0, ncol = 0.0;
     for (int kl = 0; kl <= P.d && kl <= TB; ++kl) {
         ncol += (double)binom_host(TB, kl);
@@ -1555,7 +1555,8 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
     if (use_colb(P)) {                                // butterflies over the high dims
         // columns per block: as many as fit 64 KB, at most 8 (FP32) or 4 (FP64)
         const size_t es = P.prec == 0 ? 8 : 4;
-        const int cpb = (int)std::min<size_t>((size_t)(64 * 1024) / (es << h), P.prec == 0 ? 4 : 8);
+        // (one column of up to 128 KB from h = 14 in FP32, 13 in FP64)
+        const int cpb = (int)std::max<size_t>(1, std::min<size_t>((size_t)(64 * 1024) / (es << h), P.prec == 0 ? 4 : 8));
         uint64_t ncol = 0;
         for (int k = 0; k <= P.d && k <= TB; ++k) ncol += binom_host(TB, k);
         const uint32_t ncb = colb_columns(P);
@@ -1582,8 +1583,11 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         } else if (cpb >= 4) {
             launch_or_record(KID_COLB4, k_upzeta13_colb<float, 4>, gb, 256, smb, s, P.n, P.d, P.K,
                              (const float*)tab, (float*)A, P.js, nodes, ncb);
-        } else {
+        } else if (cpb == 2) {
             launch_or_record(KID_COLB2, k_upzeta13_colb<float, 2>, gb, 256, smb, s, P.n, P.d, P.K,
+                             (const float*)tab, (float*)A, P.js, nodes, ncb);
+        } else {
+            launch_or_record(KID_COLB1, k_upzeta13_colb<float, 1>, gb, 256, smb, s, P.n, P.d, P.K,
                              (const float*)tab, (float*)A, P.js, nodes, ncb);
         }
     } else if (nrow * 4 * 8 <= 160 * 1024) {          // warp per tile, 8 tiles per block
@@ -1708,6 +1712,7 @@ cudaError_t set_tile13_attributes()
     SETA((k_upzeta13_colb<float, 8>))
     SETA((k_upzeta13_colb<float, 4>))
     SETA((k_upzeta13_colb<float, 2>))
+    SETA((k_upzeta13_colb<float, 1>))
     SETA((k_upzeta13_colb<double, 4>))
     SETA((k_upzeta13_colb<double, 2>))
     SETA((k_upzeta13_colb<double, 1>))
