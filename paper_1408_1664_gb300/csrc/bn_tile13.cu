@@ -682,7 +682,7 @@ __device__ __forceinline__ void colb_steps(T* v, uint32_t H2, int h, int CPB)
 template <typename T, int CPB>
 __global__ void __launch_bounds__(256)
 k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restrict__ A,
-                size_t js, int nodes, uint32_t ncb)
+                size_t js, int nodes, uint32_t ncb, int hc)
 {
     tab = job_ptr(tab, js);
     A = job_ptr(A, js);
@@ -697,10 +697,13 @@ k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* v = reinterpret_cast<T*>(smem_raw);           // [column of the run][H]
     const int h = n - 1 - TB;
-    const uint32_t H2 = 1u << h;
+    // hc > 0: the top hc high bits are this block's chunk, fixed; the steps
+    // run over the other hl bits and k_upzeta13_colt adds the chunks after
+    const int hl = h - hc;
+    const uint32_t H2 = 1u << hl;
     const uint32_t ncol = num_small_subsets(TB, d);
     const uint32_t nrun = (ncb + CPB - 1) / CPB;
-    const uint32_t nbb = (uint32_t)nodes * nrun;
+    const uint32_t nbb = ((uint32_t)nodes * nrun) << hc;
     const size_t asize = (size_t)nodes << (n - 1);
     if (blockIdx.x >= nbb) {                         // copies: a warp per tile
         const uint32_t tile = (blockIdx.x - nbb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -724,8 +727,10 @@ k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
         rowoff_k[threadIdx.x] = o;
     }
     __syncthreads();
-    const int i = (int)(blockIdx.x / nrun);
-    const uint32_t c0 = (blockIdx.x % nrun) * CPB;
+    const uint32_t chunk = blockIdx.x & ((1u << hc) - 1u);
+    const int i = (int)((blockIdx.x >> hc) / nrun);
+    const uint32_t c0 = ((blockIdx.x >> hc) % nrun) * CPB;
+    const uint32_t Hc = chunk << hl;                 // the chunk's high bits
     const T* tb = tab + (size_t)i * K;
     int kl[CPB];                                     // low elements of each column (-1: none)
     T mx[CPB];
@@ -738,10 +743,11 @@ k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
         mx[cc] = Lg::ninf();
     }
     for (uint32_t H = threadIdx.x; H < H2; H += blockDim.x) {
-        const int kh = __popc(H);
-        uint32_t r = 0;                              // colex rank of H among kh-subsets
+        const uint32_t Hf = Hc | H;
+        const int kh = __popc(Hf);
+        uint32_t r = 0;                              // colex rank of Hf among kh-subsets
         int t = 1;
-        for (uint32_t x = H; x; x &= x - 1, ++t) r += sb_binom(sb, __ffs(x) - 1, t);
+        for (uint32_t x = Hf; x; x &= x - 1, ++t) r += sb_binom(sb, __ffs(x) - 1, t);
         // the row of G_H in the node's table (only formed where some column reads it)
         const uint32_t row = kh <= d ? rowoff_k[kh] + r * off13[min(d - kh, TB) + 1] : 0u;
 #pragma unroll
@@ -764,7 +770,7 @@ k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
     __syncthreads();
     if (threadIdx.x == 0) {
         // a column's outputs lie in [f(G_L), its largest input + log 2^h]
-        const T hb = sizeof(T) == 4 ? T(h) : T(h) * T(0.69314718055994530942);
+        const T hb = sizeof(T) == 4 ? T(hl) : T(hl) * T(0.69314718055994530942);
         int lin = 1;
         for (int cc = 0; cc < CPB; ++cc) {
             T m = wred[0][cc];
@@ -780,13 +786,13 @@ k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
     if (lin) {
         for (uint32_t e = threadIdx.x; e < H2 * CPB; e += blockDim.x) v[e] = Lg::ex(v[e] - scale_s[e / H2]);
         __syncthreads();
-        colb_steps<true>(v, H2, h, CPB);
+        colb_steps<true>(v, H2, hl, CPB);
     } else {
-        colb_steps<false>(v, H2, h, CPB);
+        colb_steps<false>(v, H2, hl, CPB);
     }
     T* Ai = A + ((size_t)i << (n - 1));
     for (uint32_t H = threadIdx.x; H < H2; H += blockDim.x) {
-        T* o = Ai + BN_AT(((size_t)H << TB) + c0, CPB, (size_t)H2 << TB);
+        T* o = Ai + BN_AT(((size_t)(Hc | H) << TB) + c0, CPB, (size_t)1 << (n - 1));
         T y[CPB];
 #pragma unroll
         for (int cc = 0; cc < CPB; ++cc) {
@@ -802,6 +808,42 @@ k_upzeta13_colb(int n, int d, int64_t K, const T* __restrict__ tab, T* __restric
 #pragma unroll
         for (int cc = 0; cc < CPB; ++cc)
             if (c0 + cc < ncb) o[cc] = y[cc];
+    }
+}
+
+// The chunks of the column butterflies (k_upzeta13_colb with hc > 0): slot c
+// of tile (i, (q << hl) | L) holds the sum over the rows inside chunk q
+// alone; the upward zeta over the hc chunk bits, a thread per (i, L, c) with
+// c fastest (coalesced), leaves the full column sums.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_upzeta13_colt(int n, T* __restrict__ A, int nodes, uint32_t ncb, int hc)
+{
+    using Lg = LogOps<T>;
+    const int h = n - 1 - TB, hl = h - hc;
+    const uint64_t total = ((uint64_t)nodes << hl) * ncb;
+    const size_t asize = (size_t)nodes << (n - 1);
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = (uint32_t)(x % ncb);
+        const uint64_t y = x / ncb;
+        const uint32_t L = (uint32_t)(y & ((1u << hl) - 1u));
+        const int i = (int)(y >> hl);
+        T* Ai = A + ((size_t)i << (n - 1));
+        T q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < (1 << hc)) q[k] = Ai[BN_AT((((size_t)k << hl) | L) << TB | c, 1, asize)];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (b >= hc) continue;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < (1 << hc) && (k >> b & 1)) q[k] = Lg::lse(q[k], q[k ^ (1 << b)]);
+        }
+#pragma unroll
+        for (int k = 1; k < 8; ++k)
+            if (k < (1 << hc)) Ai[BN_AT((((size_t)k << hl) | L) << TB | c, 1, asize)] = q[k];
     }
 }
 
@@ -1443,6 +1485,18 @@ static uint32_t colb_columns(const Plan& P)
     return (uint32_t)c;
 }
 
+// High bits beyond one 128 KB column in shared memory: the column
+// butterflies then run per chunk of those bits, added by k_upzeta13_colt
+// (single jobs launched directly, with A in device memory, only; 4 for the
+// others, which then keep the per-tile sums).
+static int colb_chunk_bits(const Plan& P)
+{
+    const int h = P.n - 1 - TB;
+    const int hmax = P.prec == 0 ? 14 : 15;          // 2^h values of 8 or 4 bytes in 128 KB
+    if (h <= hmax) return 0;
+    return recording() || P.nj != 1 || P.spill ? 4 : h - hmax;
+}
+
 // Column sums by butterflies over the h high dimensions when they take at
 // most four fifths (FP32; four times in FP64) of the steps of the direct sums
 // (the columns with d low elements are copies either way) and a column run
@@ -1453,7 +1507,7 @@ bool use_colb(const Plan& P)
     // below h = 5 a column has at most 32 rows: the per-tile sums are cheap,
     // and the column kernel's many small blocks would cost a batch's
     // persistent kernel one work item each
-    if (h < 5 || ((size_t)(P.prec == 0 ? 8 : 4) << h) > 128 * 1024) return false;
+    if (h < 5 || colb_chunk_bits(P) > 3) return false;
     double direct = 0.0, ncol = 0.0;
     for (int kl = 0; kl <= P.d && kl <= TB; ++kl) {
         ncol += (double)binom_host(TB, kl);
@@ -1564,31 +1618,43 @@ cudaError_t launch_upzeta13(const Plan& P, const void* tab, const uint16_t* unra
         // the copy blocks follow the butterfly blocks (none when the tile
         // kernel stages those columns from the table itself)
         const bool copies = ncb < ncol && !upzeta_table_copies(P, tab, err);
-        const unsigned nblk = (unsigned)((uint64_t)nodes * ((ncb + cpb - 1) / cpb) + (copies ? (ntiles + 7) / 8 : 0));
-        const size_t smb = ((size_t)cpb << h) * es;
+        const int hc = colb_chunk_bits(P);
+        const unsigned nblk = (unsigned)(((uint64_t)nodes * ((ncb + cpb - 1) / cpb) << hc) +
+                                         (copies ? (ntiles + 7) / 8 : 0));
+        const size_t smb = ((size_t)cpb << (h - hc)) * es;
         const dim3 gb(nblk, P.nj);
         if (P.prec == 0) {
             if (cpb >= 4)
                 launch_or_record(KID_COLB4_D, k_upzeta13_colb<double, 4>, gb, 256, smb, s, P.n, P.d, P.K,
-                                 (const double*)tab, (double*)A, P.js, nodes, ncb);
+                                 (const double*)tab, (double*)A, P.js, nodes, ncb, hc);
             else if (cpb == 2)
                 launch_or_record(KID_COLB2_D, k_upzeta13_colb<double, 2>, gb, 256, smb, s, P.n, P.d, P.K,
-                                 (const double*)tab, (double*)A, P.js, nodes, ncb);
+                                 (const double*)tab, (double*)A, P.js, nodes, ncb, hc);
             else
                 launch_or_record(KID_COLB1_D, k_upzeta13_colb<double, 1>, gb, 256, smb, s, P.n, P.d, P.K,
-                                 (const double*)tab, (double*)A, P.js, nodes, ncb);
+                                 (const double*)tab, (double*)A, P.js, nodes, ncb, hc);
         } else if (cpb == 8) {
             launch_or_record(KID_COLB8, k_upzeta13_colb<float, 8>, gb, 256, smb, s, P.n, P.d, P.K,
-                             (const float*)tab, (float*)A, P.js, nodes, ncb);
+                             (const float*)tab, (float*)A, P.js, nodes, ncb, hc);
         } else if (cpb >= 4) {
             launch_or_record(KID_COLB4, k_upzeta13_colb<float, 4>, gb, 256, smb, s, P.n, P.d, P.K,
-                             (const float*)tab, (float*)A, P.js, nodes, ncb);
+                             (const float*)tab, (float*)A, P.js, nodes, ncb, hc);
         } else if (cpb == 2) {
             launch_or_record(KID_COLB2, k_upzeta13_colb<float, 2>, gb, 256, smb, s, P.n, P.d, P.K,
-                             (const float*)tab, (float*)A, P.js, nodes, ncb);
+                             (const float*)tab, (float*)A, P.js, nodes, ncb, hc);
         } else {
             launch_or_record(KID_COLB1, k_upzeta13_colb<float, 1>, gb, 256, smb, s, P.n, P.d, P.K,
-                             (const float*)tab, (float*)A, P.js, nodes, ncb);
+                             (const float*)tab, (float*)A, P.js, nodes, ncb, hc);
+        }
+        if (hc > 0) {                                 // add the chunks (never recorded)
+            const cudaError_t ec = cudaGetLastError();
+            if (ec != cudaSuccess) return ec;
+            const uint64_t total = ((uint64_t)nodes << (h - hc)) * ncb;
+            const unsigned gt = (unsigned)std::min<uint64_t>((total + 255) / 256, 152 * 64);
+            if (P.prec == 0)
+                k_upzeta13_colt<double><<<gt, 256, 0, s>>>(P.n, (double*)A, nodes, ncb, hc);
+            else
+                k_upzeta13_colt<float><<<gt, 256, 0, s>>>(P.n, (float*)A, nodes, ncb, hc);
         }
     } else if (nrow * 4 * 8 <= 160 * 1024) {          // warp per tile, 8 tiles per block
         const uint64_t ntiles = (uint64_t)nodes << h;
